@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the DP simulator hot path on GB300.
+
+One step = trace + bin the full PSF bank of the f/1.8 doublet-pair lens
+(32 field heights x 32 depths x 3 wavelengths, 256 x 256 pupil grid, 65 x 65
+L/R patches, hard binning, joint sum normalisation, FP32), render a
+1024 x 1024 RGB all-in-focus image with a Perlin depth map through that bank
+(FP32), and back-propagate a fixed output gradient through the render to the
+image and the bank (FP32).  Inputs are synthetic (workloads module) and resident in HBM before
+timing; L2 is flushed (256 MiB write) before every timed step.
+
+Prints one JSON line (rank 0).  `value` = rays traced+binned per second over
+the whole step (G rays/s); the render rate and per-kernel times are extra
+keys.  `--impl reference` times the FP64 CPU oracle instead on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "G rays/s traced+binned; DP Mpix/s rendered at 65x65 PSF; fwd+bwd ms vs plain"
+WORKLOAD = ("doublet-pair f/1.8 lens: DP PSF bank 32 fields x 32 depths x 3 wavelengths, "
+            "256x256 pupil grid, 65x65 L/R patches (hard binning, joint norm) + per-pixel "
+            "DP render of 1024x1024 RGB with a Perlin depth map")
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+# ---------------------------------------------------------------------------
+# Algorithmic FP32 work per ray (add/sub/mul/div/sqrt = 1 flop, fused
+# multiply-add = 2), counted from the formulas the trace evaluates:
+# ray generation (pupil sample, direction to the object point, normalise),
+# per surface: conic intersection (A, B, C, discriminant, root), hit point,
+# aperture test, normal, vector Snell; aspheres add Newton iterations on the
+# sag (sag, its derivative, F/F' step) and the sag-gradient normal; sensor
+# propagation and the Eq. 1/2 sub-pixel decision.
+# ---------------------------------------------------------------------------
+FLOPS_GEN = 14
+FLOPS_STOP = 12
+FLOPS_CONIC = 79
+FLOPS_NEWTON_ITER = 50
+FLOPS_ASPH_EXTRA = 15      # sag-gradient normal in place of the quadric one
+NEWTON_ITERS_ASSUMED = 3
+FLOPS_SENSOR_BIN = 26
+
+
+def flops_per_ray(table):
+    f = FLOPS_GEN + FLOPS_SENSOR_BIN
+    for row in table:
+        if int(row[W.COL_TYPE]) == W.SURF_STOP:
+            f += FLOPS_STOP
+        else:
+            f += FLOPS_CONIC
+            if np.any(row[W.COL_A4:W.COL_A4 + 5] != 0):
+                f += NEWTON_ITERS_ASSUMED * FLOPS_NEWTON_ITER + FLOPS_ASPH_EXTRA
+    return f
+
+
+def in_pupil_rays(n):
+    ix = np.arange(n)
+    a = 2 * ix + 1 - n
+    return int(((a[:, None] ** 2 + a[None, :] ** 2) <= n * n).sum())
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def setup_dist(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def build_inputs(device):
+    import torch
+    cfg = W.config_full_forward()
+    reqs = W.bank_grid(cfg["field_h_mm"], cfg["depths_mm"], cfg["lambdas_nm"],
+                       cfg["n_grid"], cfg["ks"])
+    H, Wd = cfg["sensor_hw"]
+    aif = W.aif_pink(1, 3, H, Wd, seed=1).astype(np.float32)
+    depth = W.depth_perlin(1, H, Wd, seed=2).astype(np.float32)
+    return cfg, reqs, aif, depth
+
+
+def run_ours(args, world, rank, local, dist):
+    import torch
+    import paper_2503_11213_gb300 as sd
+    from paper_2503_11213_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, reqs, aif_np, depth_np = build_inputs(dev)
+    ps = cfg["pitch_mm"]
+    sensor = sd.DPSensor(ps)
+    lens = sd.Lens(cfg["lens"], cfg["focus_mm"])
+    req_dev, total, off = sd.make_requests(reqs, device=dev)
+    n_req = len(reqs)
+    bank = torch.empty(total, dtype=torch.float32, device=dev)
+    stats = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
+    layout = sd.BankLayout(cfg["field_h_mm"], cfg["depths_mm"] / 1000.0, 3, cfg["ks"], ps)
+    aif = torch.tensor(aif_np, device=dev)
+    depth = torch.tensor(depth_np, device=dev)
+    out = torch.empty((1, 6) + aif.shape[2:], dtype=torch.float32, device=dev)
+    gout = torch.randn(out.shape, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    gaif = torch.empty_like(aif)
+    gbank = torch.empty_like(bank)
+    ws = torch.empty(max(1, sd.api.render_backward_workspace(layout, *aif.shape)),
+                     dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def trace():
+        sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=cfg["ks"],
+                        max_n=cfg["n_grid"], norm=sd.SD_NORM_JOINT, out=bank, stats=stats)
+
+    def render():
+        sd.dp_render(aif, depth, bank, layout, out=out)
+
+    def render_bwd():
+        lay = layout.c()
+        L = sd.lib()
+        sd._lib.check(L.sd_dp_render_backward(
+            sd.api._ptr(gout), sd.api._ptr(aif), sd.api._ptr(depth), sd.api._ptr(bank),
+            sd.api.ctypes.byref(lay), 1, 3, aif.shape[2], aif.shape[3], sd.api._ptr(gaif),
+            sd.api._ptr(gbank), sd.api._ptr(ws), ws.numel(), sd.api._stream()),
+            "sd_dp_render_backward")
+
+    for _ in range(args.warmup):
+        trace()
+        render()
+        render_bwd()
+    torch.cuda.synchronize()
+    rays_per_step = int(stats[:, 0].sum().item())
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            trace()
+            ev[i][1].record(stream)
+            render()
+            ev[i][2].record(stream)
+            render_bwd()
+            ev[i][3].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    t_trace = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_render = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    t_bwd = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
+    step_ms = sum(ev[i][0].elapsed_time(ev[i][3]) for i in range(args.steps)) / args.steps
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # end to end through the public API: pinned host inputs in, DP image out
+    h_req = torch.from_numpy(np.frombuffer(req_dev.cpu().numpy().tobytes(), np.uint8).copy()) \
+        .pin_memory()
+    h_aif = torch.from_numpy(aif_np).pin_memory()
+    h_depth = torch.from_numpy(depth_np).pin_memory()
+    h_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record(stream)
+        req_dev.copy_(h_req, non_blocking=True)
+        aif.copy_(h_aif, non_blocking=True)
+        depth.copy_(h_depth, non_blocking=True)
+        trace()
+        render()
+        render_bwd()
+        h_out.copy_(out, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    h2d = h_req.numel() + h_aif.numel() * 4 + h_depth.numel() * 4
+    d2h = h_out.numel() * 4  # the DP image (gradients stay on the device)
+
+    clocks = clk.summary()
+    peaks = load_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    fpr = flops_per_ray(cfg["lens"])
+    tr_ms = statistics.mean(t_trace)
+    rd_ms = statistics.mean(t_render)
+    bw_ms = statistics.mean(t_bwd)
+    H, Wd = aif.shape[2:]
+    render_flops = H * Wd * 3 * 2 * 2 * cfg["ks"] ** 2 * 2  # px, ch, L/R, 2 slices, FMA
+    trace_tflops = rays_per_step * fpr / (tr_ms * 1e-3) / 1e12
+    render_tflops = render_flops / (rd_ms * 1e-3) / 1e12
+    dominant = "trace_bin_kernel" if tr_ms >= rd_ms else "render_fwd_kernel"
+    achieved = trace_tflops if tr_ms >= rd_ms else render_tflops
+    value = world * rays_per_step / (step_ms * 1e-3) / 1e9
+    e2e_value = world * rays_per_step / (e2e_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "G rays/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step,
+                   "requests": n_req, "image": [1, 3, int(H), int(Wd)],
+                   "l2": "flushed before every step (256 MiB write), flush untimed",
+                   "parallelism": f"replica x{world}"},
+        "trace_ms": round(tr_ms, 4), "render_ms": round(rd_ms, 4),
+        "render_bwd_ms": round(bw_ms, 4),
+        "render_fwd_bwd_ms": round(rd_ms + bw_ms, 4),
+        "trace_grays_s": round(rays_per_step / (tr_ms * 1e-3) / 1e9, 4),
+        "render_mpix_s": round(H * Wd / (rd_ms * 1e-3) / 1e6, 2),
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3),
+                     "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / fp32_peak_tflops, 4), "traffic": None,
+                     "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max_mhz:.0f} MHz (max SM clock)",
+                     "flops_per_ray": fpr, "render_flops": render_flops,
+                     "trace_tflops": round(trace_tflops, 3),
+                     "render_tflops": round(render_tflops, 3)},
+        "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": 5 * args.steps,  # trace, render, bwd image, bitmap, bwd bank
+        "clocks": clocks,
+        "wall_s": round(t_wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
+    lens.free()
+    return line
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(cfg, reqs, aif_np, depth_np, budget_s):
+    """The FP64 oracle, as it stands, on a bounded sample of the same step:
+    every k-th bank request (threads over requests) and a set of rendered
+    pixels; each part scaled linearly to the full step."""
+    import oracle as O
+    cores = cpu_threads()
+    ps = cfg["pitch_mm"]
+    S = dict(ps=ps, h=W.DP_H * ps, f=W.DP_F * ps, w=W.DP_W * ps, r=W.DP_R * ps)
+    n_req = len(reqs)
+    # calibrate the sample on one request, then fill about budget/2 seconds
+    t0 = time.perf_counter()
+    O.psf_bank(cfg["lens"], cfg["focus_mm"], reqs[:1], S, n_threads=1)
+    per_req = time.perf_counter() - t0
+    n_s = int(max(cores, min(n_req, round(0.5 * budget_s * cores / max(per_req, 1e-6)))))
+    n_s = max(cores, (n_s // cores) * cores)
+    idx = np.linspace(0, n_req - 1, n_s).astype(int)
+    t0 = time.perf_counter()
+    _, st = O.psf_bank(cfg["lens"], cfg["focus_mm"], reqs[idx], S, n_threads=cores)
+    t_trace = (time.perf_counter() - t0) * n_req / n_s
+    rays = int(st[:, 0].sum()) * n_req / n_s
+    # render sample
+    cfgd = cfg["depths_mm"] / 1000.0
+    rng = np.random.default_rng(0)
+    bank = np.full((32, 32, 3, 2, cfg["ks"], cfg["ks"]), 1.0 / (2 * cfg["ks"] ** 2))
+    H, Wd = aif_np.shape[2:]
+    npx = 64 * cores
+    pix = np.stack([np.zeros(npx, int), rng.integers(0, H, npx), rng.integers(0, Wd, npx)], 1)
+    t0 = time.perf_counter()
+    O.render_bank_pixels(aif_np, depth_np, bank, cfg["field_h_mm"], cfgd, ps, pix,
+                         n_threads=cores)
+    t_render = (time.perf_counter() - t0) * (H * Wd) / npx
+    step_s = t_trace + t_render
+    return {"value": round(rays / step_s / 1e9, 6), "unit": "G rays/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n_s} of {n_req} bank requests (evenly spaced) + {npx} of {H * Wd} "
+                      f"rendered pixels, FP64 C++ oracle on {cores} threads, each part "
+                      f"scaled linearly to the full step",
+            "step_s_extrapolated": round(step_s, 3),
+            "trace_s": round(t_trace, 3), "render_s": round(t_render, 3)}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    workload timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    cfg, reqs, aif_np, depth_np = build_inputs(None)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, reqs, aif_np, depth_np, per_step)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(cfg, reqs, aif_np, depth_np, per_step)
+        vals.append(last["value"])
+    value = statistics.mean(vals)
+    step_ms = last["step_s_extrapolated"] * 1e3
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "G rays/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(step_ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": last,
+            "e2e": {"value": value, "unit": "G rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local, dist = setup_dist(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,276 @@
+/*
+ * sdirt.h -- C ABI of the GB300 (sm_103a) dual-pixel (DP) simulator hot path.
+ *
+ * Method: He et al., "Simulating Dual-Pixel Images From Ray Tracing For Depth
+ * Estimation" (ICCV 2025).  The library computes
+ *   1. a sequential real-ray trace of a lens from an object point through N x N
+ *      entrance-pupil samples (Sec. 3.1),
+ *   2. the left/right DP sub-pixel decision of every sensor hit (Sec. 3.1,
+ *      Eq. 1 inside the microlens, Eq. 2 outside) and the DP PSF pair
+ *      accumulated from unit ray energies (Eq. 3), sum-normalised (Sec. 3.2),
+ *   3. per-pixel rendering of the left/right DP images from an all-in-focus
+ *      image and a depth map with each pixel's own flipped DP PSF on the
+ *      replicate-padded image (supplement, "Local DP PSF convolution"),
+ *   and the adjoints of 2 (bilinear splat) and 3.
+ *
+ * Conventions shared by every call
+ *   - Units: mm for lengths, nm for wavelengths, metres for depth maps.
+ *     z runs along the optical axis toward the sensor; the vertex of surface 0
+ *     is at z = 0; radius > 0 puts the centre of curvature at +z.
+ *   - Ownership: the caller owns every device buffer and the stream.  The
+ *     library owns only the opaque sd_lens (a host struct plus one slot of a
+ *     __constant__ lens table on each device it was uploaded to).  No call
+ *     allocates device memory except sd_lens_load, which allocates none either
+ *     (constant memory is static); hot calls never allocate.
+ *   - Errors: every function returns sd_status.  Argument errors are reported
+ *     synchronously before anything is launched.  SD_ERR_CUDA wraps a failed
+ *     CUDA runtime call (the CUDA error is kept in sd_last_cuda_error()).
+ *     Ray-level failures (vignetting, TIR, no intersection, Newton
+ *     non-convergence) are statistics, not errors.
+ *   - Streams: every device call is asynchronous on the given stream
+ *     (0 = legacy default stream).
+ *   - Thread safety: calls on distinct lenses and streams may run
+ *     concurrently; sd_lens_load/sd_lens_free serialise on a library mutex.
+ */
+#ifndef SDIRT_H
+#define SDIRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sd_status;
+enum {
+  SD_OK = 0,
+  SD_ERR_ARG = 1,          /* null pointer, size out of range, bad enum */
+  SD_ERR_LENS = 2,         /* invalid prescription (see sd_lens_load) */
+  SD_ERR_UNSUPPORTED = 3,  /* valid but not supported (e.g. ks > 127) */
+  SD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  SD_ERR_CAPACITY = 5      /* library table full (lens slots) */
+};
+
+/* ------------------------------------------------------------------------
+ * Lens (Sec. 3.1 lens model; Tables S1/S2 columns)
+ * ---------------------------------------------------------------------- */
+enum { SD_SURF_REFRACT = 0, SD_SURF_STOP = 1 };
+#define SD_MAX_SURFACES 32
+#define SD_MAX_LENSES 16
+
+typedef struct sd_surface {
+  int32_t type;          /* SD_SURF_REFRACT or SD_SURF_STOP (flat aperture) */
+  int32_t reserved;
+  double radius;         /* mm; 0 = flat */
+  double thickness;      /* mm to the next surface; last: to the sensor */
+  double nd, vd;         /* medium after the surface; nd = 1 is air; vd <= 0
+                            means non-dispersive (n = nd at every wavelength) */
+  double semi_diameter;  /* clear aperture radius, mm (stop radius for a stop) */
+  double conic;          /* k */
+  double asph[5];        /* a4, a6, a8, a10, a12 (sag terms a_2m rho^2m) */
+} sd_surface;
+
+typedef struct sd_lens sd_lens; /* opaque */
+
+/* Paraxial (first-order) data of a lens at one wavelength and object depth. */
+typedef struct sd_paraxial {
+  double efl, bfl;        /* effective and back focal length, mm */
+  double z_ep, r_ep;      /* entrance pupil plane z and radius (image of the
+                             stop in object space, Sec. 3.1) */
+  double sensor_dist;     /* last surface vertex -> sensor, mm */
+  double m_sensor;        /* paraxial chief-ray height on the sensor per unit
+                             object height at this depth */
+  double img_dist;        /* paraxial image distance after the last vertex */
+  double z_sensor;        /* sensor plane z */
+} sd_paraxial;
+
+/*
+ * Validates a prescription of n (<= SD_MAX_SURFACES) surfaces, exactly one of
+ * them SD_SURF_STOP, and uploads it to a slot of the device lens table of the
+ * current CUDA device.  When focus_mm > 0 the last thickness is replaced by
+ * the paraxial image distance (587.5618 nm) of an axial object focus_mm in
+ * front of surface 0, i.e. the sensor is put in focus for that depth.
+ * Validation: finite numbers, nd >= 1, semi_diameter > 0, no aperture larger
+ * than its sphere (1 - (1+k) c^2 sd^2 >= 0), positive thickness except between
+ * a stop and its neighbour, positive sensor distance.
+ * Returns SD_ERR_LENS on a bad prescription, SD_ERR_CAPACITY when all
+ * SD_MAX_LENSES slots are in use.  *out is owned by the caller and released
+ * by sd_lens_free.  Host call; synchronous (cudaMemcpyToSymbol).
+ */
+sd_status sd_lens_load(const sd_surface* surfs, int n, double focus_mm,
+                       sd_lens** out);
+
+/* Paraxial data (FP64, host) at lambda_nm for an object at depth_mm. */
+sd_status sd_lens_paraxial(const sd_lens* lens, double lambda_nm,
+                           double depth_mm, sd_paraxial* out);
+
+/* Changes one lens parameter and re-uploads the device image.  Parameter
+ * id = surface*8 + j with j = 0 curvature (1/mm), 1 conic, 2..6 a4..a12,
+ * 7 thickness after the surface (the last surface's thickness is the sensor
+ * distance).  Later traces compute ray generation (object point, entrance
+ * pupil) from the changed lens.  Host call; synchronous. */
+sd_status sd_lens_set_param(sd_lens* lens, int param_id, double value);
+
+sd_status sd_lens_free(sd_lens* lens);
+
+/* ------------------------------------------------------------------------
+ * DP sensor (Sec. 3.1: microlens radius r, focal length f, sub-pixel to
+ * microlens distance h, sub-pixel width w, pixel pitch ps; Eq. S1 gives
+ * h = 0.78 ps, f = 1.44 ps, w = 0.30 ps, r = 0.50 ps).  All in mm; f > h.
+ * ---------------------------------------------------------------------- */
+typedef struct sd_dp_sensor {
+  double pitch_mm, h_mm, f_mm, w_mm, r_mm;
+} sd_dp_sensor;
+
+/* ------------------------------------------------------------------------
+ * PSF requests.  One request = one object point p: the field height h_mm is
+ * the image height on the sensor (along +x) at which the paraxial chief ray
+ * lands; the object sits at depth_mm in front of surface 0 at the object
+ * height that makes this so.  Rays: N x N cell-centred samples on the
+ * entrance-pupil square kept inside the pupil disc (exactly: (2i+1-N)^2 +
+ * (2j+1-N)^2 <= N^2).  The PSF patch [2][ks][ks] (L plane then R plane, row
+ * index along +y, column along +x) is centred on (h_mm, 0).
+ * ---------------------------------------------------------------------- */
+typedef struct sd_psf_request {
+  double h_mm;
+  double depth_mm;
+  double lambda_nm;
+  int32_t n_grid;      /* N, 2..2048 */
+  int32_t ks;          /* odd, 1..127 */
+  int32_t lens;        /* index into the lens array of the call */
+  int32_t reserved;
+  int64_t out_offset;  /* element offset of this PSF pair in the output */
+} sd_psf_request;      /* 48 bytes, device-resident */
+
+enum { SD_BIN_HARD = 0, SD_BIN_BILINEAR = 1 };
+enum { SD_NORM_NONE = 0, SD_NORM_JOINT = 1, SD_NORM_SEPARATE = 2,
+       SD_NORM_PER_RAY = 3 };
+enum { SD_F32 = 0, SD_BF16 = 1, SD_F16 = 2 };
+
+typedef struct sd_trace_opts {
+  int32_t mode;         /* SD_BIN_HARD (unit impulse into the landing
+                           pixel, Eq. 3) or SD_BIN_BILINEAR (unit energy split
+                           over the 4 nearest pixel centres; L/R from the
+                           landing pixel; differentiable in the lens) */
+  int32_t norm;         /* SD_NORM_*: JOINT sum(L+R) = 1 (Sec. 3.2 sum
+                           normalisation), SEPARATE each plane sums to 1,
+                           PER_RAY divide by the launched ray count */
+  int32_t out_dtype;    /* SD_F32, SD_BF16 or SD_F16 */
+  int32_t newton_iters; /* asphere Newton iteration cap (0 = 12) */
+  int32_t max_ks;       /* required: largest ks of any request (odd, <= 127);
+                           sizes the shared-memory patch */
+  int32_t max_n_grid;   /* largest N of any request (0 = 512, <= 2048) */
+  int32_t reserved[2];
+} sd_trace_opts;
+
+/* Per-request statistics (int64 each, device, nullable). */
+enum { SD_STAT_LAUNCHED = 0, SD_STAT_REACHED, SD_STAT_L, SD_STAT_R,
+       SD_STAT_DP_MISSED, SD_STAT_CLIPPED, SD_STAT_VIGNETTED, SD_STAT_OTHER,
+       SD_N_STATS };
+
+/*
+ * Traces every request and writes its DP PSF pair at out + out_offset (in
+ * elements of out_dtype).  lenses[0..n_lenses) must have been loaded on the
+ * current device.  req and stats (n_req x SD_N_STATS int64, nullable) are
+ * device pointers; out is device memory large enough for every request.
+ * Each PSF is computed by one thread block with a shared-memory patch: no
+ * global atomics; results are written exactly once.  Hard mode is exact
+ * integer counting (deterministic); bilinear mode accumulates FP32 weights
+ * with shared-memory atomics (order-dependent rounding).
+ * Stats: launched = reached + vignetted + other; reached = L + R +
+ * DP-missed + clipped (a ray whose landing pixel is outside the patch).
+ */
+sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
+                          const sd_dp_sensor* sensor,
+                          const sd_psf_request* req, int n_req,
+                          const sd_trace_opts* opts, void* out,
+                          int64_t* stats, void* stream);
+
+/*
+ * Per-ray record of one request (test and debugging aid): for the k-th
+ * in-pupil ray in raster order (pupil row major), rec[k*8 ..] = x, y, dx, dy,
+ * dz (landing point and unit direction, FP32), state (0 reached, 1 no
+ * intersection, 2 clipped by an aperture, 3 TIR, 4 Newton failed,
+ * 5 backwards), side (0 L, 1 R, 2 DP-missed), packed pixel (b * 65536 + a,
+ * or -1 outside the patch) -- the last three as floats.  rec is device
+ * memory of max_rays * 8 floats; n_rays (device int32) receives the count.
+ */
+sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
+                           const sd_psf_request* req_host,
+                           const sd_trace_opts* opts, float* rec,
+                           int max_rays, int32_t* n_rays, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Rendering (supplement, "Local DP PSF convolution")
+ *   out_L[n,c,y,x] = sum_{i,j} Ipad[n,c,y+i,x+j] K_L(y,x,c)[ks-1-i][ks-1-j]
+ * with Ipad the image replicate-padded by p = (ks-1)/2, likewise R, output
+ * channels [L(0..C-1), R(0..C-1)] (N, 2C, H, W).
+ * Bank mode: K(y,x,c) = (1-t) B[f][z0][l] + t B[f][z0+1][l] with l = c when
+ * the bank holds C wavelengths (else 0), f the field height nearest to the
+ * pixel's radial image height rho = |((x,y) - ((W-1)/2,(H-1)/2)) * pitch|,
+ * (z0, t) the bracket of the pixel depth linear in inverse depth, clamped
+ * to the first/last slice.  This selection is computed in FP32 without
+ * contraction: X = ((float)x - 0.5f*(W-1)) * pitch, rho = sqrtf(X*X + Y*Y),
+ * q = 1.0f / depth, iq_j = 1.0f / depths_m[j].
+ * ---------------------------------------------------------------------- */
+#define SD_MAX_BANK_FIELDS 256
+#define SD_MAX_BANK_DEPTHS 256
+
+typedef struct sd_bank_layout {
+  int32_t n_field, n_depth, n_lambda, ks;   /* bank [F][Z][NL][2][ks][ks] */
+  int32_t dtype;                            /* SD_F32 / SD_BF16 / SD_F16 */
+  int32_t reserved;
+  const float* field_h_mm;  /* host, F ascending field heights (mm) */
+  const float* depths_m;    /* host, Z ascending depths (m) */
+  float pitch_mm;           /* sensor pixel pitch of the rendered image */
+  float reserved2;
+} sd_bank_layout;
+
+/*
+ * aif (N,C,H,W) and out (N,2C,H,W) in image_dtype (SD_F32 / SD_BF16 /
+ * SD_F16); depth_m (N,H,W) FP32; bank in layout->dtype.  All device, dense,
+ * 16-byte aligned.  Accumulation is FP32.  C must equal n_lambda or
+ * n_lambda must be 1.  Deterministic (no atomics across blocks).
+ */
+sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
+                       const sd_bank_layout* layout, int N, int C, int H,
+                       int W, int image_dtype, void* out, void* stream);
+
+/*
+ * Adjoint of sd_dp_render (bank mode), FP32 only: given grad_out (N,2C,H,W)
+ * writes grad_aif (N,C,H,W) and grad_bank (bank layout), both overwritten;
+ * either may be null to skip it.
+ *   grad_aif: each (segment, slice) item scatters its weighted gradients into
+ *     a shared padded tile, folded onto the image with FP32 atomics (the
+ *     result is not bitwise reproducible run to run).
+ *   grad_bank: one thread block per (slice, wavelength) accumulates over the
+ *     tiles that use the slice in a fixed order (deterministic).  Needs a
+ *     device workspace of sd_dp_render_backward_workspace() bytes (a bitmap
+ *     of the slices each 64x32 tile uses); ignored when grad_bank is null.
+ * Returns SD_ERR_ARG when the workspace is missing or too small.
+ */
+sd_status sd_dp_render_backward(const float* grad_out, const float* aif,
+                                const float* depth_m, const float* bank,
+                                const sd_bank_layout* layout, int N, int C,
+                                int H, int W, float* grad_aif,
+                                float* grad_bank, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Device workspace bytes sd_dp_render_backward needs for these sizes. */
+sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
+                                          int C, int H, int W, size_t* bytes);
+
+/* ------------------------------------------------------------------------
+ * Library information
+ * ---------------------------------------------------------------------- */
+const char* sd_status_string(sd_status s);
+/* last CUDA error code seen by the library on this thread (0 if none) */
+int sd_last_cuda_error(void);
+/* version as 10000*major + 100*minor + patch */
+int sd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDIRT_H */

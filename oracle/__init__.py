@@ -78,9 +78,11 @@ def lib():
         L.or_render_bank_bwd.argtypes = [pd, pd, i, i, i, i, pf, pd, i, i, i, i,
                                          pf, pf, f, pd, pd]
         L.or_render_select.argtypes = [i, i, pf, pf, i, pf, i, f, pd]
+        L.or_render_bank_pixels.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf, f,
+                                            pi, i, pd, i]
         for fn in ("or_lens_info", "or_trace_hits", "or_psf_bank", "or_trace_functional",
                    "or_trace_grad", "or_render_bank", "or_render_map",
-                   "or_render_bank_bwd", "or_render_select"):
+                   "or_render_bank_bwd", "or_render_select", "or_render_bank_pixels"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -220,6 +222,22 @@ def render_bank(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, n_threads=1)
                                 _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
                                 float(np.float32(pitch_mm)), _pd(out), n_threads),
            "render_bank")
+    return out
+
+
+def render_bank_pixels(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, pix, n_threads=1):
+    """Bank-mode render of the pixels pix (k, 3) = (n, y, x) -> (k, 2C)."""
+    a = _f64(aif)
+    N, C, H, W = a.shape
+    dm = _f32(depth_m)
+    b = _f64(bank)
+    F, Z, NL, _, ks, _ = b.shape
+    px = np.ascontiguousarray(pix, dtype=np.int32)
+    out = np.zeros((len(px), 2 * C))
+    _check(lib().or_render_bank_pixels(_pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z, NL, ks,
+                                       _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
+                                       float(np.float32(pitch_mm)), _pi(px), len(px),
+                                       _pd(out), n_threads), "render_bank_pixels")
     return out
 
 

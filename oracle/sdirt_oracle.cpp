@@ -1076,6 +1076,42 @@ int or_render_bank(const double* aif, int N, int C, int H, int W,
   return 0;
 }
 
+// Bank-mode render of selected pixels only: pix[i*3..] = (n, y, x);
+// out[i*2C + c] = L of channel c, out[i*2C + C + c] = R.
+int or_render_bank_pixels(const double* aif, int N, int C, int H, int W,
+                          const float* depth_m, const double* bank, int F, int Z,
+                          int NL, int ks, const float* field_h_mm,
+                          const float* depths_m, float pitch_mm, const int* pix,
+                          int npix, double* out, int n_threads) {
+  if (!aif || !depth_m || !bank || !pix || !out || ks < 1 || ks % 2 == 0) return -1;
+  if (!(NL == C || NL == 1)) return -4;
+  std::vector<float> iq(Z);
+  for (int j = 0; j < Z; ++j) iq[j] = 1.0f / depths_m[j];
+  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm};
+  int p = (ks - 1) / 2;
+  parallel_for(npix, n_threads, [&](int i) {
+    int n = pix[3 * i], y = pix[3 * i + 1], x = pix[3 * i + 2];
+    std::vector<double> K(2 * (size_t)ks * ks);
+    for (int c = 0; c < C; ++c) {
+      int lam = (NL == C) ? c : 0;
+      pixel_kernel(B, y, x, H, W, depth_m[((size_t)n * H + y) * W + x], lam, K.data(),
+                   nullptr);
+      const double* img = aif + ((size_t)n * C + c) * H * W;
+      double accL = 0, accR = 0;
+      for (int a = 0; a < ks; ++a)
+        for (int b = 0; b < ks; ++b) {
+          double v = img[(size_t)clampi(y + a - p, 0, H - 1) * W + clampi(x + b - p, 0, W - 1)];
+          int kk = (ks - 1 - a) * ks + (ks - 1 - b);
+          accL += v * K[kk];
+          accR += v * K[(size_t)ks * ks + kk];
+        }
+      out[(size_t)i * 2 * C + c] = accL;
+      out[(size_t)i * 2 * C + C + c] = accR;
+    }
+  });
+  return 0;
+}
+
 // Map-mode render: psf_map (H,W,2,ks,ks) f64.
 int or_render_map(const double* aif, int N, int C, int H, int W,
                   const double* psf_map, int ks, double* out) {

@@ -1,0 +1,117 @@
+"""ctypes declarations of the C ABI in include/sdirt.h (marshalling only).
+
+Loading fails loudly when libsdirt.so is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libsdirt.so"
+
+SD_OK, SD_ERR_ARG, SD_ERR_LENS, SD_ERR_UNSUPPORTED, SD_ERR_CUDA, SD_ERR_CAPACITY = range(6)
+SD_SURF_REFRACT, SD_SURF_STOP = 0, 1
+SD_BIN_HARD, SD_BIN_BILINEAR = 0, 1
+SD_NORM_NONE, SD_NORM_JOINT, SD_NORM_SEPARATE, SD_NORM_PER_RAY = range(4)
+SD_F32, SD_BF16, SD_F16 = 0, 1, 2
+SD_N_STATS = 8
+SD_MAX_SURFACES = 32
+SD_MAX_LENSES = 16
+
+
+class SdSurface(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("radius", ctypes.c_double), ("thickness", ctypes.c_double),
+                ("nd", ctypes.c_double), ("vd", ctypes.c_double),
+                ("semi_diameter", ctypes.c_double), ("conic", ctypes.c_double),
+                ("asph", ctypes.c_double * 5)]
+
+
+class SdParaxial(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("efl", "bfl", "z_ep", "r_ep", "sensor_dist", "m_sensor", "img_dist", "z_sensor")]
+
+
+class SdSensor(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("pitch_mm", "h_mm", "f_mm", "w_mm", "r_mm")]
+
+
+class SdTraceOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("norm", ctypes.c_int32),
+                ("out_dtype", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("max_ks", ctypes.c_int32), ("max_n_grid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class SdBankLayout(ctypes.Structure):
+    _fields_ = [("n_field", ctypes.c_int32), ("n_depth", ctypes.c_int32),
+                ("n_lambda", ctypes.c_int32), ("ks", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("field_h_mm", ctypes.POINTER(ctypes.c_float)),
+                ("depths_m", ctypes.POINTER(ctypes.c_float)),
+                ("pitch_mm", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
+# sd_psf_request as a numpy record (48 bytes, device-resident array)
+REQUEST_DTYPE = np.dtype([("h_mm", "<f8"), ("depth_mm", "<f8"), ("lambda_nm", "<f8"),
+                          ("n_grid", "<i4"), ("ks", "<i4"), ("lens", "<i4"),
+                          ("reserved", "<i4"), ("out_offset", "<i8")])
+assert REQUEST_DTYPE.itemsize == 48
+
+# every exported symbol of include/sdirt.h
+EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
+           "sd_dp_psf_trace", "sd_dp_trace_hits", "sd_dp_render", "sd_dp_render_backward",
+           "sd_dp_render_backward_workspace", "sd_status_string", "sd_last_cuda_error",
+           "sd_version")
+
+_lib = None
+
+
+class SdError(RuntimeError):
+    def __init__(self, status, what):
+        name = lib().sd_status_string(status).decode() if _lib else str(status)
+        extra = ""
+        if status == SD_ERR_CUDA and _lib:
+            extra = f" (cudaError {_lib.sd_last_cuda_error()})"
+        super().__init__(f"{what}: {name}{extra}")
+        self.status = status
+
+
+def check(status, what):
+    if status != SD_OK:
+        raise SdError(status, what)
+
+
+def lib():
+    """Loads libsdirt.so (build it with paper_2503_11213_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"sdirt CUDA library not built: {_LIB_PATH} is missing "
+                           "(run paper_2503_11213_gb300.build.build()); there is no "
+                           "CPU fallback")
+    import torch  # noqa: F401  -- load the CUDA runtime torch uses first
+    L = ctypes.CDLL(str(_LIB_PATH))
+    P = ctypes.POINTER
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.sd_lens_load.argtypes = [P(SdSurface), i32, dbl, P(vp)]
+    L.sd_lens_paraxial.argtypes = [vp, dbl, dbl, P(SdParaxial)]
+    L.sd_lens_set_param.argtypes = [vp, i32, dbl]
+    L.sd_lens_free.argtypes = [vp]
+    L.sd_dp_psf_trace.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts), vp, vp, vp]
+    L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
+    L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
+    L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,
+                                        vp, vp, vp, ctypes.c_size_t, vp]
+    L.sd_dp_render_backward_workspace.argtypes = [P(SdBankLayout), i32, i32, i32, i32,
+                                                  P(ctypes.c_size_t)]
+    L.sd_status_string.argtypes = [i32]
+    L.sd_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "sd_status_string":
+            getattr(L, name).restype = i32
+    _lib = L
+    return L

@@ -1,0 +1,218 @@
+"""PyTorch-facing API of the DP simulator hot path.
+
+Every function marshals tensors into the C ABI of include/sdirt.h and runs on
+the current CUDA stream; all arithmetic happens in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: L.SD_F32, torch.bfloat16: L.SD_BF16, torch.float16: L.SD_F16}
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("expected contiguous CUDA tensors")
+
+
+@dataclass
+class DPSensor:
+    """DP pixel structure (Sec. 3.1); defaults are Eq. (S1) multiples of ps."""
+    pitch_mm: float
+    h: float = 0.78
+    f: float = 1.44
+    w: float = 0.30
+    r: float = 0.50
+
+    def c(self):
+        ps = self.pitch_mm
+        return L.SdSensor(ps, self.h * ps, self.f * ps, self.w * ps, self.r * ps)
+
+
+class Lens:
+    """A lens prescription uploaded to the device lens table.
+
+    table: (n, 12) float64 rows (type, radius, thickness, nd, vd,
+    semi-diameter, conic, a4..a12), as produced by ``workloads``.
+    """
+
+    def __init__(self, table, focus_mm: float = 0.0):
+        lib = L.lib()
+        tab = np.asarray(table, dtype=np.float64)
+        n = tab.shape[0]
+        arr = (L.SdSurface * n)()
+        for i, r in enumerate(tab):
+            s = arr[i]
+            s.type = int(r[0])
+            s.radius, s.thickness, s.nd, s.vd, s.semi_diameter, s.conic = map(float, r[1:7])
+            for j in range(5):
+                s.asph[j] = float(r[7 + j])
+        h = ctypes.c_void_p()
+        L.check(lib.sd_lens_load(arr, n, float(focus_mm), ctypes.byref(h)), "sd_lens_load")
+        self._h = h
+        self.n_surfaces = n
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("lens already freed")
+        return self._h
+
+    def paraxial(self, lambda_nm=587.5618, depth_mm=1000.0):
+        out = L.SdParaxial()
+        L.check(L.lib().sd_lens_paraxial(self.handle, float(lambda_nm), float(depth_mm),
+                                         ctypes.byref(out)), "sd_lens_paraxial")
+        return {k: getattr(out, k) for k, _ in L.SdParaxial._fields_}
+
+    def set_param(self, param_id: int, value: float):
+        L.check(L.lib().sd_lens_set_param(self.handle, int(param_id), float(value)),
+                "sd_lens_set_param")
+
+    def free(self):
+        if self._h is not None:
+            L.lib().sd_lens_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_requests(reqs, ks_offsets=True, device="cuda"):
+    """Structured numpy requests (fields h_mm, depth_mm, lambda_nm, n_grid, ks
+    and optionally lens) -> (device uint8 tensor of sd_psf_request, total
+    output elements, per-request offsets)."""
+    n = len(reqs)
+    rec = np.zeros(n, dtype=L.REQUEST_DTYPE)
+    for f in ("h_mm", "depth_mm", "lambda_nm", "n_grid", "ks"):
+        rec[f] = reqs[f]
+    if "lens" in reqs.dtype.names:
+        rec["lens"] = reqs["lens"]
+    sizes = 2 * rec["ks"].astype(np.int64) ** 2
+    off = np.zeros(n, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)[:-1]
+    rec["out_offset"] = off
+    total = int(sizes.sum())
+    dev = torch.from_numpy(rec.view(np.uint8).copy()).to(device)
+    return dev, total, off
+
+
+def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=512,
+                 mode=L.SD_BIN_HARD, norm=L.SD_NORM_JOINT, dtype=torch.float32,
+                 out=None, stats=None, newton_iters=0):
+    """Traces the requests (device array from make_requests) into a flat bank."""
+    lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
+    handles = (ctypes.c_void_p * len(lenses))(*[l.handle.value for l in lenses])
+    if out is None:
+        out = torch.empty(total, dtype=dtype, device=req_dev.device)
+    if stats is None:
+        stats = torch.zeros((n_req, L.SD_N_STATS), dtype=torch.int64, device=req_dev.device)
+    _need_cuda(req_dev, out, stats)
+    opts = L.SdTraceOpts(mode, norm, _DT[out.dtype], newton_iters, max_ks, max_n)
+    sen = sensor.c()
+    L.check(L.lib().sd_dp_psf_trace(handles, len(lenses), ctypes.byref(sen), _ptr(req_dev),
+                                    n_req, ctypes.byref(opts), _ptr(out), _ptr(stats),
+                                    _stream()), "sd_dp_psf_trace")
+    return out, stats
+
+
+HIT_FIELDS = ("x", "y", "dx", "dy", "dz", "state", "side", "pixel")
+
+
+def trace_hits(lens: Lens, sensor: DPSensor, req, device="cuda"):
+    """Per-ray records of one request (structured numpy element)."""
+    q = np.zeros(1, dtype=L.REQUEST_DTYPE)
+    for f in ("h_mm", "depth_mm", "lambda_nm", "n_grid", "ks"):
+        q[f] = req[f]
+    n = int(req["n_grid"])
+    rec = torch.zeros((n * n, 8), dtype=torch.float32, device=device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=device)
+    sen = sensor.c()
+    opts = L.SdTraceOpts(0, 0, 0, 0, int(req["ks"]), n)
+    L.check(L.lib().sd_dp_trace_hits(lens.handle, ctypes.byref(sen),
+                                     q.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts),
+                                     _ptr(rec), n * n, _ptr(cnt), _stream()),
+            "sd_dp_trace_hits")
+    k = int(cnt.item())
+    rec = rec[:k]
+    return {f: rec[:, j] for j, f in enumerate(HIT_FIELDS)}
+
+
+class BankLayout:
+    """Bank [F][Z][NL][2][ks][ks] description for the renderer."""
+
+    def __init__(self, field_h_mm, depths_m, n_lambda, ks, pitch_mm, dtype=torch.float32):
+        self.fh = np.ascontiguousarray(field_h_mm, dtype=np.float32)
+        self.dm = np.ascontiguousarray(depths_m, dtype=np.float32)
+        self.n_lambda, self.ks, self.pitch_mm, self.dtype = n_lambda, ks, pitch_mm, dtype
+
+    def c(self):
+        return L.SdBankLayout(len(self.fh), len(self.dm), self.n_lambda, self.ks,
+                              _DT[self.dtype], 0,
+                              self.fh.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              self.dm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              float(self.pitch_mm), 0.0)
+
+    def shape(self):
+        return (len(self.fh), len(self.dm), self.n_lambda, 2, self.ks, self.ks)
+
+
+def dp_render(aif, depth_m, bank, layout: BankLayout, out=None):
+    """aif (N,C,H,W) f32/bf16/f16, depth (N,H,W) f32 metres, bank in
+    layout.dtype -> DP image (N,2C,H,W) in aif's dtype."""
+    N, C, H, W = aif.shape
+    if out is None:
+        out = torch.empty((N, 2 * C, H, W), dtype=aif.dtype, device=aif.device)
+    _need_cuda(aif, depth_m, bank, out)
+    if bank.dtype != layout.dtype or depth_m.dtype != torch.float32:
+        raise ValueError("bank dtype must match the layout; depth must be float32")
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render(_ptr(aif), _ptr(depth_m), _ptr(bank), ctypes.byref(lay),
+                                 N, C, H, W, _DT[aif.dtype], _ptr(out), _stream()),
+            "sd_dp_render")
+    return out
+
+
+def render_backward_workspace(layout: BankLayout, N, C, H, W):
+    n = ctypes.c_size_t(0)
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render_backward_workspace(ctypes.byref(lay), N, C, H, W,
+                                                    ctypes.byref(n)),
+            "sd_dp_render_backward_workspace")
+    return n.value
+
+
+def dp_render_backward(grad_out, aif, depth_m, bank, layout: BankLayout, need_aif=True,
+                       need_bank=True, workspace=None):
+    """Adjoint of dp_render (FP32): (grad_aif or None, grad_bank or None)."""
+    N, C, H, W = aif.shape
+    ga = torch.empty_like(aif) if need_aif else None
+    gb = torch.empty_like(bank) if need_bank else None
+    if need_bank and workspace is None:
+        nbytes = render_backward_workspace(layout, N, C, H, W)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=aif.device)
+    _need_cuda(grad_out, aif, depth_m, bank, ga, gb)
+    lay = layout.c()
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    L.check(L.lib().sd_dp_render_backward(_ptr(grad_out), _ptr(aif), _ptr(depth_m), _ptr(bank),
+                                          ctypes.byref(lay), N, C, H, W, _ptr(ga), _ptr(gb),
+                                          _ptr(workspace), ws_bytes, _stream()),
+            "sd_dp_render_backward")
+    return ga, gb

@@ -1,0 +1,899 @@
+// Lens table, paraxial set-up and the DP PSF trace kernels (sm_103a).
+//
+// Sec. 3.1 of He et al. (ICCV 2025): a ray set A from the object point p to
+// N x N entrance-pupil samples is refracted surface by surface (Snell's law)
+// to the sensor plane; each landing point O_k with direction D_k is assigned
+// to the left or right sub-pixel of its DP pixel with the boundary lines of
+// Eq. (1) (inside the microlens) or Eq. (2) (outside), and PSF_L / PSF_R
+// accumulate unit ray energies (Eq. 3), then are sum-normalised (Sec. 3.2).
+//
+// GPU design: one thread per ray, the lens prescription in __constant__
+// memory (uniform across a warp), one thread block per PSF request with the
+// [2][ks][ks] patch in shared memory.  Hard binning uses warp-aggregated
+// shared-memory integer atomics (__match_any_sync on the destination bin);
+// no global atomics.  The per-request paraxial set-up (entrance pupil,
+// object point, refractive indices at the request wavelength) runs in FP64
+// in the block prologue; the per-ray trace is FP32.
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sd {
+
+// ---------------------------------------------------------------------------
+// Device lens image
+// ---------------------------------------------------------------------------
+struct DevSurf {
+  float c, k;       // curvature (1/mm) and conic
+  float a[5];       // a4..a12
+  float da[5];      // (m) * a_2m: derivative coefficients of the sag in u = rho^2
+  float t;          // thickness after the surface (mm); last: sensor distance
+  float sd2;        // clear semi-diameter squared
+  int type;         // SD_SURF_REFRACT / SD_SURF_STOP
+  int asph;         // any a_2m != 0 -> Newton refinement
+  int flat;         // c == 0 -> plane start
+  int pad;
+};
+
+struct DevLens {
+  int n, stop;
+  double z_front;   // most negative z of surface 0 inside its aperture
+  double sd_stop;
+  double c[SD_MAX_SURFACES], t[SD_MAX_SURFACES];
+  double A[SD_MAX_SURFACES], B[SD_MAX_SURFACES];  // Cauchy n = A + B/lam^2 (um)
+  int type[SD_MAX_SURFACES];
+  DevSurf s[SD_MAX_SURFACES];
+};
+
+__constant__ DevLens c_lens[SD_MAX_LENSES];
+
+// ---------------------------------------------------------------------------
+// Paraxial optics (FP64), shared by host and device code
+// ---------------------------------------------------------------------------
+struct PYU {
+  double y, u, n;
+};
+
+__host__ __device__ inline double cauchy(double A, double B, double lam_um) {
+  return A + B / (lam_um * lam_um);
+}
+
+// y-nu trace of a ray given at the vertex plane of surface `from` (before it
+// refracts) through surfaces [from, to); ends at the vertex plane of `to`.
+// nlam[s] is the index after surface s at the working wavelength.
+__host__ __device__ inline PYU parax(const DevLens& L, const double* nlam,
+                                     double y, double u, int from, int to) {
+  double n = from > 0 ? nlam[from - 1] : 1.0;
+  for (int s = from; s < to; ++s) {
+    double n2 = nlam[s];
+    if (L.type[s] == SD_SURF_REFRACT) u = (n * u - y * (n2 - n) * L.c[s]) / n2;
+    n = n2;
+    y = y + L.t[s] * u;
+  }
+  PYU r;
+  r.y = y;
+  r.u = u;
+  r.n = n;
+  return r;
+}
+
+struct RayGen {
+  double x_o;      // object height (mm), object at z = -depth
+  double z_ep, r_ep;
+  double z_start;  // plane where rays start
+};
+
+// Entrance pupil = paraxial image of the stop in object space; object height
+// from the paraxial chief ray (through the pupil centre) landing at h on the
+// sensor plane.
+__host__ __device__ inline RayGen ray_gen(const DevLens& L, const double* nlam,
+                                          double h_mm, double depth_mm) {
+  RayGen g;
+  PYU a = parax(L, nlam, 1.0, 0.0, 0, L.stop);
+  PYU b = parax(L, nlam, 0.0, 1.0, 0, L.stop);
+  g.z_ep = b.y / a.y;
+  g.r_ep = fabs(L.sd_stop / a.y);
+  double u0 = -1.0 / (g.z_ep + depth_mm);
+  PYU c = parax(L, nlam, 1.0 + u0 * depth_mm, u0, 0, L.n);
+  g.x_o = h_mm / c.y;
+  g.z_start = (g.z_ep <= L.z_front) ? g.z_ep : L.z_front - 1.0;
+  return g;
+}
+
+__host__ __device__ inline void indices_at(const DevLens& L, double lam_nm, double* nlam) {
+  double lam = lam_nm * 1e-3;
+  for (int s = 0; s < L.n; ++s) nlam[s] = cauchy(L.A[s], L.B[s], lam);
+}
+
+// image distance after the last vertex for an axial object at depth d
+inline double image_distance(const DevLens& L, const double* nlam, double d) {
+  PYU r = parax(L, nlam, 1.0, 1.0 / d, 0, L.n - 1);
+  int s = L.n - 1;
+  double n2 = nlam[s], u = r.u;
+  if (L.type[s] == SD_SURF_REFRACT) u = (r.n * r.u - r.y * (n2 - r.n) * L.c[s]) / n2;
+  return -r.y / u;
+}
+
+}  // namespace sd
+
+// ---------------------------------------------------------------------------
+// Host lens object
+// ---------------------------------------------------------------------------
+struct sd_lens {
+  int slot;
+  int device;
+  sd::DevLens img;
+};
+
+namespace sd {
+namespace {
+
+std::mutex g_mu;
+bool g_used[SD_MAX_LENSES];
+
+void cauchy_fit(double nd, double vd, double* A, double* B) {
+  if (vd <= 0.0 || nd == 1.0) {
+    *A = nd;
+    *B = 0.0;
+    return;
+  }
+  const double lF = 0.4861327, lC = 0.6562725, ld = 0.5875618;  // um
+  *B = (nd - 1.0) / vd / (1.0 / (lF * lF) - 1.0 / (lC * lC));
+  *A = nd - *B / (ld * ld);
+}
+
+bool fin(double v) { return std::isfinite(v); }
+
+// fills the FP32 view of surface s from the FP64 parameters
+void refresh_surface(DevLens& L, int s, const double* k, const double* a,
+                     double sd) {
+  DevSurf& d = L.s[s];
+  d.c = (float)L.c[s];
+  d.k = (float)k[0];
+  bool asph = false;
+  for (int j = 0; j < 5; ++j) {
+    d.a[j] = (float)a[j];
+    d.da[j] = (float)((j + 2) * a[j]);
+    asph |= (a[j] != 0.0);
+  }
+  d.t = (float)L.t[s];
+  d.sd2 = (float)(sd * sd);
+  d.type = L.type[s];
+  d.asph = (d.type == SD_SURF_REFRACT) && asph;
+  d.flat = (d.type == SD_SURF_STOP) || (L.c[s] == 0.0);
+}
+
+double sag_at(double c, double k, const double* a, double rho) {
+  double u = rho * rho;
+  double arg = 1.0 - (1.0 + k) * c * c * u;
+  if (arg < 0) arg = 0;
+  double z = c * u / (1.0 + std::sqrt(arg));
+  double up = u;
+  for (int j = 0; j < 5; ++j) {
+    up *= u;
+    z += a[j] * up;
+  }
+  return z;
+}
+
+// per-lens FP64 parameters not kept in the device image
+struct HostExtra {
+  double k[SD_MAX_SURFACES];
+  double a[SD_MAX_SURFACES][5];
+  double sd[SD_MAX_SURFACES];
+};
+HostExtra g_extra[SD_MAX_LENSES];
+
+sd_status upload(const sd_lens* lens) {
+  int dev = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != lens->device) return SD_ERR_ARG;
+  SD_CUDA_TRY(cudaMemcpyToSymbol(c_lens, &lens->img, sizeof(DevLens),
+                                 sizeof(DevLens) * lens->slot));
+  return SD_OK;
+}
+
+void finish_image(DevLens& L, const HostExtra& X) {
+  for (int s = 0; s < L.n; ++s) refresh_surface(L, s, &X.k[s], X.a[s], X.sd[s]);
+  L.sd_stop = X.sd[L.stop];
+  double zf = 0.0;
+  if (L.type[0] == SD_SURF_REFRACT)
+    zf = std::min(0.0, sag_at(L.c[0], X.k[0], X.a[0], X.sd[0]));
+  L.z_front = zf;
+}
+
+}  // namespace
+}  // namespace sd
+
+extern "C" {
+
+sd_status sd_lens_load(const sd_surface* surfs, int n, double focus_mm,
+                       sd_lens** out) {
+  using namespace sd;
+  if (!surfs || !out || n < 1 || n > SD_MAX_SURFACES) return SD_ERR_ARG;
+  if (!std::isfinite(focus_mm)) return SD_ERR_ARG;
+  *out = nullptr;
+  DevLens L;
+  std::memset(&L, 0, sizeof L);
+  HostExtra X;
+  std::memset(&X, 0, sizeof X);
+  L.n = n;
+  L.stop = -1;
+  for (int i = 0; i < n; ++i) {
+    const sd_surface& s = surfs[i];
+    if (s.type != SD_SURF_REFRACT && s.type != SD_SURF_STOP) return SD_ERR_LENS;
+    double vals[] = {s.radius, s.thickness, s.nd, s.vd, s.semi_diameter, s.conic,
+                     s.asph[0], s.asph[1], s.asph[2], s.asph[3], s.asph[4]};
+    for (double v : vals)
+      if (!fin(v)) return SD_ERR_LENS;
+    if (s.nd < 1.0 || s.semi_diameter <= 0.0 || s.thickness < 0.0) return SD_ERR_LENS;
+    if (s.type == SD_SURF_STOP) {
+      if (L.stop >= 0) return SD_ERR_LENS;  // exactly one stop
+      L.stop = i;
+    }
+    L.type[i] = s.type;
+    L.c[i] = (s.type == SD_SURF_STOP || s.radius == 0.0) ? 0.0 : 1.0 / s.radius;
+    L.t[i] = s.thickness;
+    cauchy_fit(s.nd, s.vd, &L.A[i], &L.B[i]);
+    X.k[i] = s.type == SD_SURF_STOP ? 0.0 : s.conic;
+    for (int j = 0; j < 5; ++j) X.a[i][j] = s.type == SD_SURF_STOP ? 0.0 : s.asph[j];
+    X.sd[i] = s.semi_diameter;
+    if (s.type == SD_SURF_REFRACT &&
+        1.0 - (1.0 + X.k[i]) * L.c[i] * L.c[i] * X.sd[i] * X.sd[i] < 0.0)
+      return SD_ERR_LENS;  // aperture beyond the conic's rim
+  }
+  if (L.stop < 0) return SD_ERR_LENS;
+  if (focus_mm > 0) {
+    double nlam[SD_MAX_SURFACES];
+    indices_at(L, 587.5618, nlam);
+    double d = image_distance(L, nlam, focus_mm);
+    if (!(d > 0) || !std::isfinite(d)) return SD_ERR_LENS;
+    L.t[n - 1] = d;
+  }
+  if (!(L.t[n - 1] > 0)) return SD_ERR_LENS;
+  finish_image(L, X);
+
+  int dev = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  int slot = -1;
+  for (int i = 0; i < SD_MAX_LENSES; ++i)
+    if (!g_used[i]) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return SD_ERR_CAPACITY;
+  sd_lens* lens = new sd_lens;
+  lens->slot = slot;
+  lens->device = dev;
+  lens->img = L;
+  g_extra[slot] = X;
+  sd_status st = upload(lens);
+  if (st != SD_OK) {
+    delete lens;
+    return st;
+  }
+  g_used[slot] = true;
+  *out = lens;
+  return SD_OK;
+}
+
+sd_status sd_lens_paraxial(const sd_lens* lens, double lambda_nm, double depth_mm,
+                           sd_paraxial* out) {
+  using namespace sd;
+  if (!lens || !out || !(lambda_nm > 0) || !(depth_mm > 0)) return SD_ERR_ARG;
+  const DevLens& L = lens->img;
+  double nlam[SD_MAX_SURFACES];
+  indices_at(L, lambda_nm, nlam);
+  PYU r = parax(L, nlam, 1.0, 0.0, 0, L.n - 1);
+  int s = L.n - 1;
+  double n2 = nlam[s], u = r.u;
+  if (L.type[s] == SD_SURF_REFRACT) u = (r.n * r.u - r.y * (n2 - r.n) * L.c[s]) / n2;
+  out->efl = -1.0 / (n2 * u);
+  out->bfl = -r.y / u;
+  RayGen g = ray_gen(L, nlam, 1.0, depth_mm);
+  out->z_ep = g.z_ep;
+  out->r_ep = g.r_ep;
+  out->sensor_dist = L.t[L.n - 1];
+  out->m_sensor = 1.0 / g.x_o;
+  out->img_dist = image_distance(L, nlam, depth_mm);
+  double z = 0;
+  for (int i = 0; i < L.n; ++i) z += L.t[i];
+  out->z_sensor = z;
+  return SD_OK;
+}
+
+sd_status sd_lens_set_param(sd_lens* lens, int pid, double value) {
+  using namespace sd;
+  if (!lens || !std::isfinite(value)) return SD_ERR_ARG;
+  DevLens& L = lens->img;
+  int s = pid / 8, j = pid % 8;
+  if (pid < 0 || s >= L.n) return SD_ERR_ARG;
+  HostExtra& X = g_extra[lens->slot];
+  if (L.type[s] == SD_SURF_STOP && j != 7) return SD_ERR_ARG;
+  if (j == 0)
+    L.c[s] = value;
+  else if (j == 1)
+    X.k[s] = value;
+  else if (j == 7) {
+    if (value < 0 || (s == L.n - 1 && value <= 0)) return SD_ERR_LENS;
+    L.t[s] = value;
+  } else
+    X.a[s][j - 2] = value;
+  finish_image(L, X);
+  return upload(lens);
+}
+
+sd_status sd_lens_free(sd_lens* lens) {
+  if (!lens) return SD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sd::g_mu);
+  sd::g_used[lens->slot] = false;
+  delete lens;
+  return SD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Trace kernels
+// ---------------------------------------------------------------------------
+namespace sd {
+
+enum { ST_OK = 0, ST_MISS = 1, ST_CLIP = 2, ST_TIR = 3, ST_NEWTON = 4, ST_BACK = 5 };
+
+struct SensorF {
+  float ps, inv_ps, h, w, r2, fh;  // fh = (f - h) / f
+};
+
+struct TraceParams {
+  const sd_psf_request* req;
+  int n_req;
+  int slots[SD_MAX_LENSES];
+  int n_lenses;
+  SensorF sen;
+  int norm;
+  int newton_max;
+  int max_n;           // capacity of the row tables
+  int max_ks;
+  void* out;
+  long long* stats;
+  // hit dump (test path)
+  float* rec;
+  int max_rays;
+  int* n_rays;
+};
+
+// Per-request context computed by the block prologue.
+struct ReqCtx {
+  float x_o, scale;     // object height; pupil sample spacing r_ep / N
+  float vz;             // z_ep + depth (axial length from p to the EP plane)
+  float z_start, s_start, z_ep;
+  float xc, yc;
+  int slot, N, ks, total;
+  int ok;
+  float eta[SD_MAX_SURFACES];    // n_before / n_after at the request wavelength
+  float omeg2[SD_MAX_SURFACES];  // 1 - eta^2 (evaluated in FP64)
+};
+
+// Integer square root floor(sqrt(v)) for 0 <= v < 2^24.
+__device__ __forceinline__ int isqrt_floor(int v) {
+  int r = (int)sqrtf((float)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+// Number of in-pupil samples of pupil row iy and the first column index.
+__device__ __forceinline__ void row_span(int N, int iy, int* cnt, int* lo) {
+  int b = 2 * iy + 1 - N;
+  int rem = N * N - b * b;
+  int am = isqrt_floor(rem);
+  // a = 2 ix + 1 - N has the parity of N + 1: largest such |a| <= sqrt(rem)
+  if ((am + N + 1) & 1) am -= 1;
+  *cnt = am + 1;
+  *lo = (N - 1 - am) >> 1;
+}
+
+// Block prologue: paraxial set-up (FP64, thread 0) and pupil row tables.
+__device__ void setup_request(const TraceParams& P, const sd_psf_request& q,
+                              ReqCtx& ctx, int* prefix, int* lo) {
+  if (threadIdx.x == 0) {
+    int li = q.lens;
+    ctx.ok = (li >= 0 && li < P.n_lenses && q.n_grid >= 2 && q.n_grid <= P.max_n &&
+              q.ks >= 1 && (q.ks & 1) && q.ks <= P.max_ks && q.depth_mm > 0 &&
+              q.lambda_nm > 0);
+    if (ctx.ok) {
+      int slot = P.slots[li];
+      const DevLens& L = c_lens[slot];
+      double nlam[SD_MAX_SURFACES];
+      indices_at(L, q.lambda_nm, nlam);
+      double nb = 1.0;
+      for (int s = 0; s < L.n; ++s) {
+        double e = nb / nlam[s];
+        ctx.eta[s] = (float)e;
+        ctx.omeg2[s] = (float)(1.0 - e * e);
+        nb = nlam[s];
+      }
+      RayGen g = ray_gen(L, nlam, q.h_mm, q.depth_mm);
+      ctx.x_o = (float)g.x_o;
+      ctx.scale = (float)(g.r_ep / q.n_grid);
+      ctx.vz = (float)(g.z_ep + q.depth_mm);
+      ctx.z_ep = (float)g.z_ep;
+      ctx.z_start = (float)g.z_start;
+      ctx.s_start = (float)((g.z_start + q.depth_mm) / (g.z_ep + q.depth_mm));
+      ctx.xc = (float)q.h_mm;
+      ctx.yc = 0.f;
+      ctx.slot = slot;
+      ctx.N = q.n_grid;
+      ctx.ks = q.ks;
+    } else {
+      ctx.N = 0;
+      ctx.ks = 0;
+    }
+  }
+  __syncthreads();
+  int N = ctx.N;
+  // pupil row spans, then an exclusive prefix over rows (one warp scans)
+  for (int iy = threadIdx.x; iy < N; iy += blockDim.x) {
+    int c, l;
+    row_span(N, iy, &c, &l);
+    prefix[iy + 1] = c;
+    lo[iy] = l;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int lane = threadIdx.x;
+    int carry = 0;
+    for (int base = 0; base < N; base += 32) {
+      int i = base + lane;
+      int v = (i < N) ? prefix[i + 1] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (i < N) prefix[i + 1] = v + carry;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) {
+      prefix[0] = 0;
+      ctx.total = carry;
+    }
+  }
+  __syncthreads();
+}
+
+// 1/sqrt(x) to about half an ulp: hardware estimate plus one Newton step
+// (unit vectors feed Snell's law, whose output direction error is
+// multiplied by the remaining path length to the sensor).
+__device__ __forceinline__ float rsqrt_refined(float x) {
+  float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+
+// Sequential trace (FP32) of one ray in surface-0-vertex-local coordinates.
+// On success (x, y) is the sensor landing point and (dx, dy, dz) the unit
+// direction.  Positions are kept relative to the current surface vertex.
+__device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta,
+                                         const float* __restrict__ omeg2, int newton_max, float& x, float& y, float& z,
+                                         float& dx, float& dy, float& dz) {
+  const DevLens& L = c_lens[slot];
+  const int n = L.n;
+  for (int s = 0; s < n; ++s) {
+    const DevSurf& S = L.s[s];
+    float t;
+    if (S.flat) {
+      if (!(dz > 0.f)) return ST_BACK;
+      t = -z / dz;
+    } else {
+      // conic: A t^2 - 2 B t + C = 0 (|d| = 1), root nearest the vertex in
+      // the cancellation-free form t = C / (B + sqrt(B^2 - A C))
+      float kk = 1.f + S.k;
+      float A = S.c * fmaf(S.k * dz, dz, 1.f);
+      float B = dz - S.c * (x * dx + y * dy + kk * z * dz);
+      float C = S.c * (x * x + y * y + kk * z * z) - 2.f * z;
+      float disc = B * B - A * C;
+      if (disc < 0.f) return ST_MISS;
+      float den = B + sqrtf(disc);
+      if (!(den > 0.f)) return ST_MISS;
+      t = C / den;
+    }
+    if (S.asph) {
+      // Newton on F(t) = z + t dz - sag(rho(t)^2), started at the conic root
+      int it = 0;
+      for (; it < newton_max; ++it) {
+        float px = fmaf(t, dx, x), py = fmaf(t, dy, y);
+        float u = px * px + py * py;
+        float arg = 1.f - (1.f + S.k) * S.c * S.c * u;
+        if (arg < 0.f) return ST_NEWTON;
+        float q = sqrtf(arg);
+        float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.a[4], S.a[3]), S.a[2]), S.a[1]), S.a[0]);
+        float zs = S.c * u / (1.f + q) + u * u * poly;
+        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
+        float dzdu = (q > 0.f ? 0.5f * S.c / q : 0.f) + u * dpoly;
+        float F = fmaf(t, dz, z) - zs;
+        float dF = dz - 2.f * dzdu * (px * dx + py * dy);
+        float step = F / dF;
+        t -= step;
+        if (fabsf(step) < 1e-5f) break;
+      }
+      if (it == newton_max) return ST_NEWTON;
+    }
+    x = fmaf(t, dx, x);
+    y = fmaf(t, dy, y);
+    z = fmaf(t, dz, z);
+    float rho2 = x * x + y * y;
+    if (rho2 > S.sd2) return ST_CLIP;
+    if (S.type == SD_SURF_REFRACT) {
+      float nx, ny, nz;
+      if (S.asph) {
+        float u = rho2;
+        float q = sqrtf(fmaxf(1.f - (1.f + S.k) * S.c * S.c * u, 0.f));
+        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
+        float dzdu = (q > 0.f ? 0.5f * S.c / q : 0.f) + u * dpoly;
+        nx = -2.f * x * dzdu;
+        ny = -2.f * y * dzdu;
+        nz = 1.f;
+      } else {
+        // gradient of the quadric c(x^2+y^2) + c(1+k) z^2 - 2 z, oriented +z
+        nx = -S.c * x;
+        ny = -S.c * y;
+        nz = 1.f - S.c * (1.f + S.k) * z;
+      }
+      float inv = rsqrt_refined(nx * nx + ny * ny + nz * nz);
+      nx *= inv;
+      ny *= inv;
+      nz *= inv;
+      // vector Snell's law with the normal along the propagation:
+      // d' = e d + g n with g = cos(t_t) - e cos(t_i), evaluated as
+      // (1 - e^2) / (cos(t_t) + e cos(t_i)) to avoid the cancellation
+      float e = eta[s];
+      float cosi = nx * dx + ny * dy + nz * dz;
+      float k2 = 1.f - e * e * (1.f - cosi * cosi);
+      if (k2 < 0.f) return ST_TIR;
+      float g = __fdiv_rn(omeg2[s], sqrtf(k2) + e * cosi);
+      dx = fmaf(e, dx, g * nx);
+      dy = fmaf(e, dy, g * ny);
+      dz = fmaf(e, dz, g * nz);
+    }
+    z -= S.t;  // vertex-local coordinate of the next surface (or the sensor)
+  }
+  if (!(dz > 0.f)) return ST_BACK;
+  float t = -z / dz;
+  x = fmaf(t, dx, x);
+  y = fmaf(t, dy, y);
+  return ST_OK;
+}
+
+// Eq. (1)/(2): s = offset on the sub-pixel plane relative to the pixel centre;
+// L for 0 <= s < w, R for -w <= s < 0, else missed.
+__device__ __forceinline__ int dp_side(const SensorF& S, float dxp, float dyp, float tan_t) {
+  bool inside = dxp * dxp + dyp * dyp <= S.r2;
+  float s = inside ? fmaf(dxp, S.fh, S.h * tan_t) : fmaf(S.h, tan_t, dxp);
+  if (s >= 0.f && s < S.w) return 0;
+  if (s >= -S.w && s < 0.f) return 1;
+  return 2;
+}
+
+// Generates ray k of the request (in pupil raster order over in-pupil samples).
+__device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, const int* lo,
+                                         int k, float& x, float& y, float& z, float& dx,
+                                         float& dy, float& dz) {
+  int N = ctx.N;
+  // binary search: row iy with prefix[iy] <= k < prefix[iy+1]
+  int a = 0, b = N;
+  while (b - a > 1) {
+    int m = (a + b) >> 1;
+    if (prefix[m] <= k) a = m; else b = m;
+  }
+  int iy = a;
+  int ix = lo[iy] + (k - prefix[iy]);
+  float ex = (float)(2 * ix + 1 - N) * ctx.scale;
+  float ey = (float)(2 * iy + 1 - N) * ctx.scale;
+  float vx = ex - ctx.x_o, vy = ey, vz = ctx.vz;
+  float inv = rsqrt_refined(vx * vx + vy * vy + vz * vz);
+  dx = vx * inv;
+  dy = vy * inv;
+  dz = vz * inv;
+  if (ctx.s_start == 1.f) {
+    x = ex;
+    y = ey;
+  } else {
+    x = fmaf(ctx.s_start, vx, ctx.x_o);
+    y = ctx.s_start * vy;
+  }
+  z = ctx.z_start;
+}
+
+// bytes of the pupil row tables (prefix[N+1], lo[N]), 16-byte multiple
+__host__ __device__ inline size_t table_bytes(int max_n) {
+  return (((size_t)(2 * max_n + 1) * 4) + 15) & ~(size_t)15;
+}
+
+template <class OutT>
+__device__ __forceinline__ void store_out(void* out, long long idx, float v) {
+  reinterpret_cast<OutT*>(out)[idx] = from_f32<OutT>(v);
+}
+
+// One block per request.  MODE 0: hard counts (u32), 1: bilinear (f32).
+template <int MODE, class OutT>
+__global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ReqCtx ctx;
+  __shared__ unsigned int s_stats[SD_N_STATS];
+  __shared__ float s_red[2][32];
+  int* prefix = reinterpret_cast<int*>(smem);
+  int* lo = prefix + (P.max_n + 1);
+  unsigned int* patch = reinterpret_cast<unsigned int*>(smem + table_bytes(P.max_n));
+  float* patchf = reinterpret_cast<float*>(patch);
+
+  const int r = blockIdx.x;
+  const sd_psf_request q = P.req[r];
+  if (threadIdx.x < SD_N_STATS) s_stats[threadIdx.x] = 0;
+  setup_request(P, q, ctx, prefix, lo);
+  const int ks = ctx.ks, ks2 = ks * ks, p = (ks - 1) >> 1;
+  for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) patch[i] = 0u;
+  __syncthreads();
+
+  const SensorF S = P.sen;
+  const int total = ctx.N ? ctx.total : 0;
+  const int lane = threadIdx.x & 31;
+  unsigned int c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0,
+               c_clip = 0;
+  for (int base = 0; base < total; base += blockDim.x) {
+    int k = base + threadIdx.x;
+    int key = -1;
+    float fx = 0.f, fy = 0.f;
+    int side = 2;
+    if (k < total) {
+      float x, y, z, dx, dy, dz;
+      make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
+      int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
+      if (st == ST_OK) {
+        ++c_reached;
+        fx = (x - ctx.xc) * S.inv_ps + (float)p;
+        fy = (y - ctx.yc) * S.inv_ps + (float)p;
+        float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+        side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+        bool inpatch = af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks;
+        if (!inpatch) {
+          ++c_clip;
+          if (MODE == 0) side = 2;  // nothing to deposit
+        } else if (side == 2) {
+          ++c_miss;
+        } else {
+          if (side == 0) ++c_l; else ++c_r;
+        }
+        if (MODE == 0 && inpatch && side < 2) key = side * ks2 + (int)bf * ks + (int)af;
+      } else if (st == ST_CLIP) {
+        ++c_vign;
+      } else {
+        ++c_other;
+      }
+    }
+    if (MODE == 0) {
+      // warp-aggregated shared-memory increment of the landing bin
+      unsigned int m = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&patch[key], (unsigned)__popc(m));
+    } else if (side < 2) {
+      float a0f = floorf(fx), b0f = floorf(fy);
+      float wx = fx - a0f, wy = fy - b0f;
+      int a0 = (int)a0f, b0 = (int)b0f;
+      float* P0 = patchf + side * ks2;
+#pragma unroll
+      for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+        for (int jx = 0; jx < 2; ++jx) {
+          int aa = a0 + jx, bb = b0 + jy;
+          if (aa >= 0 && aa < ks && bb >= 0 && bb < ks)
+            atomicAdd(&P0[bb * ks + aa], (jx ? wx : 1.f - wx) * (jy ? wy : 1.f - wy));
+        }
+    }
+  }
+  // block statistics
+  atomicAdd(&s_stats[SD_STAT_REACHED], c_reached);
+  atomicAdd(&s_stats[SD_STAT_VIGNETTED], c_vign);
+  atomicAdd(&s_stats[SD_STAT_OTHER], c_other);
+  atomicAdd(&s_stats[SD_STAT_L], c_l);
+  atomicAdd(&s_stats[SD_STAT_R], c_r);
+  atomicAdd(&s_stats[SD_STAT_DP_MISSED], c_miss);
+  atomicAdd(&s_stats[SD_STAT_CLIPPED], c_clip);
+  __syncthreads();
+
+  // sums of the L and R planes for the normalisation
+  float sl = 0.f, sr = 0.f;
+  for (int i = threadIdx.x; i < ks2; i += blockDim.x) {
+    if (MODE == 0) {
+      sl += (float)patch[i];
+      sr += (float)patch[ks2 + i];
+    } else {
+      sl += patchf[i];
+      sr += patchf[ks2 + i];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  if (lane == 0) {
+    s_red[0][threadIdx.x >> 5] = sl;
+    s_red[1][threadIdx.x >> 5] = sr;
+  }
+  __syncthreads();
+  float SL = 0.f, SR = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    SL += s_red[0][w];
+    SR += s_red[1][w];
+  }
+  float scl = 1.f, scr = 1.f;
+  if (P.norm == SD_NORM_JOINT) {
+    float s = SL + SR;
+    scl = scr = s > 0.f ? 1.f / s : 0.f;
+  } else if (P.norm == SD_NORM_SEPARATE) {
+    scl = SL > 0.f ? 1.f / SL : 0.f;
+    scr = SR > 0.f ? 1.f / SR : 0.f;
+  } else if (P.norm == SD_NORM_PER_RAY) {
+    scl = scr = total > 0 ? 1.f / (float)total : 0.f;
+  }
+  if (ctx.N) {
+    long long base = q.out_offset;
+    for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) {
+      float v = (MODE == 0) ? (float)patch[i] : patchf[i];
+      store_out<OutT>(P.out, base + i, v * (i < ks2 ? scl : scr));
+    }
+  }
+  if (P.stats && threadIdx.x < SD_N_STATS) {
+    long long v = threadIdx.x == SD_STAT_LAUNCHED ? (long long)total
+                                                   : (long long)s_stats[threadIdx.x];
+    P.stats[(long long)r * SD_N_STATS + threadIdx.x] = v;
+  }
+}
+
+// Per-ray records of one request (test path).
+__global__ void __launch_bounds__(256) trace_hits_kernel(TraceParams P, sd_psf_request q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ReqCtx ctx;
+  int* prefix = reinterpret_cast<int*>(smem);
+  int* lo = prefix + (P.max_n + 1);
+  setup_request(P, q, ctx, prefix, lo);
+  const SensorF S = P.sen;
+  const int ks = ctx.ks, p = (ks - 1) >> 1;
+  const int total = ctx.N ? ctx.total : 0;
+  if (threadIdx.x == 0) *P.n_rays = total;
+  for (int k = threadIdx.x; k < total && k < P.max_rays; k += blockDim.x) {
+    float x, y, z, dx, dy, dz;
+    make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
+    int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
+    float* o = P.rec + (long long)k * 8;
+    float side = 2.f, pix = -1.f;
+    if (st == ST_OK) {
+      float fx = (x - ctx.xc) * S.inv_ps + (float)p;
+      float fy = (y - ctx.yc) * S.inv_ps + (float)p;
+      float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+      side = (float)dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+      if (af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks) pix = bf * 65536.f + af;
+    } else {
+      x = y = dx = dy = dz = 0.f;
+    }
+    o[0] = x;
+    o[1] = y;
+    o[2] = dx;
+    o[3] = dy;
+    o[4] = dz;
+    o[5] = (float)st;
+    o[6] = side;
+    o[7] = pix;
+  }
+}
+
+size_t trace_smem_bytes(int max_n, int max_ks) {
+  return table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
+}
+
+sd_status fill_params(TraceParams& P, const sd_lens* const* lenses, int n_lenses,
+                      const sd_dp_sensor* sensor, const sd_trace_opts* opts) {
+  if (!lenses || n_lenses < 1 || n_lenses > SD_MAX_LENSES || !sensor) return SD_ERR_ARG;
+  int dev = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  for (int i = 0; i < n_lenses; ++i) {
+    if (!lenses[i] || lenses[i]->device != dev) return SD_ERR_ARG;
+    P.slots[i] = lenses[i]->slot;
+  }
+  P.n_lenses = n_lenses;
+  const sd_dp_sensor& s = *sensor;
+  if (!(s.pitch_mm > 0) || !(s.f_mm > s.h_mm) || s.h_mm < 0 || !(s.w_mm > 0) ||
+      s.r_mm < 0)
+    return SD_ERR_ARG;
+  P.sen.ps = (float)s.pitch_mm;
+  P.sen.inv_ps = (float)(1.0 / s.pitch_mm);
+  P.sen.h = (float)s.h_mm;
+  P.sen.w = (float)s.w_mm;
+  P.sen.r2 = (float)(s.r_mm * s.r_mm);
+  P.sen.fh = (float)((s.f_mm - s.h_mm) / s.f_mm);
+  P.norm = opts ? opts->norm : SD_NORM_JOINT;
+  if (P.norm < 0 || P.norm > 3) return SD_ERR_ARG;
+  P.newton_max = (opts && opts->newton_iters > 0) ? opts->newton_iters : 12;
+  return SD_OK;
+}
+
+}  // namespace sd
+
+extern "C" {
+
+sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
+                          const sd_dp_sensor* sensor, const sd_psf_request* req,
+                          int n_req, const sd_trace_opts* opts, void* out,
+                          int64_t* stats, void* stream) {
+  using namespace sd;
+  if (!opts || !out || (n_req > 0 && !req) || n_req < 0) return SD_ERR_ARG;
+  if (n_req == 0) return SD_OK;
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  sd_status st = fill_params(P, lenses, n_lenses, sensor, opts);
+  if (st != SD_OK) return st;
+  if (opts->mode != SD_BIN_HARD && opts->mode != SD_BIN_BILINEAR) return SD_ERR_ARG;
+  if (opts->out_dtype < SD_F32 || opts->out_dtype > SD_F16) return SD_ERR_ARG;
+  int max_ks = opts->max_ks;
+  int max_n = opts->max_n_grid > 0 ? opts->max_n_grid : 512;
+  if (max_ks < 1 || !(max_ks & 1)) return SD_ERR_ARG;
+  if (max_ks > 127 || max_n > 2048 || max_n < 2) return SD_ERR_UNSUPPORTED;
+  P.req = req;
+  P.n_req = n_req;
+  P.max_n = max_n;
+  P.max_ks = max_ks;
+  P.out = out;
+  P.stats = reinterpret_cast<long long*>(stats);
+  size_t smem = trace_smem_bytes(max_n, max_ks);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int threads = 256;
+#define SD_LAUNCH(MODE, T)                                                          \
+  do {                                                                              \
+    auto kfn = trace_bin_kernel<MODE, T>;                                           \
+    SD_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)smem));                                   \
+    kfn<<<n_req, threads, smem, s>>>(P);                                            \
+  } while (0)
+  if (opts->mode == SD_BIN_HARD) {
+    if (opts->out_dtype == SD_F32) SD_LAUNCH(0, float);
+    else if (opts->out_dtype == SD_BF16) SD_LAUNCH(0, __nv_bfloat16);
+    else SD_LAUNCH(0, __half);
+  } else {
+    if (opts->out_dtype == SD_F32) SD_LAUNCH(1, float);
+    else if (opts->out_dtype == SD_BF16) SD_LAUNCH(1, __nv_bfloat16);
+    else SD_LAUNCH(1, __half);
+  }
+#undef SD_LAUNCH
+  return launch_status();
+}
+
+sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
+                           const sd_psf_request* req_host, const sd_trace_opts* opts,
+                           float* rec, int max_rays, int32_t* n_rays, void* stream) {
+  using namespace sd;
+  if (!lens || !req_host || !rec || !n_rays || max_rays < 0) return SD_ERR_ARG;
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  const sd_lens* ls[1] = {lens};
+  sd_status st = fill_params(P, ls, 1, sensor, opts);
+  if (st != SD_OK) return st;
+  if (req_host->n_grid < 2 || req_host->n_grid > 2048) return SD_ERR_ARG;
+  if (req_host->ks < 1 || !(req_host->ks & 1)) return SD_ERR_ARG;
+  P.max_n = req_host->n_grid;
+  P.max_ks = req_host->ks;
+  P.rec = rec;
+  P.max_rays = max_rays;
+  P.n_rays = n_rays;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  sd_psf_request q = *req_host;
+  q.lens = 0;  // the request is passed by value
+  size_t smem = table_bytes(P.max_n);
+  SD_CUDA_TRY(cudaFuncSetAttribute(trace_hits_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  trace_hits_kernel<<<1, 256, smem, s>>>(P, q);
+  return launch_status();
+}
+
+}  // extern "C"

@@ -1,0 +1,557 @@
+// Adjoint of the per-pixel DP render (supplement, "Local DP PSF convolution").
+//
+// Forward (bank mode): out_s(y,x) = sum_{u,v} Ipad(y+u, x+v) Kf_s(y,x)[u][v],
+// side s in {L, R}, Kf = the pixel's kernel flipped in both axes, and the
+// kernel a two-slice blend K = (1-t) B[key] + t B[key+1].  With G_s = dLoss/
+// dout_s the adjoints are
+//   dIpad(y+u, x+v) += sum_s G_s(y,x) Kf_s(y,x)[u][v]      (then the replicate
+//                      padding folds every padded position onto its clamped
+//                      source pixel),
+//   dB[key][s][ks-1-u][ks-1-v] += sum_{pixels using key} w(y,x) G_s(y,x)
+//                      Ipad(y+u, x+v)   with w = 1-t or t.
+// Three kernels:
+//   slice_bitmap_kernel     per (image, tile): which bank slices the tile uses
+//                           (a bitmap in the caller's workspace);
+//   render_bwd_img_kernel   per (tile, channel): the forward's work list of
+//                           (segment, slice) items; each lane scatters its
+//                           segment's weighted gradients through a register
+//                           window of 8 taps into a shared padded tile, which
+//                           is then folded into grad_aif with global atomics
+//                           (FP32 addition order varies: not bitwise
+//                           reproducible);
+//   render_bwd_bank_kernel  per (slice, wavelength): visits, in a fixed order,
+//                           the tiles whose bitmap holds the slice; threads own
+//                           8-tap strips of the kernel and accumulate over the
+//                           tile's segments in a fixed order: deterministic.
+
+#include "render_common.cuh"
+
+namespace sd {
+
+constexpr int TXB = 64;            // tile width of the bitmap / bank-gradient pass
+constexpr int NT_BM = 256;         // threads of the bitmap kernel (= TXB*RT_Y/SEG)
+
+inline size_t bitmap_words(int F, int Z) { return ((size_t)F * Z + 31) / 32; }
+
+inline void bwd_tiles(int H, int W, int* tx, int* ty) {
+  *tx = (W + TXB - 1) / TXB;
+  *ty = (H + RT_Y - 1) / RT_Y;
+}
+
+// ---------------------------------------------------------------------------
+// 1. slice bitmap per (image, tile)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT_BM) slice_bitmap_kernel(const RenderParams P,
+                                                             unsigned* __restrict__ bm,
+                                                             int words) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned* sb = reinterpret_cast<unsigned*>(smem);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < words; i += NT_BM) sb[i] = 0u;
+  __syncthreads();
+  const int n = blockIdx.z, tx0 = blockIdx.x * TXB, ty0 = blockIdx.y * RT_Y;
+  const int col = tid % TXB, rb = tid / TXB;
+  const bool two = P.Z > 1;
+  for (int j = 0; j < SEG; ++j) {
+    int yy = ty0 + rb * SEG + j, xx = tx0 + col;
+    if (yy >= P.H || xx >= P.W) continue;
+    int key;
+    float t;
+    select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &key, &t);
+    if (!two || t < 1.f) atomicOr(&sb[key >> 5], 1u << (key & 31));
+    if (two && t > 0.f) atomicOr(&sb[(key + 1) >> 5], 1u << ((key + 1) & 31));
+  }
+  __syncthreads();
+  size_t tile = ((size_t)n * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  for (int i = tid; i < words; i += NT_BM) bm[tile * words + i] = sb[i];
+}
+
+// ---------------------------------------------------------------------------
+// 2. image gradient
+// ---------------------------------------------------------------------------
+template <int TX, int VB>
+struct BwdImgSmem {
+  static constexpr int NT = 4 * TX, NW = NT / 32, NPX = TX * RT_Y, MW = NT / 32;
+  __host__ __device__ static int ku(int ks) { return (ks + SEG - 1) / SEG * SEG; }
+  __host__ __device__ static size_t kbuf_words(int ks) { return (size_t)2 * (2 * ku(ks) * VB); }
+  __host__ __device__ static size_t pad_words(int ks) {
+    return (size_t)(TX + ks - 1) * (RT_Y + ks - 1 + SEG);
+  }
+  static size_t bytes(int ks) {
+    size_t w = pad_words(ks) + NW * kbuf_words(ks) + 3 * (size_t)NPX  // dIpad, K, gL/gR, t
+               + (size_t)RK * MW + (RK + 1) + MAX_CHUNKS + NPX / 2;
+    return 4 * w;
+  }
+};
+
+template <int TX, int VB, int KSMAX>
+__global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderParams P,
+                                                                   const float* __restrict__ gout,
+                                                                   float* __restrict__ gaif) {
+  using SM = BwdImgSmem<TX, VB>;
+  constexpr int NT = SM::NT, NW = SM::NW, NPX = SM::NPX, MW = SM::MW;
+  constexpr int NR = (2 * ((KSMAX + SEG - 1) / SEG * SEG) * VB + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
+  const int S = P.halo_w;
+  float* dpad = reinterpret_cast<float*>(smem);
+  float* kbuf = dpad + SM::pad_words(ks);
+  float* gL = kbuf + NW * SM::kbuf_words(ks);
+  float* gR = gL + NPX;
+  float* pt = gR + NPX;
+  unsigned* mask = reinterpret_cast<unsigned*>(pt + NPX);
+  int* kpre = reinterpret_cast<int*>(mask + RK * MW);
+  int* chunks = kpre + RK + 1;
+  unsigned short* prel = reinterpret_cast<unsigned short*>(chunks + MAX_CHUNKS);
+  __shared__ int s_kmin, s_kmax, s_nchunks, s_next;
+
+  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * RT_Y;
+  const int n = blockIdx.z / P.C, c = blockIdx.z - n * P.C;
+  const int lam = (P.NL == P.C) ? c : 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int H = P.H, W = P.W;
+  const bool two = (P.Z > 1);
+
+  const int seg_col = tid % TX, seg_rb = tid / TX;
+  int kmin_t = 0x7fffffff, kmax_t = -1;
+  int key_j[SEG];
+  float t_j[SEG];
+  const float* goL = gout + (((size_t)n * 2 * P.C + c) * H) * W;
+  const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * H) * W;
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    int yy = ty0 + seg_rb * SEG + j, xx = tx0 + seg_col;
+    int pix = (seg_rb * SEG + j) * TX + seg_col;
+    key_j[j] = -1;
+    t_j[j] = 0.f;
+    float a = 0.f, b = 0.f;
+    if (yy < H && xx < W) {
+      float d = P.depth[((size_t)n * H + yy) * W + xx];
+      select_slice(P, yy, xx, d, &key_j[j], &t_j[j]);
+      kmin_t = min(kmin_t, key_j[j]);
+      kmax_t = max(kmax_t, key_j[j] + (two ? 1 : 0));
+      a = goL[(size_t)yy * W + xx];
+      b = goR[(size_t)yy * W + xx];
+    }
+    pt[pix] = t_j[j];
+    gL[pix] = a;
+    gR[pix] = b;
+  }
+  if (tid == 0) {
+    s_kmin = 0x7fffffff;
+    s_kmax = -1;
+  }
+  for (int i = tid; i < (int)SM::pad_words(ks); i += NT) dpad[i] = 0.f;
+  __syncthreads();
+  atomicMin(&s_kmin, kmin_t);
+  atomicMax(&s_kmax, kmax_t);
+  __syncthreads();
+  const int kmin = s_kmin, kmax = s_kmax;
+#pragma unroll
+  for (int j = 0; j < SEG; ++j)
+    prel[(seg_rb * SEG + j) * TX + seg_col] =
+        (unsigned short)(key_j[j] >= 0 ? key_j[j] - kmin : 0xffff);
+
+  float* kb = kbuf + warp * SM::kbuf_words(ks);
+  const int nblk = (ks + VB - 1) / VB;
+  const int KU = SM::ku(ks);
+  const int kb_elems = 2 * KU * VB;
+
+  for (int wbase = kmin; wbase <= kmax; wbase += RK) {
+    for (int i = tid; i < RK * MW; i += NT) mask[i] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      int k0 = key_j[j];
+      if (k0 < 0) continue;
+      float t = t_j[j];
+      if ((!two || t < 1.f) && k0 >= wbase && k0 < wbase + RK)
+        atomicOr(&mask[(k0 - wbase) * MW + warp], 1u << lane);
+      if (two && t > 0.f && k0 + 1 >= wbase && k0 + 1 < wbase + RK)
+        atomicOr(&mask[(k0 + 1 - wbase) * MW + warp], 1u << lane);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int carry = 0;
+      for (int k0 = 0; k0 < RK; k0 += 32) {
+        int k = k0 + lane;
+        int cnt = 0;
+        for (int w = 0; w < MW; ++w) cnt += __popc(mask[k * MW + w]);
+        int nch = (cnt + 31) >> 5;
+        int v = nch;
+        for (int o = 1; o < 32; o <<= 1) {
+          int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        kpre[k] = carry + v - nch;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+      }
+      if (lane == 0) {
+        kpre[RK] = carry;
+        s_nchunks = carry;
+      }
+    }
+    __syncthreads();
+    const int nchunks = s_nchunks;
+    for (int k = tid; k < RK; k += NT)
+      for (int q = kpre[k]; q < kpre[k + 1]; ++q) chunks[q] = (k << 8) | (q - kpre[k]);
+    if (tid == 0) s_next = NW;
+    __syncthreads();
+
+    for (int ch = warp; ch < nchunks;) {
+      const int rel = chunks[ch] >> 8, sub = chunks[ch] & 0xff;
+      const int key = wbase + rel;
+      int want = sub * 32 + lane, seg = -1;
+      for (int w = 0; w < MW; ++w) {
+        unsigned m = mask[rel * MW + w];
+        int pc = __popc(m);
+        if (seg < 0 && want >= 0 && want < pc) {
+          for (int q = 0; q < want; ++q) m &= m - 1;
+          seg = w * 32 + __ffs(m) - 1;
+        }
+        want -= pc;
+      }
+      const bool act = seg >= 0;
+      const int sg = act ? seg : 0;
+      const int col = sg % TX, rb = sg / TX;
+      // weighted gradients of the segment's pixels for this slice
+      float GL[SEG], GR[SEG];
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        int pix = (rb * SEG + j) * TX + col;
+        unsigned short r16 = prel[pix];
+        float w = 0.f;
+        if (act && r16 != 0xffff) {
+          int k0 = kmin + (int)r16;
+          float t = pt[pix];
+          w = (k0 == key) ? (two ? 1.f - t : 1.f) : ((two && k0 + 1 == key) ? t : 0.f);
+        }
+        GL[j] = w * gL[pix];
+        GR[j] = w * gR[pix];
+      }
+      const int f = key / P.Z, z = key - f * P.Z;
+      const float* KL = reinterpret_cast<const float*>(P.bank) +
+                        (((size_t)f * P.Z + z) * P.NL + lam) * 2 * ks2;
+      const float* KR = KL + ks2;
+      float pre[NR];
+      auto fetch = [&](int b) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          int e = lane + 32 * r;
+          float v = 0.f;
+          if (e < kb_elems) {
+            int side = e & 1, uv = e >> 1, u = uv / VB, vv = uv - u * VB;
+            int v_ = b * VB + vv;
+            if (v_ < ks && u < ks) v = __ldg((side ? KR : KL) + (ks - 1 - u) * ks + (ks - 1 - v_));
+          }
+          pre[r] = v;
+        }
+      };
+      auto commit = [&](float* dst) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          int e = lane + 32 * r;
+          if (e < kb_elems) dst[e] = pre[r];
+        }
+      };
+      fetch(0);
+      commit(kb);
+      __syncwarp();
+      float* base = dpad + (rb * SEG) * S + col;
+      for (int b = 0; b < nblk; ++b) {
+        const float* kcur = kb + (b & 1) * kb_elems;
+        if (b + 1 < nblk) fetch(b + 1);
+        const int vmax = min(VB, ks - b * VB);
+        for (int vv = 0; vv < vmax; ++vv) {
+          float* colp = base + b * VB + vv;
+          const float2* kp = reinterpret_cast<const float2*>(kcur) + vv;
+          // ring of the taps u = r-7 .. r of column v (zero outside [0, ks))
+          float kl[SEG], kr[SEG];
+#pragma unroll
+          for (int j = 0; j < SEG; ++j) kl[j] = kr[j] = 0.f;
+          for (int r0 = 0; r0 < KU + SEG; r0 += SEG) {
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) {
+              const int r = r0 + q;
+              float2 w2 = r < KU ? kp[r * VB] : make_float2(0.f, 0.f);
+              kl[q] = w2.x;
+              kr[q] = w2.y;
+              // contribution to padded row rb*SEG + r: sum_j G_j Kf[r-j]
+              float acc = 0.f;
+#pragma unroll
+              for (int j = 0; j < SEG; ++j) {
+                acc = fmaf(GL[j], kl[(q - j + SEG) % SEG], acc);
+                acc = fmaf(GR[j], kr[(q - j + SEG) % SEG], acc);
+              }
+              if (r < ks + SEG - 1 && acc != 0.f) atomicAdd(colp + r * S, acc);
+            }
+          }
+        }
+        if (b + 1 < nblk) commit(kb + ((b + 1) & 1) * kb_elems);
+        __syncwarp();
+      }
+      int nxt = 0;
+      if (lane == 0) nxt = atomicAdd(&s_next, 1);
+      ch = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    __syncthreads();
+  }
+  // fold the padded tile onto the image (replicate padding adjoint)
+  float* ga = gaif + ((size_t)n * P.C + c) * H * W;
+  for (int i = tid; i < P.halo_h * S; i += NT) {
+    float v = dpad[i];
+    if (v == 0.f) continue;
+    int r = i / S, cc = i - r * S;
+    int yy = min(max(ty0 + r - p, 0), H - 1);
+    int xx = min(max(tx0 + cc - p, 0), W - 1);
+    atomicAdd(&ga[(size_t)yy * W + xx], v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. bank gradient, one block per (slice key, wavelength)
+// ---------------------------------------------------------------------------
+template <int NT, int SPT>
+__global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams P,
+                                                             const float* __restrict__ gout,
+                                                             const unsigned* __restrict__ bm,
+                                                             int words, int ntx, int nty,
+                                                             float* __restrict__ gbank) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
+  const int KU = (ks + SEG - 1) / SEG * SEG;
+  const int S = TXB + ks - 1;
+  const int HH = RT_Y + ks - 1 + SEG;
+  constexpr int NPX = TXB * RT_Y, NSEG = NPX / SEG;
+  float* halo = reinterpret_cast<float*>(smem);          // HH x S
+  float2* G = reinterpret_cast<float2*>(halo + (size_t)HH * S);  // NPX (L, R)
+  int* segs = reinterpret_cast<int*>(G + NPX);            // NSEG
+  __shared__ int s_nseg, s_wcnt[NSEG / 32];
+
+  const int key = blockIdx.x, lam = blockIdx.y;
+  const int tid = threadIdx.x;
+  const bool two = P.Z > 1;
+  const int nstrip = ks * (KU / SEG);
+  float acc[SPT][2 * SEG];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s)
+#pragma unroll
+    for (int i = 0; i < 2 * SEG; ++i) acc[s][i] = 0.f;
+
+  const int kw = key >> 5;
+  const unsigned kbit = 1u << (key & 31);
+  const int c_lo = (P.NL == P.C) ? lam : 0, c_hi = (P.NL == P.C) ? lam + 1 : P.C;
+  for (int n = 0; n < P.N; ++n)
+    for (int ty = 0; ty < nty; ++ty)
+      for (int tx = 0; tx < ntx; ++tx) {
+        size_t tile = ((size_t)n * nty + ty) * ntx + tx;
+        if (!(bm[tile * words + kw] & kbit)) continue;
+        const int tx0 = tx * TXB, ty0 = ty * RT_Y;
+        for (int c = c_lo; c < c_hi; ++c) {
+          __syncthreads();
+          const float* img = reinterpret_cast<const float*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
+          for (int i = tid; i < HH * S; i += NT) {
+            int r = i / S, cc = i - r * S;
+            int yy = min(max(ty0 + r - p, 0), P.H - 1);
+            int xx = min(max(tx0 + cc - p, 0), P.W - 1);
+            halo[i] = img[(size_t)yy * P.W + xx];
+          }
+          const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
+          const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
+          // weighted gradients of this slice; the segments that use it, listed
+          // in ascending order (ballot within a warp, prefix over warps)
+          bool any = false;
+          if (tid < NSEG) {
+            int col = tid % TXB, rb = tid / TXB;
+            for (int j = 0; j < SEG; ++j) {
+              int yy = ty0 + rb * SEG + j, xx = tx0 + col;
+              float2 g = make_float2(0.f, 0.f);
+              if (yy < P.H && xx < P.W) {
+                int k0;
+                float t;
+                select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &k0, &t);
+                float w = (k0 == key) ? (two ? 1.f - t : 1.f)
+                                      : ((two && k0 + 1 == key) ? t : 0.f);
+                if (w != 0.f) {
+                  g.x = w * goL[(size_t)yy * P.W + xx];
+                  g.y = w * goR[(size_t)yy * P.W + xx];
+                  any = true;
+                }
+              }
+              G[(rb * SEG + j) * TXB + col] = g;
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, any);
+          const int rank = __popc(bal & ((1u << (tid & 31)) - 1));
+          if (tid < NSEG && (tid & 31) == 0) s_wcnt[tid >> 5] = __popc(bal);
+          __syncthreads();
+          if (tid == 0) {
+            int run = 0;
+            for (int w = 0; w < NSEG / 32; ++w) {
+              int cnt = s_wcnt[w];
+              s_wcnt[w] = run;
+              run += cnt;
+            }
+            s_nseg = run;
+          }
+          __syncthreads();
+          if (any) segs[s_wcnt[tid >> 5] + rank] = tid;
+          __syncthreads();
+          const int nseg = s_nseg;
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            int st = tid + s * NT;
+            if (st >= nstrip) continue;
+            int v = st % ks, u0 = (st / ks) * SEG;
+            for (int q = 0; q < nseg; ++q) {
+              int sgi = segs[q];
+              int col = sgi % TXB, rb = sgi / TXB;
+              const float* colp = halo + (rb * SEG + u0) * S + col + v;
+              float img[2 * SEG - 1];
+#pragma unroll
+              for (int i = 0; i < 2 * SEG - 1; ++i) img[i] = colp[i * S];
+#pragma unroll
+              for (int j = 0; j < SEG; ++j) {
+                float2 g = G[(rb * SEG + j) * TXB + col];
+#pragma unroll
+                for (int uu = 0; uu < SEG; ++uu) {
+                  acc[s][uu] = fmaf(g.x, img[j + uu], acc[s][uu]);
+                  acc[s][SEG + uu] = fmaf(g.y, img[j + uu], acc[s][SEG + uu]);
+                }
+              }
+            }
+          }
+        }
+      }
+  // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v]
+  float* out = gbank + ((size_t)key * P.NL + lam) * 2 * ks2;
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    int st = tid + s * NT;
+    if (st >= nstrip) continue;
+    int v = st % ks, u0 = (st / ks) * SEG;
+#pragma unroll
+    for (int uu = 0; uu < SEG; ++uu) {
+      int u = u0 + uu;
+      if (u >= ks) continue;
+      size_t o = (size_t)(ks - 1 - u) * ks + (ks - 1 - v);
+      out[o] = acc[s][uu];
+      out[ks2 + o] = acc[s][SEG + uu];
+    }
+  }
+}
+
+template <int NT, int SPT>
+sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsigned* bm, int words,
+                          int ntx, int nty, float* gbank, cudaStream_t s) {
+  const int ks = P.ks;
+  size_t smem = (size_t)(RT_Y + ks - 1 + SEG) * (TXB + ks - 1) * 4 + (size_t)TXB * RT_Y * 8 +
+                (size_t)(TXB * RT_Y / SEG) * 4;
+  auto k = render_bwd_bank_kernel<NT, SPT>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(P.F * P.Z, P.NL);
+  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, gbank);
+  return launch_status();
+}
+
+template <int TX, int VB, int KSMAX>
+sd_status launch_img_bwd(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
+  using SM = BwdImgSmem<TX, VB>;
+  P.halo_w = TX + P.ks - 1;
+  P.halo_h = RT_Y + P.ks - 1 + SEG;
+  size_t smem = SM::bytes(P.ks);
+  auto k = render_bwd_img_kernel<TX, VB, KSMAX>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((P.W + TX - 1) / TX, (P.H + RT_Y - 1) / RT_Y, P.N * P.C);
+  k<<<grid, SM::NT, smem, s>>>(P, gout, gaif);
+  return launch_status();
+}
+
+constexpr size_t SMEM_CAP_B = 227 * 1024;
+
+sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
+                    RenderParams& P) {
+  if (N < 0 || C < 1 || H < 0 || W < 0) return SD_ERR_ARG;
+  if ((long long)N * C > 65535 || (long long)H * W > (1ll << 31)) return SD_ERR_UNSUPPORTED;
+  std::memset(&P, 0, sizeof P);
+  sd_status st = check_layout(layout, P);
+  if (st != SD_OK) return st;
+  if (layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
+  if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
+  if ((long long)P.F * P.Z > 65000) return SD_ERR_UNSUPPORTED;
+  P.N = N;
+  P.C = C;
+  P.H = H;
+  P.W = W;
+  return SD_OK;
+}
+
+}  // namespace sd
+
+extern "C" {
+
+sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, int C,
+                                          int H, int W, size_t* bytes) {
+  using namespace sd;
+  if (!bytes) return SD_ERR_ARG;
+  RenderParams P;
+  sd_status st = setup_bwd(layout, N, C, H, W, P);
+  if (st != SD_OK) return st;
+  int tx, ty;
+  bwd_tiles(H, W, &tx, &ty);
+  *bytes = (size_t)N * tx * ty * bitmap_words(P.F, P.Z) * 4;
+  return SD_OK;
+}
+
+sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const float* depth_m,
+                                const float* bank, const sd_bank_layout* layout, int N, int C,
+                                int H, int W, float* grad_aif, float* grad_bank,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace sd;
+  if (!grad_out || !aif || !depth_m || !bank) return SD_ERR_ARG;
+  RenderParams P;
+  sd_status st = setup_bwd(layout, N, C, H, W, P);
+  if (st != SD_OK) return st;
+  P.aif = aif;
+  P.depth = depth_m;
+  P.bank = bank;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  size_t bank_elems = (size_t)P.F * P.Z * P.NL * 2 * P.ks * P.ks;
+  if (N == 0 || H == 0 || W == 0) {
+    if (grad_bank) SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
+    return SD_OK;
+  }
+  if (grad_aif) {
+    SD_CUDA_TRY(cudaMemsetAsync(grad_aif, 0, (size_t)N * C * H * W * 4, s));
+    sd_status r;
+    if (P.ks <= 65 && BwdImgSmem<128, 4>::bytes(P.ks) <= SMEM_CAP_B)
+      r = launch_img_bwd<128, 4, 65>(P, grad_out, grad_aif, s);
+    else if (BwdImgSmem<64, 4>::bytes(P.ks) <= SMEM_CAP_B)
+      r = launch_img_bwd<64, 4, 127>(P, grad_out, grad_aif, s);
+    else
+      r = launch_img_bwd<64, 2, 127>(P, grad_out, grad_aif, s);
+    if (r != SD_OK) return r;
+  }
+  if (grad_bank) {
+    int tx, ty;
+    bwd_tiles(H, W, &tx, &ty);
+    size_t words = bitmap_words(P.F, P.Z);
+    size_t need = (size_t)N * tx * ty * words * 4;
+    if (!workspace || workspace_bytes < need) return SD_ERR_ARG;
+    unsigned* bm = reinterpret_cast<unsigned*>(workspace);
+    dim3 g1(tx, ty, N);
+    slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
+    sd_status r = launch_status();
+    if (r != SD_OK) return r;
+    int KU = (P.ks + SEG - 1) / SEG * SEG;
+    int nstrip = P.ks * (KU / SEG);
+    if (nstrip <= 256 * 3)
+      r = launch_bank_bwd<256, 3>(P, grad_out, bm, (int)words, tx, ty, grad_bank, s);
+    else
+      r = launch_bank_bwd<512, 4>(P, grad_out, bm, (int)words, tx, ty, grad_bank, s);
+    if (r != SD_OK) return r;
+  }
+  return SD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Definitions shared by the render forward and backward kernels.
+#pragma once
+
+#include <cstring>
+
+#include "common.cuh"
+
+namespace sd {
+
+constexpr int SEG = 8;          // rows per segment (one lane's pixels)
+constexpr int RT_Y = 32;        // tile height (rows)
+constexpr int RK = 256;         // slice keys per window
+constexpr int MAX_CHUNKS = 512;   // >= NT*2*SEG/32 + RK for NT <= 512
+
+struct RenderParams {
+  const void* aif;
+  const float* depth;
+  const void* bank;
+  void* out;
+  int N, C, H, W;
+  int F, Z, NL, ks;
+  float pitch;
+  int halo_w;      // row stride of the staged tile (floats)
+  int halo_h;
+  float fh[SD_MAX_BANK_FIELDS];
+  float iq[SD_MAX_BANK_DEPTHS];  // 1.0f / depth_m[j] (strictly descending)
+};
+
+// Per-pixel bank selection in FP32 without contraction (the same sequence of
+// IEEE operations as the oracle's selection).
+__device__ __forceinline__ void select_slice(const RenderParams& P, int row, int col,
+                                             float depth, int* key, float* t) {
+  float X = __fmul_rn(__fsub_rn((float)col, 0.5f * (float)(P.W - 1)), P.pitch);
+  float Y = __fmul_rn(__fsub_rn((float)row, 0.5f * (float)(P.H - 1)), P.pitch);
+  float rho = __fsqrt_rn(__fadd_rn(__fmul_rn(X, X), __fmul_rn(Y, Y)));
+  int F = P.F, f;
+  if (rho <= P.fh[0]) {
+    f = 0;
+  } else if (rho >= P.fh[F - 1]) {
+    f = F - 1;
+  } else {
+    int a = 0, b = F - 1;  // fh[a] <= rho < fh[b]
+    while (b - a > 1) {
+      int m = (a + b) >> 1;
+      if (P.fh[m] <= rho) a = m; else b = m;
+    }
+    float dlo = __fsub_rn(rho, P.fh[a]);
+    float dhi = __fsub_rn(P.fh[a + 1], rho);
+    f = (dhi < dlo) ? a + 1 : a;
+  }
+  int Z = P.Z, z0;
+  float tt;
+  if (Z == 1) {
+    z0 = 0;
+    tt = 0.f;
+  } else {
+    float q = __fdiv_rn(1.0f, depth);
+    if (q >= P.iq[0]) {
+      z0 = 0;
+      tt = 0.f;
+    } else if (q <= P.iq[Z - 1]) {
+      z0 = Z - 2;
+      tt = 1.f;
+    } else {
+      int a = 0, b = Z - 1;  // iq[a] >= q > iq[b]
+      while (b - a > 1) {
+        int m = (a + b) >> 1;
+        if (P.iq[m] >= q) a = m; else b = m;
+      }
+      z0 = a;
+      tt = __fdiv_rn(__fsub_rn(P.iq[a], q), __fsub_rn(P.iq[a], P.iq[a + 1]));
+    }
+  }
+  *key = f * Z + z0;
+  *t = tt;
+}
+
+inline sd_status check_layout(const sd_bank_layout* L, RenderParams& P) {
+  if (!L || !L->field_h_mm || !L->depths_m) return SD_ERR_ARG;
+  if (L->n_field < 1 || L->n_field > SD_MAX_BANK_FIELDS || L->n_depth < 1 ||
+      L->n_depth > SD_MAX_BANK_DEPTHS || L->n_lambda < 1)
+    return SD_ERR_ARG;
+  if (L->ks < 1 || !(L->ks & 1)) return SD_ERR_ARG;
+  if (L->ks > 127) return SD_ERR_UNSUPPORTED;
+  if (!(L->pitch_mm > 0)) return SD_ERR_ARG;
+  for (int i = 0; i < L->n_field; ++i) {
+    P.fh[i] = L->field_h_mm[i];
+    if (i && !(P.fh[i] > P.fh[i - 1])) return SD_ERR_ARG;
+  }
+  for (int j = 0; j < L->n_depth; ++j) {
+    if (!(L->depths_m[j] > 0)) return SD_ERR_ARG;
+    P.iq[j] = 1.0f / L->depths_m[j];
+    if (j && !(L->depths_m[j] > L->depths_m[j - 1])) return SD_ERR_ARG;
+  }
+  P.F = L->n_field;
+  P.Z = L->n_depth;
+  P.NL = L->n_lambda;
+  P.ks = L->ks;
+  P.pitch = L->pitch_mm;
+  return SD_OK;
+}
+
+}  // namespace sd
