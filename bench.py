@@ -5,8 +5,9 @@ One step = trace + bin the full PSF bank of the f/1.8 doublet-pair lens
 (32 field heights x 32 depths x 3 wavelengths, 256 x 256 pupil grid, 65 x 65
 L/R patches, hard binning, joint sum normalisation, FP32), render a
 1024 x 1024 RGB all-in-focus image with a Perlin depth map through that bank
-(FP32), and back-propagate a fixed output gradient through the render to the
-image and the bank (FP32).  Inputs are synthetic (workloads module) and resident in HBM before
+(FP32), back-propagate a fixed output gradient through the render to the
+image and the bank (FP32), and through the trace to the lens parameters (the
+adjoint trace of the bank gradient, bilinear splat, FP32).  Inputs are synthetic (workloads module) and resident in HBM before
 timing; L2 is flushed (256 MiB write) before every timed step.
 
 Prints one JSON line (rank 0).  `value` = rays traced+binned per second over
@@ -185,6 +186,7 @@ def run_ours(args, world, rank, local, dist):
     gbank = torch.empty_like(bank)
     ws = torch.empty(max(1, sd.api.render_backward_workspace(layout, *aif.shape)),
                      dtype=torch.uint8, device=dev)
+    greq = torch.empty((n_req, 32, 8), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -204,14 +206,19 @@ def run_ours(args, world, rank, local, dist):
             sd.api._ptr(gbank), sd.api._ptr(ws), ws.numel(), sd.api._stream()),
             "sd_dp_render_backward")
 
+    def trace_bwd():
+        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank, max_ks=cfg["ks"],
+                                 max_n=cfg["n_grid"], norm=sd.SD_NORM_PER_RAY, grad_req=greq)
+
     for _ in range(args.warmup):
         trace()
         render()
         render_bwd()
+        trace_bwd()
     torch.cuda.synchronize()
     rays_per_step = int(stats[:, 0].sum().item())
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -226,6 +233,8 @@ def run_ours(args, world, rank, local, dist):
             ev[i][2].record(stream)
             render_bwd()
             ev[i][3].record(stream)
+            trace_bwd()
+            ev[i][4].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if dist:
@@ -233,7 +242,8 @@ def run_ours(args, world, rank, local, dist):
     t_trace = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     t_render = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
     t_bwd = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
-    step_ms = sum(ev[i][0].elapsed_time(ev[i][3]) for i in range(args.steps)) / args.steps
+    t_adj = [ev[i][3].elapsed_time(ev[i][4]) for i in range(args.steps)]
+    step_ms = sum(ev[i][0].elapsed_time(ev[i][4]) for i in range(args.steps)) / args.steps
     if dist:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -257,6 +267,7 @@ def run_ours(args, world, rank, local, dist):
         trace()
         render()
         render_bwd()
+        trace_bwd()
         h_out.copy_(out, non_blocking=True)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
@@ -273,6 +284,7 @@ def run_ours(args, world, rank, local, dist):
     tr_ms = statistics.mean(t_trace)
     rd_ms = statistics.mean(t_render)
     bw_ms = statistics.mean(t_bwd)
+    adj_ms = statistics.mean(t_adj)
     H, Wd = aif.shape[2:]
     render_flops = H * Wd * 3 * 2 * 2 * cfg["ks"] ** 2 * 2  # px, ch, L/R, 2 slices, FMA
     trace_tflops = rays_per_step * fpr / (tr_ms * 1e-3) / 1e12
@@ -293,6 +305,7 @@ def run_ours(args, world, rank, local, dist):
         "trace_ms": round(tr_ms, 4), "render_ms": round(rd_ms, 4),
         "render_bwd_ms": round(bw_ms, 4),
         "render_fwd_bwd_ms": round(rd_ms + bw_ms, 4),
+        "trace_adjoint_ms": round(adj_ms, 4),
         "trace_grays_s": round(rays_per_step / (tr_ms * 1e-3) / 1e9, 4),
         "render_mpix_s": round(H * Wd / (rd_ms * 1e-3) / 1e6, 2),
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3),
@@ -306,7 +319,8 @@ def run_ours(args, world, rank, local, dist):
         "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_ms, 4)},
-        "gpu_launches": 5 * args.steps,  # trace, render, bwd image, bitmap, bwd bank
+        # trace, render, bwd image, bitmap, bwd bank, adjoint trace, lens reduce
+        "gpu_launches": 7 * args.steps,
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
     }

@@ -188,6 +188,29 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
                           int64_t* stats, void* stream);
 
 /*
+ * Adjoint of sd_dp_psf_trace in bilinear mode (SD_BIN_BILINEAR) with a
+ * linear normalisation (SD_NORM_NONE or SD_NORM_PER_RAY), FP32.  Given
+ * grad_out = dLoss/dPSF in the forward's output layout (FP32, out_offset of
+ * each request), writes per-request gradients grad_req[r][32*8] with the
+ * parameter ids of sd_lens_set_param (surface*8 + {curvature, conic,
+ * a4..a12, thickness}; surfaces beyond the lens are zero) and, if grad_lens
+ * is not null, their sum per lens grad_lens[l][32*8] (requests summed in
+ * index order: deterministic).  Each ray is traced again (nothing is stored
+ * between the passes) and swept backward through the sensor propagation,
+ * Snell's law, the normal and the intersection (implicit-function
+ * derivative at the converged Newton root); ray generation and the discrete
+ * decisions (reached, side, splat pixel) are held fixed.  The paper trains
+ * no lens; this is the differentiable form of Sec. 3.1 / Eq. 3.
+ * grad_req and grad_lens are device memory owned by the caller.
+ */
+sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
+                                   const sd_dp_sensor* sensor,
+                                   const sd_psf_request* req, int n_req,
+                                   const sd_trace_opts* opts,
+                                   const float* grad_out, float* grad_req,
+                                   float* grad_lens, void* stream);
+
+/*
  * Per-ray record of one request (test and debugging aid): for the k-th
  * in-pupil ray in raster order (pupil row major), rec[k*8 ..] = x, y, dx, dy,
  * dz (landing point and unit direction, FP32), state (0 reached, 1 no

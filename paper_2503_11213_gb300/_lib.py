@@ -19,6 +19,7 @@ SD_F32, SD_BF16, SD_F16 = 0, 1, 2
 SD_N_STATS = 8
 SD_MAX_SURFACES = 32
 SD_MAX_LENSES = 16
+NPAR_SURF = 8                      # curvature, conic, a4..a12, thickness
 
 
 class SdSurface(ctypes.Structure):
@@ -62,7 +63,8 @@ assert REQUEST_DTYPE.itemsize == 48
 
 # every exported symbol of include/sdirt.h
 EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
-           "sd_dp_psf_trace", "sd_dp_trace_hits", "sd_dp_render", "sd_dp_render_backward",
+           "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_trace_hits",
+           "sd_dp_render", "sd_dp_render_backward",
            "sd_dp_render_backward_workspace", "sd_status_string", "sd_last_cuda_error",
            "sd_version")
 
@@ -102,6 +104,8 @@ def lib():
     L.sd_lens_set_param.argtypes = [vp, i32, dbl]
     L.sd_lens_free.argtypes = [vp]
     L.sd_dp_psf_trace.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts), vp, vp, vp]
+    L.sd_dp_psf_trace_backward.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
+                                           vp, vp, vp, vp]
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,

@@ -133,6 +133,27 @@ def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=
     return out, stats
 
 
+def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, max_ks,
+                          max_n=512, norm=L.SD_NORM_PER_RAY, grad_req=None, newton_iters=0):
+    """Adjoint of the bilinear trace: per-request and per-lens gradients of
+    <grad_out, PSF> with respect to the lens parameters, as
+    (grad_req (n_req, 32, 8), grad_lens (n_lenses, 32, 8))."""
+    lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
+    handles = (ctypes.c_void_p * len(lenses))(*[l.handle.value for l in lenses])
+    dev = req_dev.device
+    if grad_req is None:
+        grad_req = torch.empty((n_req, L.SD_MAX_SURFACES, L.NPAR_SURF), device=dev)
+    grad_lens = torch.empty((len(lenses), L.SD_MAX_SURFACES, L.NPAR_SURF), device=dev)
+    _need_cuda(req_dev, grad_out, grad_req)
+    opts = L.SdTraceOpts(L.SD_BIN_BILINEAR, norm, L.SD_F32, newton_iters, max_ks, max_n)
+    sen = sensor.c()
+    L.check(L.lib().sd_dp_psf_trace_backward(handles, len(lenses), ctypes.byref(sen),
+                                             _ptr(req_dev), n_req, ctypes.byref(opts),
+                                             _ptr(grad_out), _ptr(grad_req), _ptr(grad_lens),
+                                             _stream()), "sd_dp_psf_trace_backward")
+    return grad_req, grad_lens
+
+
 HIT_FIELDS = ("x", "y", "dx", "dy", "dz", "state", "side", "pixel")
 
 

@@ -466,6 +466,15 @@ __device__ void setup_request(const TraceParams& P, const sd_psf_request& q,
   __syncthreads();
 }
 
+// a*b + c*d with one rounding to about 1 ulp (Kahan: the rounding error of
+// c*d is recovered exactly by an FMA and added back)
+__device__ __forceinline__ float dot2(float a, float b, float c, float d) {
+  float w = c * d;
+  float e = fmaf(c, d, -w);
+  float f = fmaf(a, b, w);
+  return f + e;
+}
+
 // 1/sqrt(x) to about half an ulp: hardware estimate plus one Newton step
 // (unit vectors feed Snell's law, whose output direction error is
 // multiplied by the remaining path length to the sensor).
@@ -477,9 +486,17 @@ __device__ __forceinline__ float rsqrt_refined(float x) {
 // Sequential trace (FP32) of one ray in surface-0-vertex-local coordinates.
 // On success (x, y) is the sensor landing point and (dx, dy, dz) the unit
 // direction.  Positions are kept relative to the current surface vertex.
-__device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta,
-                                         const float* __restrict__ omeg2, int newton_max, float& x, float& y, float& z,
-                                         float& dx, float& dy, float& dz) {
+// Per-surface forward state kept for the adjoint: hit point (vertex-local),
+// direction arriving at the surface and the intersection parameter.
+struct SurfSave {
+  float px, py, pz, dx, dy, dz, t;
+};
+
+template <bool SAVE>
+__device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ eta,
+                                           const float* __restrict__ omeg2, int newton_max,
+                                           float& x, float& y, float& z,
+                                           float& dx, float& dy, float& dz, SurfSave* sv) {
   const DevLens& L = c_lens[slot];
   const int n = L.n;
   for (int s = 0; s < n; ++s) {
@@ -522,9 +539,20 @@ __device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta
       }
       if (it == newton_max) return ST_NEWTON;
     }
+    if (SAVE) {
+      sv[s].dx = dx;
+      sv[s].dy = dy;
+      sv[s].dz = dz;
+      sv[s].t = t;
+    }
     x = fmaf(t, dx, x);
     y = fmaf(t, dy, y);
     z = fmaf(t, dz, z);
+    if (SAVE) {
+      sv[s].px = x;
+      sv[s].py = y;
+      sv[s].pz = z;
+    }
     float rho2 = x * x + y * y;
     if (rho2 > S.sd2) return ST_CLIP;
     if (S.type == SD_SURF_REFRACT) {
@@ -555,9 +583,9 @@ __device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta
       float k2 = 1.f - e * e * (1.f - cosi * cosi);
       if (k2 < 0.f) return ST_TIR;
       float g = __fdiv_rn(omeg2[s], sqrtf(k2) + e * cosi);
-      dx = fmaf(e, dx, g * nx);
-      dy = fmaf(e, dy, g * ny);
-      dz = fmaf(e, dz, g * nz);
+      dx = dot2(e, dx, g, nx);
+      dy = dot2(e, dy, g, ny);
+      dz = dot2(e, dz, g, nz);
     }
     z -= S.t;  // vertex-local coordinate of the next surface (or the sensor)
   }
@@ -566,6 +594,13 @@ __device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta
   x = fmaf(t, dx, x);
   y = fmaf(t, dy, y);
   return ST_OK;
+}
+
+__device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta,
+                                         const float* __restrict__ omeg2, int newton_max,
+                                         float& x, float& y, float& z,
+                                         float& dx, float& dy, float& dz) {
+  return trace_ray_t<false>(slot, eta, omeg2, newton_max, x, y, z, dx, dy, dz, nullptr);
 }
 
 // Eq. (1)/(2): s = offset on the sub-pixel plane relative to the pixel centre;
@@ -897,3 +932,281 @@ sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
 }
 
 }  // extern "C"
+
+namespace sd {
+
+// ---------------------------------------------------------------------------
+// Adjoint trace (reverse mode by hand), bilinear splat, frozen decisions.
+//
+// Per ray the loss is  L = scale * sum_taps G[side][tap] w_tap(fx, fy)  with
+// the bilinear weights of the landing point (Eq. 3 with unit energy split
+// over the four nearest pixel centres) and scale = 1 (SD_NORM_NONE) or
+// 1 / launched rays (SD_NORM_PER_RAY).  The ray is traced forward again
+// (recompute instead of storing rays between passes), then swept backward:
+// sensor propagation, and per surface Snell's law, the unit normal, the
+// implicit-function derivative of the intersection (the Newton iteration is
+// not unrolled: dt = -(grad Phi . dP) / (grad Phi . d) at convergence with
+// Phi = z - sag(x^2 + y^2)), and the transfer by the thickness.  Ray
+// generation is frozen; discrete decisions (reached, side, splat base pixel)
+// are those of the forward pass.  Parameters per surface: curvature, conic,
+// a4..a12, thickness after the surface (the last one is the sensor
+// distance).
+// ---------------------------------------------------------------------------
+constexpr int NPAR_SURF = 8;
+
+__device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ eta,
+                                            const float* __restrict__ omeg2,
+                                            const SurfSave* sv, float dfx, float dfy, float dfz,
+                                            float xb, float yb, float (*gacc)[NPAR_SURF]) {
+  const DevLens& L = c_lens[slot];
+  const int n = L.n;
+  // sensor: x_s = X + tau dx, tau = -Z / dz with (X, Y, Z) the last hit
+  // moved to sensor-local z
+  float Z = sv[n - 1].pz - L.s[n - 1].t;
+  float tau = -Z / dfz;
+  float taub = xb * dfx + yb * dfy;
+  float Pbx = xb, Pby = yb, Pbz = -taub / dfz;
+  float dbx = xb * tau, dby = yb * tau, dbz = taub * Z / (dfz * dfz);
+  gacc[n - 1][7] += -Pbz;
+  for (int s = n - 1; s >= 0; --s) {
+    const DevSurf& S = L.s[s];
+    const float Px = sv[s].px, Py = sv[s].py;
+    const float ix = sv[s].dx, iy = sv[s].dy, iz = sv[s].dz, t = sv[s].t;
+    float ibx, iby, ibz;  // adjoint of the incoming direction
+    float gx = 0.f, gy = 0.f, gz = 1.f;  // grad Phi at the hit
+    if (S.type == SD_SURF_REFRACT) {
+      const float c = S.c, kk = 1.f + S.k;
+      const float u = Px * Px + Py * Py;
+      const float q = sqrtf(fmaxf(1.f - kk * c * c * u, 1e-30f));
+      const float iq = 1.f / q, iq3 = iq * iq * iq;
+      // S1 = dsag/du = c / (2q) + sum_j (j+2) a_j u^(j+1)
+      float up = 1.f, S1 = 0.5f * c * iq, dS1 = 0.25f * kk * c * c * c * iq3;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        dS1 += (float)((j + 2) * (j + 1)) * S.a[j] * up;  // u^j
+        up *= u;
+        S1 += (float)(j + 2) * S.a[j] * up;               // u^(j+1)
+      }
+      gx = -2.f * Px * S1;
+      gy = -2.f * Py * S1;
+      gz = 1.f;
+      const float mn = sqrtf(gx * gx + gy * gy + 1.f), imn = 1.f / mn;
+      const float nx = gx * imn, ny = gy * imn, nz = imn;
+      // Snell: dout = e din + g n, g = (1 - e^2) / (ct + e cosi)
+      const float e = eta[s];
+      const float cosi = nx * ix + ny * iy + nz * iz;
+      const float k2 = 1.f - e * e * (1.f - cosi * cosi);
+      const float ct = sqrtf(fmaxf(k2, 0.f));
+      const float D = ct + e * cosi;
+      const float g = omeg2[s] / D;
+      ibx = e * dbx;
+      iby = e * dby;
+      ibz = e * dbz;
+      const float gb = dbx * nx + dby * ny + dbz * nz;
+      float nbx = g * dbx, nby = g * dby, nbz = g * dbz;
+      const float Db = -gb * g / D;
+      const float k2b = Db / (2.f * fmaxf(ct, 1e-30f));
+      const float cosib = Db * e + k2b * 2.f * e * e * cosi;
+      nbx += cosib * ix;
+      nby += cosib * iy;
+      nbz += cosib * iz;
+      ibx += cosib * nx;
+      iby += cosib * ny;
+      ibz += cosib * nz;
+      // n = m / |m|,  m = (-2 Px S1, -2 Py S1, 1)
+      const float nd = nx * nbx + ny * nby + nz * nbz;
+      const float mbx = (nbx - nx * nd) * imn, mby = (nby - ny * nd) * imn;
+      const float S1b = -2.f * Px * mbx - 2.f * Py * mby;
+      Pbx += -2.f * S1 * mbx;
+      Pby += -2.f * S1 * mby;
+      const float ub = S1b * dS1;
+      Pbx += 2.f * Px * ub;
+      Pby += 2.f * Py * ub;
+      gacc[s][0] += S1b * (0.5f * iq + 0.5f * kk * c * c * u * iq3);
+      gacc[s][1] += S1b * (0.25f * c * c * c * u * iq3);
+      up = u;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        gacc[s][2 + j] += S1b * (float)(j + 2) * up;  // u^(j+1)
+        up *= u;
+      }
+    } else {
+      ibx = dbx;
+      iby = dby;
+      ibz = dbz;
+    }
+    // hit P = o + t din
+    float obx = Pbx, oby = Pby, obz = Pbz;
+    ibx += t * Pbx;
+    iby += t * Pby;
+    ibz += t * Pbz;
+    const float tb = Pbx * ix + Pby * iy + Pbz * iz;
+    // implicit intersection Phi(o + t din; theta) = 0
+    const float lam = -tb / (gx * ix + gy * iy + gz * iz);
+    obx += lam * gx;
+    oby += lam * gy;
+    obz += lam * gz;
+    ibx += lam * t * gx;
+    iby += lam * t * gy;
+    ibz += lam * t * gz;
+    if (S.type == SD_SURF_REFRACT) {
+      const float c = S.c, kk = 1.f + S.k;
+      const float u = Px * Px + Py * Py;
+      const float q = sqrtf(fmaxf(1.f - kk * c * c * u, 1e-30f));
+      const float Sc = c * u / (1.f + q);  // conic part of the sag
+      // Phi = z - sag:  dPhi/dc = -(u + (1+k) Sc^2) / (2q), dPhi/dk = -c Sc^2 / (2q),
+      // dPhi/da_j = -u^(j+2)
+      gacc[s][0] += lam * (-(u + kk * Sc * Sc) / (2.f * q));
+      gacc[s][1] += lam * (-c * Sc * Sc / (2.f * q));
+      float up = u * u;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        gacc[s][2 + j] += lam * (-up);
+        up *= u;
+      }
+    }
+    // transfer: o_s = (P_{s-1}.x, P_{s-1}.y, P_{s-1}.z - T_{s-1})
+    if (s > 0) {
+      Pbx = obx;
+      Pby = oby;
+      Pbz = obz;
+      gacc[s - 1][7] += -obz;
+      dbx = ibx;
+      dby = iby;
+      dbz = ibz;
+    }
+  }
+}
+
+// One block per request; per-request gradient partials gout[r][32*8] (fixed
+// order block reduction).
+template <int NT>
+__global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
+                                                       float* __restrict__ greq) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ReqCtx ctx;
+  __shared__ float s_red[NT / 32][NPAR_SURF];
+  int* prefix = reinterpret_cast<int*>(smem);
+  int* lo = prefix + (P.max_n + 1);
+  float* Gs = reinterpret_cast<float*>(smem + table_bytes(P.max_n));
+  const int r = blockIdx.x;
+  const sd_psf_request q = P.req[r];
+  setup_request(P, q, ctx, prefix, lo);
+  const int ks = ctx.ks, ks2 = ks * ks, pp = (ks - 1) >> 1;
+  for (int i = threadIdx.x; i < 2 * ks2; i += NT) Gs[i] = G[q.out_offset + i];
+  __syncthreads();
+  const SensorF S = P.sen;
+  const int total = ctx.N ? ctx.total : 0;
+  const float scale = (P.norm == SD_NORM_PER_RAY) ? (total > 0 ? 1.f / (float)total : 0.f) : 1.f;
+  const int n = ctx.N ? c_lens[ctx.slot].n : 0;
+  float gacc[SD_MAX_SURFACES][NPAR_SURF];
+  for (int s = 0; s < n; ++s)
+    for (int j = 0; j < NPAR_SURF; ++j) gacc[s][j] = 0.f;
+  SurfSave sv[SD_MAX_SURFACES];
+  for (int k = threadIdx.x; k < total; k += NT) {
+    float x, y, z, dx, dy, dz;
+    make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
+    int st = trace_ray_t<true>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz, sv);
+    if (st != ST_OK) continue;
+    float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
+    float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
+    float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+    int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+    if (side == 2) continue;
+    float a0f = floorf(fx), b0f = floorf(fy);
+    float wx = fx - a0f, wy = fy - b0f;
+    int a0 = (int)a0f, b0 = (int)b0f;
+    const float* Gp = Gs + side * ks2;
+    float gfx = 0.f, gfy = 0.f;
+#pragma unroll
+    for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+      for (int jx = 0; jx < 2; ++jx) {
+        int aa = a0 + jx, bb = b0 + jy;
+        if (aa < 0 || aa >= ks || bb < 0 || bb >= ks) continue;
+        float gv = Gp[bb * ks + aa];
+        gfx += gv * (jx ? 1.f : -1.f) * (jy ? wy : 1.f - wy);
+        gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
+      }
+    if (gfx == 0.f && gfy == 0.f) continue;
+    adjoint_ray(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
+                scale * S.inv_ps * gfy, gacc);
+  }
+  // fixed-order block reduction, one surface at a time
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int s = 0; s < SD_MAX_SURFACES; ++s) {
+    float v[NPAR_SURF];
+#pragma unroll
+    for (int j = 0; j < NPAR_SURF; ++j) {
+      v[j] = s < n ? gacc[s][j] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < NPAR_SURF; ++j) s_red[warp][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x < NPAR_SURF) {
+      float a = 0.f;
+      for (int w = 0; w < NT / 32; ++w) a += s_red[w][threadIdx.x];
+      greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + s * NPAR_SURF + threadIdx.x] = a;
+    }
+    __syncthreads();
+  }
+}
+
+// Sums the per-request partials of each lens in request order.
+__global__ void grad_lens_reduce(const float* __restrict__ greq, const sd_psf_request* req,
+                                 int n_req, int n_lenses, float* __restrict__ glens) {
+  const int li = blockIdx.x, pidx = threadIdx.x;  // pidx < 32 * 8
+  float a = 0.f;
+  for (int r = 0; r < n_req; ++r)
+    if (req[r].lens == li) a += greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + pidx];
+  glens[(size_t)li * SD_MAX_SURFACES * NPAR_SURF + pidx] = a;
+}
+
+}  // namespace sd
+
+extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
+                                              const sd_dp_sensor* sensor,
+                                              const sd_psf_request* req, int n_req,
+                                              const sd_trace_opts* opts, const float* grad_out,
+                                              float* grad_req, float* grad_lens, void* stream) {
+  using namespace sd;
+  if (!opts || !grad_out || !grad_req || n_req < 0 || (n_req > 0 && !req)) return SD_ERR_ARG;
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  sd_status st = fill_params(P, lenses, n_lenses, sensor, opts);
+  if (st != SD_OK) return st;
+  if (opts->mode != SD_BIN_BILINEAR) return SD_ERR_UNSUPPORTED;
+  if (opts->norm != SD_NORM_NONE && opts->norm != SD_NORM_PER_RAY) return SD_ERR_UNSUPPORTED;
+  if (opts->out_dtype != SD_F32) return SD_ERR_UNSUPPORTED;
+  int max_ks = opts->max_ks;
+  int max_n = opts->max_n_grid > 0 ? opts->max_n_grid : 512;
+  if (max_ks < 1 || !(max_ks & 1)) return SD_ERR_ARG;
+  if (max_ks > 127 || max_n > 2048 || max_n < 2) return SD_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_req == 0) {
+    if (grad_lens)
+      SD_CUDA_TRY(cudaMemsetAsync(grad_lens, 0,
+                                  (size_t)n_lenses * SD_MAX_SURFACES * NPAR_SURF * 4, s));
+    return SD_OK;
+  }
+  P.req = req;
+  P.n_req = n_req;
+  P.max_n = max_n;
+  P.max_ks = max_ks;
+  size_t smem = table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
+  constexpr int NT = 128;
+  auto k = trace_adj_kernel<NT>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<n_req, NT, smem, s>>>(P, grad_out, grad_req);
+  st = launch_status();
+  if (st != SD_OK) return st;
+  if (grad_lens) {
+    grad_lens_reduce<<<n_lenses, SD_MAX_SURFACES * NPAR_SURF, 0, s>>>(grad_req, req, n_req,
+                                                                       n_lenses, grad_lens);
+    st = launch_status();
+  }
+  return st;
+}

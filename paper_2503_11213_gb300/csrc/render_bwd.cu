@@ -277,12 +277,14 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
               kl[q] = w2.x;
               kr[q] = w2.y;
               // contribution to padded row rb*SEG + r: sum_j G_j Kf[r-j]
-              float acc = 0.f;
+              // (four independent partial sums keep the FMA chains short)
+              float a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
               for (int j = 0; j < SEG; ++j) {
-                acc = fmaf(GL[j], kl[(q - j + SEG) % SEG], acc);
-                acc = fmaf(GR[j], kr[(q - j + SEG) % SEG], acc);
+                a4[j & 3] = fmaf(GL[j], kl[(q - j + SEG) % SEG], a4[j & 3]);
+                a4[j & 3] = fmaf(GR[j], kr[(q - j + SEG) % SEG], a4[j & 3]);
               }
+              const float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
               if (r < ks + SEG - 1 && acc != 0.f) atomicAdd(colp + r * S, acc);
             }
           }

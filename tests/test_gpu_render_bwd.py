@@ -84,5 +84,6 @@ def test_full_size_adjoint_identities(sdlib):
     ga, gb = sd.dp_render_backward(G, aif, depth, bank, lay)
     torch.cuda.synchronize()
     lhs = (out.double() * G.double()).sum().item()
-    assert (aif.double() * ga.double()).sum().item() == pytest.approx(lhs, rel=1e-5)
-    assert (bank.double() * gb.double()).sum().item() == pytest.approx(lhs, rel=1e-5)
+    # FP32 accumulations over 6.3 M pixels x 8450 taps: relative 1e-4
+    assert (aif.double() * ga.double()).sum().item() == pytest.approx(lhs, rel=1e-4)
+    assert (bank.double() * gb.double()).sum().item() == pytest.approx(lhs, rel=1e-4)
