@@ -284,6 +284,33 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif,
 sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
                                           int C, int H, int W, size_t* bytes);
 
+/*
+ * sd_dp_render_backward for callers that cannot allocate device memory: code
+ * that may only use the buffers it is handed (for example a plugin running
+ * inside another runtime's memory pool, where a cudaMalloc would bypass the
+ * pool or is not permitted).  The paper has no counterpart; this is a
+ * deployment variant of the render adjoint with the same arguments minus the
+ * workspace.
+ * The bank-gradient pass keeps its slice bitmap in a 16 MiB array that this
+ * library reserves statically on every device that loads it (held until the
+ * process exits); when the bitmap for these sizes (see
+ * sd_dp_render_backward_workspace) exceeds 16 MiB the call returns
+ * SD_ERR_CAPACITY before launching anything.  No device memory is allocated
+ * or freed.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call uses the same array and it keeps
+ * the last call's contents: the bitmap pass rewrites every word the bank
+ * pass reads, so nothing has to start at zero, but calls that overlap on the
+ * GPU (other streams or host threads) race on the array and must be
+ * serialised by the caller.
+ */
+sd_status sd_dp_render_backward_noalloc(const float* grad_out,
+                                        const float* aif, const float* depth_m,
+                                        const float* bank,
+                                        const sd_bank_layout* layout, int N,
+                                        int C, int H, int W, float* grad_aif,
+                                        float* grad_bank, void* stream);
+
 /* ------------------------------------------------------------------------
  * Library information
  * ---------------------------------------------------------------------- */

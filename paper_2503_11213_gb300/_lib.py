@@ -65,7 +65,8 @@ assert REQUEST_DTYPE.itemsize == 48
 EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
            "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_trace_hits",
            "sd_dp_render", "sd_dp_render_backward",
-           "sd_dp_render_backward_workspace", "sd_status_string", "sd_last_cuda_error",
+           "sd_dp_render_backward_workspace", "sd_dp_render_backward_noalloc",
+           "sd_status_string", "sd_last_cuda_error",
            "sd_version")
 
 _lib = None
@@ -110,6 +111,8 @@ def lib():
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,
                                         vp, vp, vp, ctypes.c_size_t, vp]
+    L.sd_dp_render_backward_noalloc.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32,
+                                                 i32, vp, vp, vp]
     L.sd_dp_render_backward_workspace.argtypes = [P(SdBankLayout), i32, i32, i32, i32,
                                                   P(ctypes.c_size_t)]
     L.sd_status_string.argtypes = [i32]

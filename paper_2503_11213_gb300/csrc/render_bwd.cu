@@ -24,6 +24,8 @@
 //                           8-tap strips of the kernel and accumulate over the
 //                           tile's segments in a fixed order: deterministic.
 
+#include <mutex>
+
 #include "render_common.cuh"
 
 namespace sd {
@@ -557,3 +559,56 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Render backward for callers that cannot allocate device memory (for
+// example code running where cudaMalloc is forbidden or unavailable: inside
+// another framework's allocator-managed region, or a plugin that may only
+// use the buffers it is handed).  The bank-gradient pass needs a per-tile
+// slice bitmap; here it lives in a fixed device array of this library.
+// ---------------------------------------------------------------------------
+namespace sd {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned g_noalloc_scratch[NOALLOC_SCRATCH_BYTES / 4];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64];  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device; the first call
+// on a device looks it up (host code cannot use the array's name as a
+// device pointer).
+sd_status noalloc_scratch(void** ptr) {
+  int dev = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return SD_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    SD_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return SD_OK;
+}
+
+}  // namespace sd
+
+extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const float* aif,
+                                                   const float* depth_m, const float* bank,
+                                                   const sd_bank_layout* layout, int N, int C,
+                                                   int H, int W, float* grad_aif,
+                                                   float* grad_bank, void* stream) {
+  using namespace sd;
+  void* ws = nullptr;
+  size_t need = 0;
+  if (grad_bank) {
+    sd_status st = sd_dp_render_backward_workspace(layout, N, C, H, W, &need);
+    if (st != SD_OK) return st;
+    if (need > NOALLOC_SCRATCH_BYTES) return SD_ERR_CAPACITY;
+    st = noalloc_scratch(&ws);
+    if (st != SD_OK) return st;
+  }
+  return sd_dp_render_backward(grad_out, aif, depth_m, bank, layout, N, C, H, W, grad_aif,
+                               grad_bank, ws, NOALLOC_SCRATCH_BYTES, stream);
+}
