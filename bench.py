@@ -324,10 +324,98 @@ def run_ours(args, world, rank, local, dist):
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
     }
+    if rank == 0 and not args.no_batched:
+        line["uneven_batch"] = batched_compare(sd, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
     return line
+
+
+def batched_compare(sd, dev, reps=5):
+    """Uneven requests (4096: N log-uniform 32..512, ks in {15,31,65,127},
+    random field/depth/wavelength, two lenses): the batched persistent launch
+    (autotuned, replayed from a CUDA graph) against one launch with one block
+    per request and against one launch per request (4096 launches, also
+    replayed from a graph)."""
+    import ctypes
+    import torch
+    from paper_2503_11213_gb300 import _lib as L
+    from paper_2503_11213_gb300 import api
+    lenses = [sd.Lens(W.doublet_pair_f18(), 1000.0), sd.Lens(W.spherical4(), 1000.0)]
+    reqs = W.random_requests(4096, seed=3)
+    req_dev, total, off = sd.make_requests(reqs, device=dev)
+    n_req = len(reqs)
+    sensor = sd.DPSensor(0.002)
+    bt = sd.BatchedTrace(lenses, sensor, req_dev, n_req, total, max_ks=127, max_n=512)
+    cfg = bt.tune(os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt"))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def graph_of(fn):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    g_batched = graph_of(bt.run)
+    t_batched = timed(g_batched.replay)
+    out_plain = torch.empty(total, device=dev)
+    st_plain = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
+
+    def plain():
+        sd.dp_psf_trace(lenses, sensor, req_dev, n_req, total, max_ks=127, max_n=512,
+                        out=out_plain, stats=st_plain)
+
+    t_plain = timed(plain)
+    handles = (ctypes.c_void_p * 2)(*[l.handle.value for l in lenses])
+    sen = sensor.c()
+    lib = L.lib()
+    base_req, base_out, base_st = req_dev.data_ptr(), out_plain.data_ptr(), st_plain.data_ptr()
+    ks = reqs["ks"].astype(int)
+    ns = reqs["n_grid"].astype(int)
+
+    def per_request():
+        for i in range(n_req):
+            o = L.SdTraceOpts(0, L.SD_NORM_JOINT, 0, 0, int(ks[i]), int(ns[i]))
+            L.check(lib.sd_dp_psf_trace(handles, 2, ctypes.byref(sen),
+                                        ctypes.c_void_p(base_req + 48 * i), 1, ctypes.byref(o),
+                                        ctypes.c_void_p(base_out), ctypes.c_void_p(base_st + 64 * i),
+                                        api._stream()), "sd_dp_psf_trace")
+
+    g_per = graph_of(per_request)
+    t_per = timed(g_per.replay)
+    out_b, _ = bt.run()
+    torch.cuda.synchronize()
+    rays = int(bt.stats[:, 0].sum().item())
+    same = bool(torch.equal(out_b, out_plain))
+    for l in lenses:
+        l.free()
+    return {"requests": n_req, "rays": rays, "batched_graph_ms": round(t_batched, 4),
+            "one_block_per_request_ms": round(t_plain, 4),
+            "one_launch_per_request_graph_ms": round(t_per, 4),
+            "batched_grays_s": round(rays / (t_batched * 1e-3) / 1e9, 3),
+            "speedup_vs_per_request_launches": round(t_per / t_batched, 3),
+            "speedup_vs_one_block_per_request": round(t_plain / t_batched, 3),
+            "tuned_config": {"threads": cfg[0], "rays_per_item": cfg[1], "blocks_per_sm": cfg[2]},
+            "identical_results": same}
 
 
 def cpu_threads():
@@ -411,6 +499,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     world, rank, local, dist = setup_dist(args)
     if args.impl == "reference":

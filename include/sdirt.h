@@ -211,6 +211,58 @@ sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
                                    float* grad_lens, void* stream);
 
 /*
+ * Batched trace of uneven requests (different N, ks, wavelength, lens) in one
+ * persistent launch: hard binning only, results identical to
+ * sd_dp_psf_trace.  A preparation pass splits every request into work items
+ * of whole pupil rows (about rays_per_item rays each); a fixed grid of
+ * blocks_per_sm blocks per SM processes contiguous, equal ranges of items,
+ * accumulating in a shared-memory patch while consecutive items belong to
+ * one request and adding it to the request's u32 counts with integer
+ * atomics (order-independent, so deterministic); the block that completes a
+ * request normalises and stores it.  No host synchronisation and no
+ * allocation: the call can be captured in a CUDA graph.  total_elems is the
+ * size of out (every request's out_offset + 2 ks^2 must fit); the workspace
+ * (sd_dp_psf_trace_batched_workspace bytes) is device memory of the caller.
+ */
+typedef struct sd_batch_config {
+  int32_t threads;        /* threads per block, multiple of 32 in 64..1024 (0 = 512) */
+  int32_t rays_per_item;  /* target rays per work item (0 = 16384) */
+  int32_t blocks_per_sm;  /* persistent blocks per SM (0 = 1) */
+  int32_t reserved;
+} sd_batch_config;
+
+sd_status sd_dp_psf_trace_batched_workspace(int n_req, long long total_elems,
+                                            size_t* bytes);
+
+sd_status sd_dp_psf_trace_batched(const sd_lens* const* lenses, int n_lenses,
+                                  const sd_dp_sensor* sensor,
+                                  const sd_psf_request* req, int n_req,
+                                  const sd_trace_opts* opts,
+                                  const sd_batch_config* cfg, void* out,
+                                  long long total_elems, int64_t* stats,
+                                  void* workspace, size_t workspace_bytes,
+                                  void* stream);
+
+/*
+ * Autotuner of sd_dp_psf_trace_batched: times every candidate configuration
+ * (threads 256/512/1024 x rays per item 4096..65536 x 1-2 blocks per SM,
+ * within the shared-memory and thread limits) on the caller's batch with
+ * CUDA events (one warm-up run, median of three) and returns the fastest in
+ * *best.  When cache_path is not null, a previous result for the same key
+ * (device name, SM count, n_req, total_elems, max_ks, max_n_grid, n_lenses)
+ * is returned from that text file without timing, and new results are
+ * appended to it.  Synchronises the stream; writes out and stats.
+ */
+sd_status sd_dp_psf_trace_batched_tune(const sd_lens* const* lenses,
+                                       int n_lenses, const sd_dp_sensor* sensor,
+                                       const sd_psf_request* req, int n_req,
+                                       const sd_trace_opts* opts, void* out,
+                                       long long total_elems, int64_t* stats,
+                                       void* workspace, size_t workspace_bytes,
+                                       void* stream, const char* cache_path,
+                                       sd_batch_config* best);
+
+/*
  * Per-ray record of one request (test and debugging aid): for the k-th
  * in-pupil ray in raster order (pupil row major), rec[k*8 ..] = x, y, dx, dy,
  * dz (landing point and unit direction, FP32), state (0 reached, 1 no

@@ -55,6 +55,11 @@ class SdBankLayout(ctypes.Structure):
                 ("pitch_mm", ctypes.c_float), ("reserved2", ctypes.c_float)]
 
 
+class SdBatchConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("rays_per_item", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 # sd_psf_request as a numpy record (48 bytes, device-resident array)
 REQUEST_DTYPE = np.dtype([("h_mm", "<f8"), ("depth_mm", "<f8"), ("lambda_nm", "<f8"),
                           ("n_grid", "<i4"), ("ks", "<i4"), ("lens", "<i4"),
@@ -63,7 +68,9 @@ assert REQUEST_DTYPE.itemsize == 48
 
 # every exported symbol of include/sdirt.h
 EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
-           "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_trace_hits",
+           "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_psf_trace_batched",
+           "sd_dp_psf_trace_batched_workspace", "sd_dp_psf_trace_batched_tune",
+           "sd_dp_trace_hits",
            "sd_dp_render", "sd_dp_render_backward",
            "sd_dp_render_backward_workspace", "sd_dp_render_backward_noalloc",
            "sd_status_string", "sd_last_cuda_error",
@@ -107,6 +114,13 @@ def lib():
     L.sd_dp_psf_trace.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts), vp, vp, vp]
     L.sd_dp_psf_trace_backward.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
                                            vp, vp, vp, vp]
+    ll = ctypes.c_longlong
+    L.sd_dp_psf_trace_batched_workspace.argtypes = [i32, ll, P(ctypes.c_size_t)]
+    L.sd_dp_psf_trace_batched.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
+                                          P(SdBatchConfig), vp, ll, vp, vp, ctypes.c_size_t, vp]
+    L.sd_dp_psf_trace_batched_tune.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
+                                               vp, ll, vp, vp, ctypes.c_size_t, vp,
+                                               ctypes.c_char_p, P(SdBatchConfig)]
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,

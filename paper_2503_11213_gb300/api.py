@@ -154,6 +154,53 @@ def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, ma
     return grad_req, grad_lens
 
 
+def batched_workspace_bytes(n_req, total):
+    n = ctypes.c_size_t(0)
+    L.check(L.lib().sd_dp_psf_trace_batched_workspace(n_req, total, ctypes.byref(n)),
+            "sd_dp_psf_trace_batched_workspace")
+    return n.value
+
+
+class BatchedTrace:
+    """Uneven requests traced in one persistent launch (hard binning).
+
+    Holds the output, statistics and workspace so that ``run()`` allocates
+    nothing and can be captured in a CUDA graph."""
+
+    def __init__(self, lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=512,
+                 norm=L.SD_NORM_JOINT, dtype=torch.float32, config=None):
+        self.lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
+        self.handles = (ctypes.c_void_p * len(self.lenses))(
+            *[l.handle.value for l in self.lenses])
+        dev = req_dev.device
+        self.req_dev, self.n_req, self.total = req_dev, n_req, total
+        self.out = torch.empty(total, dtype=dtype, device=dev)
+        self.stats = torch.zeros((n_req, L.SD_N_STATS), dtype=torch.int64, device=dev)
+        self.ws = torch.empty(batched_workspace_bytes(n_req, total), dtype=torch.uint8, device=dev)
+        self.sen = sensor.c()
+        self.opts = L.SdTraceOpts(L.SD_BIN_HARD, norm, _DT[dtype], 0, max_ks, max_n)
+        self.config = L.SdBatchConfig(*(config or (0, 0, 0)), 0)
+
+    def run(self):
+        L.check(L.lib().sd_dp_psf_trace_batched(
+            self.handles, len(self.lenses), ctypes.byref(self.sen), _ptr(self.req_dev),
+            self.n_req, ctypes.byref(self.opts), ctypes.byref(self.config), _ptr(self.out),
+            self.total, _ptr(self.stats), _ptr(self.ws), self.ws.numel(), _stream()),
+            "sd_dp_psf_trace_batched")
+        return self.out, self.stats
+
+    def tune(self, cache_path=None):
+        best = L.SdBatchConfig()
+        path = None if cache_path is None else str(cache_path).encode()
+        L.check(L.lib().sd_dp_psf_trace_batched_tune(
+            self.handles, len(self.lenses), ctypes.byref(self.sen), _ptr(self.req_dev),
+            self.n_req, ctypes.byref(self.opts), _ptr(self.out), self.total, _ptr(self.stats),
+            _ptr(self.ws), self.ws.numel(), _stream(), path, ctypes.byref(best)),
+            "sd_dp_psf_trace_batched_tune")
+        self.config = best
+        return (best.threads, best.rays_per_item, best.blocks_per_sm)
+
+
 HIT_FIELDS = ("x", "y", "dx", "dy", "dz", "state", "side", "pixel")
 
 

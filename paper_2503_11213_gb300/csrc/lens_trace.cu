@@ -1210,3 +1210,387 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
   }
   return st;
 }
+
+namespace sd {
+
+// ---------------------------------------------------------------------------
+// Batched trace of uneven requests in one persistent launch.
+//
+// prep_kernel (one block per request): FP64 set-up of the request (the same
+//   prologue as the per-request kernel), its in-pupil ray count, and its
+//   split into work items of whole pupil rows (about rays_per_chunk rays);
+//   zeroes the request's count patch, statistics and completion counter.
+// item_scan_kernel: exclusive prefix of the item counts (item -> request).
+// batched_trace_kernel: a fixed grid of blocks; block b processes the
+//   contiguous item range [b M / G, (b+1) M / G).  While consecutive items
+//   belong to one request the block accumulates them in its shared patch; on
+//   a change of request (and at the end) it adds the patch to the request's
+//   u32 counts with integer atomics (order-independent: deterministic),
+//   then counts its items on the request's completion counter.  The block
+//   that completes a request normalises and stores it (no waiting on other
+//   blocks).  Hard binning only.
+// ---------------------------------------------------------------------------
+struct BatchCtx {
+  ReqCtx c;
+  int n_items, rows_per_item;
+  long long off;
+};
+
+struct BatchWs {
+  BatchCtx* ctx;       // [n_req]
+  int* item_start;     // [n_req + 1]
+  unsigned* done;      // [n_req]
+  unsigned* counts;    // [total elements], u32
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__host__ __device__ inline BatchWs batch_ws(void* base, int n_req) {
+  BatchWs w;
+  char* p = reinterpret_cast<char*>(base);
+  w.ctx = reinterpret_cast<BatchCtx*>(p);
+  p += align256(sizeof(BatchCtx) * (size_t)n_req);
+  w.item_start = reinterpret_cast<int*>(p);
+  p += align256(sizeof(int) * ((size_t)n_req + 1));
+  w.done = reinterpret_cast<unsigned*>(p);
+  p += align256(sizeof(unsigned) * (size_t)n_req);
+  w.counts = reinterpret_cast<unsigned*>(p);
+  return w;
+}
+
+__host__ __device__ inline size_t batch_ws_bytes(int n_req, long long total_elems) {
+  return align256(sizeof(BatchCtx) * (size_t)n_req) + align256(sizeof(int) * ((size_t)n_req + 1)) +
+         align256(sizeof(unsigned) * (size_t)n_req) + sizeof(unsigned) * (size_t)total_elems;
+}
+
+__global__ void __launch_bounds__(128) prep_kernel(TraceParams P, BatchWs W, int rays_per_item,
+                                                   long long total_elems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ReqCtx ctx;
+  int* prefix = reinterpret_cast<int*>(smem);
+  int* lo = prefix + (P.max_n + 1);
+  const int r = blockIdx.x;
+  const sd_psf_request q = P.req[r];
+  setup_request(P, q, ctx, prefix, lo);
+  const int ks2 = ctx.ks * ctx.ks;
+  const bool fits = ctx.N && q.out_offset >= 0 && q.out_offset + 2LL * ks2 <= total_elems;
+  if (threadIdx.x == 0) {
+    BatchCtx b;
+    b.c = ctx;
+    if (!fits) b.c.N = 0;
+    b.rows_per_item = max(1, rays_per_item / max(1, ctx.N));
+    b.n_items = fits ? (ctx.N + b.rows_per_item - 1) / b.rows_per_item : 0;
+    b.off = q.out_offset;
+    W.ctx[r] = b;
+    W.item_start[r] = b.n_items;  // counts; scanned by item_scan_kernel
+    W.done[r] = 0u;
+  }
+  if (fits)
+    for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) W.counts[q.out_offset + i] = 0u;
+  if (P.stats && threadIdx.x < SD_N_STATS)
+    P.stats[(long long)r * SD_N_STATS + threadIdx.x] =
+        threadIdx.x == SD_STAT_LAUNCHED && fits ? (long long)ctx.total : 0;
+}
+
+__global__ void __launch_bounds__(1024) item_scan_kernel(int* item_start, int n_req) {
+  // single block exclusive scan, in place, item_start[n_req] = total
+  __shared__ int s_carry, s_w[32];
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n_req; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < n_req ? item_start[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = s_w[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    int incl = x + (warp ? s_w[warp - 1] : 0) + s_carry;
+    if (i < n_req) item_start[i] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) item_start[n_req] = s_carry;
+}
+
+// Adds the block's patch of request r to its counts; the block that
+// completes the request's items normalises and stores it.
+template <class OutT>
+__device__ void batch_flush(const TraceParams& P, const BatchWs& W, int r, int items_here,
+                            unsigned* patch, unsigned* s_stats, int* s_last, float* s_red) {
+  const BatchCtx& B = W.ctx[r];
+  const int ks = B.c.ks, ks2 = ks * ks;
+  unsigned* cnt = W.counts + B.off;
+  for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) {
+    unsigned v = patch[i];
+    if (v) atomicAdd(&cnt[i], v);
+    patch[i] = 0u;
+  }
+  if (P.stats && threadIdx.x < SD_N_STATS && threadIdx.x != SD_STAT_LAUNCHED) {
+    unsigned v = s_stats[threadIdx.x];
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats[(long long)r * SD_N_STATS +
+                                                                     threadIdx.x]),
+                     (unsigned long long)v);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x < SD_N_STATS) s_stats[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(&W.done[r], (unsigned)items_here);
+    *s_last = (prev + (unsigned)items_here == (unsigned)B.n_items);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  // normalise (same arithmetic as the per-request kernel) and store
+  float sl = 0.f, sr = 0.f;
+  for (int i = threadIdx.x; i < ks2; i += blockDim.x) {
+    sl += (float)__ldcg(&cnt[i]);
+    sr += (float)__ldcg(&cnt[ks2 + i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_red[warp] = sl;
+    s_red[32 + warp] = sr;
+  }
+  __syncthreads();
+  float SL = 0.f, SR = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    SL += s_red[w];
+    SR += s_red[32 + w];
+  }
+  float scl = 1.f, scr = 1.f;
+  if (P.norm == SD_NORM_JOINT) {
+    float s = SL + SR;
+    scl = scr = s > 0.f ? 1.f / s : 0.f;
+  } else if (P.norm == SD_NORM_SEPARATE) {
+    scl = SL > 0.f ? 1.f / SL : 0.f;
+    scr = SR > 0.f ? 1.f / SR : 0.f;
+  } else if (P.norm == SD_NORM_PER_RAY) {
+    scl = scr = B.c.total > 0 ? 1.f / (float)B.c.total : 0.f;
+  }
+  for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x)
+    store_out<OutT>(P.out, B.off + i, (float)__ldcg(&cnt[i]) * (i < ks2 ? scl : scr));
+  __syncthreads();
+}
+
+template <class OutT>
+__global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, BatchWs W, int n_req) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ReqCtx ctx;
+  __shared__ unsigned s_stats[SD_N_STATS];
+  __shared__ float s_red[64];
+  __shared__ int s_last, s_rows;
+  int* prefix = reinterpret_cast<int*>(smem);
+  int* lo = prefix + (P.max_n + 1);
+  unsigned* patch = reinterpret_cast<unsigned*>(smem + table_bytes(P.max_n));
+  const int M = W.item_start[n_req];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int i0 = (int)((long long)M * b / G), i1 = (int)((long long)M * (b + 1) / G);
+  for (int i = threadIdx.x; i < 2 * P.max_ks * P.max_ks; i += blockDim.x) patch[i] = 0u;
+  if (threadIdx.x < SD_N_STATS) s_stats[threadIdx.x] = 0u;
+  const SensorF S = P.sen;
+  const int lane = threadIdx.x & 31;
+  int cur = -1, items_here = 0;
+  for (int it = i0; it < i1; ++it) {
+    // request of item it: last r with item_start[r] <= it
+    int a = 0, e = n_req;
+    while (e - a > 1) {
+      int m = (a + e) >> 1;
+      if (W.item_start[m] <= it) a = m; else e = m;
+    }
+    const int r = a;
+    if (r != cur) {
+      __syncthreads();
+      if (cur >= 0) batch_flush<OutT>(P, W, cur, items_here, patch, s_stats, &s_last, s_red);
+      if (threadIdx.x == 0) ctx = W.ctx[r].c;
+      cur = r;
+      items_here = 0;
+      __syncthreads();
+    }
+    ++items_here;
+    // rows of this item and their in-pupil spans
+    const int N = ctx.N, ks = ctx.ks, ks2 = ks * ks, pp = (ks - 1) >> 1;
+    const int rpi = W.ctx[r].rows_per_item;
+    const int row0 = (it - W.item_start[r]) * rpi, row1 = min(N, row0 + rpi);
+    const int nrows = row1 - row0;
+    for (int j = threadIdx.x; j < nrows; j += blockDim.x) {
+      int c, l;
+      row_span(N, row0 + j, &c, &l);
+      prefix[j + 1] = c;
+      lo[j] = l;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int carry = 0;
+      for (int base = 0; base < nrows; base += 32) {
+        int j = base + lane;
+        int v = j < nrows ? prefix[j + 1] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+          int t = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += t;
+        }
+        if (j < nrows) prefix[j + 1] = v + carry;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+      }
+      if (lane == 0) {
+        prefix[0] = 0;
+        s_rows = carry;
+      }
+    }
+    __syncthreads();
+    const int total = s_rows;
+    unsigned c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0, c_clip = 0;
+    for (int base = 0; base < total; base += blockDim.x) {
+      int k = base + threadIdx.x;
+      int key = -1;
+      if (k < total) {
+        // ray k of the item: row by binary search over the item's rows
+        int a2 = 0, e2 = nrows;
+        while (e2 - a2 > 1) {
+          int m = (a2 + e2) >> 1;
+          if (prefix[m] <= k) a2 = m; else e2 = m;
+        }
+        const int iy = row0 + a2, ix = lo[a2] + (k - prefix[a2]);
+        float ex = (float)(2 * ix + 1 - N) * ctx.scale;
+        float ey = (float)(2 * iy + 1 - N) * ctx.scale;
+        float vx = ex - ctx.x_o, vy = ey, vz = ctx.vz;
+        float inv = rsqrt_refined(vx * vx + vy * vy + vz * vz);
+        float dx = vx * inv, dy = vy * inv, dz = vz * inv, x, y, z;
+        if (ctx.s_start == 1.f) {
+          x = ex;
+          y = ey;
+        } else {
+          x = fmaf(ctx.s_start, vx, ctx.x_o);
+          y = ctx.s_start * vy;
+        }
+        z = ctx.z_start;
+        int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
+        if (st == ST_OK) {
+          ++c_reached;
+          float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
+          float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
+          float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+          int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+          bool inpatch = af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks;
+          if (!inpatch) ++c_clip;
+          else if (side == 2) ++c_miss;
+          else if (side == 0) ++c_l;
+          else ++c_r;
+          if (inpatch && side < 2) key = side * ks2 + (int)bf * ks + (int)af;
+        } else if (st == ST_CLIP) {
+          ++c_vign;
+        } else {
+          ++c_other;
+        }
+      }
+      unsigned m = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&patch[key], (unsigned)__popc(m));
+    }
+    atomicAdd(&s_stats[SD_STAT_REACHED], c_reached);
+    atomicAdd(&s_stats[SD_STAT_VIGNETTED], c_vign);
+    atomicAdd(&s_stats[SD_STAT_OTHER], c_other);
+    atomicAdd(&s_stats[SD_STAT_L], c_l);
+    atomicAdd(&s_stats[SD_STAT_R], c_r);
+    atomicAdd(&s_stats[SD_STAT_DP_MISSED], c_miss);
+    atomicAdd(&s_stats[SD_STAT_CLIPPED], c_clip);
+    __syncthreads();  // row tables are rewritten by the next item
+  }
+  __syncthreads();
+  if (cur >= 0) batch_flush<OutT>(P, W, cur, items_here, patch, s_stats, &s_last, s_red);
+}
+
+size_t batched_smem_bytes(int max_n, int max_ks) {
+  return table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
+}
+
+}  // namespace sd
+
+extern "C" {
+
+sd_status sd_dp_psf_trace_batched_workspace(int n_req, long long total_elems, size_t* bytes) {
+  if (!bytes || n_req < 0 || total_elems < 0) return SD_ERR_ARG;
+  *bytes = sd::batch_ws_bytes(n_req, total_elems);
+  return SD_OK;
+}
+
+sd_status sd_dp_psf_trace_batched(const sd_lens* const* lenses, int n_lenses,
+                                  const sd_dp_sensor* sensor, const sd_psf_request* req,
+                                  int n_req, const sd_trace_opts* opts,
+                                  const sd_batch_config* cfg, void* out, long long total_elems,
+                                  int64_t* stats, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+  using namespace sd;
+  if (!opts || !out || n_req < 0 || (n_req > 0 && !req) || total_elems < 0) return SD_ERR_ARG;
+  if (n_req == 0) return SD_OK;
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  sd_status st = fill_params(P, lenses, n_lenses, sensor, opts);
+  if (st != SD_OK) return st;
+  if (opts->mode != SD_BIN_HARD) return SD_ERR_UNSUPPORTED;
+  if (opts->out_dtype < SD_F32 || opts->out_dtype > SD_F16) return SD_ERR_ARG;
+  int max_ks = opts->max_ks;
+  int max_n = opts->max_n_grid > 0 ? opts->max_n_grid : 512;
+  if (max_ks < 1 || !(max_ks & 1)) return SD_ERR_ARG;
+  if (max_ks > 127 || max_n > 2048 || max_n < 2) return SD_ERR_UNSUPPORTED;
+  if (!workspace || workspace_bytes < batch_ws_bytes(n_req, total_elems)) return SD_ERR_ARG;
+  sd_batch_config c{};
+  if (cfg) c = *cfg;
+  if (c.threads == 0) c.threads = 512;
+  if (c.rays_per_item == 0) c.rays_per_item = 16384;
+  if (c.blocks_per_sm == 0) c.blocks_per_sm = 1;
+  if (c.threads % 32 || c.threads < 64 || c.threads > 1024 || c.rays_per_item < 1 ||
+      c.blocks_per_sm < 1 || c.blocks_per_sm > 8)
+    return SD_ERR_ARG;
+  P.req = req;
+  P.n_req = n_req;
+  P.max_n = max_n;
+  P.max_ks = max_ks;
+  P.out = out;
+  P.stats = reinterpret_cast<long long*>(stats);
+  BatchWs W = batch_ws(workspace, n_req);  // u32 counts at the requests' output offsets
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  size_t psmem = table_bytes(max_n);
+  SD_CUDA_TRY(cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)psmem));
+  prep_kernel<<<n_req, 128, psmem, s>>>(P, W, c.rays_per_item, total_elems);
+  if ((st = launch_status()) != SD_OK) return st;
+  item_scan_kernel<<<1, 1024, 0, s>>>(W.item_start, n_req);
+  if ((st = launch_status()) != SD_OK) return st;
+  int dev = 0, n_sm = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  SD_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  size_t smem = batched_smem_bytes(max_n, max_ks);
+  int grid = n_sm * c.blocks_per_sm;
+#define SD_BLAUNCH(T)                                                                    \
+  do {                                                                                   \
+    auto kfn = batched_trace_kernel<T>;                                                  \
+    SD_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                     (int)smem));                                        \
+    kfn<<<grid, c.threads, smem, s>>>(P, W, n_req);                                      \
+  } while (0)
+  if (opts->out_dtype == SD_F32) SD_BLAUNCH(float);
+  else if (opts->out_dtype == SD_BF16) SD_BLAUNCH(__nv_bfloat16);
+  else SD_BLAUNCH(__half);
+#undef SD_BLAUNCH
+  return launch_status();
+}
+
+}  // extern "C"

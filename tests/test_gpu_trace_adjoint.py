@@ -62,7 +62,9 @@ def smooth_G(ks, phase):
 
 def test_adjoint_exact_on_smooth_functional(sdlib):
     """Strict check of the reverse sweep (Snell, normals, Newton intersection
-    by the implicit function theorem, thicknesses, sensor distance)."""
+    by the implicit function theorem, thicknesses, sensor distance), request
+    by request: the per-request gradients are large and cancel in their sum,
+    so each request's partial is compared with its own oracle gradient."""
     sd = sdlib
     cfg = W.config_full_forward()
     tab, ps, focus = cfg["lens"], cfg["pitch_mm"], cfg["focus_mm"]
@@ -71,7 +73,6 @@ def test_adjoint_exact_on_smooth_functional(sdlib):
     G = [smooth_G(65, 0.3 * i) for i in range(len(reqs))]
     pids = config3_params(tab)
     S = oracle_sensor(ps)
-    ref = O.trace_grad(tab, focus, reqs, S, G, pids, n_threads=8)
     lens = sd.Lens(tab, focus)
     dev, total, off = sd.make_requests(reqs)
     g = torch.tensor(np.concatenate([x.ravel() for x in G]), dtype=torch.float32, device="cuda")
@@ -79,11 +80,17 @@ def test_adjoint_exact_on_smooth_functional(sdlib):
                                            max_n=64)
     torch.cuda.synchronize()
     h = param_scales(tab, info, pids)
-    gs = glens.cpu().numpy().reshape(-1)[pids].astype(np.float64) * h
-    rs = ref * h
-    print("smooth functional scaled error:", np.array2string(gs - rs, precision=3))
-    assert np.linalg.norm(gs - rs) <= 1e-3 * np.linalg.norm(rs)
-    assert np.abs(gs - rs).max() <= 2e-3 * np.abs(rs).max()
+    rel = []
+    for r in range(len(reqs)):
+        ref = O.trace_grad(tab, focus, reqs[r:r + 1], S, G[r:r + 1], pids) * h
+        got = greq[r].cpu().numpy().reshape(-1)[pids].astype(np.float64) * h
+        rel.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    rel = np.array(rel)
+    print("smooth functional per-request relative error:", np.array2string(rel, precision=2))
+    # most requests agree to ~1e-5; the compact near-focus PSFs to ~2e-3
+    # (FP32/FP64 splat-pixel decisions of a few rays)
+    assert np.median(rel) <= 1e-4
+    assert rel.max() <= 5e-3
     lens.free()
 
 
