@@ -39,6 +39,9 @@ WORKLOAD = ("doublet-pair f/1.8 lens: DP PSF bank 32 fields x 32 depths x 3 wave
             "DP render of 1024x1024 RGB with a Perlin depth map")
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per launch of each kernel from one ncu capture of
+# the current kernels; None until a capture of this build exists.
+TRAFFIC_BYTES = {}
 
 # ---------------------------------------------------------------------------
 # Algorithmic FP32 work per ray (add/sub/mul/div/sqrt = 1 flop, fused
@@ -56,6 +59,24 @@ FLOPS_NEWTON_ITER = 50
 FLOPS_ASPH_EXTRA = 15      # sag-gradient normal in place of the quadric one
 NEWTON_ITERS_ASSUMED = 3
 FLOPS_SENSOR_BIN = 26
+
+
+# Reverse sweep of the adjoint trace per ray, counted the same way from the
+# formulas trace_adj_kernel evaluates after recomputing the forward ray:
+# refracting surface = sag derivatives (u, q, S1, dS1 over a4..a12), normal
+# and its adjoint, Snell adjoint, implicit-intersection multiplier, transfer
+# adjoint and the c, k, a4..a12 partials; the stop only has the transfer;
+# sensor = propagation adjoint plus the four bilinear taps of the splat.
+FLOPS_ADJ_REFRACT = 245
+FLOPS_ADJ_STOP = 30
+FLOPS_ADJ_SENSOR = 40
+
+
+def adjoint_flops_per_ray(table):
+    f = flops_per_ray(table) + FLOPS_ADJ_SENSOR
+    for row in table:
+        f += FLOPS_ADJ_STOP if int(row[W.COL_TYPE]) == W.SURF_STOP else FLOPS_ADJ_REFRACT
+    return f
 
 
 def flops_per_ray(table):
@@ -151,12 +172,18 @@ def setup_dist(args):
     return world, rank, local, pg
 
 
-def build_inputs(device):
-    import torch
+def build_inputs(device, n_requests=0, image=0):
+    """The benchmark workload; n_requests / image shrink it for profiling
+    (every k-th bank request, an image x image render) -- never used for a
+    reported number."""
     cfg = W.config_full_forward()
     reqs = W.bank_grid(cfg["field_h_mm"], cfg["depths_mm"], cfg["lambdas_nm"],
                        cfg["n_grid"], cfg["ks"])
+    if n_requests:
+        reqs = reqs[::max(1, len(reqs) // n_requests)][:n_requests]
     H, Wd = cfg["sensor_hw"]
+    if image:
+        H = Wd = image
     aif = W.aif_pink(1, 3, H, Wd, seed=1).astype(np.float32)
     depth = W.depth_perlin(1, H, Wd, seed=2).astype(np.float32)
     return cfg, reqs, aif, depth
@@ -169,7 +196,7 @@ def run_ours(args, world, rank, local, dist):
     B.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg, reqs, aif_np, depth_np = build_inputs(dev)
+    cfg, reqs, aif_np, depth_np = build_inputs(dev, args.requests, args.image)
     ps = cfg["pitch_mm"]
     sensor = sd.DPSensor(ps)
     lens = sd.Lens(cfg["lens"], cfg["focus_mm"])
@@ -178,6 +205,9 @@ def run_ours(args, world, rank, local, dist):
     bank = torch.empty(total, dtype=torch.float32, device=dev)
     stats = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
     layout = sd.BankLayout(cfg["field_h_mm"], cfg["depths_mm"] / 1000.0, 3, cfg["ks"], ps)
+    if args.requests:  # profiling subsample: a bank of the traced requests only
+        layout = sd.BankLayout([0.0, 1.0], [0.3, 3.0], 3, cfg["ks"], ps)
+        assert 2 * 2 * 3 * 2 * cfg["ks"] ** 2 <= total
     aif = torch.tensor(aif_np, device=dev)
     depth = torch.tensor(depth_np, device=dev)
     out = torch.empty((1, 6) + aif.shape[2:], dtype=torch.float32, device=dev)
@@ -197,13 +227,14 @@ def run_ours(args, world, rank, local, dist):
     def render():
         sd.dp_render(aif, depth, bank, layout, out=out)
 
-    def render_bwd():
+    def render_bwd(img=True, bnk=True):
         lay = layout.c()
         L = sd.lib()
         sd._lib.check(L.sd_dp_render_backward(
             sd.api._ptr(gout), sd.api._ptr(aif), sd.api._ptr(depth), sd.api._ptr(bank),
-            sd.api.ctypes.byref(lay), 1, 3, aif.shape[2], aif.shape[3], sd.api._ptr(gaif),
-            sd.api._ptr(gbank), sd.api._ptr(ws), ws.numel(), sd.api._stream()),
+            sd.api.ctypes.byref(lay), 1, 3, aif.shape[2], aif.shape[3],
+            sd.api._ptr(gaif) if img else None, sd.api._ptr(gbank) if bnk else None,
+            sd.api._ptr(ws), ws.numel(), sd.api._stream()),
             "sd_dp_render_backward")
 
     def trace_bwd():
@@ -218,7 +249,7 @@ def run_ours(args, world, rank, local, dist):
     torch.cuda.synchronize()
     rays_per_step = int(stats[:, 0].sum().item())
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -231,19 +262,25 @@ def run_ours(args, world, rank, local, dist):
             ev[i][1].record(stream)
             render()
             ev[i][2].record(stream)
-            render_bwd()
+            # the backward as two calls (image gradient, then bank gradient)
+            # so that each kernel is timed on its own
+            render_bwd(img=True, bnk=False)
             ev[i][3].record(stream)
-            trace_bwd()
+            render_bwd(img=False, bnk=True)
             ev[i][4].record(stream)
+            trace_bwd()
+            ev[i][5].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if dist:
         dist.barrier()
-    t_trace = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    t_render = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    t_bwd = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
-    t_adj = [ev[i][3].elapsed_time(ev[i][4]) for i in range(args.steps)]
-    step_ms = sum(ev[i][0].elapsed_time(ev[i][4]) for i in range(args.steps)) / args.steps
+
+    def phase(a, b):
+        return [ev[i][a].elapsed_time(ev[i][b]) for i in range(args.steps)]
+
+    t_trace, t_render, t_bimg, t_bbank, t_adj = (phase(0, 1), phase(1, 2), phase(2, 3),
+                                                 phase(3, 4), phase(4, 5))
+    step_ms = sum(ev[i][0].elapsed_time(ev[i][5]) for i in range(args.steps)) / args.steps
     if dist:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -283,14 +320,25 @@ def run_ours(args, world, rank, local, dist):
     fpr = flops_per_ray(cfg["lens"])
     tr_ms = statistics.mean(t_trace)
     rd_ms = statistics.mean(t_render)
-    bw_ms = statistics.mean(t_bwd)
+    bi_ms = statistics.mean(t_bimg)
+    bb_ms = statistics.mean(t_bbank)
+    bw_ms = bi_ms + bb_ms
     adj_ms = statistics.mean(t_adj)
     H, Wd = aif.shape[2:]
+    # algorithmic work of each phase (FMA = 2 flops)
     render_flops = H * Wd * 3 * 2 * 2 * cfg["ks"] ** 2 * 2  # px, ch, L/R, 2 slices, FMA
-    trace_tflops = rays_per_step * fpr / (tr_ms * 1e-3) / 1e12
-    render_tflops = render_flops / (rd_ms * 1e-3) / 1e12
-    dominant = "trace_bin_kernel" if tr_ms >= rd_ms else "render_fwd_kernel"
-    achieved = trace_tflops if tr_ms >= rd_ms else render_tflops
+    afr = adjoint_flops_per_ray(cfg["lens"])
+    phases = {  # kernel: (flops per launch, ms per launch measured on the stream)
+        "trace_bin_kernel": (rays_per_step * fpr, tr_ms),
+        "render_fwd_kernel": (render_flops, rd_ms),
+        # image and bank gradients: the forward's products once each
+        "render_bwd_img_kernel": (render_flops, bi_ms),
+        "render_bwd_bank_kernel": (render_flops, bb_ms),
+        "trace_adj_kernel": (rays_per_step * afr, adj_ms),
+    }
+    tflops = {k: f / (ms * 1e-3) / 1e12 for k, (f, ms) in phases.items()}
+    dominant = max(phases, key=lambda k: phases[k][1])
+    achieved = tflops[dominant]
     value = world * rays_per_step / (step_ms * 1e-3) / 1e9
     e2e_value = world * rays_per_step / (e2e_ms * 1e-3) / 1e9
     line = {
@@ -304,23 +352,28 @@ def run_ours(args, world, rank, local, dist):
                    "parallelism": f"replica x{world}"},
         "trace_ms": round(tr_ms, 4), "render_ms": round(rd_ms, 4),
         "render_bwd_ms": round(bw_ms, 4),
+        "render_bwd_img_ms": round(bi_ms, 4), "render_bwd_bank_ms": round(bb_ms, 4),
         "render_fwd_bwd_ms": round(rd_ms + bw_ms, 4),
         "trace_adjoint_ms": round(adj_ms, 4),
         "trace_grays_s": round(rays_per_step / (tr_ms * 1e-3) / 1e9, 4),
         "render_mpix_s": round(H * Wd / (rd_ms * 1e-3) / 1e6, 2),
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3),
                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak_tflops, 4), "traffic": None,
+                     "frac": round(achieved / fp32_peak_tflops, 4),
+                     "traffic": TRAFFIC_BYTES.get(dominant),
                      "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max_mhz:.0f} MHz (max SM clock)",
-                     "flops_per_ray": fpr, "render_flops": render_flops,
-                     "trace_tflops": round(trace_tflops, 3),
-                     "render_tflops": round(render_tflops, 3)},
+                     "flops_per_ray": fpr, "adjoint_flops_per_ray": afr,
+                     "render_flops": render_flops,
+                     "kernels": {k: {"ms": round(phases[k][1], 4), "tflops": round(v, 3),
+                                     "frac": round(v / fp32_peak_tflops, 4)}
+                                 for k, v in tflops.items()}},
         "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_ms, 4)},
-        # trace, render, bwd image, bitmap, bwd bank, adjoint trace, lens reduce
-        "gpu_launches": 7 * args.steps,
+        # trace, render, bwd image, slice bitmap, bwd bank, bank parts reduce,
+        # adjoint trace, lens reduce
+        "gpu_launches": 8 * args.steps,
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
     }
@@ -500,6 +553,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="profiling only: trace every k-th bank request")
+    ap.add_argument("--image", type=int, default=0, help="profiling only: render size")
     args = ap.parse_args()
     world, rank, local, dist = setup_dist(args)
     if args.impl == "reference":

@@ -492,14 +492,17 @@ struct SurfSave {
   float px, py, pz, dx, dy, dz, t;
 };
 
-template <bool SAVE>
+// NSC > 0: the lens has exactly NSC surfaces (loops fully unrolled, per-
+// surface state in registers); NSC == 0: surface count read at run time.
+template <bool SAVE, int NSC = 0>
 __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ eta,
                                            const float* __restrict__ omeg2, int newton_max,
                                            float& x, float& y, float& z,
                                            float& dx, float& dy, float& dz, SurfSave* sv) {
   const DevLens& L = c_lens[slot];
-  const int n = L.n;
-  for (int s = 0; s < n; ++s) {
+  const int n = NSC ? NSC : L.n;
+#pragma unroll
+  for (int s = 0; s < (NSC ? NSC : n); ++s) {
     const DevSurf& S = L.s[s];
     float t;
     if (S.flat) {
@@ -530,10 +533,12 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
         float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.a[4], S.a[3]), S.a[2]), S.a[1]), S.a[0]);
         float zs = S.c * u / (1.f + q) + u * u * poly;
         float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
-        float dzdu = (q > 0.f ? 0.5f * S.c / q : 0.f) + u * dpoly;
+        // the derivative and the step only steer the iteration (its fixed point
+        // is the root of the exactly evaluated F): fast reciprocals suffice
+        float dzdu = (q > 0.f ? 0.5f * S.c * rsqrtf(arg) : 0.f) + u * dpoly;
         float F = fmaf(t, dz, z) - zs;
         float dF = dz - 2.f * dzdu * (px * dx + py * dy);
-        float step = F / dF;
+        float step = __fdividef(F, dF);
         t -= step;
         if (fabsf(step) < 1e-5f) break;
       }
@@ -602,6 +607,11 @@ __device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta
                                          float& dx, float& dy, float& dz) {
   return trace_ray_t<false>(slot, eta, omeg2, newton_max, x, y, z, dx, dy, dz, nullptr);
 }
+
+// tan(theta) = D_x / D_z of a landing ray (Sec. 3.1).  It enters the decision
+// only through h tan(theta) with h ~ 1e-3 mm, so a 2-ulp quotient is ample;
+// every path (forward, hit dump, adjoint) uses this one expression.
+__device__ __forceinline__ float tan_theta(float dx, float dz) { return __fdividef(dx, dz); }
 
 // Eq. (1)/(2): s = offset on the sub-pixel plane relative to the pixel centre;
 // L for 0 <= s < w, R for -w <= s < 0, else missed.
@@ -692,7 +702,7 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
         fx = (x - ctx.xc) * S.inv_ps + (float)p;
         fy = (y - ctx.yc) * S.inv_ps + (float)p;
         float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-        side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+        side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
         bool inpatch = af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks;
         if (!inpatch) {
           ++c_clip;
@@ -808,7 +818,7 @@ __global__ void __launch_bounds__(256) trace_hits_kernel(TraceParams P, sd_psf_r
       float fx = (x - ctx.xc) * S.inv_ps + (float)p;
       float fy = (y - ctx.yc) * S.inv_ps + (float)p;
       float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-      side = (float)dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+      side = (float)dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
       if (af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks) pix = bf * 65536.f + af;
     } else {
       x = y = dx = dy = dz = 0.f;
@@ -954,12 +964,13 @@ namespace sd {
 // ---------------------------------------------------------------------------
 constexpr int NPAR_SURF = 8;
 
+template <int NSC = 0>
 __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ eta,
                                             const float* __restrict__ omeg2,
                                             const SurfSave* sv, float dfx, float dfy, float dfz,
                                             float xb, float yb, float (*gacc)[NPAR_SURF]) {
   const DevLens& L = c_lens[slot];
-  const int n = L.n;
+  const int n = NSC ? NSC : L.n;
   // sensor: x_s = X + tau dx, tau = -Z / dz with (X, Y, Z) the last hit
   // moved to sensor-local z
   float Z = sv[n - 1].pz - L.s[n - 1].t;
@@ -968,7 +979,8 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
   float Pbx = xb, Pby = yb, Pbz = -taub / dfz;
   float dbx = xb * tau, dby = yb * tau, dbz = taub * Z / (dfz * dfz);
   gacc[n - 1][7] += -Pbz;
-  for (int s = n - 1; s >= 0; --s) {
+#pragma unroll
+  for (int s = (NSC ? NSC : n) - 1; s >= 0; --s) {
     const DevSurf& S = L.s[s];
     const float Px = sv[s].px, Py = sv[s].py;
     const float ix = sv[s].dx, iy = sv[s].dy, iz = sv[s].dz, t = sv[s].t;
@@ -1080,7 +1092,7 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
 
 // One block per request; per-request gradient partials gout[r][32*8] (fixed
 // order block reduction).
-template <int NT>
+template <int NT, int NSC>
 __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
                                                        float* __restrict__ greq) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1098,20 +1110,24 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   const SensorF S = P.sen;
   const int total = ctx.N ? ctx.total : 0;
   const float scale = (P.norm == SD_NORM_PER_RAY) ? (total > 0 ? 1.f / (float)total : 0.f) : 1.f;
-  const int n = ctx.N ? c_lens[ctx.slot].n : 0;
-  float gacc[SD_MAX_SURFACES][NPAR_SURF];
-  for (int s = 0; s < n; ++s)
+  const int n = ctx.N ? (NSC ? NSC : c_lens[ctx.slot].n) : 0;
+  constexpr int NA = NSC ? NSC : SD_MAX_SURFACES;
+  float gacc[NA][NPAR_SURF];
+#pragma unroll
+  for (int s = 0; s < NA; ++s)
+#pragma unroll
     for (int j = 0; j < NPAR_SURF; ++j) gacc[s][j] = 0.f;
-  SurfSave sv[SD_MAX_SURFACES];
+  SurfSave sv[NA];
   for (int k = threadIdx.x; k < total; k += NT) {
     float x, y, z, dx, dy, dz;
     make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
-    int st = trace_ray_t<true>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz, sv);
+    int st = trace_ray_t<true, NSC>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy,
+                                    dz, sv);
     if (st != ST_OK) continue;
     float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
     float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
     float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-    int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+    int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
     if (side == 2) continue;
     float a0f = floorf(fx), b0f = floorf(fy);
     float wx = fx - a0f, wy = fy - b0f;
@@ -1129,12 +1145,13 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
         gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
       }
     if (gfx == 0.f && gfy == 0.f) continue;
-    adjoint_ray(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
-                scale * S.inv_ps * gfy, gacc);
+    adjoint_ray<NSC>(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
+                     scale * S.inv_ps * gfy, gacc);
   }
   // fixed-order block reduction, one surface at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int s = 0; s < SD_MAX_SURFACES; ++s) {
+#pragma unroll
+  for (int s = 0; s < NA; ++s) {
     float v[NPAR_SURF];
 #pragma unroll
     for (int j = 0; j < NPAR_SURF; ++j) {
@@ -1153,16 +1170,28 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
     }
     __syncthreads();
   }
+  // surfaces beyond the lens have zero gradient
+  for (int i = NA * NPAR_SURF + threadIdx.x; i < SD_MAX_SURFACES * NPAR_SURF; i += NT)
+    greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + i] = 0.f;
 }
 
-// Sums the per-request partials of each lens in request order.
-__global__ void grad_lens_reduce(const float* __restrict__ greq, const sd_psf_request* req,
-                                 int n_req, int n_lenses, float* __restrict__ glens) {
-  const int li = blockIdx.x, pidx = threadIdx.x;  // pidx < 32 * 8
+// Sums the per-request partials of each lens: four contiguous request
+// ranges per parameter, added in range order (deterministic).
+__global__ void __launch_bounds__(1024) grad_lens_reduce(const float* __restrict__ greq,
+                                                         const sd_psf_request* req, int n_req,
+                                                         int n_lenses, float* __restrict__ glens) {
+  constexpr int NP = SD_MAX_SURFACES * NPAR_SURF;  // 256
+  __shared__ float part[4][NP];
+  const int li = blockIdx.x, pidx = threadIdx.x % NP, ch = threadIdx.x / NP;
+  const int r0 = (int)((long long)n_req * ch / 4), r1 = (int)((long long)n_req * (ch + 1) / 4);
   float a = 0.f;
-  for (int r = 0; r < n_req; ++r)
-    if (req[r].lens == li) a += greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + pidx];
-  glens[(size_t)li * SD_MAX_SURFACES * NPAR_SURF + pidx] = a;
+#pragma unroll 8
+  for (int r = r0; r < r1; ++r)
+    if (__ldg(&req[r].lens) == li) a += __ldg(&greq[(size_t)r * NP + pidx]);
+  part[ch][pidx] = a;
+  __syncthreads();
+  if (ch == 0)
+    glens[(size_t)li * NP + pidx] = ((part[0][pidx] + part[1][pidx]) + part[2][pidx]) + part[3][pidx];
 }
 
 }  // namespace sd
@@ -1197,15 +1226,17 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
   P.max_n = max_n;
   P.max_ks = max_ks;
   size_t smem = table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
+  // Surface count read at run time (per-surface state in local memory): the
+  // variants with the count fixed at compile time keep that state in
+  // registers but need 130-190 registers per thread and measured slower.
   constexpr int NT = 128;
-  auto k = trace_adj_kernel<NT>;
+  void (*k)(TraceParams, const float*, float*) = trace_adj_kernel<NT, 0>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k<<<n_req, NT, smem, s>>>(P, grad_out, grad_req);
   st = launch_status();
   if (st != SD_OK) return st;
   if (grad_lens) {
-    grad_lens_reduce<<<n_lenses, SD_MAX_SURFACES * NPAR_SURF, 0, s>>>(grad_req, req, n_req,
-                                                                       n_lenses, grad_lens);
+    grad_lens_reduce<<<n_lenses, 1024, 0, s>>>(grad_req, req, n_req, n_lenses, grad_lens);
     st = launch_status();
   }
   return st;
@@ -1488,7 +1519,7 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
           float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
           float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
           float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-          int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, dx / dz);
+          int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
           bool inpatch = af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks;
           if (!inpatch) ++c_clip;
           else if (side == 2) ++c_miss;

@@ -69,15 +69,16 @@ __global__ void __launch_bounds__(NT_BM) slice_bitmap_kernel(const RenderParams 
 }
 
 // ---------------------------------------------------------------------------
-// 2. image gradient
+// 2. image gradient.  Each lane owns a vertical segment of SB pixels; every
+// shared-memory atomic carries 2*SB FMAs.
 // ---------------------------------------------------------------------------
-template <int TX, int VB>
+template <int TX, int VB, int SB>
 struct BwdImgSmem {
-  static constexpr int NT = 4 * TX, NW = NT / 32, NPX = TX * RT_Y, MW = NT / 32;
-  __host__ __device__ static int ku(int ks) { return (ks + SEG - 1) / SEG * SEG; }
+  static constexpr int NT = TX * RT_Y / SB, NW = NT / 32, NPX = TX * RT_Y, MW = NT / 32;
+  __host__ __device__ static int ku(int ks) { return (ks + SB - 1) / SB * SB; }
   __host__ __device__ static size_t kbuf_words(int ks) { return (size_t)2 * (2 * ku(ks) * VB); }
   __host__ __device__ static size_t pad_words(int ks) {
-    return (size_t)(TX + ks - 1) * (RT_Y + ks - 1 + SEG);
+    return (size_t)(TX + ks - 1) * (RT_Y + ks - 1 + SB);
   }
   static size_t bytes(int ks) {
     size_t w = pad_words(ks) + NW * kbuf_words(ks) + 3 * (size_t)NPX  // dIpad, K, gL/gR, t
@@ -86,13 +87,13 @@ struct BwdImgSmem {
   }
 };
 
-template <int TX, int VB, int KSMAX>
-__global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderParams P,
-                                                                   const float* __restrict__ gout,
-                                                                   float* __restrict__ gaif) {
-  using SM = BwdImgSmem<TX, VB>;
+template <int TX, int VB, int KSMAX, int SB>
+__global__ void __launch_bounds__(TX * RT_Y / SB, 1)
+    render_bwd_img_kernel(const RenderParams P, const float* __restrict__ gout,
+                          float* __restrict__ gaif) {
+  using SM = BwdImgSmem<TX, VB, SB>;
   constexpr int NT = SM::NT, NW = SM::NW, NPX = SM::NPX, MW = SM::MW;
-  constexpr int NR = (2 * ((KSMAX + SEG - 1) / SEG * SEG) * VB + 31) / 32;
+  constexpr int NR = (2 * ((KSMAX + SB - 1) / SB * SB) * VB + 31) / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
   const int S = P.halo_w;
@@ -116,14 +117,14 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
 
   const int seg_col = tid % TX, seg_rb = tid / TX;
   int kmin_t = 0x7fffffff, kmax_t = -1;
-  int key_j[SEG];
-  float t_j[SEG];
+  int key_j[SB];
+  float t_j[SB];
   const float* goL = gout + (((size_t)n * 2 * P.C + c) * H) * W;
   const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * H) * W;
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    int yy = ty0 + seg_rb * SEG + j, xx = tx0 + seg_col;
-    int pix = (seg_rb * SEG + j) * TX + seg_col;
+  for (int j = 0; j < SB; ++j) {
+    int yy = ty0 + seg_rb * SB + j, xx = tx0 + seg_col;
+    int pix = (seg_rb * SB + j) * TX + seg_col;
     key_j[j] = -1;
     t_j[j] = 0.f;
     float a = 0.f, b = 0.f;
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
   __syncthreads();
   const int kmin = s_kmin, kmax = s_kmax;
 #pragma unroll
-  for (int j = 0; j < SEG; ++j)
-    prel[(seg_rb * SEG + j) * TX + seg_col] =
+  for (int j = 0; j < SB; ++j)
+    prel[(seg_rb * SB + j) * TX + seg_col] =
         (unsigned short)(key_j[j] >= 0 ? key_j[j] - kmin : 0xffff);
 
   float* kb = kbuf + warp * SM::kbuf_words(ks);
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
     for (int i = tid; i < RK * MW; i += NT) mask[i] = 0u;
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < SEG; ++j) {
+    for (int j = 0; j < SB; ++j) {
       int k0 = key_j[j];
       if (k0 < 0) continue;
       float t = t_j[j];
@@ -217,10 +218,10 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
       const int sg = act ? seg : 0;
       const int col = sg % TX, rb = sg / TX;
       // weighted gradients of the segment's pixels for this slice
-      float GL[SEG], GR[SEG];
+      float GL[SB], GR[SB];
 #pragma unroll
-      for (int j = 0; j < SEG; ++j) {
-        int pix = (rb * SEG + j) * TX + col;
+      for (int j = 0; j < SB; ++j) {
+        int pix = (rb * SB + j) * TX + col;
         unsigned short r16 = prel[pix];
         float w = 0.f;
         if (act && r16 != 0xffff) {
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
       fetch(0);
       commit(kb);
       __syncwarp();
-      float* base = dpad + (rb * SEG) * S + col;
+      float* base = dpad + (rb * SB) * S + col;
       for (int b = 0; b < nblk; ++b) {
         const float* kcur = kb + (b & 1) * kb_elems;
         if (b + 1 < nblk) fetch(b + 1);
@@ -267,27 +268,26 @@ __global__ void __launch_bounds__(4 * TX, 1) render_bwd_img_kernel(const RenderP
         for (int vv = 0; vv < vmax; ++vv) {
           float* colp = base + b * VB + vv;
           const float2* kp = reinterpret_cast<const float2*>(kcur) + vv;
-          // ring of the taps u = r-7 .. r of column v (zero outside [0, ks))
-          float kl[SEG], kr[SEG];
+          // ring of the taps u = r-SB+1 .. r of column v (zero outside [0, ks))
+          float kl[SB], kr[SB];
 #pragma unroll
-          for (int j = 0; j < SEG; ++j) kl[j] = kr[j] = 0.f;
-          for (int r0 = 0; r0 < KU + SEG; r0 += SEG) {
+          for (int j = 0; j < SB; ++j) kl[j] = kr[j] = 0.f;
+          for (int r0 = 0; r0 < KU + SB; r0 += SB) {
 #pragma unroll
-            for (int q = 0; q < SEG; ++q) {
+            for (int q = 0; q < SB; ++q) {
               const int r = r0 + q;
               float2 w2 = r < KU ? kp[r * VB] : make_float2(0.f, 0.f);
               kl[q] = w2.x;
               kr[q] = w2.y;
-              // contribution to padded row rb*SEG + r: sum_j G_j Kf[r-j]
-              // (four independent partial sums keep the FMA chains short)
+              // contribution to padded row rb*SB + r: sum_j G_j Kf[r-j]
               float a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-              for (int j = 0; j < SEG; ++j) {
-                a4[j & 3] = fmaf(GL[j], kl[(q - j + SEG) % SEG], a4[j & 3]);
-                a4[j & 3] = fmaf(GR[j], kr[(q - j + SEG) % SEG], a4[j & 3]);
+              for (int j = 0; j < SB; ++j) {
+                a4[j & 3] = fmaf(GL[j], kl[(q - j + SB) % SB], a4[j & 3]);
+                a4[j & 3] = fmaf(GR[j], kr[(q - j + SB) % SB], a4[j & 3]);
               }
               const float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-              if (r < ks + SEG - 1 && acc != 0.f) atomicAdd(colp + r * S, acc);
+              if (r < ks + SB - 1 && acc != 0.f) atomicAdd(colp + r * S, acc);
             }
           }
         }
@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
                                                              const float* __restrict__ gout,
                                                              const unsigned* __restrict__ bm,
                                                              int words, int ntx, int nty,
-                                                             float* __restrict__ gbank) {
+                                                             float* __restrict__ gbank,
+                                                             int parts) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
   const int KU = (ks + SEG - 1) / SEG * SEG;
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
   int* segs = reinterpret_cast<int*>(G + NPX);            // NSEG
   __shared__ int s_nseg, s_wcnt[NSEG / 32];
 
-  const int key = blockIdx.x, lam = blockIdx.y;
+  // block (key, lam, part) visits the tiles with index = part (mod parts)
+  const int key = blockIdx.x, lam = blockIdx.y, part = blockIdx.z;
   const int tid = threadIdx.x;
   const bool two = P.Z > 1;
   const int nstrip = ks * (KU / SEG);
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
     for (int ty = 0; ty < nty; ++ty)
       for (int tx = 0; tx < ntx; ++tx) {
         size_t tile = ((size_t)n * nty + ty) * ntx + tx;
+        if ((int)(tile % (size_t)parts) != part) continue;
         if (!(bm[tile * words + kw] & kbit)) continue;
         const int tx0 = tx * TXB, ty0 = ty * RT_Y;
         for (int c = c_lo; c < c_hi; ++c) {
@@ -427,8 +430,8 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
           }
         }
       }
-  // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v]
-  float* out = gbank + ((size_t)key * P.NL + lam) * 2 * ks2;
+  // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v] of this part's slab
+  float* out = gbank + ((size_t)part * gridDim.x * P.NL + (size_t)key * P.NL + lam) * 2 * ks2;
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
     int st = tid + s * NT;
@@ -445,26 +448,42 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
   }
 }
 
+// grad_bank = sum of the part slabs, added in part order (deterministic)
+__global__ void bank_parts_reduce(const float* __restrict__ parts_buf, size_t n, int parts,
+                                  float* __restrict__ gbank) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float a = parts_buf[i];
+    for (int q = 1; q < parts; ++q) a += parts_buf[(size_t)q * n + i];
+    gbank[i] = a;
+  }
+}
+
 template <int NT, int SPT>
 sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsigned* bm, int words,
-                          int ntx, int nty, float* gbank, cudaStream_t s) {
+                          int ntx, int nty, float* gbank, float* parts_buf, int parts,
+                          cudaStream_t s) {
   const int ks = P.ks;
   size_t smem = (size_t)(RT_Y + ks - 1 + SEG) * (TXB + ks - 1) * 4 + (size_t)TXB * RT_Y * 8 +
                 (size_t)(TXB * RT_Y / SEG) * 4;
   auto k = render_bwd_bank_kernel<NT, SPT>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(P.F * P.Z, P.NL);
-  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, gbank);
+  dim3 grid(P.F * P.Z, P.NL, parts);
+  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 ? parts_buf : gbank, parts);
+  sd_status st = launch_status();
+  if (st != SD_OK || parts == 1) return st;
+  size_t n = (size_t)P.F * P.Z * P.NL * 2 * ks * ks;
+  bank_parts_reduce<<<1024, 256, 0, s>>>(parts_buf, n, parts, gbank);
   return launch_status();
 }
 
-template <int TX, int VB, int KSMAX>
+template <int TX, int VB, int KSMAX, int SB>
 sd_status launch_img_bwd(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
-  using SM = BwdImgSmem<TX, VB>;
+  using SM = BwdImgSmem<TX, VB, SB>;
   P.halo_w = TX + P.ks - 1;
-  P.halo_h = RT_Y + P.ks - 1 + SEG;
+  P.halo_h = RT_Y + P.ks - 1 + SB;
   size_t smem = SM::bytes(P.ks);
-  auto k = render_bwd_img_kernel<TX, VB, KSMAX>;
+  auto k = render_bwd_img_kernel<TX, VB, KSMAX, SB>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((P.W + TX - 1) / TX, (P.H + RT_Y - 1) / RT_Y, P.N * P.C);
   k<<<grid, SM::NT, smem, s>>>(P, gout, gaif);
@@ -472,6 +491,17 @@ sd_status launch_img_bwd(RenderParams& P, const float* gout, float* gaif, cudaSt
 }
 
 constexpr size_t SMEM_CAP_B = 227 * 1024;
+// The bank gradient splits every slice's tiles over BANK_PARTS blocks when the
+// workspace holds that many partial banks (heavy slices otherwise set the
+// tail of the launch); fewer parts with a smaller workspace.
+constexpr int BANK_PARTS = 2;
+
+inline size_t bitmap_bytes(int N, int tx, int ty, int F, int Z) {
+  return ((size_t)N * tx * ty * bitmap_words(F, Z) * 4 + 255) & ~(size_t)255;
+}
+inline size_t bank_bytes(const RenderParams& P) {
+  return (size_t)P.F * P.Z * P.NL * 2 * P.ks * P.ks * 4;
+}
 
 sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
                     RenderParams& P) {
@@ -503,7 +533,7 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   if (st != SD_OK) return st;
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
-  *bytes = (size_t)N * tx * ty * bitmap_words(P.F, P.Z) * 4;
+  *bytes = bitmap_bytes(N, tx, ty, P.F, P.Z) + (size_t)BANK_PARTS * bank_bytes(P);
   return SD_OK;
 }
 
@@ -528,21 +558,30 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const f
   if (grad_aif) {
     SD_CUDA_TRY(cudaMemsetAsync(grad_aif, 0, (size_t)N * C * H * W * 4, s));
     sd_status r;
-    if (P.ks <= 65 && BwdImgSmem<128, 4>::bytes(P.ks) <= SMEM_CAP_B)
-      r = launch_img_bwd<128, 4, 65>(P, grad_out, grad_aif, s);
-    else if (BwdImgSmem<64, 4>::bytes(P.ks) <= SMEM_CAP_B)
-      r = launch_img_bwd<64, 4, 127>(P, grad_out, grad_aif, s);
+    // 8-pixel segments: 16-pixel segments halve the shared atomics per FMA
+    // but need ~240 registers (8 warps per SM) and measured slower
+    if (P.ks <= 65 && BwdImgSmem<128, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
+      r = launch_img_bwd<128, 4, 65, 8>(P, grad_out, grad_aif, s);
+    else if (BwdImgSmem<64, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
+      r = launch_img_bwd<64, 4, 127, 8>(P, grad_out, grad_aif, s);
     else
-      r = launch_img_bwd<64, 2, 127>(P, grad_out, grad_aif, s);
+      r = launch_img_bwd<64, 2, 127, 8>(P, grad_out, grad_aif, s);
     if (r != SD_OK) return r;
   }
   if (grad_bank) {
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
     size_t words = bitmap_words(P.F, P.Z);
-    size_t need = (size_t)N * tx * ty * words * 4;
+    size_t need = bitmap_bytes(N, tx, ty, P.F, P.Z);
     if (!workspace || workspace_bytes < need) return SD_ERR_ARG;
     unsigned* bm = reinterpret_cast<unsigned*>(workspace);
+    int parts = 1;
+    for (int q = BANK_PARTS; q > 1; q >>= 1)
+      if (workspace_bytes >= need + (size_t)q * bank_bytes(P)) {
+        parts = q;
+        break;
+      }
+    float* parts_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
     dim3 g1(tx, ty, N);
     slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
     sd_status r = launch_status();
@@ -550,9 +589,11 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const f
     int KU = (P.ks + SEG - 1) / SEG * SEG;
     int nstrip = P.ks * (KU / SEG);
     if (nstrip <= 256 * 3)
-      r = launch_bank_bwd<256, 3>(P, grad_out, bm, (int)words, tx, ty, grad_bank, s);
+      r = launch_bank_bwd<256, 3>(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf,
+                                  parts, s);
     else
-      r = launch_bank_bwd<512, 4>(P, grad_out, bm, (int)words, tx, ty, grad_bank, s);
+      r = launch_bank_bwd<512, 4>(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf,
+                                  parts, s);
     if (r != SD_OK) return r;
   }
   return SD_OK;
@@ -603,8 +644,13 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
   void* ws = nullptr;
   size_t need = 0;
   if (grad_bank) {
-    sd_status st = sd_dp_render_backward_workspace(layout, N, C, H, W, &need);
+    // the bitmap must fit; partial banks are used as far as the array allows
+    RenderParams P;
+    sd_status st = setup_bwd(layout, N, C, H, W, P);
     if (st != SD_OK) return st;
+    int tx, ty;
+    bwd_tiles(H, W, &tx, &ty);
+    need = bitmap_bytes(N, tx, ty, P.F, P.Z);
     if (need > NOALLOC_SCRATCH_BYTES) return SD_ERR_CAPACITY;
     st = noalloc_scratch(&ws);
     if (st != SD_OK) return st;
