@@ -232,7 +232,7 @@ def run_ours(args, world, rank, local, dist):
         L = sd.lib()
         sd._lib.check(L.sd_dp_render_backward(
             sd.api._ptr(gout), sd.api._ptr(aif), sd.api._ptr(depth), sd.api._ptr(bank),
-            sd.api.ctypes.byref(lay), 1, 3, aif.shape[2], aif.shape[3],
+            sd.api.ctypes.byref(lay), 1, 3, aif.shape[2], aif.shape[3], sd.SD_F32,
             sd.api._ptr(gaif) if img else None, sd.api._ptr(gbank) if bnk else None,
             sd.api._ptr(ws), ws.numel(), sd.api._stream()),
             "sd_dp_render_backward")
@@ -379,6 +379,9 @@ def run_ours(args, world, rank, local, dist):
     }
     if rank == 0 and not args.no_batched:
         line["uneven_batch"] = batched_compare(sd, dev)
+    if rank == 0 and not args.no_extra:
+        line["differentiation_pipeline"] = pipeline_compare(sd, dev)
+        line["precision"] = precision_compare(sd, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
@@ -471,6 +474,180 @@ def batched_compare(sd, dev, reps=5):
             "identical_results": same}
 
 
+def _timed(fn, stream, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def precision_compare(sd, dev, crop=256):
+    """Render a batch of 16 RGB 2048x1536 images through a 64x64x3 bank of
+    65x65 PSFs stored in FP32, BF16 and FP16 (FP32 accumulation); time each
+    and report its error on a crop x crop corner of image 0 (all channels,
+    L and R) against the FP64 oracle render of the FP32 image and bank."""
+    import torch
+    import oracle as O
+    c = W.config_precision()
+    H, Wd = c["image_hw"]
+    a_b = W.aif_pink(2, 3, H, Wd, seed=4).astype(np.float32)
+    d_b = W.depth_perlin(2, H, Wd, seed=5).astype(np.float32)
+    aif_np, depth_np = W.flip_batch(a_b, d_b, c["batch"])
+    reqs = W.bank_grid(c["field_h_mm"], c["depths_mm"], c["lambdas_nm"], c["n_grid"], c["ks"])
+    lens = sd.Lens(c["lens"], c["focus_mm"])
+    sensor = sd.DPSensor(c["pitch_mm"])
+    req_dev, total, _ = sd.make_requests(reqs, device=dev)
+    depth = torch.tensor(depth_np, device=dev)
+    aif32 = torch.tensor(aif_np, device=dev)
+    stream = torch.cuda.current_stream()
+    px = int(c["batch"] * H * Wd)
+    res = {"batch": [c["batch"], 3, H, Wd], "bank": [64, 64, 3, 65, 65],
+           "crop": f"image 0, rows/cols 0..{crop - 1}, 3 channels x L/R vs the FP64 oracle "
+                   f"render of the FP32 image and FP32 bank"}
+    bank32 = None
+    ref = None
+    fh, dm = c["field_h_mm"], c["depths_mm"] / 1000.0
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        bank, _ = sd.dp_psf_trace(lens, sensor, req_dev, len(reqs), total, max_ks=c["ks"],
+                                  max_n=c["n_grid"], norm=sd.SD_NORM_JOINT, dtype=dt)
+        lay = sd.BankLayout(fh, dm, 3, c["ks"], c["pitch_mm"], dtype=dt)
+        aif = aif32 if dt == torch.float32 else aif32.to(dt)
+        out = torch.empty((c["batch"], 6, H, Wd), dtype=dt, device=dev)
+        t = _timed(lambda: sd.dp_render(aif, depth, bank, lay, out=out), stream, reps=3)
+        if bank32 is None:
+            bank32 = bank.cpu().numpy().reshape(64, 64, 3, 2, c["ks"], c["ks"])
+            ys, xs = np.meshgrid(np.arange(crop), np.arange(crop), indexing="ij")
+            pix = np.stack([np.zeros(crop * crop, int), ys.ravel(), xs.ravel()], 1)
+            ref = O.render_bank_pixels(aif_np[:1].astype(np.float64), depth_np[:1], bank32,
+                                       fh, dm, c["pitch_mm"], pix, n_threads=cpu_threads())
+            ref = np.asarray(ref).reshape(crop, crop, 6)
+        got = out[0, :, :crop, :crop].float().cpu().numpy().transpose(1, 2, 0)
+        err = got.astype(np.float64) - ref
+        res[name] = {"ms": round(t, 3), "mpix_s": round(px / (t * 1e-3) / 1e6, 2),
+                     "max_err_rel": float(np.abs(err).max() / np.abs(ref).max()),
+                     "rms_err_rel": float(np.sqrt((err ** 2).mean()) / np.abs(ref).max())}
+        del out, bank
+    res["bf16_speedup_vs_f32"] = round(res["f32"]["ms"] / res["bf16"]["ms"], 3)
+    res["bf16_bound"] = "max err <= 8 * 2^-9 of max|ref|"
+    lens.free()
+    return res
+
+
+def pipeline_compare(sd, dev, reps=5):
+    """Differentiation workload: trace the 32x32x3 bank at 128x128 pupil
+    samples, render a batch of 8 RGB 512x512 images, render backward to the
+    image and the bank, adjoint trace of the bank gradient.  Plain FP32 (one
+    trace block per request, FP32 bank and images, eager launches) against
+    the batched BF16 pipeline (persistent batched trace writing a BF16 bank,
+    BF16 images, FP32 gradients, the whole step replayed from one CUDA
+    graph), with the bank error of both against the FP64 oracle."""
+    import torch
+    import oracle as O
+    c = W.config_differentiation()
+    H, Wd = c["image_hw"]
+    B = c["batch"]
+    reqs = W.bank_grid(c["field_h_mm"], c["depths_mm"], c["lambdas_nm"], c["n_grid"], c["ks"])
+    n_req = len(reqs)
+    lens = sd.Lens(c["lens"], c["focus_mm"])
+    sensor = sd.DPSensor(c["pitch_mm"])
+    req_dev, total, off = sd.make_requests(reqs, device=dev)
+    aif_np = W.aif_pink(B, 3, H, Wd, seed=6).astype(np.float32)
+    depth = torch.tensor(W.depth_perlin(B, H, Wd, seed=7).astype(np.float32), device=dev)
+    gout = torch.randn((B, 6, H, Wd), device=dev, generator=torch.Generator(dev).manual_seed(1))
+    fh, dm = c["field_h_mm"], c["depths_mm"] / 1000.0
+    stream = torch.cuda.current_stream()
+    ks = c["ks"]
+
+    def make(dt):
+        lay = sd.BankLayout(fh, dm, 3, ks, c["pitch_mm"], dtype=dt)
+        aif = torch.tensor(aif_np, device=dev).to(dt)
+        out = torch.empty((B, 6, H, Wd), dtype=dt, device=dev)
+        gaif = torch.empty((B, 3, H, Wd), device=dev)
+        gbank = torch.empty(total, device=dev)
+        ws = torch.empty(sd.api.render_backward_workspace(lay, B, 3, H, Wd), dtype=torch.uint8,
+                         device=dev)
+        greq = torch.empty((n_req, 32, 8), device=dev)
+        return lay, aif, out, gaif, gbank, ws, greq
+
+    L = sd.lib()
+
+    def render_bwd(lay, aif, bank, gaif, gbank, ws):
+        lc = lay.c()
+        sd._lib.check(L.sd_dp_render_backward(
+            sd.api._ptr(gout), sd.api._ptr(aif), sd.api._ptr(depth), sd.api._ptr(bank),
+            sd.api.ctypes.byref(lc), B, 3, H, Wd, sd.api._DT[aif.dtype], sd.api._ptr(gaif),
+            sd.api._ptr(gbank), sd.api._ptr(ws), ws.numel(), sd.api._stream()),
+            "sd_dp_render_backward")
+
+    # plain FP32
+    lay32, aif32, out32, gaif32, gbank32, ws32, greq32 = make(torch.float32)
+    bank32 = torch.empty(total, device=dev)
+    st32 = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
+
+    def plain():
+        sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
+                        norm=sd.SD_NORM_JOINT, out=bank32, stats=st32)
+        sd.dp_render(aif32, depth, bank32, lay32, out=out32)
+        render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32)
+        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank32, max_ks=ks,
+                                 max_n=c["n_grid"], grad_req=greq32)
+
+    # batched BF16 under one CUDA graph
+    lay16, aif16, out16, gaif16, gbank16, ws16, greq16 = make(torch.bfloat16)
+    bt = sd.BatchedTrace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
+                         norm=sd.SD_NORM_JOINT, dtype=torch.bfloat16)
+    bt.tune(os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt"))
+
+    def batched():
+        bank16, _ = bt.run()
+        sd.dp_render(aif16, depth, bank16, lay16, out=out16)
+        render_bwd(lay16, aif16, bank16, gaif16, gbank16, ws16)
+        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank16, max_ks=ks,
+                                 max_n=c["n_grid"], grad_req=greq16)
+
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        batched()
+    stream.wait_stream(s2)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batched()
+    t_plain = _timed(plain, stream, reps)
+    t_graph = _timed(g.replay, stream, reps)
+    torch.cuda.synchronize()
+    # bank error of both against the FP64 oracle on 24 evenly spaced requests
+    idx = np.linspace(0, n_req - 1, 24).astype(int)
+    S = dict(ps=c["pitch_mm"], h=W.DP_H * c["pitch_mm"], f=W.DP_F * c["pitch_mm"],
+             w=W.DP_W * c["pitch_mm"], r=W.DP_R * c["pitch_mm"])
+    ref, _ = O.psf_bank(c["lens"], c["focus_mm"], reqs[idx], S, n_threads=cpu_threads())
+    b32 = bank32.cpu().numpy()
+    b16 = bt.out.float().cpu().numpy()
+
+    def l1(b):
+        e = [np.abs(b[off[i]:off[i] + 2 * ks * ks] - r.ravel()).sum() / np.abs(r).sum()
+             for i, r in zip(idx, ref)]
+        return float(np.mean(e)), float(np.max(e))
+
+    e32, e16 = l1(b32), l1(b16)
+    rays = int(st32[:, 0].sum().item())
+    lens.free()
+    return {"requests": n_req, "rays": rays, "images": [B, 3, H, Wd],
+            "plain_f32_ms": round(t_plain, 3), "batched_bf16_graph_ms": round(t_graph, 3),
+            "speedup": round(t_plain / t_graph, 3),
+            "bank_l1_vs_oracle": {"f32": {"mean": e32[0], "max": e32[1]},
+                                  "bf16": {"mean": e16[0], "max": e16[1]},
+                                  "sample": "24 evenly spaced requests, FP64 oracle"}}
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -553,6 +730,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the differentiation-pipeline and precision legs")
     ap.add_argument("--requests", type=int, default=0,
                     help="profiling only: trace every k-th bank request")
     ap.add_argument("--image", type=int, default=0, help="profiling only: render size")

@@ -313,24 +313,32 @@ sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
                        int W, int image_dtype, void* out, void* stream);
 
 /*
- * Adjoint of sd_dp_render (bank mode), FP32 only: given grad_out (N,2C,H,W)
- * writes grad_aif (N,C,H,W) and grad_bank (bank layout), both overwritten;
- * either may be null to skip it.
+ * Adjoint of sd_dp_render (bank mode): given grad_out (N,2C,H,W) FP32 writes
+ * grad_aif (N,C,H,W) FP32 and grad_bank (the bank's element layout, FP32),
+ * both overwritten; either may be null to skip it.  aif is read in
+ * image_dtype and the bank in layout->dtype (the storage types sd_dp_render
+ * takes); arithmetic is FP32.  Returns SD_ERR_UNSUPPORTED for another
+ * image_dtype.
  *   grad_aif: each (segment, slice) item scatters its weighted gradients into
  *     a shared padded tile, folded onto the image with FP32 atomics (the
  *     result is not bitwise reproducible run to run).
- *   grad_bank: one thread block per (slice, wavelength) accumulates over the
+ *   grad_bank: thread blocks per (slice, wavelength) accumulate over the
  *     tiles that use the slice in a fixed order (deterministic).  Needs a
- *     device workspace of sd_dp_render_backward_workspace() bytes (a bitmap
- *     of the slices each 64x32 tile uses); ignored when grad_bank is null.
- * Returns SD_ERR_ARG when the workspace is missing or too small.
+ *     device workspace of at least the bitmap of the slices each 64x32 tile
+ *     uses; with the full sd_dp_render_backward_workspace() bytes the tiles
+ *     of a slice are split over two blocks whose partial banks are then
+ *     added in a fixed order (still deterministic).  Ignored when grad_bank
+ *     is null.
+ * Returns SD_ERR_ARG when the workspace is missing or smaller than the
+ * bitmap.
  */
-sd_status sd_dp_render_backward(const float* grad_out, const float* aif,
-                                const float* depth_m, const float* bank,
+sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
+                                const float* depth_m, const void* bank,
                                 const sd_bank_layout* layout, int N, int C,
-                                int H, int W, float* grad_aif,
-                                float* grad_bank, void* workspace,
-                                size_t workspace_bytes, void* stream);
+                                int H, int W, int image_dtype,
+                                float* grad_aif, float* grad_bank,
+                                void* workspace, size_t workspace_bytes,
+                                void* stream);
 
 /* Device workspace bytes sd_dp_render_backward needs for these sizes. */
 sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
@@ -342,7 +350,8 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
  * inside another runtime's memory pool, where a cudaMalloc would bypass the
  * pool or is not permitted).  The paper has no counterpart; this is a
  * deployment variant of the render adjoint with the same arguments minus the
- * workspace.
+ * workspace and the image dtype (aif is FP32; the bank is read in
+ * layout->dtype).
  * The bank-gradient pass keeps its slice bitmap in a 16 MiB array that this
  * library reserves statically on every device that loads it (held until the
  * process exits); when the bitmap for these sizes (see

@@ -7,5 +7,8 @@ marshals PyTorch tensors into that ABI.
 from .api import (BankLayout, BatchedTrace, DPSensor, Lens, dp_psf_trace, dp_psf_trace_backward,  # noqa: F401
                   dp_render, dp_render_backward, make_requests, render_backward_workspace,
                   trace_hits)
-from ._lib import (SD_BIN_BILINEAR, SD_BIN_HARD, SD_NORM_JOINT, SD_NORM_NONE,  # noqa: F401
+from .autograd import (DPRenderFunction, DPTraceFunction, dp_psf_trace_autograd,  # noqa: F401
+                       dp_render_autograd)
+from ._lib import (SD_BF16, SD_BIN_BILINEAR, SD_BIN_HARD, SD_F16, SD_F32, SD_NORM_JOINT,  # noqa: F401
+                   SD_NORM_NONE,
                    SD_NORM_PER_RAY, SD_NORM_SEPARATE, SdError, lib)

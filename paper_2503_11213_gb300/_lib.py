@@ -124,7 +124,7 @@ def lib():
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,
-                                        vp, vp, vp, ctypes.c_size_t, vp]
+                                        i32, vp, vp, vp, ctypes.c_size_t, vp]
     L.sd_dp_render_backward_noalloc.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32,
                                                  i32, vp, vp, vp]
     L.sd_dp_render_backward_workspace.argtypes = [P(SdBankLayout), i32, i32, i32, i32,

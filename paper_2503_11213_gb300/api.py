@@ -269,18 +269,23 @@ def render_backward_workspace(layout: BankLayout, N, C, H, W):
 
 def dp_render_backward(grad_out, aif, depth_m, bank, layout: BankLayout, need_aif=True,
                        need_bank=True, workspace=None):
-    """Adjoint of dp_render (FP32): (grad_aif or None, grad_bank or None)."""
+    """Adjoint of dp_render: (grad_aif or None, grad_bank or None), both FP32;
+    aif and bank may be stored in any dtype dp_render takes."""
     N, C, H, W = aif.shape
-    ga = torch.empty_like(aif) if need_aif else None
-    gb = torch.empty_like(bank) if need_bank else None
+    dev = aif.device
+    ga = torch.empty(aif.shape, dtype=torch.float32, device=dev) if need_aif else None
+    gb = torch.empty(bank.shape, dtype=torch.float32, device=dev) if need_bank else None
     if need_bank and workspace is None:
         nbytes = render_backward_workspace(layout, N, C, H, W)
-        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=aif.device)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     _need_cuda(grad_out, aif, depth_m, bank, ga, gb)
+    if grad_out.dtype != torch.float32 or bank.dtype != layout.dtype:
+        raise ValueError("grad_out must be float32 and the bank dtype must match the layout")
     lay = layout.c()
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     L.check(L.lib().sd_dp_render_backward(_ptr(grad_out), _ptr(aif), _ptr(depth_m), _ptr(bank),
-                                          ctypes.byref(lay), N, C, H, W, _ptr(ga), _ptr(gb),
-                                          _ptr(workspace), ws_bytes, _stream()),
+                                          ctypes.byref(lay), N, C, H, W, _DT[aif.dtype],
+                                          _ptr(ga), _ptr(gb), _ptr(workspace), ws_bytes,
+                                          _stream()),
             "sd_dp_render_backward")
     return ga, gb

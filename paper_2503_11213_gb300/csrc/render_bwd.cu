@@ -87,7 +87,7 @@ struct BwdImgSmem {
   }
 };
 
-template <int TX, int VB, int KSMAX, int SB>
+template <int TX, int VB, int KSMAX, int SB, class TB>
 __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
     render_bwd_img_kernel(const RenderParams P, const float* __restrict__ gout,
                           float* __restrict__ gaif) {
@@ -233,9 +233,9 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
         GR[j] = w * gR[pix];
       }
       const int f = key / P.Z, z = key - f * P.Z;
-      const float* KL = reinterpret_cast<const float*>(P.bank) +
-                        (((size_t)f * P.Z + z) * P.NL + lam) * 2 * ks2;
-      const float* KR = KL + ks2;
+      const TB* KL = reinterpret_cast<const TB*>(P.bank) +
+                     (((size_t)f * P.Z + z) * P.NL + lam) * 2 * ks2;
+      const TB* KR = KL + ks2;
       float pre[NR];
       auto fetch = [&](int b) {
 #pragma unroll
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
           if (e < kb_elems) {
             int side = e & 1, uv = e >> 1, u = uv / VB, vv = uv - u * VB;
             int v_ = b * VB + vv;
-            if (v_ < ks && u < ks) v = __ldg((side ? KR : KL) + (ks - 1 - u) * ks + (ks - 1 - v_));
+            if (v_ < ks && u < ks)
+              v = to_f32<TB>(__ldg((side ? KR : KL) + (ks - 1 - u) * ks + (ks - 1 - v_)));
           }
           pre[r] = v;
         }
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
 // ---------------------------------------------------------------------------
 // 3. bank gradient, one block per (slice key, wavelength)
 // ---------------------------------------------------------------------------
-template <int NT, int SPT>
+template <int NT, int SPT, class TI>
 __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams P,
                                                              const float* __restrict__ gout,
                                                              const unsigned* __restrict__ bm,
@@ -356,12 +357,12 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
         const int tx0 = tx * TXB, ty0 = ty * RT_Y;
         for (int c = c_lo; c < c_hi; ++c) {
           __syncthreads();
-          const float* img = reinterpret_cast<const float*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
+          const TI* img = reinterpret_cast<const TI*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
           for (int i = tid; i < HH * S; i += NT) {
             int r = i / S, cc = i - r * S;
             int yy = min(max(ty0 + r - p, 0), P.H - 1);
             int xx = min(max(tx0 + cc - p, 0), P.W - 1);
-            halo[i] = img[(size_t)yy * P.W + xx];
+            halo[i] = to_f32<TI>(img[(size_t)yy * P.W + xx]);
           }
           const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
           const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
@@ -459,14 +460,14 @@ __global__ void bank_parts_reduce(const float* __restrict__ parts_buf, size_t n,
   }
 }
 
-template <int NT, int SPT>
+template <int NT, int SPT, class TI>
 sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsigned* bm, int words,
                           int ntx, int nty, float* gbank, float* parts_buf, int parts,
                           cudaStream_t s) {
   const int ks = P.ks;
   size_t smem = (size_t)(RT_Y + ks - 1 + SEG) * (TXB + ks - 1) * 4 + (size_t)TXB * RT_Y * 8 +
                 (size_t)(TXB * RT_Y / SEG) * 4;
-  auto k = render_bwd_bank_kernel<NT, SPT>;
+  auto k = render_bwd_bank_kernel<NT, SPT, TI>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(P.F * P.Z, P.NL, parts);
   k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 ? parts_buf : gbank, parts);
@@ -477,13 +478,13 @@ sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsign
   return launch_status();
 }
 
-template <int TX, int VB, int KSMAX, int SB>
+template <int TX, int VB, int KSMAX, int SB, class TB>
 sd_status launch_img_bwd(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
   using SM = BwdImgSmem<TX, VB, SB>;
   P.halo_w = TX + P.ks - 1;
   P.halo_h = RT_Y + P.ks - 1 + SB;
   size_t smem = SM::bytes(P.ks);
-  auto k = render_bwd_img_kernel<TX, VB, KSMAX, SB>;
+  auto k = render_bwd_img_kernel<TX, VB, KSMAX, SB, TB>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((P.W + TX - 1) / TX, (P.H + RT_Y - 1) / RT_Y, P.N * P.C);
   k<<<grid, SM::NT, smem, s>>>(P, gout, gaif);
@@ -510,7 +511,8 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
-  if (layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
+  if (layout->dtype != SD_F32 && layout->dtype != SD_BF16 && layout->dtype != SD_F16)
+    return SD_ERR_UNSUPPORTED;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
   if ((long long)P.F * P.Z > 65000) return SD_ERR_UNSUPPORTED;
   P.N = N;
@@ -518,6 +520,28 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   P.H = H;
   P.W = W;
   return SD_OK;
+}
+
+// 8-pixel segments: 16-pixel segments halve the shared atomics per FMA but
+// need ~240 registers (8 warps per SM) and measured slower
+template <class TB>
+sd_status launch_img_bwd_any(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
+  if (P.ks <= 65 && BwdImgSmem<128, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
+    return launch_img_bwd<128, 4, 65, 8, TB>(P, gout, gaif, s);
+  if (BwdImgSmem<64, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
+    return launch_img_bwd<64, 4, 127, 8, TB>(P, gout, gaif, s);
+  return launch_img_bwd<64, 2, 127, 8, TB>(P, gout, gaif, s);
+}
+
+template <class TI>
+sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const unsigned* bm,
+                              int words, int tx, int ty, float* gbank, float* parts_buf,
+                              int parts, cudaStream_t s) {
+  int KU = (P.ks + SEG - 1) / SEG * SEG;
+  int nstrip = P.ks * (KU / SEG);
+  if (nstrip <= 256 * 3)
+    return launch_bank_bwd<256, 3, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
+  return launch_bank_bwd<512, 4, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
 }
 
 }  // namespace sd
@@ -537,12 +561,15 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   return SD_OK;
 }
 
-sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const float* depth_m,
-                                const float* bank, const sd_bank_layout* layout, int N, int C,
-                                int H, int W, float* grad_aif, float* grad_bank,
-                                void* workspace, size_t workspace_bytes, void* stream) {
+sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const float* depth_m,
+                                const void* bank, const sd_bank_layout* layout, int N, int C,
+                                int H, int W, int image_dtype, float* grad_aif,
+                                float* grad_bank, void* workspace, size_t workspace_bytes,
+                                void* stream) {
   using namespace sd;
   if (!grad_out || !aif || !depth_m || !bank) return SD_ERR_ARG;
+  if (image_dtype != SD_F32 && image_dtype != SD_BF16 && image_dtype != SD_F16)
+    return SD_ERR_UNSUPPORTED;
   RenderParams P;
   sd_status st = setup_bwd(layout, N, C, H, W, P);
   if (st != SD_OK) return st;
@@ -557,15 +584,11 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const f
   }
   if (grad_aif) {
     SD_CUDA_TRY(cudaMemsetAsync(grad_aif, 0, (size_t)N * C * H * W * 4, s));
-    sd_status r;
-    // 8-pixel segments: 16-pixel segments halve the shared atomics per FMA
-    // but need ~240 registers (8 warps per SM) and measured slower
-    if (P.ks <= 65 && BwdImgSmem<128, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
-      r = launch_img_bwd<128, 4, 65, 8>(P, grad_out, grad_aif, s);
-    else if (BwdImgSmem<64, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
-      r = launch_img_bwd<64, 4, 127, 8>(P, grad_out, grad_aif, s);
-    else
-      r = launch_img_bwd<64, 2, 127, 8>(P, grad_out, grad_aif, s);
+    // the image pass reads the bank in its storage type
+    const int bt = layout->dtype;
+    sd_status r = bt == SD_F32    ? launch_img_bwd_any<float>(P, grad_out, grad_aif, s)
+                  : bt == SD_BF16 ? launch_img_bwd_any<__nv_bfloat16>(P, grad_out, grad_aif, s)
+                                  : launch_img_bwd_any<__half>(P, grad_out, grad_aif, s);
     if (r != SD_OK) return r;
   }
   if (grad_bank) {
@@ -586,14 +609,15 @@ sd_status sd_dp_render_backward(const float* grad_out, const float* aif, const f
     slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
     sd_status r = launch_status();
     if (r != SD_OK) return r;
-    int KU = (P.ks + SEG - 1) / SEG * SEG;
-    int nstrip = P.ks * (KU / SEG);
-    if (nstrip <= 256 * 3)
-      r = launch_bank_bwd<256, 3>(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf,
-                                  parts, s);
-    else
-      r = launch_bank_bwd<512, 4>(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf,
-                                  parts, s);
+    // the bank pass reads the image in its storage type
+    r = image_dtype == SD_F32
+            ? launch_bank_bwd_any<float>(P, grad_out, bm, (int)words, tx, ty, grad_bank,
+                                         parts_buf, parts, s)
+        : image_dtype == SD_BF16
+            ? launch_bank_bwd_any<__nv_bfloat16>(P, grad_out, bm, (int)words, tx, ty,
+                                                 grad_bank, parts_buf, parts, s)
+            : launch_bank_bwd_any<__half>(P, grad_out, bm, (int)words, tx, ty, grad_bank,
+                                          parts_buf, parts, s);
     if (r != SD_OK) return r;
   }
   return SD_OK;
@@ -655,6 +679,6 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
     st = noalloc_scratch(&ws);
     if (st != SD_OK) return st;
   }
-  return sd_dp_render_backward(grad_out, aif, depth_m, bank, layout, N, C, H, W, grad_aif,
-                               grad_bank, ws, NOALLOC_SCRATCH_BYTES, stream);
+  return sd_dp_render_backward(grad_out, aif, depth_m, bank, layout, N, C, H, W, SD_F32,
+                               grad_aif, grad_bank, ws, NOALLOC_SCRATCH_BYTES, stream);
 }

@@ -53,6 +53,31 @@ def test_backward_matches_oracle(sdlib, case):
     assert np.abs(got_b - ref_b).max() <= 1e-4 * np.abs(ref_b).max()
 
 
+@pytest.mark.parametrize("img_dt,bank_dt", [(torch.bfloat16, torch.bfloat16),
+                                             (torch.float32, torch.bfloat16),
+                                             (torch.float16, torch.float16)])
+def test_backward_low_precision_storage(sdlib, img_dt, bank_dt):
+    """BF16/FP16-stored image and bank: the adjoint of the render of the
+    rounded inputs, in FP32 arithmetic (same bound as FP32 storage against
+    the oracle run on the rounded values)."""
+    sd = sdlib
+    aif, depth, fh, dm, pitch, bank, G = setup(CASES[0], 21)
+    lay = sd.BankLayout(fh, dm, bank.shape[2], bank.shape[-1], pitch, dtype=bank_dt)
+    a = torch.tensor(aif, device="cuda").to(img_dt)
+    b = torch.tensor(bank, device="cuda").reshape(-1).to(bank_dt)
+    ga, gb = sd.dp_render_backward(torch.tensor(G, device="cuda"), a,
+                                   torch.tensor(depth, device="cuda"), b, lay)
+    torch.cuda.synchronize()
+    assert ga.dtype == torch.float32 and gb.dtype == torch.float32
+    a64 = a.float().cpu().numpy().astype(np.float64)
+    b64 = b.float().cpu().numpy().astype(np.float64).reshape(bank.shape)
+    ref_a, ref_b = O.render_bank_bwd(G, a64, depth, b64, fh, dm, pitch)
+    got_a = ga.cpu().numpy()
+    got_b = gb.cpu().numpy().reshape(ref_b.shape)
+    assert np.abs(got_a - ref_a).max() <= 1e-4 * np.abs(ref_a).max()
+    assert np.abs(got_b - ref_b).max() <= 1e-4 * np.abs(ref_b).max()
+
+
 def test_bank_gradient_deterministic_and_workspace_checked(sdlib):
     sd = sdlib
     aif, depth, fh, dm, pitch, bank, G = setup(CASES[0], 7)

@@ -223,6 +223,52 @@ def config_full_forward():
                 lambdas_nm=np.array(RGB_LAMBDAS_NM), n_grid=256, ks=65)
 
 
+def config_differentiation():
+    """Differentiation: the full-forward lens and bank grid at 128x128 pupil
+    samples; render backward over a batch of 8 RGB 512x512 images."""
+    c = config_full_forward()
+    c.update(n_grid=128, batch=8, image_hw=(512, 512))
+    return c
+
+
+def config_precision():
+    """Precision at full resolution: 64 field heights x 64 depths x 3
+    wavelengths of 65x65 PSFs (128x128 pupil samples), a batch of 16 RGB
+    2048x1536 images at 2 um pitch."""
+    pitch = 0.002
+    H, W = 2048, 1536
+    half_diag = 0.5 * math.hypot(H, W) * pitch
+    return dict(lens=doublet_pair_f18(), focus_mm=1000.0, pitch_mm=pitch,
+                field_h_mm=np.linspace(0.0, half_diag, 64),
+                depths_mm=inverse_uniform_depths(300.0, 3000.0, 64),
+                lambdas_nm=np.array(RGB_LAMBDAS_NM), n_grid=128, ks=65, batch=16,
+                image_hw=(H, W))
+
+
+def flip_batch(aif_bases, depth_bases, n):
+    """n (image, depth) pairs from a few base maps by flips and channel
+    rotations (cheap distinct members of a large batch): image i takes base
+    i % len, flip (i // 2) % 4 and channel rotation i // 8; its depth map
+    takes another base/flip combination."""
+    na, nd = len(aif_bases), len(depth_bases)
+    c = aif_bases[0].shape[0]
+    aif = np.empty((n,) + aif_bases[0].shape, dtype=aif_bases[0].dtype)
+    dep = np.empty((n,) + depth_bases[0].shape, dtype=depth_bases[0].dtype)
+
+    def flip(x, k):
+        if k & 1:
+            x = x[..., :, ::-1]
+        if k & 2:
+            x = x[..., ::-1, :]
+        return x
+
+    for i in range(n):
+        a = flip(aif_bases[i % na], (i // 2) % 4)
+        aif[i] = np.roll(a, (i // 8) % c, axis=0)
+        dep[i] = flip(depth_bases[(i // 2) % nd], (i + 1) % 4)
+    return aif, dep
+
+
 def random_requests(n_req, seed=3, n_lenses=2, field_max_mm=1.448,
                     d_near_mm=300.0, d_far_mm=3000.0):
     """Uneven requests: N log-uniform in [32, 512], ks uniform over
