@@ -125,13 +125,16 @@ def lens_info(table, focus_mm=1000.0, lambda_nm=587.5618, depth_mm=1000.0):
 
 
 def _req_rows(reqs):
-    """Structured request array (workloads.REQ_DTYPE) -> (n, 5) float64."""
-    r = np.zeros((len(reqs), 5))
+    """Structured request array (workloads.REQ_DTYPE) -> (n, 6) float64 rows
+    (h_mm, depth_mm, lambda_nm, n_grid, ks, v_mm); v_mm is 0 when absent."""
+    r = np.zeros((len(reqs), 6))
     r[:, 0] = reqs["h_mm"]
     r[:, 1] = reqs["depth_mm"]
     r[:, 2] = reqs["lambda_nm"]
     r[:, 3] = reqs["n_grid"]
     r[:, 4] = reqs["ks"]
+    if "v_mm" in reqs.dtype.names:
+        r[:, 5] = reqs["v_mm"]
     return r
 
 

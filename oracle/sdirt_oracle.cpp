@@ -435,14 +435,18 @@ Hit<T> trace_ray(const std::vector<Surf<T>>& L, double lam_um, Ray<T> r) {
 struct Request {
   double h_mm, depth_mm, lam_nm;
   int n_grid, ks;
+  double v_mm;  // image height along y (0 for field points on the +x axis)
 };
+
+// columns of one request row: h_mm, depth_mm, lambda_nm, n_grid, ks, v_mm
+constexpr int REQ_COLS = 6;
 
 struct Sensor {
   double ps, h, f, w, r;  // pixel pitch and DP structure (Eq. S1), all mm
 };
 
 struct RayGen {
-  double xo, z_ep, r_ep, z_start;
+  double xo, yo, z_ep, r_ep, z_start;
   double xc, yc;  // patch centre on the sensor
 };
 
@@ -460,15 +464,18 @@ RayGen ray_gen_setup(const std::vector<Surf<double>>& L, const Request& q) {
   double lam_um = q.lam_nm * 1e-3;
   Parax P = paraxial(L, lam_um, q.depth_mm);
   RayGen g{};
-  // reading: object height from the paraxial chief ray landing at (h, 0) on
-  // the sensor plane, so that the patch is centred on that landing point.
+  // reading: object point from the paraxial chief ray landing at (h, v) on
+  // the sensor plane, so that the patch is centred on that landing point
+  // (the lens is rotationally symmetric: both coordinates scale by the same
+  // chief-ray magnification).
   g.xo = q.h_mm / P.m_sensor;
+  g.yo = q.v_mm / P.m_sensor;
   g.z_ep = P.z_ep;
   g.r_ep = P.r_ep;
   double zf = front_z(L);
   g.z_start = (P.z_ep <= zf) ? P.z_ep : zf - 1.0;
   g.xc = q.h_mm;
-  g.yc = 0.0;
+  g.yc = q.v_mm;
   return g;
 }
 
@@ -477,7 +484,7 @@ Ray<T> make_ray(const RayGen& g, const Request& q, int ix, int iy) {
   int N = q.n_grid;
   double ex = (double)(2 * ix + 1 - N) / N * g.r_ep;
   double ey = (double)(2 * iy + 1 - N) / N * g.r_ep;
-  double px = g.xo, py = 0.0, pz = -q.depth_mm;
+  double px = g.xo, py = g.yo, pz = -q.depth_mm;
   double vx = ex - px, vy = ey - py, vz = g.z_ep - pz;
   double nv = std::sqrt(vx * vx + vy * vy + vz * vz);
   Ray<T> r;
@@ -661,6 +668,7 @@ Request req_from(const double* r) {
   q.lam_nm = r[2];
   q.n_grid = (int)r[3];
   q.ks = (int)r[4];
+  q.v_mm = r[5];
   return q;
 }
 
@@ -812,7 +820,7 @@ int or_trace_hits(const double* tab, int n, double focus_mm, const double* req,
   return 0;
 }
 
-// PSF bank: reqs[i*5..] = h_mm, depth_mm, lambda_nm, n_grid, ks; the PSFs are
+// PSF bank: reqs[i*REQ_COLS..] = h_mm, depth_mm, lambda_nm, n_grid, ks, v_mm; the PSFs are
 // written back to back ([2][ks][ks] each, in request order).  stats[i*8..]
 // = launched, reached, L, R, DP-missed, clipped, vignetted, other.
 int or_psf_bank(const double* tab, int n, double focus_mm, const double* reqs,
@@ -824,12 +832,12 @@ int or_psf_bank(const double* tab, int n, double focus_mm, const double* reqs,
   Sensor S = sensor_from(sensor);
   std::vector<size_t> off(n_req + 1, 0);
   for (int i = 0; i < n_req; ++i) {
-    int ks = (int)reqs[i * 5 + 4];
+    int ks = (int)reqs[i * REQ_COLS + 4];
     if (ks < 1 || ks % 2 == 0) return -4;
     off[i + 1] = off[i] + 2 * (size_t)ks * ks;
   }
   parallel_for(n_req, n_threads, [&](int i) {
-    Request q = req_from(reqs + i * 5);
+    Request q = req_from(reqs + i * REQ_COLS);
     psf_request(L, S, q, mode, bank + off[i], stats + i * N_STATS);
     normalise(bank + off[i], q.ks, norm, stats[i * N_STATS + ST_LAUNCHED]);
   });
@@ -854,7 +862,7 @@ int or_trace_functional(const double* tab, int n, double focus_mm,
   double total = 0.0;
   size_t goff = 0;
   for (int i = 0; i < n_req; ++i) {
-    Request q = req_from(reqs + i * 5);
+    Request q = req_from(reqs + i * REQ_COLS);
     RayGen g = ray_gen_setup(L0, q);
     double lam_um = q.lam_nm * 1e-3;
     int N = q.n_grid, ks = q.ks;
@@ -903,12 +911,12 @@ int or_trace_grad(const double* tab, int n, double focus_mm, const double* reqs,
   Sensor S = sensor_from(sensor);
   std::vector<size_t> goff(n_req + 1, 0);
   for (int i = 0; i < n_req; ++i) {
-    int ks = (int)reqs[i * 5 + 4];
+    int ks = (int)reqs[i * REQ_COLS + 4];
     goff[i + 1] = goff[i] + 2 * (size_t)ks * ks;
   }
   std::vector<double> part((size_t)n_req * ND, 0.0);
   parallel_for(n_req, n_threads, [&](int i) {
-    Request q = req_from(reqs + i * 5);
+    Request q = req_from(reqs + i * REQ_COLS);
     RayGen g = ray_gen_setup(L0, q);
     double lam_um = q.lam_nm * 1e-3;
     int N = q.n_grid, ks = q.ks, p = (ks - 1) / 2;

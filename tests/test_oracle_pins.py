@@ -389,3 +389,67 @@ def test_trace_functional_at_zero_matches_bank():
     psf, _ = O.psf_bank(tab, 1000.0, reqs, S, O.MODE_BILINEAR, O.NORM_PER_RAY)
     val = O.trace_functional(tab, 1000.0, reqs, S, G, freeze=True)
     assert val == pytest.approx(float((G[0] * psf[0]).sum()), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# 2-D field points (per-pixel PSF maps): the lens is rotationally symmetric,
+# so the trace must commute with rotations of the field point that map the
+# square pupil grid onto itself, and with the mirror x -> -x.
+# --------------------------------------------------------------------------
+def _req2d(h, v, depth, lam, n, ks):
+    r = np.zeros(1, dtype=W.REQ_DTYPE)
+    r["h_mm"], r["v_mm"], r["depth_mm"], r["lambda_nm"] = h, v, depth, lam
+    r["n_grid"], r["ks"] = n, ks
+    return r
+
+
+def _sorted_rows(*cols):
+    a = np.stack(cols, 1)
+    return a[np.lexsort(a.T[::-1])]
+
+
+@pytest.mark.parametrize("lens", ["doublet", "rf50"])
+def test_quarter_turn_of_field_point_rotates_hits(lens):
+    """Field point (0, rho) traces the quarter-turned rays of (rho, 0): the
+    cell-centred pupil grid is invariant under a quarter turn, so the hit
+    sets agree as sets: (x, y, dx, dy) -> (-y, x, -dy, dx)."""
+    if lens == "doublet":
+        tab, focus, ps, rho = W.doublet_pair_f18(), 1000.0, 0.002, 0.9
+    else:
+        tab, focus, ps, rho = W.canon_rf50(), 1000.0, 36.0 / 768, 9.0
+    S = dp_sensor(ps)
+    a = O.trace_hits(tab, focus, _req2d(rho, 0.0, 700.0, 587.5618, 32, 21)[0], S)
+    b = O.trace_hits(tab, focus, _req2d(0.0, rho, 700.0, 587.5618, 32, 21)[0], S)
+    ok_a, ok_b = a["state"] == 0, b["state"] == 0
+    assert ok_a.sum() == ok_b.sum() > 0
+    ra = _sorted_rows(-a["y"][ok_a], a["x"][ok_a], -a["dy"][ok_a], a["dx"][ok_a])
+    rb = _sorted_rows(b["x"][ok_b], b["y"][ok_b], b["dx"][ok_b], b["dy"][ok_b])
+    np.testing.assert_allclose(ra, rb, rtol=0, atol=1e-9)
+
+
+def test_mirrored_field_point_swaps_left_and_right():
+    """Field point (-h, v) is the x-mirror of (h, v): every ray is mirrored
+    exactly (the pupil grid is symmetric and the arithmetic is odd in x), so
+    L(a, b) at (-h, v) = R(ks-1-a, b) at (h, v) in integer counts (Eq. 1/2:
+    s changes sign under the mirror)."""
+    tab, ps = W.doublet_pair_f18(), 0.002
+    S = dp_sensor(ps)
+    for h, v, d in [(0.6, 0.0, 950.0), (0.5, -0.3, 1050.0), (1.2, 0.7, 1000.0)]:
+        reqs = np.concatenate([_req2d(h, v, d, 587.5618, 64, 31),
+                               _req2d(-h, v, d, 587.5618, 64, 31)])
+        (p, q), st = O.psf_bank(tab, 1000.0, reqs, S, O.MODE_HARD, O.NORM_NONE)
+        assert p.sum() > 100
+        np.testing.assert_array_equal(q[0], p[1][:, ::-1])
+        np.testing.assert_array_equal(q[1], p[0][:, ::-1])
+        np.testing.assert_array_equal(st[0], st[1][[0, 1, 3, 2, 4, 5, 6, 7]])
+
+
+def test_v_zero_row_equals_axis_field_point():
+    """A request with v_mm = 0 is the radial-bank request (same PSF)."""
+    cfg = W.config_singlet()
+    S = dp_sensor(cfg["pitch_mm"])
+    r1 = W.bank_grid([0.05], [800.0], [587.5618], 64, 31)
+    r2 = _req2d(0.05, 0.0, 800.0, 587.5618, 64, 31)
+    (p1,), _ = O.psf_bank(cfg["lens"], 1000.0, r1, S)
+    (p2,), _ = O.psf_bank(cfg["lens"], 1000.0, r2, S)
+    np.testing.assert_array_equal(p1, p2)

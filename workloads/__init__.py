@@ -180,7 +180,7 @@ def _table(rows):
 # sensor along +x.
 # --------------------------------------------------------------------------
 REQ_DTYPE = np.dtype([("h_mm", "f8"), ("depth_mm", "f8"), ("lambda_nm", "f8"),
-                      ("n_grid", "i4"), ("ks", "i4"), ("lens", "i4")])
+                      ("n_grid", "i4"), ("ks", "i4"), ("lens", "i4"), ("v_mm", "f8")])
 
 
 def bank_grid(field_h_mm, depths_mm, lambdas_nm, n_grid, ks):
@@ -189,7 +189,7 @@ def bank_grid(field_h_mm, depths_mm, lambdas_nm, n_grid, ks):
     for h in field_h_mm:
         for d in depths_mm:
             for lam in lambdas_nm:
-                reqs.append((h, d, lam, n_grid, ks, 0))
+                reqs.append((h, d, lam, n_grid, ks, 0, 0.0))
     return np.array(reqs, dtype=REQ_DTYPE)
 
 
@@ -267,6 +267,38 @@ def flip_batch(aif_bases, depth_bases, n):
         aif[i] = np.roll(a, (i // 8) % c, axis=0)
         dep[i] = flip(depth_bases[(i // 2) % nd], (i + 1) % 4)
     return aif, dep
+
+
+def pixel_centres_mm(rows, cols, H, W, pitch_mm):
+    """Sensor-plane coordinates (x along columns, y along rows) of pixel
+    centres relative to the sensor centre (= the optical axis)."""
+    x = (np.asarray(cols, dtype=np.float64) - 0.5 * (W - 1)) * pitch_mm
+    y = (np.asarray(rows, dtype=np.float64) - 0.5 * (H - 1)) * pitch_mm
+    return x, y
+
+
+def map_requests(depth_m, rows, cols, pitch_mm, lambda_nm, n_grid, ks):
+    """Requests of a per-pixel PSF map: one per listed pixel (rows, cols) of
+    the (H, W) depth map, at the pixel's 2-D sensor position and depth."""
+    H, W = depth_m.shape
+    x, y = pixel_centres_mm(rows, cols, H, W, pitch_mm)
+    out = np.zeros(len(x), dtype=REQ_DTYPE)
+    out["h_mm"], out["v_mm"] = x, y
+    out["depth_mm"] = depth_m[np.asarray(rows), np.asarray(cols)].astype(np.float64) * 1000.0
+    out["lambda_nm"], out["n_grid"], out["ks"] = lambda_nm, n_grid, ks
+    return out
+
+
+def config_paper_rf50():
+    """The paper's own timed workload (Sec. 4 implementation details, Table
+    S3): Canon RF50mm (Table S1) stopped down to F/4, 550 nm, focus 1 m, a
+    24 x 36 mm DP sensor of 512 x 768 pixels, a DP PSF for every pixel of a
+    depth map over 0.5-20 m, a 64 x 64 pupil grid (4096 samples) and 21 x 21
+    patches."""
+    H, W = 512, 768
+    return dict(lens=canon_rf50(), f_number=4.0, lambda_nm=550.0, focus_mm=1000.0,
+                pitch_mm=36.0 / W, sensor_hw=(H, W), n_grid=64, ks=21,
+                d_near_m=0.5, d_far_m=20.0)
 
 
 def random_requests(n_req, seed=3, n_lenses=2, field_max_mm=1.448,
