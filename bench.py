@@ -382,6 +382,7 @@ def run_ours(args, world, rank, local, dist):
     if rank == 0 and not args.no_extra:
         line["differentiation_pipeline"] = pipeline_compare(sd, dev)
         line["precision"] = precision_compare(sd, dev)
+        line["paper_workload"] = paper_workload(sd, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
@@ -452,7 +453,7 @@ def batched_compare(sd, dev, reps=5):
         for i in range(n_req):
             o = L.SdTraceOpts(0, L.SD_NORM_JOINT, 0, 0, int(ks[i]), int(ns[i]))
             L.check(lib.sd_dp_psf_trace(handles, 2, ctypes.byref(sen),
-                                        ctypes.c_void_p(base_req + 48 * i), 1, ctypes.byref(o),
+                                        ctypes.c_void_p(base_req + L.REQUEST_DTYPE.itemsize * i), 1, ctypes.byref(o),
                                         ctypes.c_void_p(base_out), ctypes.c_void_p(base_st + 64 * i),
                                         api._stream()), "sd_dp_psf_trace")
 
@@ -646,6 +647,56 @@ def pipeline_compare(sd, dev, reps=5):
             "bank_l1_vs_oracle": {"f32": {"mean": e32[0], "max": e32[1]},
                                   "bf16": {"mean": e16[0], "max": e16[1]},
                                   "sample": "24 evenly spaced requests, FP64 oracle"}}
+
+
+PAPER_TRACE_S = 801.544   # DP PSF map of 512 x 768 pixels by ray tracing (Table S3)
+PAPER_RENDER_S = 0.2      # DP image from a PSF map ("fixed cost", supplement)
+
+
+def paper_workload(sd, dev, reps=5):
+    """The paper's own timed path (Sec. 4 implementation details, Table S3):
+    RF50 (Table S1) at F/4, 550 nm, focus 1 m, a DP PSF for every pixel of a
+    512 x 768 depth map over 0.5-20 m (64 x 64 pupil grid = 4096 samples,
+    21 x 21 patches), then the DP render of a 512 x 768 RGB image from that
+    map.  The paper's times (its i7-12700K + RTX 3090) are context."""
+    import torch
+    c = W.config_paper_rf50()
+    H, Wd = c["sensor_hw"]
+    tab = sd.f_number_table(c["lens"], c["f_number"], c["lambda_nm"], c["focus_mm"])
+    lens = sd.Lens(tab, c["focus_mm"])
+    sensor = sd.DPSensor(c["pitch_mm"])
+    depth = torch.tensor(W.depth_perlin(1, H, Wd, seed=8, d_near_m=c["d_near_m"],
+                                        d_far_m=c["d_far_m"])[0].astype(np.float32), device=dev)
+    aif = torch.tensor(W.aif_pink(1, 3, H, Wd, seed=9).astype(np.float32), device=dev)
+    stream = torch.cuda.current_stream()
+    ks, n = c["ks"], c["n_grid"]
+    res = {"lens": "RF50 (Table S1) at F/4", "lambda_nm": c["lambda_nm"],
+           "map": [H, Wd, 2, ks, ks], "pupil_grid": [n, n], "depth_m": [0.5, 20.0],
+           "paper_trace_s": PAPER_TRACE_S, "paper_render_s": PAPER_RENDER_S,
+           "paper_hardware": "i7-12700K + RTX 3090 (context, not the target)"}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        pmap = torch.empty((H, Wd, 2, ks, ks), dtype=dt, device=dev)
+        stats = torch.zeros((H * Wd, 8), dtype=torch.int64, device=dev)
+        img = aif if dt == torch.float32 else aif.to(dt)
+        out = torch.empty((1, 6, H, Wd), dtype=dt, device=dev)
+        t_tr = _timed(lambda: sd.dp_psf_map(lens, sensor, depth, c["lambda_nm"], n, ks,
+                                            out=pmap, stats=stats), stream, reps)
+        t_rd = _timed(lambda: sd.dp_render_map(img, pmap, out=out), stream, reps)
+        rays = int(stats[:, 0].sum().item())
+        map_bytes = pmap.numel() * pmap.element_size()
+        io_bytes = img.numel() * img.element_size() + out.numel() * out.element_size()
+        res[name] = {"trace_ms": round(t_tr, 3), "render_ms": round(t_rd, 4),
+                     "psfs_per_s": round(H * Wd / (t_tr * 1e-3), 1),
+                     "rays": rays, "grays_s": round(rays / (t_tr * 1e-3) / 1e9, 3),
+                     "render_gbs": round((map_bytes + io_bytes) / (t_rd * 1e-3) / 1e9, 1),
+                     "trace_speedup_vs_paper": round(PAPER_TRACE_S / (t_tr * 1e-3), 1),
+                     "render_speedup_vs_paper": round(PAPER_RENDER_S / (t_rd * 1e-3), 1)}
+        del pmap, out
+    peaks = load_peaks()
+    if peaks.get("hbm_gbs"):
+        res["render_hbm_frac_f32"] = round(res["f32"]["render_gbs"] / peaks["hbm_gbs"], 3)
+    lens.free()
+    return res
 
 
 def cpu_threads():

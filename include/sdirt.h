@@ -124,13 +124,15 @@ typedef struct sd_dp_sensor {
 } sd_dp_sensor;
 
 /* ------------------------------------------------------------------------
- * PSF requests.  One request = one object point p: the field height h_mm is
- * the image height on the sensor (along +x) at which the paraxial chief ray
- * lands; the object sits at depth_mm in front of surface 0 at the object
- * height that makes this so.  Rays: N x N cell-centred samples on the
- * entrance-pupil square kept inside the pupil disc (exactly: (2i+1-N)^2 +
- * (2j+1-N)^2 <= N^2).  The PSF patch [2][ks][ks] (L plane then R plane, row
- * index along +y, column along +x) is centred on (h_mm, 0).
+ * PSF requests.  One request = one object point p (Sec. 3.1): (h_mm, v_mm)
+ * is the point of the sensor plane (x, y, relative to the optical axis) at
+ * which the paraxial chief ray lands; the object sits at depth_mm in front of
+ * surface 0 at the object point that makes this so (a radial bank uses
+ * v_mm = 0; a per-pixel PSF map uses every pixel's 2-D position).  Rays:
+ * N x N cell-centred samples on the entrance-pupil square kept inside the
+ * pupil disc (exactly: (2i+1-N)^2 + (2j+1-N)^2 <= N^2).  The PSF patch
+ * [2][ks][ks] (L plane then R plane, row index along +y, column along +x) is
+ * centred on (h_mm, v_mm).
  * ---------------------------------------------------------------------- */
 typedef struct sd_psf_request {
   double h_mm;
@@ -141,7 +143,8 @@ typedef struct sd_psf_request {
   int32_t lens;        /* index into the lens array of the call */
   int32_t reserved;
   int64_t out_offset;  /* element offset of this PSF pair in the output */
-} sd_psf_request;      /* 48 bytes, device-resident */
+  double v_mm;         /* image height along y (0 for field points on +x) */
+} sd_psf_request;      /* 56 bytes, device-resident */
 
 enum { SD_BIN_HARD = 0, SD_BIN_BILINEAR = 1 };
 enum { SD_NORM_NONE = 0, SD_NORM_JOINT = 1, SD_NORM_SEPARATE = 2,
@@ -186,6 +189,23 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
                           const sd_psf_request* req, int n_req,
                           const sd_trace_opts* opts, void* out,
                           int64_t* stats, void* stream);
+
+/*
+ * Per-pixel DP PSF map (Sec. 4 implementation details; Table S3 times it):
+ * one PSF pair for every pixel of an H x W depth map, the object point of
+ * pixel (row, col) on the paraxial chief ray through the pixel centre
+ * ((col - (W-1)/2) * pitch, (row - (H-1)/2) * pitch) at that pixel's depth
+ * (depth_m, device, H x W FP32 metres), one wavelength and one lens.  Writes
+ * out (device) as [H][W][2][ks][ks] in opts->out_dtype (the map layout the
+ * supplement's render takes) and stats (device, nullable) as
+ * [H*W][SD_N_STATS].  The same kernel as sd_dp_psf_trace with the request of
+ * each block built on the device; opts->max_ks and max_n_grid are ignored
+ * (ks and n_grid size everything).  pitch is the sensor's pixel pitch.
+ */
+sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
+                        const float* depth_m, int H, int W, double lambda_nm,
+                        int n_grid, int ks, const sd_trace_opts* opts, void* out,
+                        int64_t* stats, void* stream);
 
 /*
  * Adjoint of sd_dp_psf_trace in bilinear mode (SD_BIN_BILINEAR) with a
@@ -311,6 +331,21 @@ typedef struct sd_bank_layout {
 sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
                        const sd_bank_layout* layout, int N, int C, int H,
                        int W, int image_dtype, void* out, void* stream);
+
+/*
+ * Render from a per-pixel PSF map (supplement, "Local DP PSF convolution":
+ * the listing's form, one kernel pair per pixel shared by all channels):
+ *   out_L[n,c,y,x] = sum_{u,v} Ipad[n,c,y+u,x+v] map[y][x][0][ks-1-u][ks-1-v]
+ * (R with plane 1), Ipad replicate-padded by (ks-1)/2.  aif (N,C,H,W) and out
+ * (N,2C,H,W) in image_dtype; psf_map [H][W][2][ks][ks] in map_dtype (the
+ * layout sd_dp_psf_map writes); all device.  Accumulation FP32,
+ * deterministic.  Storage pairs as sd_dp_render (F32/F32, F32/BF16,
+ * BF16/BF16, F16/F16, F32/F16 for image/map); others return
+ * SD_ERR_UNSUPPORTED, as do ks > 127.
+ */
+sd_status sd_dp_render_map(const void* aif, const void* psf_map, int N, int C,
+                           int H, int W, int ks, int image_dtype, int map_dtype,
+                           void* out, void* stream);
 
 /*
  * Adjoint of sd_dp_render (bank mode): given grad_out (N,2C,H,W) FP32 writes

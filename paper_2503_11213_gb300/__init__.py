@@ -4,9 +4,9 @@ Ray trace of a lens, DP PSF binning and per-pixel DP rendering run in the
 CUDA library built from csrc/ (C ABI in include/sdirt.h); this package only
 marshals PyTorch tensors into that ABI.
 """
-from .api import (BankLayout, BatchedTrace, DPSensor, Lens, dp_psf_trace, dp_psf_trace_backward,  # noqa: F401
-                  dp_render, dp_render_backward, make_requests, render_backward_workspace,
-                  trace_hits)
+from .api import (BankLayout, BatchedTrace, DPSensor, Lens, dp_psf_map, dp_psf_trace,  # noqa: F401
+                  dp_psf_trace_backward, dp_render, dp_render_backward, dp_render_map,
+                  f_number_table, make_requests, render_backward_workspace, trace_hits)
 from .autograd import (DPRenderFunction, DPTraceFunction, dp_psf_trace_autograd,  # noqa: F401
                        dp_render_autograd)
 from ._lib import (SD_BF16, SD_BIN_BILINEAR, SD_BIN_HARD, SD_F16, SD_F32, SD_NORM_JOINT,  # noqa: F401

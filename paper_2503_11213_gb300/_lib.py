@@ -60,18 +60,18 @@ class SdBatchConfig(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-# sd_psf_request as a numpy record (48 bytes, device-resident array)
+# sd_psf_request as a numpy record (56 bytes, device-resident array)
 REQUEST_DTYPE = np.dtype([("h_mm", "<f8"), ("depth_mm", "<f8"), ("lambda_nm", "<f8"),
                           ("n_grid", "<i4"), ("ks", "<i4"), ("lens", "<i4"),
-                          ("reserved", "<i4"), ("out_offset", "<i8")])
-assert REQUEST_DTYPE.itemsize == 48
+                          ("reserved", "<i4"), ("out_offset", "<i8"), ("v_mm", "<f8")])
+assert REQUEST_DTYPE.itemsize == 56
 
 # every exported symbol of include/sdirt.h
 EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
            "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_psf_trace_batched",
            "sd_dp_psf_trace_batched_workspace", "sd_dp_psf_trace_batched_tune",
-           "sd_dp_trace_hits",
-           "sd_dp_render", "sd_dp_render_backward",
+           "sd_dp_trace_hits", "sd_dp_psf_map",
+           "sd_dp_render", "sd_dp_render_map", "sd_dp_render_backward",
            "sd_dp_render_backward_workspace", "sd_dp_render_backward_noalloc",
            "sd_status_string", "sd_last_cuda_error",
            "sd_version")
@@ -122,6 +122,9 @@ def lib():
                                                vp, ll, vp, vp, ctypes.c_size_t, vp,
                                                ctypes.c_char_p, P(SdBatchConfig)]
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
+    L.sd_dp_psf_map.argtypes = [vp, P(SdSensor), vp, i32, i32, dbl, i32, i32, P(SdTraceOpts),
+                                vp, vp, vp]
+    L.sd_dp_render_map.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,
                                         i32, vp, vp, vp, ctypes.c_size_t, vp]

@@ -103,8 +103,9 @@ def make_requests(reqs, ks_offsets=True, device="cuda"):
     rec = np.zeros(n, dtype=L.REQUEST_DTYPE)
     for f in ("h_mm", "depth_mm", "lambda_nm", "n_grid", "ks"):
         rec[f] = reqs[f]
-    if "lens" in reqs.dtype.names:
-        rec["lens"] = reqs["lens"]
+    for f in ("lens", "v_mm"):
+        if f in reqs.dtype.names:
+            rec[f] = reqs[f]
     sizes = 2 * rec["ks"].astype(np.int64) ** 2
     off = np.zeros(n, dtype=np.int64)
     off[1:] = np.cumsum(sizes)[:-1]
@@ -152,6 +153,59 @@ def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, ma
                                              _ptr(grad_out), _ptr(grad_req), _ptr(grad_lens),
                                              _stream()), "sd_dp_psf_trace_backward")
     return grad_req, grad_lens
+
+
+def dp_psf_map(lens: Lens, sensor: DPSensor, depth_m, lambda_nm, n_grid, ks,
+               mode=L.SD_BIN_HARD, norm=L.SD_NORM_JOINT, dtype=torch.float32, out=None,
+               stats=None, newton_iters=0):
+    """Per-pixel DP PSF map of an (H, W) depth map (metres, float32, CUDA):
+    (map (H, W, 2, ks, ks) in dtype, stats (H*W, 8))."""
+    H, W = depth_m.shape
+    dev = depth_m.device
+    if out is None:
+        out = torch.empty((H, W, 2, ks, ks), dtype=dtype, device=dev)
+    if stats is None:
+        stats = torch.zeros((H * W, L.SD_N_STATS), dtype=torch.int64, device=dev)
+    _need_cuda(depth_m, out, stats)
+    if depth_m.dtype != torch.float32:
+        raise ValueError("depth must be float32 metres")
+    opts = L.SdTraceOpts(mode, norm, _DT[out.dtype], newton_iters, ks, n_grid)
+    sen = sensor.c()
+    L.check(L.lib().sd_dp_psf_map(lens.handle, ctypes.byref(sen), _ptr(depth_m), H, W,
+                                  float(lambda_nm), int(n_grid), int(ks), ctypes.byref(opts),
+                                  _ptr(out), _ptr(stats), _stream()), "sd_dp_psf_map")
+    return out, stats
+
+
+def dp_render_map(aif, psf_map, out=None):
+    """aif (N,C,H,W) f32/bf16/f16 and a PSF map (H,W,2,ks,ks) -> DP image
+    (N,2C,H,W) in aif's dtype (one kernel pair per pixel for all channels)."""
+    N, C, H, W = aif.shape
+    ks = psf_map.shape[-1]
+    if tuple(psf_map.shape) != (H, W, 2, ks, ks):
+        raise ValueError("psf_map must be (H, W, 2, ks, ks)")
+    if out is None:
+        out = torch.empty((N, 2 * C, H, W), dtype=aif.dtype, device=aif.device)
+    _need_cuda(aif, psf_map, out)
+    L.check(L.lib().sd_dp_render_map(_ptr(aif), _ptr(psf_map), N, C, H, W, ks, _DT[aif.dtype],
+                                     _DT[psf_map.dtype], _ptr(out), _stream()),
+            "sd_dp_render_map")
+    return out
+
+
+def f_number_table(table, f_number, lambda_nm=587.5618, focus_mm=1000.0):
+    """A copy of a lens table with the stop's semi-diameter scaled so that
+    EFL / (2 r_EP) = f_number at lambda_nm (paraxial; the entrance-pupil
+    radius is proportional to the stop radius)."""
+    tab = np.array(table, dtype=np.float64, copy=True)
+    lens = Lens(tab, focus_mm)
+    try:
+        px = lens.paraxial(lambda_nm, focus_mm)
+    finally:
+        lens.free()
+    stop = int(np.nonzero(tab[:, 0] == L.SD_SURF_STOP)[0][0])
+    tab[stop, 5] *= (px["efl"] / (2.0 * f_number)) / px["r_ep"]
+    return tab
 
 
 def batched_workspace_bytes(n_req, total):
@@ -209,6 +263,8 @@ def trace_hits(lens: Lens, sensor: DPSensor, req, device="cuda"):
     q = np.zeros(1, dtype=L.REQUEST_DTYPE)
     for f in ("h_mm", "depth_mm", "lambda_nm", "n_grid", "ks"):
         q[f] = req[f]
+    if "v_mm" in req.dtype.names:
+        q["v_mm"] = req["v_mm"]
     n = int(req["n_grid"])
     rec = torch.zeros((n * n, 8), dtype=torch.float32, device=device)
     cnt = torch.zeros(1, dtype=torch.int32, device=device)

@@ -82,6 +82,7 @@ __host__ __device__ inline PYU parax(const DevLens& L, const double* nlam,
 }
 
 struct RayGen {
+  double m;        // chief-ray magnification onto the sensor plane
   double x_o;      // object height (mm), object at z = -depth
   double z_ep, r_ep;
   double z_start;  // plane where rays start
@@ -99,6 +100,7 @@ __host__ __device__ inline RayGen ray_gen(const DevLens& L, const double* nlam,
   g.r_ep = fabs(L.sd_stop / a.y);
   double u0 = -1.0 / (g.z_ep + depth_mm);
   PYU c = parax(L, nlam, 1.0 + u0 * depth_mm, u0, 0, L.n);
+  g.m = c.y;
   g.x_o = h_mm / c.y;
   g.z_start = (g.z_ep <= L.z_front) ? g.z_ep : L.z_front - 1.0;
   return g;
@@ -347,11 +349,18 @@ enum { ST_OK = 0, ST_MISS = 1, ST_CLIP = 2, ST_TIR = 3, ST_NEWTON = 4, ST_BACK =
 
 struct SensorF {
   float ps, inv_ps, h, w, r2, fh;  // fh = (f - h) / f
+  double ps_d;                     // pitch in FP64 (pixel positions of a map)
 };
 
 struct TraceParams {
   const sd_psf_request* req;
   int n_req;
+  // per-pixel PSF map mode (req == nullptr): request r is pixel r of the
+  // map_H x map_W depth map (metres), at its sensor position
+  const float* map_depth;
+  int map_H, map_W;
+  double map_lambda_nm;
+  int map_n, map_ks;
   int slots[SD_MAX_LENSES];
   int n_lenses;
   SensorF sen;
@@ -369,7 +378,8 @@ struct TraceParams {
 
 // Per-request context computed by the block prologue.
 struct ReqCtx {
-  float x_o, scale;     // object height; pupil sample spacing r_ep / N
+  float x_o, y_o;       // object point (x, y)
+  float scale;          // pupil sample spacing r_ep / N
   float vz;             // z_ep + depth (axial length from p to the EP plane)
   float z_start, s_start, z_ep;
   float xc, yc;
@@ -398,6 +408,26 @@ __device__ __forceinline__ void row_span(int N, int iy, int* cnt, int* lo) {
   *lo = (N - 1 - am) >> 1;
 }
 
+// Request r of the launch: from the request array, or in map mode built
+// for pixel r of the depth map (image position of the pixel centre relative
+// to the sensor centre, the pixel's depth, PSF at offset r * 2 ks^2).
+__device__ __forceinline__ sd_psf_request request_of(const TraceParams& P, int r) {
+  if (!P.map_depth) return P.req[r];
+  sd_psf_request q;
+  const int row = r / P.map_W, col = r - row * P.map_W;
+  const double ps = (double)P.sen.ps_d;
+  q.h_mm = ((double)col - 0.5 * (double)(P.map_W - 1)) * ps;
+  q.v_mm = ((double)row - 0.5 * (double)(P.map_H - 1)) * ps;
+  q.depth_mm = (double)P.map_depth[r] * 1000.0;
+  q.lambda_nm = P.map_lambda_nm;
+  q.n_grid = P.map_n;
+  q.ks = P.map_ks;
+  q.lens = 0;
+  q.reserved = 0;
+  q.out_offset = (long long)r * 2 * P.map_ks * P.map_ks;
+  return q;
+}
+
 // Block prologue: paraxial set-up (FP64, thread 0) and pupil row tables.
 __device__ void setup_request(const TraceParams& P, const sd_psf_request& q,
                               ReqCtx& ctx, int* prefix, int* lo) {
@@ -420,13 +450,14 @@ __device__ void setup_request(const TraceParams& P, const sd_psf_request& q,
       }
       RayGen g = ray_gen(L, nlam, q.h_mm, q.depth_mm);
       ctx.x_o = (float)g.x_o;
+      ctx.y_o = (float)(q.v_mm / g.m);
       ctx.scale = (float)(g.r_ep / q.n_grid);
       ctx.vz = (float)(g.z_ep + q.depth_mm);
       ctx.z_ep = (float)g.z_ep;
       ctx.z_start = (float)g.z_start;
       ctx.s_start = (float)((g.z_start + q.depth_mm) / (g.z_ep + q.depth_mm));
       ctx.xc = (float)q.h_mm;
-      ctx.yc = 0.f;
+      ctx.yc = (float)q.v_mm;
       ctx.slot = slot;
       ctx.N = q.n_grid;
       ctx.ks = q.ks;
@@ -638,7 +669,7 @@ __device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, c
   int ix = lo[iy] + (k - prefix[iy]);
   float ex = (float)(2 * ix + 1 - N) * ctx.scale;
   float ey = (float)(2 * iy + 1 - N) * ctx.scale;
-  float vx = ex - ctx.x_o, vy = ey, vz = ctx.vz;
+  float vx = ex - ctx.x_o, vy = ey - ctx.y_o, vz = ctx.vz;
   float inv = rsqrt_refined(vx * vx + vy * vy + vz * vz);
   dx = vx * inv;
   dy = vy * inv;
@@ -648,7 +679,7 @@ __device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, c
     y = ey;
   } else {
     x = fmaf(ctx.s_start, vx, ctx.x_o);
-    y = ctx.s_start * vy;
+    y = fmaf(ctx.s_start, vy, ctx.y_o);
   }
   z = ctx.z_start;
 }
@@ -676,7 +707,7 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
   float* patchf = reinterpret_cast<float*>(patch);
 
   const int r = blockIdx.x;
-  const sd_psf_request q = P.req[r];
+  const sd_psf_request q = request_of(P, r);
   if (threadIdx.x < SD_N_STATS) s_stats[threadIdx.x] = 0;
   setup_request(P, q, ctx, prefix, lo);
   const int ks = ctx.ks, ks2 = ks * ks, p = (ks - 1) >> 1;
@@ -853,6 +884,7 @@ sd_status fill_params(TraceParams& P, const sd_lens* const* lenses, int n_lenses
       s.r_mm < 0)
     return SD_ERR_ARG;
   P.sen.ps = (float)s.pitch_mm;
+  P.sen.ps_d = s.pitch_mm;
   P.sen.inv_ps = (float)(1.0 / s.pitch_mm);
   P.sen.h = (float)s.h_mm;
   P.sen.w = (float)s.w_mm;
@@ -900,6 +932,57 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
     SD_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)smem));                                   \
     kfn<<<n_req, threads, smem, s>>>(P);                                            \
+  } while (0)
+  if (opts->mode == SD_BIN_HARD) {
+    if (opts->out_dtype == SD_F32) SD_LAUNCH(0, float);
+    else if (opts->out_dtype == SD_BF16) SD_LAUNCH(0, __nv_bfloat16);
+    else SD_LAUNCH(0, __half);
+  } else {
+    if (opts->out_dtype == SD_F32) SD_LAUNCH(1, float);
+    else if (opts->out_dtype == SD_BF16) SD_LAUNCH(1, __nv_bfloat16);
+    else SD_LAUNCH(1, __half);
+  }
+#undef SD_LAUNCH
+  return launch_status();
+}
+
+sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
+                        const float* depth_m, int H, int W, double lambda_nm,
+                        int n_grid, int ks, const sd_trace_opts* opts, void* out,
+                        int64_t* stats, void* stream) {
+  using namespace sd;
+  if (!lens || !opts || !out || !depth_m || H < 0 || W < 0) return SD_ERR_ARG;
+  if ((long long)H * W > 0x7fffffffLL) return SD_ERR_UNSUPPORTED;
+  if (H == 0 || W == 0) return SD_OK;
+  if (!(lambda_nm > 0) || n_grid < 2 || ks < 1 || !(ks & 1)) return SD_ERR_ARG;
+  if (ks > 127 || n_grid > 2048) return SD_ERR_UNSUPPORTED;
+  if (opts->mode != SD_BIN_HARD && opts->mode != SD_BIN_BILINEAR) return SD_ERR_ARG;
+  if (opts->out_dtype < SD_F32 || opts->out_dtype > SD_F16) return SD_ERR_ARG;
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  const sd_lens* ls[1] = {lens};
+  sd_status st = fill_params(P, ls, 1, sensor, opts);
+  if (st != SD_OK) return st;
+  P.req = nullptr;
+  P.n_req = H * W;
+  P.map_depth = depth_m;
+  P.map_H = H;
+  P.map_W = W;
+  P.map_lambda_nm = lambda_nm;
+  P.map_n = n_grid;
+  P.map_ks = ks;
+  P.max_n = n_grid;
+  P.max_ks = ks;
+  P.out = out;
+  P.stats = reinterpret_cast<long long*>(stats);
+  size_t smem = trace_smem_bytes(n_grid, ks);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+#define SD_LAUNCH(MODE, T)                                                          \
+  do {                                                                              \
+    auto kfn = trace_bin_kernel<MODE, T>;                                           \
+    SD_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)smem));                                   \
+    kfn<<<H * W, 256, smem, s>>>(P);                                                \
   } while (0)
   if (opts->mode == SD_BIN_HARD) {
     if (opts->out_dtype == SD_F32) SD_LAUNCH(0, float);
@@ -1102,7 +1185,7 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   int* lo = prefix + (P.max_n + 1);
   float* Gs = reinterpret_cast<float*>(smem + table_bytes(P.max_n));
   const int r = blockIdx.x;
-  const sd_psf_request q = P.req[r];
+  const sd_psf_request q = request_of(P, r);
   setup_request(P, q, ctx, prefix, lo);
   const int ks = ctx.ks, ks2 = ks * ks, pp = (ks - 1) >> 1;
   for (int i = threadIdx.x; i < 2 * ks2; i += NT) Gs[i] = G[q.out_offset + i];
@@ -1301,7 +1384,7 @@ __global__ void __launch_bounds__(128) prep_kernel(TraceParams P, BatchWs W, int
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   const int r = blockIdx.x;
-  const sd_psf_request q = P.req[r];
+  const sd_psf_request q = request_of(P, r);
   setup_request(P, q, ctx, prefix, lo);
   const int ks2 = ctx.ks * ctx.ks;
   const bool fits = ctx.N && q.out_offset >= 0 && q.out_offset + 2LL * ks2 <= total_elems;

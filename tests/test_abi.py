@@ -53,6 +53,6 @@ def test_null_arguments_rejected_without_gpu(lib):
 
 
 def test_request_record_layout():
-    assert L.REQUEST_DTYPE.itemsize == 48
+    assert L.REQUEST_DTYPE.itemsize == 56
     assert ctypes.sizeof(L.SdSurface) == 8 + 8 * 11
     assert ctypes.sizeof(L.SdTraceOpts) == 32
