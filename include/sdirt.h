@@ -407,6 +407,17 @@ sd_status sd_dp_render_backward_noalloc(const float* grad_out,
                                         int C, int H, int W, float* grad_aif,
                                         float* grad_bank, void* stream);
 
+/*
+ * Test aid (the paper has no counterpart): evaluates, on the device, the
+ * trace's division and square-root helpers (reciprocal / reciprocal-square-
+ * root estimates with one Newton-Raphson correction) on n inputs:
+ * quot[i] = a[i] / b[i], root[i] = sqrt(a[i]) (a[i] < 0 is clamped to 0).
+ * All arrays device FP32.  Lets a test compare them with correctly rounded
+ * IEEE results.
+ */
+sd_status sd_dev_math_check(const float* a, const float* b, int n, float* quot,
+                            float* root, void* stream);
+
 /* ------------------------------------------------------------------------
  * Library information
  * ---------------------------------------------------------------------- */

@@ -36,8 +36,10 @@ struct DevSurf {
   int type;         // SD_SURF_REFRACT / SD_SURF_STOP
   int asph;         // any a_2m != 0 -> Newton refinement
   int flat;         // c == 0 -> plane start
-  int pad;
+  int kind;         // bits: 1 refracting, 2 asphere, 4 flat (one load)
 };
+
+enum { K_REFRACT = 1, K_ASPH = 2, K_FLAT = 4 };
 
 struct DevLens {
   int n, stop;
@@ -167,6 +169,8 @@ void refresh_surface(DevLens& L, int s, const double* k, const double* a,
   d.type = L.type[s];
   d.asph = (d.type == SD_SURF_REFRACT) && asph;
   d.flat = (d.type == SD_SURF_STOP) || (L.c[s] == 0.0);
+  d.kind = (d.type == SD_SURF_REFRACT ? K_REFRACT : 0) | (d.asph ? K_ASPH : 0) |
+           (d.flat ? K_FLAT : 0);
 }
 
 double sag_at(double c, double k, const double* a, double rho) {
@@ -514,6 +518,34 @@ __device__ __forceinline__ float rsqrt_refined(float x) {
   return r * fmaf(-0.5f * x * r, r, 1.5f);
 }
 
+// Hardware reciprocal estimate (rcp.approx, about 1 ulp; denormals flushed).
+__device__ __forceinline__ float rcp_est(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+
+// a / b from the reciprocal estimate and one Newton-Raphson correction of
+// the quotient (Markstein, IBM J. Res. Dev. 34(1), 1990): the FMA residual
+// a - b q0 of q0 = a rcp(b) is exact, and q0 + residual * rcp(b) is within
+// one ulp of a / b.  Branch-free; valid for the normal-range operands of the
+// trace (lengths and cosines), b != 0.
+__device__ __forceinline__ float div_nr(float a, float b) {
+  const float r = rcp_est(b);
+  const float q = a * r;
+  return fmaf(fmaf(-b, q, a), r, q);
+}
+
+// sqrt(x) for x >= 0 from the reciprocal square-root estimate and one
+// Newton correction on the residual x - s^2 (Markstein's method), within
+// about one ulp.  x is clamped to 1e-30 so that x = 0 yields 1e-15, not NaN.
+__device__ __forceinline__ float sqrt_nr(float x) {
+  x = fmaxf(x, 1e-30f);
+  const float r = rsqrtf(x);
+  const float s = x * r;
+  return fmaf(fmaf(-s, s, x), 0.5f * r, s);
+}
+
 // Sequential trace (FP32) of one ray in surface-0-vertex-local coordinates.
 // On success (x, y) is the sensor landing point and (dx, dy, dz) the unit
 // direction.  Positions are kept relative to the current surface vertex.
@@ -535,10 +567,11 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
 #pragma unroll
   for (int s = 0; s < (NSC ? NSC : n); ++s) {
     const DevSurf& S = L.s[s];
+    const int kind = S.kind;
     float t;
-    if (S.flat) {
+    if (kind & K_FLAT) {
       if (!(dz > 0.f)) return ST_BACK;
-      t = -z / dz;
+      t = div_nr(-z, dz);
     } else {
       // conic: A t^2 - 2 B t + C = 0 (|d| = 1), root nearest the vertex in
       // the cancellation-free form t = C / (B + sqrt(B^2 - A C))
@@ -548,25 +581,28 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
       float C = S.c * (x * x + y * y + kk * z * z) - 2.f * z;
       float disc = B * B - A * C;
       if (disc < 0.f) return ST_MISS;
-      float den = B + sqrtf(disc);
+      float den = B + sqrt_nr(disc);
       if (!(den > 0.f)) return ST_MISS;
-      t = C / den;
+      t = div_nr(C, den);
     }
-    if (S.asph) {
+    if (kind & K_ASPH) {
       // Newton on F(t) = z + t dz - sag(rho(t)^2), started at the conic root
+      const float sc = S.c, kc2 = (1.f + S.k) * S.c * S.c;
+      const float a0 = S.a[0], a1 = S.a[1], a2 = S.a[2], a3 = S.a[3], a4 = S.a[4];
+      const float d0 = S.da[0], d1 = S.da[1], d2 = S.da[2], d3 = S.da[3], d4 = S.da[4];
       int it = 0;
       for (; it < newton_max; ++it) {
         float px = fmaf(t, dx, x), py = fmaf(t, dy, y);
         float u = px * px + py * py;
-        float arg = 1.f - (1.f + S.k) * S.c * S.c * u;
+        float arg = 1.f - kc2 * u;
         if (arg < 0.f) return ST_NEWTON;
-        float q = sqrtf(arg);
-        float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.a[4], S.a[3]), S.a[2]), S.a[1]), S.a[0]);
-        float zs = S.c * u / (1.f + q) + u * u * poly;
-        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
+        float q = sqrt_nr(arg);
+        float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, a4, a3), a2), a1), a0);
+        float zs = div_nr(sc * u, 1.f + q) + u * u * poly;
+        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, d4, d3), d2), d1), d0);
         // the derivative and the step only steer the iteration (its fixed point
         // is the root of the exactly evaluated F): fast reciprocals suffice
-        float dzdu = (q > 0.f ? 0.5f * S.c * rsqrtf(arg) : 0.f) + u * dpoly;
+        float dzdu = (q > 0.f ? 0.5f * sc * rsqrtf(arg) : 0.f) + u * dpoly;
         float F = fmaf(t, dz, z) - zs;
         float dF = dz - 2.f * dzdu * (px * dx + py * dy);
         float step = __fdividef(F, dF);
@@ -591,13 +627,13 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
     }
     float rho2 = x * x + y * y;
     if (rho2 > S.sd2) return ST_CLIP;
-    if (S.type == SD_SURF_REFRACT) {
+    if (kind & K_REFRACT) {
       float nx, ny, nz;
-      if (S.asph) {
+      if (kind & K_ASPH) {
         float u = rho2;
-        float q = sqrtf(fmaxf(1.f - (1.f + S.k) * S.c * S.c * u, 0.f));
+        float q = sqrt_nr(1.f - (1.f + S.k) * S.c * S.c * u);
         float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
-        float dzdu = (q > 0.f ? 0.5f * S.c / q : 0.f) + u * dpoly;
+        float dzdu = div_nr(0.5f * S.c, q) + u * dpoly;
         nx = -2.f * x * dzdu;
         ny = -2.f * y * dzdu;
         nz = 1.f;
@@ -618,7 +654,7 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
       float cosi = nx * dx + ny * dy + nz * dz;
       float k2 = 1.f - e * e * (1.f - cosi * cosi);
       if (k2 < 0.f) return ST_TIR;
-      float g = __fdiv_rn(omeg2[s], sqrtf(k2) + e * cosi);
+      float g = div_nr(omeg2[s], sqrt_nr(k2) + e * cosi);
       dx = dot2(e, dx, g, nx);
       dy = dot2(e, dy, g, ny);
       dz = dot2(e, dz, g, nz);
@@ -626,7 +662,7 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
     z -= S.t;  // vertex-local coordinate of the next surface (or the sensor)
   }
   if (!(dz > 0.f)) return ST_BACK;
-  float t = -z / dz;
+  float t = div_nr(-z, dz);
   x = fmaf(t, dx, x);
   y = fmaf(t, dy, y);
   return ST_OK;
@@ -655,17 +691,11 @@ __device__ __forceinline__ int dp_side(const SensorF& S, float dxp, float dyp, f
 }
 
 // Generates ray k of the request (in pupil raster order over in-pupil samples).
-__device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, const int* lo,
-                                         int k, float& x, float& y, float& z, float& dx,
-                                         float& dy, float& dz) {
+// Ray k given its pupil row iy (prefix[iy] <= k < prefix[iy+1]).
+__device__ __forceinline__ void make_ray_row(const ReqCtx& ctx, const int* prefix, const int* lo,
+                                             int k, int iy, float& x, float& y, float& z,
+                                             float& dx, float& dy, float& dz) {
   int N = ctx.N;
-  // binary search: row iy with prefix[iy] <= k < prefix[iy+1]
-  int a = 0, b = N;
-  while (b - a > 1) {
-    int m = (a + b) >> 1;
-    if (prefix[m] <= k) a = m; else b = m;
-  }
-  int iy = a;
   int ix = lo[iy] + (k - prefix[iy]);
   float ex = (float)(2 * ix + 1 - N) * ctx.scale;
   float ey = (float)(2 * iy + 1 - N) * ctx.scale;
@@ -682,6 +712,25 @@ __device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, c
     y = fmaf(ctx.s_start, vy, ctx.y_o);
   }
   z = ctx.z_start;
+}
+
+// Ray k of the request (binary search for its pupil row).
+__device__ __forceinline__ void make_ray(const ReqCtx& ctx, const int* prefix, const int* lo,
+                                         int k, float& x, float& y, float& z, float& dx,
+                                         float& dy, float& dz) {
+  int a = 0, b = ctx.N;
+  while (b - a > 1) {
+    int m = (a + b) >> 1;
+    if (prefix[m] <= k) a = m; else b = m;
+  }
+  make_ray_row(ctx, prefix, lo, k, a, x, y, z, dx, dy, dz);
+}
+
+// Pupil row of ray k for a thread whose k only grows: advance from the row
+// of its previous ray (a few steps instead of a binary search).
+__device__ __forceinline__ int advance_row(const int* prefix, int k, int row) {
+  while (prefix[row + 1] <= k) ++row;
+  return row;
 }
 
 // bytes of the pupil row tables (prefix[N+1], lo[N]), 16-byte multiple
@@ -719,6 +768,7 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
   const int lane = threadIdx.x & 31;
   unsigned int c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0,
                c_clip = 0;
+  int row = 0;
   for (int base = 0; base < total; base += blockDim.x) {
     int k = base + threadIdx.x;
     int key = -1;
@@ -726,7 +776,8 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
     int side = 2;
     if (k < total) {
       float x, y, z, dx, dy, dz;
-      make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
+      row = advance_row(prefix, k, row);
+      make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
       int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
       if (st == ST_OK) {
         ++c_reached;
@@ -869,6 +920,15 @@ size_t trace_smem_bytes(int max_n, int max_ks) {
   return table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
 }
 
+__global__ void math_check_kernel(const float* a, const float* b, int n, float* quot,
+                                  float* root) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    quot[i] = div_nr(a[i], b[i]);
+    root[i] = sqrt_nr(a[i]);
+  }
+}
+
 sd_status fill_params(TraceParams& P, const sd_lens* const* lenses, int n_lenses,
                       const sd_dp_sensor* sensor, const sd_trace_opts* opts) {
   if (!lenses || n_lenses < 1 || n_lenses > SD_MAX_LENSES || !sensor) return SD_ERR_ARG;
@@ -997,6 +1057,16 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
   return launch_status();
 }
 
+sd_status sd_dev_math_check(const float* a, const float* b, int n, float* quot,
+                            float* root, void* stream) {
+  using namespace sd;
+  if (n < 0 || (n > 0 && (!a || !b || !quot || !root))) return SD_ERR_ARG;
+  if (n == 0) return SD_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  math_check_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, b, n, quot, root);
+  return launch_status();
+}
+
 sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
                            const sd_psf_request* req_host, const sd_trace_opts* opts,
                            float* rec, int max_rays, int32_t* n_rays, void* stream) {
@@ -1057,10 +1127,10 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
   // sensor: x_s = X + tau dx, tau = -Z / dz with (X, Y, Z) the last hit
   // moved to sensor-local z
   float Z = sv[n - 1].pz - L.s[n - 1].t;
-  float tau = -Z / dfz;
+  float tau = div_nr(-Z, dfz);
   float taub = xb * dfx + yb * dfy;
-  float Pbx = xb, Pby = yb, Pbz = -taub / dfz;
-  float dbx = xb * tau, dby = yb * tau, dbz = taub * Z / (dfz * dfz);
+  float Pbx = xb, Pby = yb, Pbz = div_nr(-taub, dfz);
+  float dbx = xb * tau, dby = yb * tau, dbz = div_nr(taub * Z, dfz * dfz);
   gacc[n - 1][7] += -Pbz;
 #pragma unroll
   for (int s = (NSC ? NSC : n) - 1; s >= 0; --s) {
@@ -1072,8 +1142,8 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
     if (S.type == SD_SURF_REFRACT) {
       const float c = S.c, kk = 1.f + S.k;
       const float u = Px * Px + Py * Py;
-      const float q = sqrtf(fmaxf(1.f - kk * c * c * u, 1e-30f));
-      const float iq = 1.f / q, iq3 = iq * iq * iq;
+      const float q = sqrt_nr(1.f - kk * c * c * u);
+      const float iq = div_nr(1.f, q), iq3 = iq * iq * iq;
       // S1 = dsag/du = c / (2q) + sum_j (j+2) a_j u^(j+1)
       float up = 1.f, S1 = 0.5f * c * iq, dS1 = 0.25f * kk * c * c * c * iq3;
 #pragma unroll
@@ -1085,22 +1155,22 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       gx = -2.f * Px * S1;
       gy = -2.f * Py * S1;
       gz = 1.f;
-      const float mn = sqrtf(gx * gx + gy * gy + 1.f), imn = 1.f / mn;
+      const float imn = rsqrt_refined(gx * gx + gy * gy + 1.f);
       const float nx = gx * imn, ny = gy * imn, nz = imn;
       // Snell: dout = e din + g n, g = (1 - e^2) / (ct + e cosi)
       const float e = eta[s];
       const float cosi = nx * ix + ny * iy + nz * iz;
       const float k2 = 1.f - e * e * (1.f - cosi * cosi);
-      const float ct = sqrtf(fmaxf(k2, 0.f));
+      const float ct = sqrt_nr(k2);
       const float D = ct + e * cosi;
-      const float g = omeg2[s] / D;
+      const float g = div_nr(omeg2[s], D);
       ibx = e * dbx;
       iby = e * dby;
       ibz = e * dbz;
       const float gb = dbx * nx + dby * ny + dbz * nz;
       float nbx = g * dbx, nby = g * dby, nbz = g * dbz;
-      const float Db = -gb * g / D;
-      const float k2b = Db / (2.f * fmaxf(ct, 1e-30f));
+      const float Db = div_nr(-gb * g, D);
+      const float k2b = div_nr(Db, 2.f * ct);
       const float cosib = Db * e + k2b * 2.f * e * e * cosi;
       nbx += cosib * ix;
       nby += cosib * iy;
@@ -1137,7 +1207,7 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
     ibz += t * Pbz;
     const float tb = Pbx * ix + Pby * iy + Pbz * iz;
     // implicit intersection Phi(o + t din; theta) = 0
-    const float lam = -tb / (gx * ix + gy * iy + gz * iz);
+    const float lam = div_nr(-tb, gx * ix + gy * iy + gz * iz);
     obx += lam * gx;
     oby += lam * gy;
     obz += lam * gz;
@@ -1147,12 +1217,13 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
     if (S.type == SD_SURF_REFRACT) {
       const float c = S.c, kk = 1.f + S.k;
       const float u = Px * Px + Py * Py;
-      const float q = sqrtf(fmaxf(1.f - kk * c * c * u, 1e-30f));
-      const float Sc = c * u / (1.f + q);  // conic part of the sag
+      const float q = sqrt_nr(1.f - kk * c * c * u);
+      const float Sc = div_nr(c * u, 1.f + q);  // conic part of the sag
+      const float i2q = div_nr(0.5f, q);
       // Phi = z - sag:  dPhi/dc = -(u + (1+k) Sc^2) / (2q), dPhi/dk = -c Sc^2 / (2q),
       // dPhi/da_j = -u^(j+2)
-      gacc[s][0] += lam * (-(u + kk * Sc * Sc) / (2.f * q));
-      gacc[s][1] += lam * (-c * Sc * Sc / (2.f * q));
+      gacc[s][0] += lam * (-(u + kk * Sc * Sc) * i2q);
+      gacc[s][1] += lam * (-c * Sc * Sc * i2q);
       float up = u * u;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
@@ -1201,9 +1272,11 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
 #pragma unroll
     for (int j = 0; j < NPAR_SURF; ++j) gacc[s][j] = 0.f;
   SurfSave sv[NA];
+  int row = 0;
   for (int k = threadIdx.x; k < total; k += NT) {
     float x, y, z, dx, dy, dz;
-    make_ray(ctx, prefix, lo, k, x, y, z, dx, dy, dz);
+    row = advance_row(prefix, k, row);
+    make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
     int st = trace_ray_t<true, NSC>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy,
                                     dz, sv);
     if (st != ST_OK) continue;

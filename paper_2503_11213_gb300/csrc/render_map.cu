@@ -6,14 +6,15 @@
 //
 // The map is read exactly once and dominates the traffic (2 ks^2 values per
 // pixel against C image values), so the kernel is built around streaming it:
-// one block per (8 x 32 tile, image, channel group), the tile and its halo of
-// the group's channels staged in shared memory, one warp per tile row.  For
-// each of its 32 pixels a warp reads the pixel's kernel pair with coalesced
-// loads (the next 32*NCH values are in flight while the current ones are
-// used, across pixel boundaries), multiplies each value
-// with the staged image tap of every channel of the group (a per-block table
-// maps a kernel index to its tap offset) and reduces over the warp; the lane
-// owning the pixel keeps the sums and the row is stored coalesced at the end.
+// one block per (8 x 32 tile, image, group of up to 4 channels), the tile and
+// its halo staged in shared memory with the group's channels interleaved (one
+// vector load per tap), one warp per tile row.  For each of its 32 pixels a
+// warp reads the pixel's L and R kernels with coalesced loads (the next
+// 32*NTAP taps are in flight while the current ones are used, across pixel
+// boundaries); a lane takes a tap, loads the staged image values of every
+// channel once and feeds both sides (a per-block table maps a tap to its
+// offset); the warp reduces, and the lane owning the pixel keeps the sums,
+// stored coalesced at the end.
 // Deterministic (fixed reduction order).
 
 #include <cstring>
@@ -25,105 +26,112 @@ namespace sd {
 constexpr int MT_X = 32;      // tile width (pixels) = lanes
 constexpr int MT_Y = 8;       // tile height = warps per block
 constexpr int MAP_NT = 32 * MT_Y;
-constexpr int MAX_CP = 4;     // channels per pass
-constexpr int NCH = 16;       // kernel values per lane per item
+constexpr int NTAP = 8;       // taps per lane per item (L and R values each)
 
 struct MapParams {
   const void* aif;
   const void* map;
   void* out;
   int N, C, H, W, ks;
-  int cp;       // channels staged per pass
-  int S;        // row stride of the staged tile (MT_X + ks - 1)
+  int S;        // row stride of the staged tile (MT_X + ks - 1), in taps
 };
 
-__host__ __device__ inline size_t map_smem_bytes(int ks, int cp) {
-  const size_t S = MT_X + ks - 1, R = MT_Y + ks - 1;
-  return (size_t)cp * S * R * 4 + (size_t)ks * ks * 4;
+// CW channels interleaved per staged tap: one shared load brings all of them
+template <int CW> struct Vec;
+template <> struct Vec<1> { using T = float; };
+template <> struct Vec<2> { using T = float2; };
+template <> struct Vec<4> { using T = float4; };
+__device__ __forceinline__ float comp(float v, int) { return v; }
+__device__ __forceinline__ float comp(float2 v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ float comp(float4 v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
-template <class TI, class TM>
+__host__ __device__ inline size_t map_smem_bytes(int ks, int cw) {
+  const size_t S = MT_X + ks - 1, R = MT_Y + ks - 1;
+  return (size_t)cw * S * R * 4 + (size_t)ks * ks * 4;
+}
+
+template <class TI, class TM, int CW>
 __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
+  using V = typename Vec<CW>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks, S = P.S, R = MT_Y + ks - 1;
-  float* tile = reinterpret_cast<float*>(smem);                 // [cp][R][S]
-  int* offs = reinterpret_cast<int*>(tile + (size_t)P.cp * R * S);  // [ks2]
+  float* tile = reinterpret_cast<float*>(smem);                      // [R][S][CW]
+  int* offs = reinterpret_cast<int*>(tile + (size_t)CW * R * S);     // [ks2]
+  const V* vtile = reinterpret_cast<const V*>(tile);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = blockIdx.x * MT_X, y0 = blockIdx.y * MT_Y;
-  const int groups = (P.C + P.cp - 1) / P.cp;
-  const int n = blockIdx.z / groups, c0 = (blockIdx.z - n * groups) * P.cp;
-  const int cp = min(P.cp, P.C - c0);
+  const int groups = (P.C + CW - 1) / CW;
+  const int n = blockIdx.z / groups, c0 = (blockIdx.z - n * groups) * CW;
+  const int cp = min(CW, P.C - c0);
   const size_t plane = (size_t)P.H * P.W;
 
-  // kernel index e = (u', v') -> offset of its tap from the pixel's staged
-  // position (y - y0, x - x0): (2p - u', 2p - v') in the tile with halo p
+  // tap e = (u', v') of a kernel -> its image tap relative to the pixel's
+  // staged position: (2p - u', 2p - v') in the tile with halo p
   for (int e = tid; e < ks2; e += MAP_NT) {
     int u = e / ks, v = e - u * ks;
     offs[e] = (2 * p - u) * S + (2 * p - v);
   }
-  const TI* img = reinterpret_cast<const TI*>(P.aif);
-  for (int c = 0; c < cp; ++c) {
-    const TI* src = img + ((size_t)n * P.C + c0 + c) * plane;
-    float* dst = tile + (size_t)c * R * S;
-    for (int i = tid; i < R * S; i += MAP_NT) {
-      int r = i / S, q = i - r * S;
-      int yy = min(max(y0 + r - p, 0), P.H - 1);
-      int xx = min(max(x0 + q - p, 0), P.W - 1);
-      dst[i] = to_f32<TI>(src[(size_t)yy * P.W + xx]);
-    }
+  const TI* img = reinterpret_cast<const TI*>(P.aif) + ((size_t)n * P.C + c0) * plane;
+  for (int i = tid; i < R * S; i += MAP_NT) {
+    int r = i / S, q = i - r * S;
+    int yy = min(max(y0 + r - p, 0), P.H - 1);
+    int xx = min(max(x0 + q - p, 0), P.W - 1);
+    const size_t src = (size_t)yy * P.W + xx;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      tile[(size_t)i * CW + c] = c < cp ? to_f32<TI>(img[c * plane + src]) : 0.f;
   }
   __syncthreads();
 
   const int y = y0 + warp;
   if (y >= P.H) return;
-  float keep[2][MAX_CP];
+  float keep[2][CW];
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < MAX_CP; ++c) keep[s][c] = 0.f;
-  const TM* mrow = reinterpret_cast<const TM*>(P.map) + ((size_t)y * P.W + x0) * 2 * ks2;
+  for (int c = 0; c < CW; ++c) keep[0][c] = keep[1][c] = 0.f;
+  const int E = 2 * ks2;
+  const TM* mrow = reinterpret_cast<const TM*>(P.map) + ((size_t)y * P.W + x0) * E;
   const int xmax = min(MT_X, P.W - x0);
-  // the row's kernels as one stream of (pixel, chunk) items of 32*NCH
-  // values; the next item is loaded while the current one is used
-  const int E = 2 * ks2, nchunk = (E + 32 * NCH - 1) / (32 * NCH), items = xmax * nchunk;
-  const size_t RS = (size_t)R * S;
-  float cur[NCH], nxt[NCH];
-  auto load = [&](float* dst, int it) {
-    const int px = it / nchunk, ch = it - px * nchunk;
-    const TM* K = mrow + (size_t)px * E + ch * 32 * NCH;
-    const int lim = E - ch * 32 * NCH;
+  // the row's kernels as a stream of (pixel, tap chunk) items of 32*NTAP
+  // taps (L and R values of each); the next item is loaded while the current
+  // one is used
+  const int nch = (ks2 + 32 * NTAP - 1) / (32 * NTAP), items = xmax * nch;
+  float curL[NTAP], curR[NTAP], nxtL[NTAP], nxtR[NTAP];
+  auto load = [&](float* dl, float* dr, int it) {
+    const int px = it / nch, ch = it - px * nch;
+    const TM* K = mrow + (size_t)px * E;
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) {
-      const int e = lane + 32 * j;
-      dst[j] = e < lim ? to_f32<TM>(__ldg(K + e)) : 0.f;
+    for (int j = 0; j < NTAP; ++j) {
+      const int e = ch * 32 * NTAP + lane + 32 * j;
+      const bool in = e < ks2;
+      dl[j] = in ? to_f32<TM>(__ldg(K + e)) : 0.f;
+      dr[j] = in ? to_f32<TM>(__ldg(K + ks2 + e)) : 0.f;
     }
   };
-  float aL[MAX_CP], aR[MAX_CP];
+  float aL[CW], aR[CW];
 #pragma unroll
-  for (int c = 0; c < MAX_CP; ++c) aL[c] = aR[c] = 0.f;
-  load(cur, 0);
+  for (int c = 0; c < CW; ++c) aL[c] = aR[c] = 0.f;
+  load(curL, curR, 0);
   for (int it = 0; it < items; ++it) {
-    if (it + 1 < items) load(nxt, it + 1);
-    const int px = it / nchunk, ch = it - px * nchunk;
-    const float* tb = tile + warp * S + px;
+    if (it + 1 < items) load(nxtL, nxtR, it + 1);
+    const int px = it / nch, ch = it - px * nch;
+    const int base = warp * S + px;
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) {
-      const int e = ch * 32 * NCH + lane + 32 * j;
+    for (int j = 0; j < NTAP; ++j) {
+      const int e = ch * 32 * NTAP + lane + 32 * j;
       if (e < ks2) {
-        const float* t = tb + offs[e];
+        const V v = vtile[base + offs[e]];
 #pragma unroll
-        for (int c = 0; c < MAX_CP; ++c)
-          if (c < cp) aL[c] = fmaf(t[c * RS], cur[j], aL[c]);
-      } else if (e < E) {
-        const float* t = tb + offs[e - ks2];
-#pragma unroll
-        for (int c = 0; c < MAX_CP; ++c)
-          if (c < cp) aR[c] = fmaf(t[c * RS], cur[j], aR[c]);
+        for (int c = 0; c < CW; ++c) {
+          aL[c] = fmaf(comp(v, c), curL[j], aL[c]);
+          aR[c] = fmaf(comp(v, c), curR[j], aR[c]);
+        }
       }
     }
-    if (ch == nchunk - 1) {
+    if (ch == nch - 1) {
 #pragma unroll
-      for (int c = 0; c < MAX_CP; ++c) {
+      for (int c = 0; c < CW; ++c) {
         if (c < cp) {
           float l = aL[c], r = aR[c];
 #pragma unroll
@@ -140,13 +148,16 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) cur[j] = nxt[j];
+    for (int j = 0; j < NTAP; ++j) {
+      curL[j] = nxtL[j];
+      curR[j] = nxtR[j];
+    }
   }
   const int x = x0 + lane;
   if (lane < xmax) {
     TI* out = reinterpret_cast<TI*>(P.out);
 #pragma unroll
-    for (int c = 0; c < MAX_CP; ++c)
+    for (int c = 0; c < CW; ++c)
       if (c < cp) {
         out[(((size_t)n * 2 * P.C + c0 + c) * P.H + y) * P.W + x] = from_f32<TI>(keep[0][c]);
         out[(((size_t)n * 2 * P.C + P.C + c0 + c) * P.H + y) * P.W + x] =
@@ -155,22 +166,27 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
   }
 }
 
-template <class TI, class TM>
-sd_status launch_map(MapParams& P, cudaStream_t s) {
-  constexpr size_t cap = 227 * 1024;
-  int cp = min(MAX_CP, P.C);
-  while (cp > 1 && map_smem_bytes(P.ks, cp) > cap) --cp;
-  if (map_smem_bytes(P.ks, cp) > cap) return SD_ERR_UNSUPPORTED;
-  P.cp = cp;
-  P.S = MT_X + P.ks - 1;
-  const size_t smem = map_smem_bytes(P.ks, cp);
-  auto k = render_map_kernel<TI, TM>;
+template <class TI, class TM, int CW>
+sd_status launch_map_cw(MapParams& P, cudaStream_t s) {
+  const size_t smem = map_smem_bytes(P.ks, CW);
+  auto k = render_map_kernel<TI, TM, CW>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int groups = (P.C + cp - 1) / cp;
+  const int groups = (P.C + CW - 1) / CW;
   if ((long long)P.N * groups > 65535) return SD_ERR_UNSUPPORTED;
   dim3 grid((P.W + MT_X - 1) / MT_X, (P.H + MT_Y - 1) / MT_Y, P.N * groups);
   k<<<grid, MAP_NT, smem, s>>>(P);
   return launch_status();
+}
+
+template <class TI, class TM>
+sd_status launch_map(MapParams& P, cudaStream_t s) {
+  constexpr size_t cap = 227 * 1024;
+  P.S = MT_X + P.ks - 1;
+  // widest channel interleave that fits: 4 (RGB in one pass), 2, 1
+  if (P.C > 2 && map_smem_bytes(P.ks, 4) <= cap) return launch_map_cw<TI, TM, 4>(P, s);
+  if (P.C > 1 && map_smem_bytes(P.ks, 2) <= cap) return launch_map_cw<TI, TM, 2>(P, s);
+  if (map_smem_bytes(P.ks, 1) <= cap) return launch_map_cw<TI, TM, 1>(P, s);
+  return SD_ERR_UNSUPPORTED;
 }
 
 }  // namespace sd
