@@ -691,12 +691,12 @@ __device__ __forceinline__ int dp_side(const SensorF& S, float dxp, float dyp, f
 }
 
 // Generates ray k of the request (in pupil raster order over in-pupil samples).
-// Ray k given its pupil row iy (prefix[iy] <= k < prefix[iy+1]).
-__device__ __forceinline__ void make_ray_row(const ReqCtx& ctx, const int* prefix, const int* lo,
-                                             int k, int iy, float& x, float& y, float& z,
-                                             float& dx, float& dy, float& dz) {
-  int N = ctx.N;
-  int ix = lo[iy] + (k - prefix[iy]);
+// Ray through pupil sample (ix, iy) of the request: from the object point
+// to the sample on the EP plane, started on that plane (or on the start
+// plane in front of surface 0).
+__device__ __forceinline__ void pupil_ray(const ReqCtx& ctx, int ix, int iy, float& x, float& y,
+                                          float& z, float& dx, float& dy, float& dz) {
+  const int N = ctx.N;
   float ex = (float)(2 * ix + 1 - N) * ctx.scale;
   float ey = (float)(2 * iy + 1 - N) * ctx.scale;
   float vx = ex - ctx.x_o, vy = ey - ctx.y_o, vz = ctx.vz;
@@ -712,6 +712,13 @@ __device__ __forceinline__ void make_ray_row(const ReqCtx& ctx, const int* prefi
     y = fmaf(ctx.s_start, vy, ctx.y_o);
   }
   z = ctx.z_start;
+}
+
+// Ray k given its pupil row iy (prefix[iy] <= k < prefix[iy+1]).
+__device__ __forceinline__ void make_ray_row(const ReqCtx& ctx, const int* prefix, const int* lo,
+                                             int k, int iy, float& x, float& y, float& z,
+                                             float& dx, float& dy, float& dz) {
+  pupil_ray(ctx, lo[iy] + (k - prefix[iy]), iy, x, y, z, dx, dy, dz);
 }
 
 // Ray k of the request (binary search for its pupil row).
@@ -1645,30 +1652,15 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
     __syncthreads();
     const int total = s_rows;
     unsigned c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0, c_clip = 0;
+    int row = 0;
     for (int base = 0; base < total; base += blockDim.x) {
       int k = base + threadIdx.x;
       int key = -1;
       if (k < total) {
-        // ray k of the item: row by binary search over the item's rows
-        int a2 = 0, e2 = nrows;
-        while (e2 - a2 > 1) {
-          int m = (a2 + e2) >> 1;
-          if (prefix[m] <= k) a2 = m; else e2 = m;
-        }
-        const int iy = row0 + a2, ix = lo[a2] + (k - prefix[a2]);
-        float ex = (float)(2 * ix + 1 - N) * ctx.scale;
-        float ey = (float)(2 * iy + 1 - N) * ctx.scale;
-        float vx = ex - ctx.x_o, vy = ey, vz = ctx.vz;
-        float inv = rsqrt_refined(vx * vx + vy * vy + vz * vz);
-        float dx = vx * inv, dy = vy * inv, dz = vz * inv, x, y, z;
-        if (ctx.s_start == 1.f) {
-          x = ex;
-          y = ey;
-        } else {
-          x = fmaf(ctx.s_start, vx, ctx.x_o);
-          y = ctx.s_start * vy;
-        }
-        z = ctx.z_start;
+        // ray k of the item (k grows within the item: advance the row)
+        row = advance_row(prefix, k, row);
+        float x, y, z, dx, dy, dz;
+        pupil_ray(ctx, lo[row] + (k - prefix[row]), row0 + row, x, y, z, dx, dy, dz);
         int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
         if (st == ST_OK) {
           ++c_reached;

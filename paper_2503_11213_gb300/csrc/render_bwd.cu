@@ -273,23 +273,32 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
           float kl[SB], kr[SB];
 #pragma unroll
           for (int j = 0; j < SB; ++j) kl[j] = kr[j] = 0.f;
+          // contribution to padded row rb*SB + r: sum_j G_j Kf[r-j].  Rows
+          // r < KU: every tap row exists and every padded row is in the tile
+          // (KU <= ks + SB - 1); rows KU .. KU+SB-1 only drain the ring into
+          // the rows below ks + SB - 1.
+          const float2* kq = kp;
+          float* dq = colp;
           for (int r0 = 0; r0 < KU + SB; r0 += SB) {
+            const bool tail = r0 >= KU;
 #pragma unroll
             for (int q = 0; q < SB; ++q) {
-              const int r = r0 + q;
-              float2 w2 = r < KU ? kp[r * VB] : make_float2(0.f, 0.f);
+              const float2 w2 = tail ? make_float2(0.f, 0.f) : kq[q * VB];
               kl[q] = w2.x;
               kr[q] = w2.y;
-              // contribution to padded row rb*SB + r: sum_j G_j Kf[r-j]
               float a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-              for (int j = 0; j < SB; ++j) {
-                a4[j & 3] = fmaf(GL[j], kl[(q - j + SB) % SB], a4[j & 3]);
-                a4[j & 3] = fmaf(GR[j], kr[(q - j + SB) % SB], a4[j & 3]);
+              for (int jj = 0; jj < SB; ++jj) {
+                a4[jj & 3] = fmaf(GL[jj], kl[(q - jj + SB) % SB], a4[jj & 3]);
+                a4[jj & 3] = fmaf(GR[jj], kr[(q - jj + SB) % SB], a4[jj & 3]);
               }
+              // zero taps are common (the L and R halves of a blur disc),
+              // and skipping their atomics is what sets this loop's speed
               const float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-              if (r < ks + SB - 1 && acc != 0.f) atomicAdd(colp + r * S, acc);
+              if ((!tail || r0 + q < ks + SB - 1) && acc != 0.f) atomicAdd(dq + q * S, acc);
             }
+            kq += SB * VB;
+            dq += SB * S;
           }
         }
         if (b + 1 < nblk) commit(kb + ((b + 1) & 1) * kb_elems);

@@ -12,17 +12,23 @@ from gpu_helpers import oracle_sensor, split
 pytestmark = pytest.mark.gpu
 
 
-def batch(sd, n_req, seed):
+def batch(sd, n_req, seed, two_d=False):
     lenses = [sd.Lens(W.doublet_pair_f18(), 1000.0), sd.Lens(W.spherical4(), 1000.0)]
     reqs = W.random_requests(n_req, seed=seed)
+    if two_d:  # 2-D field points (per-pixel maps): rotate each field height
+        phi = np.random.default_rng(seed + 100).uniform(0, 2 * np.pi, n_req)
+        h = reqs["h_mm"].copy()
+        reqs["h_mm"], reqs["v_mm"] = h * np.cos(phi), h * np.sin(phi)
     dev, total, off = sd.make_requests(reqs)
     return lenses, reqs, dev, total, off
 
 
-@pytest.mark.parametrize("config", [None, (256, 4096, 1), (1024, 65536, 1), (512, 2048, 2)])
-def test_batched_equals_per_request_kernel(sdlib, config):
+@pytest.mark.parametrize("config,two_d", [(None, False), ((256, 4096, 1), False),
+                                          ((1024, 65536, 1), False), ((512, 2048, 2), False),
+                                          (None, True)])
+def test_batched_equals_per_request_kernel(sdlib, config, two_d):
     sd = sdlib
-    lenses, reqs, dev, total, off = batch(sd, 160, seed=3)
+    lenses, reqs, dev, total, off = batch(sd, 160, seed=3, two_d=two_d)
     sensor = sd.DPSensor(0.002)
     ref, ref_st = sd.dp_psf_trace(lenses, sensor, dev, len(reqs), total, max_ks=127, max_n=512)
     bt = sd.BatchedTrace(lenses, sensor, dev, len(reqs), total, max_ks=127, max_n=512,
