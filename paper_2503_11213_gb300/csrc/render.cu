@@ -217,7 +217,25 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
           if (e < kb_elems) dst[e] = pre[r];
         }
       };
+      // rows [ulo, uhi] of the fetched block holding a non-zero tap (of
+      // either side): blur discs leave many kernel rows empty
+      auto extent = [&](int& ulo, int& uhi) {
+        unsigned lo_l = 0xffffffffu, hi_l = 0u;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          int e = lane + 32 * r;
+          if (e < kb_elems && pre[r] != 0.f) {
+            unsigned u = (unsigned)((e >> 1) / VB);
+            lo_l = min(lo_l, u);
+            hi_l = max(hi_l, u + 1u);
+          }
+        }
+        ulo = (int)__reduce_min_sync(0xffffffffu, lo_l);
+        uhi = (int)__reduce_max_sync(0xffffffffu, hi_l) - 1;
+      };
+      int ulo_n, uhi_n;
       fetch(0);
+      extent(ulo_n, uhi_n);
       commit(kb);
       __syncwarp();
       float aL[SEG], aR[SEG];
@@ -226,16 +244,19 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
       const float* base = halo + (rb * SEG) * S + col;
       for (int b = 0; b < nblk; ++b) {
         const float* kcur = kb + (b & 1) * kb_elems;
+        const int ulo = ulo_n, uhi = uhi_n;
         if (b + 1 < nblk) fetch(b + 1);  // loads in flight during the compute
-        const int vmax = min(VB, ks - b * VB);
+        // rows u0 in [u_begin, uhi]: the taps outside are zero (KU = ks
+        // rounded up to SEG; the padding taps are zero too)
+        const int u_begin = (ulo / SEG) * SEG;
+        const int vmax = uhi < 0 ? 0 : min(VB, ks - b * VB);
         for (int vv = 0; vv < vmax; ++vv) {
           const float* colp = base + b * VB + vv;
           float win[SEG];
 #pragma unroll
-          for (int j = 0; j < SEG; ++j) win[j] = colp[j * S];
+          for (int j = 0; j < SEG; ++j) win[j] = colp[(u_begin + j) * S];
           const float2* kp = reinterpret_cast<const float2*>(kcur) + vv;
-          // KU = ks rounded up to SEG; the padding taps are zero
-          for (int u0 = 0; u0 < KU; u0 += SEG) {
+          for (int u0 = u_begin; u0 <= uhi; u0 += SEG) {
 #pragma unroll
             for (int q = 0; q < SEG; ++q) {
               const int u = u0 + q;
@@ -249,7 +270,10 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
             }
           }
         }
-        if (b + 1 < nblk) commit(kb + ((b + 1) & 1) * kb_elems);
+        if (b + 1 < nblk) {
+          extent(ulo_n, uhi_n);
+          commit(kb + ((b + 1) & 1) * kb_elems);
+        }
         __syncwarp();
       }
       if (act) {

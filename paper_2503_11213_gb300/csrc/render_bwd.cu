@@ -258,14 +258,35 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
           if (e < kb_elems) dst[e] = pre[r];
         }
       };
+      // rows [ulo, uhi] of the fetched block holding a non-zero tap
+      auto extent = [&](int& ulo, int& uhi) {
+        unsigned lo_l = 0xffffffffu, hi_l = 0u;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          int e = lane + 32 * r;
+          if (e < kb_elems && pre[r] != 0.f) {
+            unsigned u = (unsigned)((e >> 1) / VB);
+            lo_l = min(lo_l, u);
+            hi_l = max(hi_l, u + 1u);
+          }
+        }
+        ulo = (int)__reduce_min_sync(0xffffffffu, lo_l);
+        uhi = (int)__reduce_max_sync(0xffffffffu, hi_l) - 1;
+      };
+      int ulo_n, uhi_n;
       fetch(0);
+      extent(ulo_n, uhi_n);
       commit(kb);
       __syncwarp();
       float* base = dpad + (rb * SB) * S + col;
       for (int b = 0; b < nblk; ++b) {
         const float* kcur = kb + (b & 1) * kb_elems;
+        const int ulo = ulo_n, uhi = uhi_n;
         if (b + 1 < nblk) fetch(b + 1);
-        const int vmax = min(VB, ks - b * VB);
+        // taps outside rows [ulo, uhi] are zero: padded rows r in
+        // [r_begin, uhi + SB) are the only ones that can receive anything
+        const int r_begin = (ulo / SB) * SB;
+        const int vmax = uhi < 0 ? 0 : min(VB, ks - b * VB);
         for (int vv = 0; vv < vmax; ++vv) {
           float* colp = base + b * VB + vv;
           const float2* kp = reinterpret_cast<const float2*>(kcur) + vv;
@@ -277,9 +298,9 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
           // r < KU: every tap row exists and every padded row is in the tile
           // (KU <= ks + SB - 1); rows KU .. KU+SB-1 only drain the ring into
           // the rows below ks + SB - 1.
-          const float2* kq = kp;
-          float* dq = colp;
-          for (int r0 = 0; r0 < KU + SB; r0 += SB) {
+          const float2* kq = kp + r_begin * VB;
+          float* dq = colp + r_begin * S;
+          for (int r0 = r_begin; r0 < uhi + SB; r0 += SB) {
             const bool tail = r0 >= KU;
 #pragma unroll
             for (int q = 0; q < SB; ++q) {
@@ -301,7 +322,10 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
             dq += SB * S;
           }
         }
-        if (b + 1 < nblk) commit(kb + ((b + 1) & 1) * kb_elems);
+        if (b + 1 < nblk) {
+          extent(ulo_n, uhi_n);
+          commit(kb + ((b + 1) & 1) * kb_elems);
+        }
         __syncwarp();
       }
       int nxt = 0;
