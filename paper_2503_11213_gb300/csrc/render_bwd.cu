@@ -362,6 +362,8 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
   const int S = TXB + ks - 1;
   const int HH = RT_Y + ks - 1 + SEG;
   constexpr int NPX = TXB * RT_Y, NSEG = NPX / SEG;
+  // one thread per segment builds the segment list below
+  static_assert(NT >= NSEG, "the bank-gradient block needs a thread per segment");
   float* halo = reinterpret_cast<float*>(smem);          // HH x S
   float2* G = reinterpret_cast<float2*>(halo + (size_t)HH * S);  // NPX (L, R)
   int* segs = reinterpret_cast<int*>(G + NPX);            // NSEG
