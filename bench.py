@@ -39,9 +39,11 @@ WORKLOAD = ("doublet-pair f/1.8 lens: DP PSF bank 32 fields x 32 depths x 3 wave
             "DP render of 1024x1024 RGB with a Perlin depth map")
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch of each kernel from one ncu capture of
-# the current kernels; None until a capture of this build exists.
-TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel: trace_adj_kernel over 1536 of the 3072 requests read 90.30 MB and
+# wrote 222.96 MB; its traffic grows with the requests, so a full launch moves
+# twice that.  Must be re-measured whenever the kernel changes.
+TRAFFIC_BYTES = {"trace_adj_kernel": int(2 * (90.299904 + 222.958848) * 1e6)}
 
 # ---------------------------------------------------------------------------
 # Algorithmic FP32 work per ray (add/sub/mul/div/sqrt = 1 flop, fused
