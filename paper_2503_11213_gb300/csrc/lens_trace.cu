@@ -551,8 +551,9 @@ __device__ __forceinline__ float sqrt_nr(float x) {
 // direction.  Positions are kept relative to the current surface vertex.
 // Per-surface forward state kept for the adjoint: hit point (vertex-local),
 // direction arriving at the surface and the intersection parameter.
-struct SurfSave {
-  float px, py, pz, dx, dy, dz, t;
+struct AdjState {
+  float t[SD_MAX_SURFACES];  // intersection parameter at every surface
+  float px, py, pz;          // hit point at the last surface (vertex-local)
 };
 
 // NSC > 0: the lens has exactly NSC surfaces (loops fully unrolled, per-
@@ -561,7 +562,7 @@ template <bool SAVE, int NSC = 0>
 __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ eta,
                                            const float* __restrict__ omeg2, int newton_max,
                                            float& x, float& y, float& z,
-                                           float& dx, float& dy, float& dz, SurfSave* sv) {
+                                           float& dx, float& dy, float& dz, AdjState* sv) {
   const DevLens& L = c_lens[slot];
   const int n = NSC ? NSC : L.n;
 #pragma unroll
@@ -611,19 +612,14 @@ __device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ e
       }
       if (it == newton_max) return ST_NEWTON;
     }
-    if (SAVE) {
-      sv[s].dx = dx;
-      sv[s].dy = dy;
-      sv[s].dz = dz;
-      sv[s].t = t;
-    }
+    if (SAVE) sv->t[s] = t;
     x = fmaf(t, dx, x);
     y = fmaf(t, dy, y);
     z = fmaf(t, dz, z);
-    if (SAVE) {
-      sv[s].px = x;
-      sv[s].py = y;
-      sv[s].pz = z;
+    if (SAVE && s == n - 1) {
+      sv->px = x;
+      sv->py = y;
+      sv->pz = z;
     }
     float rho2 = x * x + y * y;
     if (rho2 > S.sd2) return ST_CLIP;
@@ -1124,29 +1120,42 @@ namespace sd {
 // ---------------------------------------------------------------------------
 constexpr int NPAR_SURF = 8;
 
-template <int NSC = 0>
+// Reverse sweep of one ray.  The forward pass kept only t at every surface
+// and the hit point at the last one: going backwards, the incoming direction
+// at a surface follows from its outgoing one by inverting Snell's law at the
+// hit point (cos t_t = n . d_out, sin^2 t_i = sin^2 t_t / e^2, d_in =
+// (d_out - g n) / e), and the previous hit point is P - t d_in (plus the
+// thickness), so no per-surface state is stored.  `emit(s, v)` receives the
+// 8 parameter adjoints of surface s (v[7] = thickness after it) and is
+// called by every lane of the warp for s = n-1 .. 0.
+template <class Emit>
 __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ eta,
-                                            const float* __restrict__ omeg2,
-                                            const SurfSave* sv, float dfx, float dfy, float dfz,
-                                            float xb, float yb, float (*gacc)[NPAR_SURF]) {
+                                            const float* __restrict__ omeg2, const AdjState& sv,
+                                            float dfx, float dfy, float dfz, float xb, float yb,
+                                            Emit emit) {
   const DevLens& L = c_lens[slot];
-  const int n = NSC ? NSC : L.n;
-  // sensor: x_s = X + tau dx, tau = -Z / dz with (X, Y, Z) the last hit
-  // moved to sensor-local z
-  float Z = sv[n - 1].pz - L.s[n - 1].t;
+  const int n = L.n;
+  float Px = sv.px, Py = sv.py, Pz = sv.pz;  // hit point at surface s
+  float ox = dfx, oy = dfy, oz = dfz;        // direction leaving surface s
+  // sensor: x_s = X + tau dx, tau = -Z / dz with Z the last hit moved to
+  // sensor-local z
+  float Z = Pz - L.s[n - 1].t;
   float tau = div_nr(-Z, dfz);
   float taub = xb * dfx + yb * dfy;
   float Pbx = xb, Pby = yb, Pbz = div_nr(-taub, dfz);
   float dbx = xb * tau, dby = yb * tau, dbz = div_nr(taub * Z, dfz * dfz);
-  gacc[n - 1][7] += -Pbz;
-#pragma unroll
-  for (int s = (NSC ? NSC : n) - 1; s >= 0; --s) {
+  float tcarry = -Pbz;  // adjoint of the thickness after surface s
+  for (int s = n - 1; s >= 0; --s) {
     const DevSurf& S = L.s[s];
-    const float Px = sv[s].px, Py = sv[s].py;
-    const float ix = sv[s].dx, iy = sv[s].dy, iz = sv[s].dz, t = sv[s].t;
-    float ibx, iby, ibz;  // adjoint of the incoming direction
+    const float t = sv.t[s];
+    float v[NPAR_SURF];
+#pragma unroll
+    for (int j = 0; j < NPAR_SURF; ++j) v[j] = 0.f;
+    v[7] = tcarry;
+    float ix = ox, iy = oy, iz = oz;  // direction arriving at the surface
+    float ibx, iby, ibz;              // adjoint of the incoming direction
     float gx = 0.f, gy = 0.f, gz = 1.f;  // grad Phi at the hit
-    if (S.type == SD_SURF_REFRACT) {
+    if (S.kind & K_REFRACT) {
       const float c = S.c, kk = 1.f + S.k;
       const float u = Px * Px + Py * Py;
       const float q = sqrt_nr(1.f - kk * c * c * u);
@@ -1165,12 +1174,14 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       const float imn = rsqrt_refined(gx * gx + gy * gy + 1.f);
       const float nx = gx * imn, ny = gy * imn, nz = imn;
       // Snell: dout = e din + g n, g = (1 - e^2) / (ct + e cosi)
-      const float e = eta[s];
-      const float cosi = nx * ix + ny * iy + nz * iz;
-      const float k2 = 1.f - e * e * (1.f - cosi * cosi);
-      const float ct = sqrt_nr(k2);
+      const float e = eta[s], ie = div_nr(1.f, e);
+      const float ct = nx * ox + ny * oy + nz * oz;
+      const float cosi = sqrt_nr(1.f - (1.f - ct * ct) * ie * ie);
       const float D = ct + e * cosi;
       const float g = div_nr(omeg2[s], D);
+      ix = (ox - g * nx) * ie;
+      iy = (oy - g * ny) * ie;
+      iz = (oz - g * nz) * ie;
       ibx = e * dbx;
       iby = e * dby;
       ibz = e * dbz;
@@ -1194,12 +1205,12 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       const float ub = S1b * dS1;
       Pbx += 2.f * Px * ub;
       Pby += 2.f * Py * ub;
-      gacc[s][0] += S1b * (0.5f * iq + 0.5f * kk * c * c * u * iq3);
-      gacc[s][1] += S1b * (0.25f * c * c * c * u * iq3);
+      v[0] += S1b * (0.5f * iq + 0.5f * kk * c * c * u * iq3);
+      v[1] += S1b * (0.25f * c * c * c * u * iq3);
       up = u;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        gacc[s][2 + j] += S1b * (float)(j + 2) * up;  // u^(j+1)
+        v[2 + j] += S1b * (float)(j + 2) * up;  // u^(j+1)
         up *= u;
       }
     } else {
@@ -1221,7 +1232,7 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
     ibx += lam * t * gx;
     iby += lam * t * gy;
     ibz += lam * t * gz;
-    if (S.type == SD_SURF_REFRACT) {
+    if (S.kind & K_REFRACT) {
       const float c = S.c, kk = 1.f + S.k;
       const float u = Px * Px + Py * Py;
       const float q = sqrt_nr(1.f - kk * c * c * u);
@@ -1229,41 +1240,89 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       const float i2q = div_nr(0.5f, q);
       // Phi = z - sag:  dPhi/dc = -(u + (1+k) Sc^2) / (2q), dPhi/dk = -c Sc^2 / (2q),
       // dPhi/da_j = -u^(j+2)
-      gacc[s][0] += lam * (-(u + kk * Sc * Sc) * i2q);
-      gacc[s][1] += lam * (-c * Sc * Sc * i2q);
+      v[0] += lam * (-(u + kk * Sc * Sc) * i2q);
+      v[1] += lam * (-c * Sc * Sc * i2q);
       float up = u * u;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        gacc[s][2 + j] += lam * (-up);
+        v[2 + j] += lam * (-up);
         up *= u;
       }
     }
+    emit(s, v);
     // transfer: o_s = (P_{s-1}.x, P_{s-1}.y, P_{s-1}.z - T_{s-1})
     if (s > 0) {
       Pbx = obx;
       Pby = oby;
       Pbz = obz;
-      gacc[s - 1][7] += -obz;
+      tcarry = -obz;
       dbx = ibx;
       dby = iby;
       dbz = ibz;
+      const float Tp = L.s[s - 1].t;
+      Px = fmaf(-t, ix, Px);
+      Py = fmaf(-t, iy, Py);
+      Pz = fmaf(-t, iz, Pz) + Tp;
+      ox = ix;
+      oy = iy;
+      oz = iz;
     }
   }
 }
 
-// One block per request; per-request gradient partials gout[r][32*8] (fixed
-// order block reduction).
-template <int NT, int NSC>
+// Sum over the 32 lanes of a warp of 8 values per lane, as a reduce-scatter:
+// on return, lane l holds the warp total of value (l >> 2) & 7 when
+// (l & 3) == 0 (each exchange halves the values a lane carries).
+__device__ __forceinline__ float warp_sum8(const float (&v)[NPAR_SURF], int lane) {
+  float a[4], b[2], c;
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float send = h16 ? v[i] : v[i + 4];
+    float keep = h16 ? v[i + 4] : v[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // a[i] holds value i + 4 * h16
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    float send = h8 ? a[i] : a[i + 2];
+    float keep = h8 ? a[i + 2] : a[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // b[i] holds value i + 2 * h8 + 4 * h16
+  {
+    float send = h4 ? b[0] : b[1];
+    float keep = h4 ? b[1] : b[0];
+    c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  // c holds value h4 + 2 * h8 + 4 * h16, summed over the lanes that differ
+  // only in bits 2..4; finish over bits 0..1
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
+// One block per request; per-request gradient partials greq[r][32*8].  The
+// warps of a block run their rays' reverse sweeps in lockstep; after each
+// surface the warp's 8 parameter adjoints are summed across its lanes
+// (reduce-scatter) and added by one lane per parameter to the warp's row of
+// a shared accumulator; the rows are added in warp order at the end (fixed
+// order: deterministic).
+template <int NT>
 __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
                                                        float* __restrict__ greq) {
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ReqCtx ctx;
-  __shared__ float s_red[NT / 32][NPAR_SURF];
+  __shared__ float s_acc[NW][SD_MAX_SURFACES][NPAR_SURF];
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   float* Gs = reinterpret_cast<float*>(smem + table_bytes(P.max_n));
   const int r = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const sd_psf_request q = request_of(P, r);
+  for (int i = threadIdx.x; i < NW * SD_MAX_SURFACES * NPAR_SURF; i += NT)
+    (&s_acc[0][0][0])[i] = 0.f;
   setup_request(P, q, ctx, prefix, lo);
   const int ks = ctx.ks, ks2 = ks * ks, pp = (ks - 1) >> 1;
   for (int i = threadIdx.x; i < 2 * ks2; i += NT) Gs[i] = G[q.out_offset + i];
@@ -1271,71 +1330,70 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   const SensorF S = P.sen;
   const int total = ctx.N ? ctx.total : 0;
   const float scale = (P.norm == SD_NORM_PER_RAY) ? (total > 0 ? 1.f / (float)total : 0.f) : 1.f;
-  const int n = ctx.N ? (NSC ? NSC : c_lens[ctx.slot].n) : 0;
-  constexpr int NA = NSC ? NSC : SD_MAX_SURFACES;
-  float gacc[NA][NPAR_SURF];
-#pragma unroll
-  for (int s = 0; s < NA; ++s)
-#pragma unroll
-    for (int j = 0; j < NPAR_SURF; ++j) gacc[s][j] = 0.f;
-  SurfSave sv[NA];
+  const int n = ctx.N ? c_lens[ctx.slot].n : 0;
+  AdjState sv;
   int row = 0;
-  for (int k = threadIdx.x; k < total; k += NT) {
-    float x, y, z, dx, dy, dz;
-    row = advance_row(prefix, k, row);
-    make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
-    int st = trace_ray_t<true, NSC>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy,
-                                    dz, sv);
-    if (st != ST_OK) continue;
-    float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
-    float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
-    float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-    int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
-    if (side == 2) continue;
-    float a0f = floorf(fx), b0f = floorf(fy);
-    float wx = fx - a0f, wy = fy - b0f;
-    int a0 = (int)a0f, b0 = (int)b0f;
-    const float* Gp = Gs + side * ks2;
-    float gfx = 0.f, gfy = 0.f;
+  for (int base = 0; base < total; base += NT) {
+    const int k = base + threadIdx.x;
+    float x, y, z, dx = 0.f, dy = 0.f, dz = 1.f, gfx = 0.f, gfy = 0.f;
+    bool need = false;
+    if (k < total) {
+      row = advance_row(prefix, k, row);
+      make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
+      int st = trace_ray_t<true>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz,
+                                 &sv);
+      if (st == ST_OK) {
+        float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
+        float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
+        float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+        int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
+        if (side != 2) {
+          float a0f = floorf(fx), b0f = floorf(fy);
+          float wx = fx - a0f, wy = fy - b0f;
+          int a0 = (int)a0f, b0 = (int)b0f;
+          const float* Gp = Gs + side * ks2;
 #pragma unroll
-    for (int jy = 0; jy < 2; ++jy)
+          for (int jy = 0; jy < 2; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 2; ++jx) {
-        int aa = a0 + jx, bb = b0 + jy;
-        if (aa < 0 || aa >= ks || bb < 0 || bb >= ks) continue;
-        float gv = Gp[bb * ks + aa];
-        gfx += gv * (jx ? 1.f : -1.f) * (jy ? wy : 1.f - wy);
-        gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
+            for (int jx = 0; jx < 2; ++jx) {
+              int aa = a0 + jx, bb = b0 + jy;
+              if (aa < 0 || aa >= ks || bb < 0 || bb >= ks) continue;
+              float gv = Gp[bb * ks + aa];
+              gfx += gv * (jx ? 1.f : -1.f) * (jy ? wy : 1.f - wy);
+              gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
+            }
+          need = gfx != 0.f || gfy != 0.f;
+        }
       }
-    if (gfx == 0.f && gfy == 0.f) continue;
-    adjoint_ray<NSC>(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
-                     scale * S.inv_ps * gfy, gacc);
-  }
-  // fixed-order block reduction, one surface at a time
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int s = 0; s < NA; ++s) {
-    float v[NPAR_SURF];
-#pragma unroll
-    for (int j = 0; j < NPAR_SURF; ++j) {
-      v[j] = s < n ? gacc[s][j] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
     }
-    if (lane == 0)
-#pragma unroll
-      for (int j = 0; j < NPAR_SURF; ++j) s_red[warp][j] = v[j];
-    __syncthreads();
-    if (threadIdx.x < NPAR_SURF) {
-      float a = 0.f;
-      for (int w = 0; w < NT / 32; ++w) a += s_red[w][threadIdx.x];
-      greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + s * NPAR_SURF + threadIdx.x] = a;
+    // the whole warp sweeps when any lane needs it; the others contribute
+    // exact zeros (their values are selected away, never multiplied)
+    if (!__any_sync(0xffffffffu, need)) continue;
+    if (!need) {
+      // a harmless state for lanes without a contribution
+      sv.px = sv.py = 0.f;
+      sv.pz = 0.f;
+      for (int s2 = 0; s2 < n; ++s2) sv.t[s2] = 0.f;
+      dx = dy = 0.f;
+      dz = 1.f;
     }
-    __syncthreads();
+    adjoint_ray(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
+                scale * S.inv_ps * gfy, [&](int s2, float (&v)[NPAR_SURF]) {
+#pragma unroll
+                  for (int j2 = 0; j2 < NPAR_SURF; ++j2) v[j2] = need ? v[j2] : 0.f;
+                  const float tot = warp_sum8(v, lane);
+                  if ((lane & 3) == 0) s_acc[warp][s2][(lane >> 2) & 7] += tot;
+                });
   }
-  // surfaces beyond the lens have zero gradient
-  for (int i = NA * NPAR_SURF + threadIdx.x; i < SD_MAX_SURFACES * NPAR_SURF; i += NT)
-    greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + i] = 0.f;
+  __syncthreads();
+  // per-request partials: warps added in order
+  for (int i = threadIdx.x; i < SD_MAX_SURFACES * NPAR_SURF; i += NT) {
+    const int s2 = i / NPAR_SURF, j2 = i - s2 * NPAR_SURF;
+    float a = 0.f;
+    if (s2 < n)
+      for (int w = 0; w < NW; ++w) a += s_acc[w][s2][j2];
+    greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + i] = a;
+  }
 }
 
 // Sums the per-request partials of each lens: four contiguous request
@@ -1389,11 +1447,12 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
   P.max_n = max_n;
   P.max_ks = max_ks;
   size_t smem = table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
-  // Surface count read at run time (per-surface state in local memory): the
-  // variants with the count fixed at compile time keep that state in
-  // registers but need 130-190 registers per thread and measured slower.
-  constexpr int NT = 128;
-  void (*k)(TraceParams, const float*, float*) = trace_adj_kernel<NT, 0>;
+  // Surface count read at run time; the forward keeps one t per surface (a
+  // local array) and the reverse sweep rebuilds the rest.  Variants with the
+  // count fixed at compile time and the whole per-surface state in registers
+  // needed 130-190 registers per thread and measured slower.
+  constexpr int NT = 256;
+  void (*k)(TraceParams, const float*, float*) = trace_adj_kernel<NT>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k<<<n_req, NT, smem, s>>>(P, grad_out, grad_req);
   st = launch_status();
