@@ -418,6 +418,17 @@ sd_status sd_dp_render_backward_noalloc(const float* grad_out,
 sd_status sd_dev_math_check(const float* a, const float* b, int n, float* quot,
                             float* root, void* stream);
 
+/*
+ * Test aid (the paper has no counterpart): runs the tensor-core (tcgen05)
+ * path of the BF16 render on a fixed small product, D = A[u:u+128, :] B^T
+ * with A (136 x 32) and B (16 x 32) BF16 row-major and D (128 x 16) FP32, all
+ * device memory; u in [0, 8] is the row offset applied through the
+ * shared-memory descriptor.  *status (device int, zeroed by the caller)
+ * becomes 1 if the completion wait timed out.
+ */
+sd_status sd_dev_tc_check(const void* a, const void* b, int u, float* d,
+                          int32_t* status, void* stream);
+
 /* ------------------------------------------------------------------------
  * Library information
  * ---------------------------------------------------------------------- */
