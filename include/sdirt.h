@@ -348,6 +348,25 @@ sd_status sd_dp_render_map(const void* aif, const void* psf_map, int N, int C,
                            void* out, void* stream);
 
 /*
+ * sd_dp_render for BF16 images on the tensor cores (tcgen05, FP32
+ * accumulation in tensor memory): aif (N,C,H,W) and out (N,2C,H,W) BF16,
+ * depth_m (N,H,W) FP32, bank in layout->dtype (SD_BF16, or SD_F32 rounded to
+ * BF16), all device.  Same selection, padding and output layout as
+ * sd_dp_render.  Needs a device workspace of sd_dp_render_tc_workspace()
+ * bytes, 256-byte aligned (a BF16 re-layout of the bank written by the call
+ * and, in its first word, an error flag set to 1 if a tensor-core completion
+ * wait ever gave up).  Supports ks <= 65 (SD_ERR_UNSUPPORTED otherwise).
+ * Deterministic.
+ */
+sd_status sd_dp_render_tc(const void* aif, const float* depth_m, const void* bank,
+                          const sd_bank_layout* layout, int N, int C, int H,
+                          int W, void* out, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Workspace bytes of sd_dp_render_tc for this bank layout. */
+sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, size_t* bytes);
+
+/*
  * Adjoint of sd_dp_render (bank mode): given grad_out (N,2C,H,W) FP32 writes
  * grad_aif (N,C,H,W) FP32 and grad_bank (the bank's element layout, FP32),
  * both overwritten; either may be null to skip it.  aif is read in

@@ -71,7 +71,7 @@ EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_fre
            "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_psf_trace_batched",
            "sd_dp_psf_trace_batched_workspace", "sd_dp_psf_trace_batched_tune",
            "sd_dp_trace_hits", "sd_dp_psf_map",
-           "sd_dp_render", "sd_dp_render_map", "sd_dp_render_backward",
+           "sd_dp_render", "sd_dp_render_map", "sd_dp_render_tc", "sd_dp_render_tc_workspace", "sd_dp_render_backward",
            "sd_dp_render_backward_workspace", "sd_dp_render_backward_noalloc",
            "sd_dev_math_check", "sd_dev_tc_check", "sd_status_string", "sd_last_cuda_error",
            "sd_version")
@@ -124,6 +124,9 @@ def lib():
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
     L.sd_dp_psf_map.argtypes = [vp, P(SdSensor), vp, i32, i32, dbl, i32, i32, P(SdTraceOpts),
                                 vp, vp, vp]
+    L.sd_dp_render_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, vp, vp,
+                                  ctypes.c_size_t, vp]
+    L.sd_dp_render_tc_workspace.argtypes = [P(SdBankLayout), P(ctypes.c_size_t)]
     L.sd_dp_render_map.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,

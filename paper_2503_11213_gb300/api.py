@@ -314,6 +314,36 @@ def dp_render(aif, depth_m, bank, layout: BankLayout, out=None):
     return out
 
 
+def render_tc_workspace(layout: BankLayout):
+    n = ctypes.c_size_t(0)
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render_tc_workspace(ctypes.byref(lay), ctypes.byref(n)),
+            "sd_dp_render_tc_workspace")
+    return n.value
+
+
+def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=None):
+    """dp_render of a BF16 image on the tensor cores: aif (N,C,H,W) bf16,
+    depth (N,H,W) f32, bank bf16 (or f32, rounded) -> (N,2C,H,W) bf16.
+    The workspace's first int32 is an error flag (1 = a completion wait
+    gave up)."""
+    N, C, H, W = aif.shape
+    if aif.dtype != torch.bfloat16:
+        raise ValueError("the tensor-core render takes a bfloat16 image")
+    if out is None:
+        out = torch.empty((N, 2 * C, H, W), dtype=torch.bfloat16, device=aif.device)
+    if workspace is None:
+        workspace = torch.empty(render_tc_workspace(layout), dtype=torch.uint8, device=aif.device)
+    _need_cuda(aif, depth_m, bank, out, workspace)
+    if bank.dtype != layout.dtype or depth_m.dtype != torch.float32:
+        raise ValueError("bank dtype must match the layout; depth must be float32")
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render_tc(_ptr(aif), _ptr(depth_m), _ptr(bank), ctypes.byref(lay),
+                                    N, C, H, W, _ptr(out), _ptr(workspace), workspace.numel(),
+                                    _stream()), "sd_dp_render_tc")
+    return out
+
+
 def render_backward_workspace(layout: BankLayout, N, C, H, W):
     n = ctypes.c_size_t(0)
     lay = layout.c()

@@ -73,9 +73,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 // Waits for phase `parity` of the mbarrier with at most `limit` polls;
 // returns false when the limit is reached (the caller reports an error).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+// With `abort` non-null the wait also gives up as soon as *abort is set (by
+// any CTA whose own wait gave up), so a failing launch ends quickly.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                          const volatile int* abort = nullptr) {
   const uint32_t a = smem_u32(bar);
   for (uint32_t i = 0; i < limit; ++i) {
+    if (abort && (i & 1023u) == 1023u && *abort) return false;
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
