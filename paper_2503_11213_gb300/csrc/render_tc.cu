@@ -2,22 +2,24 @@
 // images through a BF16 bank on the 5th-generation tensor cores (tcgen05),
 // FP32 accumulation in tensor memory.
 //
-// A CTA renders a tile of 16 rows x 8 columns = 128 pixels (the MMA's M) of
+// A CTA renders a tile of 32 rows x 4 columns = 128 pixels (the MMA's M) of
 // one channel.  For kernel row u the tile's outputs are a product
 //   D[(g, i), n] += sum_v Ipad[y0+g+u, x0+i+v] * Kf_n[u][v],
 // rows (g, i) = pixel (tile row g, column i), columns n = (side, slice slot)
 // of the up to 8 bank slices the tile's pixels use (N = 16), K = v.  The
 // A operand is the image tile staged once in shared memory in the
-// no-swizzle K-major core-matrix layout with the 8 column shifts i as the 8
-// rows of each core matrix, so that the operand of kernel row u is the same
-// buffer with its descriptor start moved by u core-matrix rows; the B
-// operand of each kernel row comes from a BF16 copy of the bank re-laid out
-// once per call (flipped, rows padded to a multiple of 16) and is streamed
-// through two shared buffers, 16 kernel rows at a time, while the tensor
-// core works on the other.  One thread issues the MMAs; an mbarrier per
-// buffer reports their completion.  The epilogue reads each pixel's row of
-// D from tensor memory and blends its two slices with the depth weight.
-// Tiles using more than 8 slices run one pass per 8.
+// no-swizzle K-major core-matrix layout, each image row as 4 consecutive
+// 16-byte rows (its 4 column shifts i), so that the operand of kernel row
+// u is the same buffer with its descriptor start moved by u image rows; the
+// B operand of each kernel row comes from a BF16 copy of the bank re-laid
+// out once per call (flipped, rows padded to a multiple of 16) and is
+// copied asynchronously (cp.async) into two shared buffers, 8 kernel rows at
+// a time, one chunk ahead of the tensor core.  One thread issues the MMAs;
+// an mbarrier per buffer reports their completion.  The epilogue reads each
+// pixel's row of D from tensor memory and blends its two slices with the
+// depth weight.  Tiles using more than 8 slices run one pass per 8.  Two
+// CTAs share an SM (about 102 KB of shared memory each at ks = 65), so one
+// stages its tile while the other's MMAs run.
 //
 // Also a device check of the building blocks: one CTA computes D = A_u B^T
 // for a 128-row window (starting at row u) of a K-major BF16 matrix, K = 32
@@ -84,14 +86,16 @@ __global__ void __launch_bounds__(128) tc_check_kernel(const __nv_bfloat16* __re
 // ---------------------------------------------------------------------------
 // BF16 render
 // ---------------------------------------------------------------------------
-constexpr int TR_Y = 16, TR_X = 8, TR_NT = 128, TR_N = 16, TR_UC = 16;
-constexpr int TR_MAXK = 2 * TR_NT;   // candidate slices of a tile (2 per pixel)
+constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 8;
+constexpr int TR_MAXK = 2 * TR_M;   // candidate slices of a tile (2 per pixel)
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
 
 __host__ __device__ inline int tr_kp(int ks) { return (ks + 15) / 16 * 16; }
+// A: KB K-blocks of R image rows x TR_X shifts x 16 B; B: 2 buffers of
+// TR_UC kernel rows x KB K-blocks x N rows x 16 B
 __host__ __device__ inline size_t tr_smem(int ks) {
   const int KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  return (size_t)KB * R * 128 + (size_t)2 * TR_UC * KB * 256;
+  return (size_t)KB * R * TR_X * 16 + (size_t)2 * TR_UC * KB * TR_N * 16;
 }
 inline size_t tr_bp_bytes(const RenderParams& P) {
   return (size_t)P.F * P.Z * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
@@ -126,15 +130,26 @@ __device__ __forceinline__ bool wait_flag(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
-__global__ void __launch_bounds__(TR_NT, 1) render_tc_kernel(const RenderParams P,
+// 16-byte asynchronous global -> shared copy; bytes = 0 writes zeros
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+__global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams P,
                                                              const __nv_bfloat16* __restrict__ bp,
                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ int s_cand[TR_MAXK], s_uniq[TR_MAXK], s_wcnt[2 * TR_NT / 32], s_nuniq;
+  __shared__ int s_cand[TR_MAXK], s_uniq[TR_MAXK], s_wcnt[TR_NT / 32], s_nuniq;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar[2];
   const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  const uint32_t LBO_A = (uint32_t)R * 128u, USTR = (uint32_t)KB * 256u;
+  const uint32_t LBO_A = (uint32_t)R * TR_X * 16u, USTR = (uint32_t)KB * TR_N * 16u;
   unsigned char* Asm = smem;
   unsigned char* Bsm = smem + (size_t)KB * LBO_A;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -144,35 +159,38 @@ __global__ void __launch_bounds__(TR_NT, 1) render_tc_kernel(const RenderParams 
   const int H = P.H, W = P.W;
   const bool two = P.Z > 1;
 
-  // 1. this thread's pixel (= its tensor-memory lane): selection
-  const int yy = y0 + (tid >> 3), xx = x0 + (tid & 7);
-  const bool valid = yy < H && xx < W;
+  // 1. threads 0..127: pixel m = tid (tensor-memory lane m) = tile row m / 4,
+  // column m % 4; selection and candidate slices
+  const bool pix = tid < TR_M;
+  const int yy = y0 + (tid >> 2), xx = x0 + (tid & 3);
+  const bool valid = pix && yy < H && xx < W;
   int key = -1;
   float t = 0.f;
   if (valid) select_slice(P, yy, xx, P.depth[((size_t)n * H + yy) * W + xx], &key, &t);
   const bool use0 = valid && (!two || t < 1.f), use1 = valid && two && t > 0.f;
-  s_cand[2 * tid] = use0 ? key : -1;
-  s_cand[2 * tid + 1] = use1 ? key + 1 : -1;
+  if (pix) {
+    s_cand[2 * tid] = use0 ? key : -1;
+    s_cand[2 * tid + 1] = use1 ? key + 1 : -1;
+  }
 
-  // 2. stage the image tile: core matrix (row r, K block kb) holds the 8
-  // shifts i of Ipad[y0 + r][x0 + i + 8 kb + e], e = 0..7
+  // 2. stage the image tile: 16-byte row (image row r, shift i) of K block
+  // kb holds Ipad[y0 + r][x0 + i + 8 kb + e], e = 0..7
   const unsigned short* img =
       reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * H * W;
   for (int pr = tid; pr < R * KB; pr += TR_NT) {
     const int r = pr / KB, kb = pr - r * KB;
     const size_t rowoff = (size_t)min(max(y0 + r - p, 0), H - 1) * W;
-    uint32_t v16[16];
+    uint32_t v[TR_X + 7];
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      v16[j] = img[rowoff + min(max(x0 + 8 * kb + j - p, 0), W - 1)];
-    unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * 128;
+    for (int j = 0; j < TR_X + 7; ++j) v[j] = img[rowoff + min(max(x0 + 8 * kb + j - p, 0), W - 1)];
+    unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_X * 16;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TR_X; ++i) {
       uint4 w;
-      w.x = v16[i] | (v16[i + 1] << 16);
-      w.y = v16[i + 2] | (v16[i + 3] << 16);
-      w.z = v16[i + 4] | (v16[i + 5] << 16);
-      w.w = v16[i + 6] | (v16[i + 7] << 16);
+      w.x = v[i] | (v[i + 1] << 16);
+      w.y = v[i + 2] | (v[i + 3] << 16);
+      w.z = v[i + 4] | (v[i + 5] << 16);
+      w.w = v[i + 6] | (v[i + 7] << 16);
       *reinterpret_cast<uint4*>(dst + i * 16) = w;
     }
   }
@@ -181,23 +199,18 @@ __global__ void __launch_bounds__(TR_NT, 1) render_tc_kernel(const RenderParams 
     tc::mbar_init(&s_bar[0], 1);
     tc::mbar_init(&s_bar[1], 1);
   }
-  tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
 
-  // 3. distinct slices of the tile, in candidate order
-  int first[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = 2 * tid + q, kq = s_cand[j];
-    bool f = kq >= 0;
-    for (int m = 0; m < j && f; ++m) f = s_cand[m] != kq;
-    first[q] = f ? 1 : 0;
-  }
+  // 3. distinct slices of the tile, in candidate order (thread j: candidate j)
   {
-    int cnt = first[0] + first[1], incl = cnt;
+    const int kq = s_cand[tid];
+    bool f = kq >= 0;
+    for (int m = 0; m < tid && f; ++m) f = s_cand[m] != kq;
+    const int cnt = f ? 1 : 0;
+    int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -207,97 +220,111 @@ __global__ void __launch_bounds__(TR_NT, 1) render_tc_kernel(const RenderParams 
     __syncthreads();
     int base = 0;
     for (int w = 0; w < warp; ++w) base += s_wcnt[w];
-    int pos = base + incl - cnt;
-    if (first[0]) s_uniq[pos++] = s_cand[2 * tid];
-    if (first[1]) s_uniq[pos] = s_cand[2 * tid + 1];
+    if (f) s_uniq[base + incl - 1] = kq;
     if (tid == TR_NT - 1) s_nuniq = base + incl;
   }
   __syncthreads();
   const int nuniq = s_nuniq;
   int idx0 = -1, idx1 = -1;
-  for (int m = 0; m < nuniq; ++m) {
-    const int km = s_uniq[m];
-    if (use0 && km == key) idx0 = m;
-    if (use1 && km == key + 1) idx1 = m;
-  }
+  if (pix)
+    for (int m = 0; m < nuniq; ++m) {
+      const int km = s_uniq[m];
+      if (use0 && km == key) idx0 = m;
+      if (use1 && km == key + 1) idx1 = m;
+    }
   const float w0 = two ? 1.f - t : 1.f, w1 = t;
 
-  // 4. passes of up to 8 slices: B streamed in chunks of TR_UC kernel rows
+  // 4. passes of up to 8 slices; B chunks of TR_UC kernel rows copied
+  // asynchronously into two buffers, one chunk ahead of the tensor core
   const int nch = (ks + TR_UC - 1) / TR_UC;
   const int npass = (nuniq + 7) / 8;
-  const uint32_t idesc = tc::idesc_bf16_f32(128, TR_N);
+  const int nsteps = npass * nch;
+  const int ngran = TR_UC * KB * TR_N;
+  const uint32_t idesc = tc::idesc_bf16_f32(TR_M, TR_N);
   const uint32_t a_base = tc::smem_u32(Asm), b_base = tc::smem_u32(Bsm);
   uint32_t ph[2] = {0u, 0u};
   bool busy[2] = {false, false};
-  bool ok = true;
   float outL = 0.f, outR = 0.f;
-  for (int pass = 0; pass < npass; ++pass) {
-    for (int ch = 0; ch < nch; ++ch) {
-      const int buf = ch & 1;
-      if (busy[buf]) {  // the tensor core may still read this buffer
-        ok = wait_flag(&s_bar[buf], ph[buf], err) && ok;
-        ph[buf] ^= 1u;
-        busy[buf] = false;
+  auto issue = [&](int step) {  // copies of chunk `step` into buffer step & 1
+    const int pass = step / nch, ch = step - pass * nch, buf = step & 1;
+    const uint32_t bdst = b_base + (uint32_t)buf * TR_UC * USTR;
+    for (int g = tid; g < ngran; g += TR_NT) {
+      const int ul = g / (KB * TR_N), rem = g - ul * KB * TR_N;
+      const int kb = rem / TR_N, nn = rem - kb * TR_N;
+      const int slot = pass * 8 + (nn & 7), side = nn >> 3, u = ch * TR_UC + ul;
+      const void* src = bp;
+      uint32_t bytes = 0;
+      if (slot < nuniq && u < ks) {
+        const size_t kl = (size_t)s_uniq[slot] * P.NL + lam;
+        src = bp + ((kl * ks + u) * 2 + side) * KP + 8 * kb;
+        bytes = 16;
       }
-      // rows (kernel row ul, K block kb, column nn = side * 8 + slot)
-      unsigned char* bdst = Bsm + (size_t)buf * TR_UC * USTR;
-      const int urows = min(TR_UC, ks - ch * TR_UC);
-      for (int e = tid; e < urows * KB * TR_N; e += TR_NT) {
-        const int ul = e / (KB * TR_N), rem = e - ul * KB * TR_N;
-        const int kb = rem / TR_N, nn = rem - kb * TR_N;
-        const int slot = pass * 8 + (nn & 7), side = nn >> 3, u = ch * TR_UC + ul;
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (slot < nuniq) {
-          const size_t kl = (size_t)s_uniq[slot] * P.NL + lam;
-          w = __ldg(reinterpret_cast<const uint4*>(bp + ((kl * ks + u) * 2 + side) * KP +
-                                                   8 * kb));
-        }
-        *reinterpret_cast<uint4*>(bdst + (size_t)ul * USTR + kb * 256 + nn * 16) = w;
-      }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        const uint32_t bb = b_base + (uint32_t)buf * TR_UC * USTR;
-        for (int ul = 0; ul < urows; ++ul) {
-          const int u = ch * TR_UC + ul;
-          for (int kq = 0; kq < KP / 16; ++kq) {
-            const uint64_t ad =
-                tc::smem_desc(a_base + (uint32_t)u * 128u + (uint32_t)kq * 2u * LBO_A, LBO_A, 128);
-            const uint64_t bd =
-                tc::smem_desc(bb + (uint32_t)ul * USTR + (uint32_t)kq * 512u, 256, 128);
-            tc::mma_bf16(tmem, ad, bd, idesc, !(ch == 0 && ul == 0 && kq == 0));
-          }
-        }
-        tc::commit(&s_bar[buf]);
-      }
-      busy[buf] = true;
+      cp16(bdst + (uint32_t)ul * USTR + kb * 256 + nn * 16, src, bytes);
     }
-    // every MMA of the pass has completed once both buffers report
-    for (int b = 0; b < 2; ++b)
-      if (busy[b]) {
-        ok = wait_flag(&s_bar[b], ph[b], err) && ok;
-        ph[b] ^= 1u;
-        busy[b] = false;
+    cp_commit();
+  };
+  if (nsteps > 0) issue(0);
+  for (int step = 0; step < nsteps; ++step) {
+    const int pass = step / nch, ch = step - pass * nch, buf = step & 1;
+    if (step + 1 < nsteps) {
+      const int nb = buf ^ 1;
+      if (busy[nb]) {  // the tensor core may still read that buffer
+        wait_flag(&s_bar[nb], ph[nb], err);
+        ph[nb] ^= 1u;
+        busy[nb] = false;
       }
-    tc::fence_after_sync();
-    float v[16];
-    tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
-#pragma unroll
-    for (int sl = 0; sl < 8; ++sl) {
-      const int ui = pass * 8 + sl;
-      if (ui == idx0) {
-        outL = fmaf(w0, v[sl], outL);
-        outR = fmaf(w0, v[8 + sl], outR);
-      }
-      if (ui == idx1) {
-        outL = fmaf(w1, v[sl], outL);
-        outR = fmaf(w1, v[8 + sl], outR);
-      }
+      issue(step + 1);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
+    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t bb = b_base + (uint32_t)buf * TR_UC * USTR;
+      const int urows = min(TR_UC, ks - ch * TR_UC);
+      for (int ul = 0; ul < urows; ++ul) {
+        const int u = ch * TR_UC + ul;
+        for (int kq = 0; kq < KP / 16; ++kq) {
+          const uint64_t ad = tc::smem_desc(
+              a_base + (uint32_t)u * TR_X * 16u + (uint32_t)kq * 2u * LBO_A, LBO_A, 128);
+          const uint64_t bd = tc::smem_desc(bb + (uint32_t)ul * USTR + (uint32_t)kq * 512u, 256, 128);
+          tc::mma_bf16(tmem, ad, bd, idesc, !(ch == 0 && ul == 0 && kq == 0));
+        }
+      }
+      tc::commit(&s_bar[buf]);
+    }
+    busy[buf] = true;
+    if (ch == nch - 1) {
+      // end of a pass: wait for its MMAs, then fold its slots into the pixels
+      for (int b = 0; b < 2; ++b)
+        if (busy[b]) {
+          wait_flag(&s_bar[b], ph[b], err);
+          ph[b] ^= 1u;
+          busy[b] = false;
+        }
+      tc::fence_after_sync();
+      if (warp < TR_M / 32) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+#pragma unroll
+        for (int sl = 0; sl < 8; ++sl) {
+          const int ui = pass * 8 + sl;
+          if (ui == idx0) {
+            outL = fmaf(w0, v[sl], outL);
+            outR = fmaf(w0, v[8 + sl], outR);
+          }
+          if (ui == idx1) {
+            outL = fmaf(w1, v[sl], outL);
+            outR = fmaf(w1, v[8 + sl], outR);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
   }
   if (valid) {
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P.out);
