@@ -13,12 +13,12 @@
 // u is the same buffer with its descriptor start moved by u image rows; the
 // B operand of each kernel row comes from a BF16 copy of the bank re-laid
 // out once per call (flipped, rows padded to a multiple of 16) and is
-// copied asynchronously (cp.async) into two shared buffers, 8 kernel rows at
-// a time, one chunk ahead of the tensor core.  One thread issues the MMAs;
+// copied asynchronously (cp.async) into a ring of four shared buffers, 4
+// kernel rows at a time, two chunks ahead of the tensor core.  One thread issues the MMAs;
 // an mbarrier per buffer reports their completion.  The epilogue reads each
 // pixel's row of D from tensor memory and blends its two slices with the
 // depth weight.  Tiles using more than 8 slices run one pass per 8.  Two
-// CTAs share an SM (about 102 KB of shared memory each at ks = 65), so one
+// CTAs share an SM (about 103 KB of shared memory each at ks = 65), so one
 // stages its tile while the other's MMAs run.
 //
 // Also a device check of the building blocks: one CTA computes D = A_u B^T
@@ -86,16 +86,19 @@ __global__ void __launch_bounds__(128) tc_check_kernel(const __nv_bfloat16* __re
 // ---------------------------------------------------------------------------
 // BF16 render
 // ---------------------------------------------------------------------------
-constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 8;
+constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 4, TR_NB = 4;
+constexpr int TR_AHEAD = 2;  // chunks copied ahead of the tensor core
+constexpr int TR_GPT = 4;  // B granules per thread per chunk (TR_UC * KB * TR_N / TR_NT, KB <= 10)
 constexpr int TR_MAXK = 2 * TR_M;   // candidate slices of a tile (2 per pixel)
+constexpr int TR_WIN = 4096;        // slice keys of a tile as bits above its smallest
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
 
 __host__ __device__ inline int tr_kp(int ks) { return (ks + 15) / 16 * 16; }
-// A: KB K-blocks of R image rows x TR_X shifts x 16 B; B: 2 buffers of
+// A: KB K-blocks of R image rows x TR_X shifts x 16 B; B: TR_NB buffers of
 // TR_UC kernel rows x KB K-blocks x N rows x 16 B
 __host__ __device__ inline size_t tr_smem(int ks) {
   const int KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  return (size_t)KB * R * TR_X * 16 + (size_t)2 * TR_UC * KB * TR_N * 16;
+  return (size_t)KB * R * TR_X * 16 + (size_t)TR_NB * TR_UC * KB * TR_N * 16;
 }
 inline size_t tr_bp_bytes(const RenderParams& P) {
   return (size_t)P.F * P.Z * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
@@ -146,8 +149,10 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_cand[TR_MAXK], s_uniq[TR_MAXK], s_wcnt[TR_NT / 32], s_nuniq;
+  __shared__ unsigned s_bits[TR_WIN / 32];
+  __shared__ int s_wpre[TR_WIN / 32], s_kmin, s_over;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ __align__(8) uint64_t s_bar[TR_NB];
   const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
   const uint32_t LBO_A = (uint32_t)R * TR_X * 16u, USTR = (uint32_t)KB * TR_N * 16u;
   unsigned char* Asm = smem;
@@ -159,6 +164,12 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   const int H = P.H, W = P.W;
   const bool two = P.Z > 1;
 
+  for (int i = tid; i < TR_WIN / 32; i += TR_NT) s_bits[i] = 0u;
+  if (tid == 0) {
+    s_kmin = 0x7fffffff;
+    s_over = 0;
+  }
+  __syncthreads();
   // 1. threads 0..127: pixel m = tid (tensor-memory lane m) = tile row m / 4,
   // column m % 4; selection and candidate slices
   const bool pix = tid < TR_M;
@@ -171,6 +182,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   if (pix) {
     s_cand[2 * tid] = use0 ? key : -1;
     s_cand[2 * tid + 1] = use1 ? key + 1 : -1;
+    if (use0 || use1) atomicMin(&s_kmin, use0 ? key : key + 1);
   }
 
   // 2. stage the image tile: 16-byte row (image row r, shift i) of K block
@@ -180,9 +192,24 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   for (int pr = tid; pr < R * KB; pr += TR_NT) {
     const int r = pr / KB, kb = pr - r * KB;
     const size_t rowoff = (size_t)min(max(y0 + r - p, 0), H - 1) * W;
-    uint32_t v[TR_X + 7];
+    const int xs = x0 + 8 * kb - p;  // image column of element 0
+    uint32_t v[TR_X + 8];
+    const unsigned short* src0 = img + rowoff + xs;
+    if (xs >= 0 && xs + TR_X + 8 <= W && (reinterpret_cast<uintptr_t>(src0) & 7) == 0) {
+      // interior and the absolute address 8-byte aligned (image planes of an
+      // odd size start at odd element offsets): three 8-byte loads
 #pragma unroll
-    for (int j = 0; j < TR_X + 7; ++j) v[j] = img[rowoff + min(max(x0 + 8 * kb + j - p, 0), W - 1)];
+      for (int q = 0; q < (TR_X + 8) / 4; ++q) {
+        const uint2 w = *reinterpret_cast<const uint2*>(src0 + 4 * q);
+        v[4 * q] = w.x & 0xffffu;
+        v[4 * q + 1] = w.x >> 16;
+        v[4 * q + 2] = w.y & 0xffffu;
+        v[4 * q + 3] = w.y >> 16;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < TR_X + 7; ++j) v[j] = img[rowoff + min(max(xs + j, 0), W - 1)];
+    }
     unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_X * 16;
 #pragma unroll
     for (int i = 0; i < TR_X; ++i) {
@@ -195,17 +222,60 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     }
   }
   if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
-  if (tid == 0) {
-    tc::mbar_init(&s_bar[0], 1);
-    tc::mbar_init(&s_bar[1], 1);
-  }
+  if (tid == 0)
+    for (int b = 0; b < TR_NB; ++b) tc::mbar_init(&s_bar[b], 1);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
 
-  // 3. distinct slices of the tile, in candidate order (thread j: candidate j)
+  // 3. distinct slices of the tile in ascending order: a bitmap of the
+  // candidate keys above the tile's smallest (an exhaustive comparison if a
+  // key lies beyond the window), then prefix counts
+  const int kmin = s_kmin;
   {
+    const int kq = s_cand[tid];
+    if (kq >= 0) {
+      const int d = kq - kmin;
+      if (d < TR_WIN) atomicOr(&s_bits[d >> 5], 1u << (d & 31));
+      else s_over = 1;
+    }
+  }
+  __syncthreads();
+  const bool over = s_over != 0;
+  if (!over) {
+    if (warp == 0) {  // exclusive prefix of the bit counts of the words
+      int c4[TR_WIN / 32 / 32], tot = 0;
+#pragma unroll
+      for (int q = 0; q < TR_WIN / 32 / 32; ++q) {
+        c4[q] = __popc(s_bits[lane * (TR_WIN / 32 / 32) + q]);
+        tot += c4[q];
+      }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - tot;
+#pragma unroll
+      for (int q = 0; q < TR_WIN / 32 / 32; ++q) {
+        s_wpre[lane * (TR_WIN / 32 / 32) + q] = run;
+        run += c4[q];
+      }
+      if (lane == 31) s_nuniq = incl;
+    }
+    __syncthreads();
+    for (int w = tid; w < TR_WIN / 32; w += TR_NT) {
+      unsigned b = s_bits[w];
+      int pos = s_wpre[w];
+      while (b) {
+        const int bit = __ffs(b) - 1;
+        b &= b - 1;
+        s_uniq[pos++] = kmin + 32 * w + bit;
+      }
+    }
+  } else {
     const int kq = s_cand[tid];
     bool f = kq >= 0;
     for (int m = 0; m < tid && f; ++m) f = s_cand[m] != kq;
@@ -225,55 +295,92 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   }
   __syncthreads();
   const int nuniq = s_nuniq;
-  int idx0 = -1, idx1 = -1;
-  if (pix)
-    for (int m = 0; m < nuniq; ++m) {
-      const int km = s_uniq[m];
-      if (use0 && km == key) idx0 = m;
-      if (use1 && km == key + 1) idx1 = m;
+  auto slot_of = [&](int k) {
+    if (!over) {
+      const int d = k - kmin;
+      return s_wpre[d >> 5] + __popc(s_bits[d >> 5] & ((1u << (d & 31)) - 1u));
     }
+    int idx = -1;
+    for (int m = 0; m < nuniq; ++m)
+      if (s_uniq[m] == k) idx = m;
+    return idx;
+  };
+  const int idx0 = use0 ? slot_of(key) : -1;
+  const int idx1 = use1 ? slot_of(key + 1) : -1;
   const float w0 = two ? 1.f - t : 1.f, w1 = t;
 
   // 4. passes of up to 8 slices; B chunks of TR_UC kernel rows copied
-  // asynchronously into two buffers, one chunk ahead of the tensor core
+  // asynchronously into a ring of TR_NB buffers, TR_AHEAD chunks ahead of
+  // the tensor core (a buffer is refilled TR_NB - TR_AHEAD chunks after its
+  // MMAs were issued)
   const int nch = (ks + TR_UC - 1) / TR_UC;
   const int npass = (nuniq + 7) / 8;
   const int nsteps = npass * nch;
   const int ngran = TR_UC * KB * TR_N;
   const uint32_t idesc = tc::idesc_bf16_f32(TR_M, TR_N);
   const uint32_t a_base = tc::smem_u32(Asm), b_base = tc::smem_u32(Bsm);
-  uint32_t ph[2] = {0u, 0u};
-  bool busy[2] = {false, false};
+  // this thread's granules of a chunk: (kernel row ul, K block kb, column
+  // nn) with nn the fastest index; the same for every chunk
+  uint32_t g_dst[TR_GPT];
+  int g_src[TR_GPT], g_ul[TR_GPT], g_nn[TR_GPT];
+#pragma unroll
+  for (int q = 0; q < TR_GPT; ++q) {
+    const int g = tid + q * TR_NT;
+    const int nn = g & (TR_N - 1), rest = g >> 4;
+    const int kb = rest % KB, ul = rest / KB;
+    g_dst[q] = (uint32_t)ul * USTR + kb * 256 + nn * 16;
+    g_src[q] = (nn >> 3) * KP + 8 * kb;  // side row and K block within a kernel row
+    g_ul[q] = g < ngran ? ul : TR_UC;    // TR_UC: no granule
+    g_nn[q] = nn & 7;
+  }
+  uint32_t ph[TR_NB];
+  bool busy[TR_NB];
+#pragma unroll
+  for (int b = 0; b < TR_NB; ++b) {
+    ph[b] = 0u;
+    busy[b] = false;
+  }
   float outL = 0.f, outR = 0.f;
-  auto issue = [&](int step) {  // copies of chunk `step` into buffer step & 1
-    const int pass = step / nch, ch = step - pass * nch, buf = step & 1;
-    const uint32_t bdst = b_base + (uint32_t)buf * TR_UC * USTR;
-    for (int g = tid; g < ngran; g += TR_NT) {
-      const int ul = g / (KB * TR_N), rem = g - ul * KB * TR_N;
-      const int kb = rem / TR_N, nn = rem - kb * TR_N;
-      const int slot = pass * 8 + (nn & 7), side = nn >> 3, u = ch * TR_UC + ul;
+  int i_pass = 0, i_ch = 0, i_buf = 0;  // the next chunk to copy
+  auto issue = [&]() {  // copies of the next chunk into its ring buffer
+    const int pass = i_pass, ch = i_ch;
+    const uint32_t bdst = b_base + (uint32_t)i_buf * TR_UC * USTR;
+    if (++i_ch == nch) {
+      i_ch = 0;
+      ++i_pass;
+    }
+    i_buf = (i_buf + 1) % TR_NB;
+#pragma unroll
+    for (int q = 0; q < TR_GPT; ++q) {
+      if (g_ul[q] >= TR_UC) continue;
+      const int slot = pass * 8 + g_nn[q], u = ch * TR_UC + g_ul[q];
       const void* src = bp;
       uint32_t bytes = 0;
       if (slot < nuniq && u < ks) {
         const size_t kl = (size_t)s_uniq[slot] * P.NL + lam;
-        src = bp + ((kl * ks + u) * 2 + side) * KP + 8 * kb;
+        src = bp + (kl * ks + u) * 2 * KP + g_src[q];
         bytes = 16;
       }
-      cp16(bdst + (uint32_t)ul * USTR + kb * 256 + nn * 16, src, bytes);
+      cp16(bdst + g_dst[q], src, bytes);
     }
     cp_commit();
   };
-  if (nsteps > 0) issue(0);
+  // descriptors: the start-address field is the low 14 bits (address >> 4),
+  // so moving an operand by k bytes adds k >> 4
+  const uint64_t a_desc0 = tc::smem_desc(a_base, LBO_A, 128);
+  const uint64_t b_desc0 = tc::smem_desc(b_base, 256, 128);
+  for (int q = 0; q < TR_AHEAD && q < nsteps; ++q) issue();
+  int pass = 0, ch = 0, buf = 0;
   for (int step = 0; step < nsteps; ++step) {
-    const int pass = step / nch, ch = step - pass * nch, buf = step & 1;
-    if (step + 1 < nsteps) {
-      const int nb = buf ^ 1;
-      if (busy[nb]) {  // the tensor core may still read that buffer
-        wait_flag(&s_bar[nb], ph[nb], err);
-        ph[nb] ^= 1u;
-        busy[nb] = false;
+    if (step + TR_AHEAD < nsteps) {
+      if (busy[i_buf]) {  // MMAs of chunk step + TR_AHEAD - TR_NB read it
+        wait_flag(&s_bar[i_buf], ph[i_buf], err);
+        ph[i_buf] ^= 1u;
+        busy[i_buf] = false;
       }
-      issue(step + 1);
+      issue();
+      cp_wait<TR_AHEAD>();
+    } else if (step + 1 < nsteps) {
       cp_wait<1>();
     } else {
       cp_wait<0>();
@@ -283,23 +390,27 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t bb = b_base + (uint32_t)buf * TR_UC * USTR;
       const int urows = min(TR_UC, ks - ch * TR_UC);
+      uint64_t ad = a_desc0 + ((uint64_t)(ch * TR_UC) * TR_X);  // u rows of 64 B = 4 x 16 B
+      uint64_t bd = b_desc0 + (uint64_t)((uint32_t)buf * TR_UC * USTR >> 4);
       for (int ul = 0; ul < urows; ++ul) {
-        const int u = ch * TR_UC + ul;
+        uint64_t a = ad, b = bd;
         for (int kq = 0; kq < KP / 16; ++kq) {
-          const uint64_t ad = tc::smem_desc(
-              a_base + (uint32_t)u * TR_X * 16u + (uint32_t)kq * 2u * LBO_A, LBO_A, 128);
-          const uint64_t bd = tc::smem_desc(bb + (uint32_t)ul * USTR + (uint32_t)kq * 512u, 256, 128);
-          tc::mma_bf16(tmem, ad, bd, idesc, !(ch == 0 && ul == 0 && kq == 0));
+          tc::mma_bf16(tmem, a, b, idesc, !(ch == 0 && ul == 0 && kq == 0));
+          a += (uint64_t)(2u * LBO_A >> 4);
+          b += (uint64_t)(512u >> 4);
         }
+        ad += (uint64_t)TR_X;              // next image row: 64 B
+        bd += (uint64_t)(USTR >> 4);
       }
       tc::commit(&s_bar[buf]);
     }
     busy[buf] = true;
-    if (ch == nch - 1) {
+    const bool pass_end = ch == nch - 1;
+    if (pass_end) {
       // end of a pass: wait for its MMAs, then fold its slots into the pixels
-      for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int b = 0; b < TR_NB; ++b)
         if (busy[b]) {
           wait_flag(&s_bar[b], ph[b], err);
           ph[b] ^= 1u;
@@ -324,6 +435,13 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       }
       tc::fence_before_sync();
       __syncthreads();
+    }
+    buf = (buf + 1) % TR_NB;
+    if (pass_end) {
+      ch = 0;
+      ++pass;
+    } else {
+      ++ch;
     }
   }
   if (valid) {
