@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(128) tc_check_kernel(const __nv_bfloat16* __re
 // BF16 render
 // ---------------------------------------------------------------------------
 constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 4, TR_NB = 4;
-constexpr int TR_AHEAD = 2;  // chunks copied ahead of the tensor core
-constexpr int TR_GPT = 4;  // B granules per thread per chunk (TR_UC * KB * TR_N / TR_NT, KB <= 10)
+constexpr int TR_NPROD = TR_NT - 32;  // producer threads (warps 1..7)
+constexpr int TR_GPT = 3;  // B granules per producer per chunk (TR_UC * KB * TR_N <= 640)
 constexpr int TR_MAXK = 2 * TR_M;   // candidate slices of a tile (2 per pixel)
 constexpr int TR_WIN = 4096;        // slice keys of a tile as bits above its smallest
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   __shared__ unsigned s_bits[TR_WIN / 32];
   __shared__ int s_wpre[TR_WIN / 32], s_kmin, s_over;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_bar[TR_NB];
+  __shared__ __align__(8) uint64_t s_full[TR_NB], s_empty[TR_NB], s_acc;
+  __shared__ long long s_rowb[8];
   const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
   const uint32_t LBO_A = (uint32_t)R * TR_X * 16u, USTR = (uint32_t)KB * TR_N * 16u;
   unsigned char* Asm = smem;
@@ -222,8 +223,14 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     }
   }
   if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
-  if (tid == 0)
-    for (int b = 0; b < TR_NB; ++b) tc::mbar_init(&s_bar[b], 1);
+  if (tid == 0) {
+    for (int b = 0; b < TR_NB; ++b) {
+      tc::mbar_init(&s_full[b], TR_NPROD);
+      tc::mbar_init(&s_empty[b], 1);
+    }
+    tc::mbar_init(&s_acc, 1);
+  }
+  tc::fence_async_smem();  // the staged tile, read by the tensor core
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -309,140 +316,113 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   const int idx1 = use1 ? slot_of(key + 1) : -1;
   const float w0 = two ? 1.f - t : 1.f, w1 = t;
 
-  // 4. passes of up to 8 slices; B chunks of TR_UC kernel rows copied
-  // asynchronously into a ring of TR_NB buffers, TR_AHEAD chunks ahead of
-  // the tensor core (a buffer is refilled TR_NB - TR_AHEAD chunks after its
-  // MMAs were issued)
+  // 4. passes of up to 8 slices.  Warps 1..7 copy the B chunks (TR_UC
+  // kernel rows) into a ring of TR_NB buffers with cp.async and report each
+  // full buffer on its mbarrier; thread 0 waits for a full buffer, issues
+  // its MMAs and lets the tensor core report the buffer empty again, so no
+  // CTA barrier sits inside a pass.  At the end of a pass the tensor core
+  // reports the accumulator, warps 0..3 fold it into their pixels, and the
+  // CTA synchronises before the next pass overwrites it.
   const int nch = (ks + TR_UC - 1) / TR_UC;
   const int npass = (nuniq + 7) / 8;
-  const int nsteps = npass * nch;
   const int ngran = TR_UC * KB * TR_N;
   const uint32_t idesc = tc::idesc_bf16_f32(TR_M, TR_N);
   const uint32_t a_base = tc::smem_u32(Asm), b_base = tc::smem_u32(Bsm);
-  // this thread's granules of a chunk: (kernel row ul, K block kb, column
-  // nn) with nn the fastest index; the same for every chunk
+  const uint64_t a_desc0 = tc::smem_desc(a_base, LBO_A, 128);
+  const uint64_t b_desc0 = tc::smem_desc(b_base, 256, 128);
+  // this producer's granules of a chunk: (kernel row ul, K block kb, column
+  // nn), nn fastest; the same for every chunk
+  const int ptid = tid - 32;
   uint32_t g_dst[TR_GPT];
-  int g_src[TR_GPT], g_ul[TR_GPT], g_nn[TR_GPT];
+  int g_off[TR_GPT], g_ul[TR_GPT], g_sl[TR_GPT];
 #pragma unroll
   for (int q = 0; q < TR_GPT; ++q) {
-    const int g = tid + q * TR_NT;
+    const int g = ptid + q * TR_NPROD;
     const int nn = g & (TR_N - 1), rest = g >> 4;
     const int kb = rest % KB, ul = rest / KB;
     g_dst[q] = (uint32_t)ul * USTR + kb * 256 + nn * 16;
-    g_src[q] = (nn >> 3) * KP + 8 * kb;  // side row and K block within a kernel row
-    g_ul[q] = g < ngran ? ul : TR_UC;    // TR_UC: no granule
-    g_nn[q] = nn & 7;
-  }
-  uint32_t ph[TR_NB];
-  bool busy[TR_NB];
-#pragma unroll
-  for (int b = 0; b < TR_NB; ++b) {
-    ph[b] = 0u;
-    busy[b] = false;
+    g_off[q] = (nn >> 3) * KP + 8 * kb;           // side row, K block
+    g_ul[q] = (ptid >= 0 && g < ngran) ? ul : TR_UC;  // TR_UC: no granule
+    g_sl[q] = nn & 7;
   }
   float outL = 0.f, outR = 0.f;
-  int i_pass = 0, i_ch = 0, i_buf = 0;  // the next chunk to copy
-  auto issue = [&]() {  // copies of the next chunk into its ring buffer
-    const int pass = i_pass, ch = i_ch;
-    const uint32_t bdst = b_base + (uint32_t)i_buf * TR_UC * USTR;
-    if (++i_ch == nch) {
-      i_ch = 0;
-      ++i_pass;
+  for (int pass = 0; pass < npass; ++pass) {
+    if (tid < 8) {  // element offset of each slot's flipped kernel rows
+      const int ui = pass * 8 + tid;
+      s_rowb[tid] = ui < nuniq ? ((long long)s_uniq[ui] * P.NL + lam) * ks * 2 * KP : -1;
     }
-    i_buf = (i_buf + 1) % TR_NB;
-#pragma unroll
-    for (int q = 0; q < TR_GPT; ++q) {
-      if (g_ul[q] >= TR_UC) continue;
-      const int slot = pass * 8 + g_nn[q], u = ch * TR_UC + g_ul[q];
-      const void* src = bp;
-      uint32_t bytes = 0;
-      if (slot < nuniq && u < ks) {
-        const size_t kl = (size_t)s_uniq[slot] * P.NL + lam;
-        src = bp + (kl * ks + u) * 2 * KP + g_src[q];
-        bytes = 16;
+    __syncthreads();
+    const int c0 = pass * nch;  // global index of the pass's first chunk
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int ch = 0; ch < nch; ++ch) {
+          const int c = c0 + ch, b = c % TR_NB;
+          wait_flag(&s_full[b], (uint32_t)(c / TR_NB) & 1u, err);
+          tc::fence_after_sync();
+          const int urows = min(TR_UC, ks - ch * TR_UC);
+          // the start-address field is the low 14 bits (address >> 4)
+          uint64_t ad = a_desc0 + (uint64_t)(ch * TR_UC * TR_X);  // rows of 64 B
+          uint64_t bd = b_desc0 + (uint64_t)((uint32_t)b * TR_UC * USTR >> 4);
+          for (int ul = 0; ul < urows; ++ul) {
+            uint64_t a = ad, bb = bd;
+            for (int kq = 0; kq < KP / 16; ++kq) {
+              tc::mma_bf16(tmem, a, bb, idesc, !(ch == 0 && ul == 0 && kq == 0));
+              a += (uint64_t)(2u * LBO_A >> 4);
+              bb += (uint64_t)(512u >> 4);
+            }
+            ad += (uint64_t)TR_X;
+            bd += (uint64_t)(USTR >> 4);
+          }
+          tc::commit(&s_empty[b]);
+        }
+        tc::commit(&s_acc);
       }
-      cp16(bdst + g_dst[q], src, bytes);
-    }
-    cp_commit();
-  };
-  // descriptors: the start-address field is the low 14 bits (address >> 4),
-  // so moving an operand by k bytes adds k >> 4
-  const uint64_t a_desc0 = tc::smem_desc(a_base, LBO_A, 128);
-  const uint64_t b_desc0 = tc::smem_desc(b_base, 256, 128);
-  for (int q = 0; q < TR_AHEAD && q < nsteps; ++q) issue();
-  int pass = 0, ch = 0, buf = 0;
-  for (int step = 0; step < nsteps; ++step) {
-    if (step + TR_AHEAD < nsteps) {
-      if (busy[i_buf]) {  // MMAs of chunk step + TR_AHEAD - TR_NB read it
-        wait_flag(&s_bar[i_buf], ph[i_buf], err);
-        ph[i_buf] ^= 1u;
-        busy[i_buf] = false;
-      }
-      issue();
-      cp_wait<TR_AHEAD>();
-    } else if (step + 1 < nsteps) {
-      cp_wait<1>();
+      __syncwarp();
     } else {
+      for (int ch = 0; ch < nch; ++ch) {
+        const int c = c0 + ch, b = c % TR_NB;
+        if (c >= TR_NB)  // the MMAs of chunk c - TR_NB read this buffer
+          wait_flag(&s_empty[b], (uint32_t)(c / TR_NB - 1) & 1u, err);
+        const uint32_t bdst = b_base + (uint32_t)b * TR_UC * USTR;
+#pragma unroll
+        for (int q = 0; q < TR_GPT; ++q) {
+          const int u = ch * TR_UC + g_ul[q];
+          const long long rb = s_rowb[g_sl[q]];
+          if (g_ul[q] < TR_UC && u < ks && rb >= 0)
+            cp16(bdst + g_dst[q], bp + rb + (long long)u * 2 * KP + g_off[q], 16);
+        }
+        cp_commit();
+        if (ch > 0) {  // the previous chunk has landed: report it
+          cp_wait<1>();
+          tc::fence_async_smem();
+          tc::mbar_arrive(&s_full[(c - 1) % TR_NB]);
+        }
+      }
       cp_wait<0>();
+      tc::fence_async_smem();
+      tc::mbar_arrive(&s_full[(c0 + nch - 1) % TR_NB]);
     }
-    tc::fence_async_smem();
+    // the pass's accumulator
+    if (warp < TR_M / 32) {
+      wait_flag(&s_acc, (uint32_t)pass & 1u, err);
+      tc::fence_after_sync();
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) {
+        const int ui = pass * 8 + sl;
+        if (ui == idx0) {
+          outL = fmaf(w0, v[sl], outL);
+          outR = fmaf(w0, v[8 + sl], outR);
+        }
+        if (ui == idx1) {
+          outL = fmaf(w1, v[sl], outL);
+          outR = fmaf(w1, v[8 + sl], outR);
+        }
+      }
+    }
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const int urows = min(TR_UC, ks - ch * TR_UC);
-      uint64_t ad = a_desc0 + ((uint64_t)(ch * TR_UC) * TR_X);  // u rows of 64 B = 4 x 16 B
-      uint64_t bd = b_desc0 + (uint64_t)((uint32_t)buf * TR_UC * USTR >> 4);
-      for (int ul = 0; ul < urows; ++ul) {
-        uint64_t a = ad, b = bd;
-        for (int kq = 0; kq < KP / 16; ++kq) {
-          tc::mma_bf16(tmem, a, b, idesc, !(ch == 0 && ul == 0 && kq == 0));
-          a += (uint64_t)(2u * LBO_A >> 4);
-          b += (uint64_t)(512u >> 4);
-        }
-        ad += (uint64_t)TR_X;              // next image row: 64 B
-        bd += (uint64_t)(USTR >> 4);
-      }
-      tc::commit(&s_bar[buf]);
-    }
-    busy[buf] = true;
-    const bool pass_end = ch == nch - 1;
-    if (pass_end) {
-      // end of a pass: wait for its MMAs, then fold its slots into the pixels
-#pragma unroll
-      for (int b = 0; b < TR_NB; ++b)
-        if (busy[b]) {
-          wait_flag(&s_bar[b], ph[b], err);
-          ph[b] ^= 1u;
-          busy[b] = false;
-        }
-      tc::fence_after_sync();
-      if (warp < TR_M / 32) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
-#pragma unroll
-        for (int sl = 0; sl < 8; ++sl) {
-          const int ui = pass * 8 + sl;
-          if (ui == idx0) {
-            outL = fmaf(w0, v[sl], outL);
-            outR = fmaf(w0, v[8 + sl], outR);
-          }
-          if (ui == idx1) {
-            outL = fmaf(w1, v[sl], outL);
-            outR = fmaf(w1, v[8 + sl], outR);
-          }
-        }
-      }
-      tc::fence_before_sync();
-      __syncthreads();
-    }
-    buf = (buf + 1) % TR_NB;
-    if (pass_end) {
-      ch = 0;
-      ++pass;
-    } else {
-      ++ch;
-    }
   }
   if (valid) {
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P.out);
