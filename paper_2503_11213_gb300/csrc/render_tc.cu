@@ -90,15 +90,19 @@ constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 4
 constexpr int TR_NPROD = TR_NT - 32;  // producer threads (warps 1..7)
 constexpr int TR_GPT = 3;  // B granules per producer per chunk (TR_UC * KB * TR_N <= 640)
 constexpr int TR_MAXK = 2 * TR_M;   // candidate slices of a tile (2 per pixel)
+constexpr int TR_SI = 4;            // staged (row, K block) items per thread
 constexpr int TR_WIN = 4096;        // slice keys of a tile as bits above its smallest
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
 
 __host__ __device__ inline int tr_kp(int ks) { return (ks + 15) / 16 * 16; }
 // A: KB K-blocks of R image rows x TR_X shifts x 16 B; B: TR_NB buffers of
 // TR_UC kernel rows x KB K-blocks x N rows x 16 B
+// K-block stride of the staged A operand: 16 bytes more than the block, so
+// that the staging stores of consecutive K blocks fall into different banks
+__host__ __device__ inline uint32_t tr_lbo_a(int ks) { return (uint32_t)(TR_Y + ks - 1) * TR_X * 16u + 16u; }
 __host__ __device__ inline size_t tr_smem(int ks) {
-  const int KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  return (size_t)KB * R * TR_X * 16 + (size_t)TR_NB * TR_UC * KB * TR_N * 16;
+  const int KP = tr_kp(ks), KB = KP / 8;
+  return (size_t)KB * tr_lbo_a(ks) + (size_t)TR_NB * TR_UC * KB * TR_N * 16;
 }
 inline size_t tr_bp_bytes(const RenderParams& P) {
   return (size_t)P.F * P.Z * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   __shared__ __align__(8) uint64_t s_full[TR_NB], s_empty[TR_NB], s_acc;
   __shared__ long long s_rowb[8];
   const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  const uint32_t LBO_A = (uint32_t)R * TR_X * 16u, USTR = (uint32_t)KB * TR_N * 16u;
+  const uint32_t LBO_A = tr_lbo_a(ks), USTR = (uint32_t)KB * TR_N * 16u;
   unsigned char* Asm = smem;
   unsigned char* Bsm = smem + (size_t)KB * LBO_A;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -172,54 +176,74 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   }
   __syncthreads();
   // 1. threads 0..127: pixel m = tid (tensor-memory lane m) = tile row m / 4,
-  // column m % 4; selection and candidate slices
+  // column m % 4.  Its depth is loaded first and used after the staging
+  // loads below have been issued.
   const bool pix = tid < TR_M;
   const int yy = y0 + (tid >> 2), xx = x0 + (tid & 3);
   const bool valid = pix && yy < H && xx < W;
+  const float dep = valid ? P.depth[((size_t)n * H + yy) * W + xx] : 1.f;
+
+  // 2. stage the image tile: 16-byte row (image row r, shift i) of K block
+  // kb holds Ipad[y0 + r][x0 + i + 8 kb + e], e = 0..7.  Every thread first
+  // loads the 12 image values of each of its (row, K block) items (packed in
+  // pairs), then builds and stores the 4 shifted rows of each.
+  const unsigned short* img =
+      reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * H * W;
+  const int nitem = R * KB;  // <= TR_SI * TR_NT (checked on the host)
+  uint32_t raw[TR_SI][6];
+#pragma unroll
+  for (int q = 0; q < TR_SI; ++q) {
+    const int pr = tid + q * TR_NT;
+    if (pr < nitem) {
+      const int r = pr / KB, kb = pr - r * KB;
+      const size_t rowoff = (size_t)min(max(y0 + r - p, 0), H - 1) * W;
+      const int xs = x0 + 8 * kb - p;  // image column of element 0
+      const unsigned short* src0 = img + rowoff + xs;
+      if (xs >= 0 && xs + TR_X + 8 <= W && (reinterpret_cast<uintptr_t>(src0) & 7) == 0) {
+        // interior and the absolute address 8-byte aligned (image planes of
+        // an odd size start at odd element offsets): three 8-byte loads
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+          const uint2 d = *reinterpret_cast<const uint2*>(src0 + 4 * w);
+          raw[q][2 * w] = d.x;
+          raw[q][2 * w + 1] = d.y;
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < 6; ++w) {
+          const uint32_t lo = img[rowoff + min(max(xs + 2 * w, 0), W - 1)];
+          const uint32_t hi = 2 * w + 1 < TR_X + 7 ? img[rowoff + min(max(xs + 2 * w + 1, 0), W - 1)] : 0u;
+          raw[q][w] = lo | (hi << 16);
+        }
+      }
+    }
+  }
   int key = -1;
   float t = 0.f;
-  if (valid) select_slice(P, yy, xx, P.depth[((size_t)n * H + yy) * W + xx], &key, &t);
+  if (valid) select_slice(P, yy, xx, dep, &key, &t);
   const bool use0 = valid && (!two || t < 1.f), use1 = valid && two && t > 0.f;
   if (pix) {
     s_cand[2 * tid] = use0 ? key : -1;
     s_cand[2 * tid + 1] = use1 ? key + 1 : -1;
     if (use0 || use1) atomicMin(&s_kmin, use0 ? key : key + 1);
   }
-
-  // 2. stage the image tile: 16-byte row (image row r, shift i) of K block
-  // kb holds Ipad[y0 + r][x0 + i + 8 kb + e], e = 0..7
-  const unsigned short* img =
-      reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * H * W;
-  for (int pr = tid; pr < R * KB; pr += TR_NT) {
-    const int r = pr / KB, kb = pr - r * KB;
-    const size_t rowoff = (size_t)min(max(y0 + r - p, 0), H - 1) * W;
-    const int xs = x0 + 8 * kb - p;  // image column of element 0
-    uint32_t v[TR_X + 8];
-    const unsigned short* src0 = img + rowoff + xs;
-    if (xs >= 0 && xs + TR_X + 8 <= W && (reinterpret_cast<uintptr_t>(src0) & 7) == 0) {
-      // interior and the absolute address 8-byte aligned (image planes of an
-      // odd size start at odd element offsets): three 8-byte loads
 #pragma unroll
-      for (int q = 0; q < (TR_X + 8) / 4; ++q) {
-        const uint2 w = *reinterpret_cast<const uint2*>(src0 + 4 * q);
-        v[4 * q] = w.x & 0xffffu;
-        v[4 * q + 1] = w.x >> 16;
-        v[4 * q + 2] = w.y & 0xffffu;
-        v[4 * q + 3] = w.y >> 16;
+  for (int q = 0; q < TR_SI; ++q) {
+    const int pr = tid + q * TR_NT;
+    if (pr < nitem) {
+      const int r = pr / KB, kb = pr - r * KB;
+      // element e of the item: half (e & 1) of word e / 2
+      auto el = [&](int e) { return (raw[q][e >> 1] >> (16 * (e & 1))) & 0xffffu; };
+      unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_X * 16;
+#pragma unroll
+      for (int i = 0; i < TR_X; ++i) {
+        uint4 w;
+        w.x = el(i) | (el(i + 1) << 16);
+        w.y = el(i + 2) | (el(i + 3) << 16);
+        w.z = el(i + 4) | (el(i + 5) << 16);
+        w.w = el(i + 6) | (el(i + 7) << 16);
+        *reinterpret_cast<uint4*>(dst + i * 16) = w;
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < TR_X + 7; ++j) v[j] = img[rowoff + min(max(xs + j, 0), W - 1)];
-    }
-    unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_X * 16;
-#pragma unroll
-    for (int i = 0; i < TR_X; ++i) {
-      uint4 w;
-      w.x = v[i] | (v[i + 1] << 16);
-      w.y = v[i + 2] | (v[i + 3] << 16);
-      w.z = v[i + 4] | (v[i + 5] << 16);
-      w.w = v[i + 6] | (v[i + 7] << 16);
-      *reinterpret_cast<uint4*>(dst + i * 16) = w;
     }
   }
   if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
@@ -459,7 +483,9 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
   if (layout->dtype != SD_BF16 && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
-  if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024) return SD_ERR_UNSUPPORTED;
+  if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024 ||
+      (TR_Y + P.ks - 1) * (tr_kp(P.ks) / 8) > TR_SI * TR_NT)
+    return SD_ERR_UNSUPPORTED;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
   if ((long long)N * C > 65535 || (long long)H * W > (1ll << 31) ||
       (H + TR_Y - 1) / TR_Y > 65535)
