@@ -2,24 +2,27 @@
 // images through a BF16 bank on the 5th-generation tensor cores (tcgen05),
 // FP32 accumulation in tensor memory.
 //
-// A CTA renders a tile of 32 rows x 4 columns = 128 pixels (the MMA's M) of
-// one channel.  For kernel row u the tile's outputs are a product
-//   D[(g, i), n] += sum_v Ipad[y0+g+u, x0+i+v] * Kf_n[u][v],
-// rows (g, i) = pixel (tile row g, column i), columns n = (side, slice slot)
-// of the up to 8 bank slices the tile's pixels use (N = 16), K = v.  The
-// A operand is the image tile staged once in shared memory in the
-// no-swizzle K-major core-matrix layout, each image row as 4 consecutive
-// 16-byte rows (its 4 column shifts i), so that the operand of kernel row
-// u is the same buffer with its descriptor start moved by u image rows; the
-// B operand of each kernel row comes from a BF16 copy of the bank re-laid
-// out once per call (flipped, rows padded to a multiple of 16) and is
-// copied asynchronously (cp.async) into a ring of four shared buffers, 4
-// kernel rows at a time, two chunks ahead of the tensor core.  One thread issues the MMAs;
-// an mbarrier per buffer reports their completion.  The epilogue reads each
-// pixel's row of D from tensor memory and blends its two slices with the
+// A CTA renders a tile of 32 rows x 16 columns of one channel as 4 column
+// blocks of 4 pixels.  For kernel row u the tile's outputs are a product
+// (M = 128, N = 64, K = the kernel row plus 3, padded to 16):
+//   D[(g, cb), (i, side, slot)] += sum_w Ipad[y0+g+u, x0+4cb+w] * Kf[u][w-i]
+// rows (g, cb) = tile row g, column block cb; columns = shift i of the
+// block's pixel x0+4cb+i, side and one of the up to 8 bank slices the tile
+// uses.  A is the image tile staged once in shared memory (no-swizzle
+// K-major core matrices, the 4 blocks of an image row as consecutive 16-byte
+// rows), so the operand of kernel row u is the same buffer with its
+// descriptor start moved by u image rows.  B holds each slice's flipped
+// kernel row 4 times, shifted by i = 0..3 (a banded copy), so one image
+// operand row serves 4 pixels x 16 (side, slot) columns: the shared-memory
+// bytes the tensor core reads per output are a quarter of those of a
+// pixels-as-rows product with N = 16.  Four producer warps build the B
+// chunks (one kernel row each) from a BF16 re-layout of the bank made once
+// per call (flipped, rows padded to a multiple of 16) into a ring of four
+// buffers and report them on mbarriers; one thread issues the MMAs and the
+// tensor core reports each buffer empty again.  The epilogue reads each
+// pixel's 16 columns from tensor memory and blends its two slices with the
 // depth weight.  Tiles using more than 8 slices run one pass per 8.  Two
-// CTAs share an SM (about 103 KB of shared memory each at ks = 65), so one
-// stages its tile while the other's MMAs run.
+// CTAs share an SM (about 108 KB of shared memory each at ks = 65).
 //
 // Also a device check of the building blocks: one CTA computes D = A_u B^T
 // for a 128-row window (starting at row u) of a K-major BF16 matrix, K = 32
@@ -86,23 +89,38 @@ __global__ void __launch_bounds__(128) tc_check_kernel(const __nv_bfloat16* __re
 // ---------------------------------------------------------------------------
 // BF16 render
 // ---------------------------------------------------------------------------
-constexpr int TR_Y = 32, TR_X = 4, TR_M = 128, TR_NT = 256, TR_N = 16, TR_UC = 4, TR_NB = 4;
-constexpr int TR_NPROD = TR_NT - 32;  // producer threads (warps 1..7)
-constexpr int TR_GPT = 3;  // B granules per producer per chunk (TR_UC * KB * TR_N <= 640)
-constexpr int TR_MAXK = 2 * TR_M;   // candidate slices of a tile (2 per pixel)
-constexpr int TR_SI = 4;            // staged (row, K block) items per thread
-constexpr int TR_WIN = 4096;        // slice keys of a tile as bits above its smallest
+constexpr int TR_Y = 32;              // tile rows
+constexpr int TR_CB = 4;              // column blocks of a tile (A rows per image row)
+constexpr int TR_J = 4;               // pixels per column block (shifted copies in B)
+constexpr int TR_XW = TR_CB * TR_J;   // tile width
+constexpr int TR_M = 128;             // A rows = TR_Y * TR_CB
+constexpr int TR_NT = 256;
+constexpr int TR_SL = 8;              // slices per pass
+constexpr int TR_SS = 2 * TR_SL;      // (side, slot) rows of B per shift
+constexpr int TR_N = TR_J * TR_SS;    // 64
+constexpr int TR_NB = 4;              // B ring buffers = producer warps 4..7
+constexpr int TR_MAXK = 2 * TR_Y * TR_XW;  // candidate slices of a tile (2 per pixel)
+constexpr int TR_SI = 4;              // staged (row, K block) items per thread
+constexpr int TR_TPL = 5;             // B tasks per producer lane and kernel row (16 KB <= 160)
+constexpr int TR_WIN = 4096;          // slice keys of a tile as bits above its smallest
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
 
+// bank rows: flipped kernel rows padded to a multiple of 16 elements
 __host__ __device__ inline int tr_kp(int ks) { return (ks + 15) / 16 * 16; }
-// A: KB K-blocks of R image rows x TR_X shifts x 16 B; B: TR_NB buffers of
-// TR_UC kernel rows x KB K-blocks x N rows x 16 B
+// K extent of the products: the kernel row plus the TR_J - 1 shifts
+__host__ __device__ inline int tr_kk(int ks) { return (ks + TR_J - 1 + 15) / 16 * 16; }
 // K-block stride of the staged A operand: 16 bytes more than the block, so
 // that the staging stores of consecutive K blocks fall into different banks
-__host__ __device__ inline uint32_t tr_lbo_a(int ks) { return (uint32_t)(TR_Y + ks - 1) * TR_X * 16u + 16u; }
+__host__ __device__ inline uint32_t tr_lbo_a(int ks) {
+  return (uint32_t)(TR_Y + ks - 1) * TR_CB * 16u + 16u;
+}
+__host__ __device__ inline size_t tr_a_bytes(int ks) {
+  return ((size_t)(tr_kk(ks) / 8) * tr_lbo_a(ks) + 1023) / 1024 * 1024;
+}
+// one B buffer: a kernel row's K blocks of TR_N rows x 16 bytes
+__host__ __device__ inline size_t tr_b_bytes(int ks) { return (size_t)(tr_kk(ks) / 8) * TR_N * 16; }
 __host__ __device__ inline size_t tr_smem(int ks) {
-  const int KP = tr_kp(ks), KB = KP / 8;
-  return (size_t)KB * tr_lbo_a(ks) + (size_t)TR_NB * TR_UC * KB * TR_N * 16;
+  return tr_a_bytes(ks) + (size_t)TR_NB * tr_b_bytes(ks);
 }
 inline size_t tr_bp_bytes(const RenderParams& P) {
   return (size_t)P.F * P.Z * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
@@ -137,33 +155,36 @@ __device__ __forceinline__ bool wait_flag(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
-// 16-byte asynchronous global -> shared copy; bytes = 0 writes zeros
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-               "r"(bytes));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// The render of one tile of 32 rows x 16 columns (4 blocks of 4 columns) of
+// one channel.  For kernel row u and slice row n = (shift i, side, slot):
+//   D[(g, cb), n] += sum_w Ipad[y0+g+u, x0+4cb+w] * Kf_(side,slot)[u][w-i]
+// so D[(g, cb), (i, side, slot)] is the output of pixel (y0+g, x0+4cb+i).
+// A (128 x K) is the image tile staged once with its 4 column blocks as
+// consecutive 16-byte rows (the operand of row u is the same buffer moved by
+// u image rows); B (64 x K) is built per kernel row from the flipped bank
+// rows: its row (i, side, slot) is the kernel row shifted right by i.
 __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams P,
                                                              const __nv_bfloat16* __restrict__ bp,
                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ int s_cand[TR_MAXK], s_uniq[TR_MAXK], s_wcnt[TR_NT / 32], s_nuniq;
+  __shared__ int s_uniq[TR_MAXK], s_wcnt[TR_NT / 32], s_nuniq;
   __shared__ unsigned s_bits[TR_WIN / 32];
   __shared__ int s_wpre[TR_WIN / 32], s_kmin, s_over;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_full[TR_NB], s_empty[TR_NB], s_acc;
-  __shared__ long long s_rowb[8];
-  const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KB = KP / 8, R = TR_Y + ks - 1;
-  const uint32_t LBO_A = tr_lbo_a(ks), USTR = (uint32_t)KB * TR_N * 16u;
+  const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KK = tr_kk(ks), KB = KK / 8,
+            R = TR_Y + ks - 1;
+  const uint32_t LBO_A = tr_lbo_a(ks), BBUF = (uint32_t)tr_b_bytes(ks);
   unsigned char* Asm = smem;
-  unsigned char* Bsm = smem + (size_t)KB * LBO_A;
+  unsigned char* Bsm = smem + tr_a_bytes(ks);
+  // candidate keys of the tile, in the B ring (free until the passes start)
+  int* s_cand = reinterpret_cast<int*>(Bsm);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * TR_X, y0 = blockIdx.y * TR_Y;
+  const int x0 = blockIdx.x * TR_XW, y0 = blockIdx.y * TR_Y;
   const int n = blockIdx.z / P.C, c = blockIdx.z - n * P.C;
   const int lam = (P.NL == P.C) ? c : 0;
   const int H = P.H, W = P.W;
@@ -175,22 +196,24 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     s_over = 0;
   }
   __syncthreads();
-  // 1. threads 0..127: pixel m = tid (tensor-memory lane m) = tile row m / 4,
-  // column m % 4.  Its depth is loaded first and used after the staging
-  // loads below have been issued.
+  // 1. threads 0..127: A row m = tid (tensor-memory lane m) = tile row m / 4,
+  // column block m % 4, pixels i = 0..3.  Depths are loaded first and used
+  // after the staging loads below have been issued.
   const bool pix = tid < TR_M;
-  const int yy = y0 + (tid >> 2), xx = x0 + (tid & 3);
-  const bool valid = pix && yy < H && xx < W;
-  const float dep = valid ? P.depth[((size_t)n * H + yy) * W + xx] : 1.f;
+  const int yy = y0 + (tid >> 2), xb = x0 + TR_J * (tid & 3);
+  float dep[TR_J];
+#pragma unroll
+  for (int i = 0; i < TR_J; ++i)
+    dep[i] = (pix && yy < H && xb + i < W) ? P.depth[((size_t)n * H + yy) * W + xb + i] : 1.f;
 
-  // 2. stage the image tile: 16-byte row (image row r, shift i) of K block
-  // kb holds Ipad[y0 + r][x0 + i + 8 kb + e], e = 0..7.  Every thread first
-  // loads the 12 image values of each of its (row, K block) items (packed in
-  // pairs), then builds and stores the 4 shifted rows of each.
+  // 2. stage the image tile: 16-byte row (image row r, block cb) of K block
+  // kb holds Ipad[y0 + r][x0 + 4 cb + 8 kb + e], e = 0..7.  Every thread
+  // first loads the 20 image values of each of its (row, K block) items
+  // (packed in pairs), then stores the 4 rows of each.
   const unsigned short* img =
       reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * H * W;
   const int nitem = R * KB;  // <= TR_SI * TR_NT (checked on the host)
-  uint32_t raw[TR_SI][6];
+  uint32_t raw[TR_SI][10];
 #pragma unroll
   for (int q = 0; q < TR_SI; ++q) {
     const int pr = tid + q * TR_NT;
@@ -199,57 +222,63 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       const size_t rowoff = (size_t)min(max(y0 + r - p, 0), H - 1) * W;
       const int xs = x0 + 8 * kb - p;  // image column of element 0
       const unsigned short* src0 = img + rowoff + xs;
-      if (xs >= 0 && xs + TR_X + 8 <= W && (reinterpret_cast<uintptr_t>(src0) & 7) == 0) {
-        // interior and the absolute address 8-byte aligned (image planes of
-        // an odd size start at odd element offsets): three 8-byte loads
+      if (xs >= 0 && xs + 20 <= W && (reinterpret_cast<uintptr_t>(src0) & 7) == 0) {
 #pragma unroll
-        for (int w = 0; w < 3; ++w) {
+        for (int w = 0; w < 5; ++w) {
           const uint2 d = *reinterpret_cast<const uint2*>(src0 + 4 * w);
           raw[q][2 * w] = d.x;
           raw[q][2 * w + 1] = d.y;
         }
       } else {
 #pragma unroll
-        for (int w = 0; w < 6; ++w) {
+        for (int w = 0; w < 10; ++w) {
           const uint32_t lo = img[rowoff + min(max(xs + 2 * w, 0), W - 1)];
-          const uint32_t hi = 2 * w + 1 < TR_X + 7 ? img[rowoff + min(max(xs + 2 * w + 1, 0), W - 1)] : 0u;
+          const uint32_t hi = img[rowoff + min(max(xs + 2 * w + 1, 0), W - 1)];
           raw[q][w] = lo | (hi << 16);
         }
       }
     }
   }
-  int key = -1;
-  float t = 0.f;
-  if (valid) select_slice(P, yy, xx, dep, &key, &t);
-  const bool use0 = valid && (!two || t < 1.f), use1 = valid && two && t > 0.f;
+  int key[TR_J];
+  float tt[TR_J];
+  unsigned use = 0;  // bit 2i: slice key of pixel i used, bit 2i+1: key + 1
+  int kmin_t = 0x7fffffff;
+#pragma unroll
+  for (int i = 0; i < TR_J; ++i) {
+    key[i] = -1;
+    tt[i] = 0.f;
+    if (pix && yy < H && xb + i < W) {
+      select_slice(P, yy, xb + i, dep[i], &key[i], &tt[i]);
+      const bool u0 = !two || tt[i] < 1.f, u1 = two && tt[i] > 0.f;
+      use |= (u0 ? 1u : 0u) << (2 * i);
+      use |= (u1 ? 1u : 0u) << (2 * i + 1);
+      kmin_t = min(kmin_t, u0 ? key[i] : key[i] + 1);
+    }
+  }
   if (pix) {
-    s_cand[2 * tid] = use0 ? key : -1;
-    s_cand[2 * tid + 1] = use1 ? key + 1 : -1;
-    if (use0 || use1) atomicMin(&s_kmin, use0 ? key : key + 1);
+#pragma unroll
+    for (int i = 0; i < TR_J; ++i) {
+      s_cand[TR_J * 2 * tid + 2 * i] = (use >> (2 * i)) & 1u ? key[i] : -1;
+      s_cand[TR_J * 2 * tid + 2 * i + 1] = (use >> (2 * i + 1)) & 1u ? key[i] + 1 : -1;
+    }
+    if (use) atomicMin(&s_kmin, kmin_t);
   }
 #pragma unroll
   for (int q = 0; q < TR_SI; ++q) {
     const int pr = tid + q * TR_NT;
     if (pr < nitem) {
       const int r = pr / KB, kb = pr - r * KB;
-      // element e of the item: half (e & 1) of word e / 2
-      auto el = [&](int e) { return (raw[q][e >> 1] >> (16 * (e & 1))) & 0xffffu; };
-      unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_X * 16;
+      unsigned char* dst = Asm + (size_t)kb * LBO_A + (size_t)r * TR_CB * 16;
 #pragma unroll
-      for (int i = 0; i < TR_X; ++i) {
-        uint4 w;
-        w.x = el(i) | (el(i + 1) << 16);
-        w.y = el(i + 2) | (el(i + 3) << 16);
-        w.z = el(i + 4) | (el(i + 5) << 16);
-        w.w = el(i + 6) | (el(i + 7) << 16);
-        *reinterpret_cast<uint4*>(dst + i * 16) = w;
-      }
+      for (int cb = 0; cb < TR_CB; ++cb)
+        *reinterpret_cast<uint4*>(dst + cb * 16) =
+            make_uint4(raw[q][2 * cb], raw[q][2 * cb + 1], raw[q][2 * cb + 2], raw[q][2 * cb + 3]);
     }
   }
-  if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
+  if (warp == 0) tc::tmem_alloc(&s_tmem, TR_N);
   if (tid == 0) {
     for (int b = 0; b < TR_NB; ++b) {
-      tc::mbar_init(&s_full[b], TR_NPROD);
+      tc::mbar_init(&s_full[b], 32);
       tc::mbar_init(&s_empty[b], 1);
     }
     tc::mbar_init(&s_acc, 1);
@@ -264,8 +293,8 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   // candidate keys above the tile's smallest (an exhaustive comparison if a
   // key lies beyond the window), then prefix counts
   const int kmin = s_kmin;
-  {
-    const int kq = s_cand[tid];
+  for (int q = tid; q < TR_MAXK; q += TR_NT) {
+    const int kq = s_cand[q];
     if (kq >= 0) {
       const int d = kq - kmin;
       if (d < TR_WIN) atomicOr(&s_bits[d >> 5], 1u << (d & 31));
@@ -307,10 +336,18 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       }
     }
   } else {
-    const int kq = s_cand[tid];
-    bool f = kq >= 0;
-    for (int m = 0; m < tid && f; ++m) f = s_cand[m] != kq;
-    const int cnt = f ? 1 : 0;
+    // first occurrences in candidate order; thread tid owns candidates
+    // 4 tid .. 4 tid + 3
+    constexpr int CPT = TR_MAXK / TR_NT;
+    int cnt = 0;
+    bool f[CPT];
+#pragma unroll
+    for (int e = 0; e < CPT; ++e) {
+      const int q = CPT * tid + e, kq = s_cand[q];
+      f[e] = kq >= 0;
+      for (int m = 0; m < q && f[e]; ++m) f[e] = s_cand[m] != kq;
+      cnt += f[e] ? 1 : 0;
+    }
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -319,12 +356,14 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     }
     if (lane == 31) s_wcnt[warp] = incl;
     __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += s_wcnt[w];
-    if (f) s_uniq[base + incl - 1] = kq;
-    if (tid == TR_NT - 1) s_nuniq = base + incl;
+    int pos = incl - cnt;
+    for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+#pragma unroll
+    for (int e = 0; e < CPT; ++e)
+      if (f[e]) s_uniq[pos++] = s_cand[CPT * tid + e];
+    if (tid == TR_NT - 1) s_nuniq = pos;
   }
-  __syncthreads();
+  __syncthreads();  // s_cand is dead from here on (the B ring reuses it)
   const int nuniq = s_nuniq;
   auto slot_of = [&](int k) {
     if (!over) {
@@ -336,126 +375,157 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       if (s_uniq[m] == k) idx = m;
     return idx;
   };
-  const int idx0 = use0 ? slot_of(key) : -1;
-  const int idx1 = use1 ? slot_of(key + 1) : -1;
-  const float w0 = two ? 1.f - t : 1.f, w1 = t;
+  int idx0[TR_J], idx1[TR_J];
+  float w0[TR_J], w1[TR_J];
+#pragma unroll
+  for (int i = 0; i < TR_J; ++i) {
+    idx0[i] = (use >> (2 * i)) & 1u ? slot_of(key[i]) : -1;
+    idx1[i] = (use >> (2 * i + 1)) & 1u ? slot_of(key[i] + 1) : -1;
+    w0[i] = two ? 1.f - tt[i] : 1.f;
+    w1[i] = tt[i];
+  }
 
-  // 4. passes of up to 8 slices.  Warps 1..7 copy the B chunks (TR_UC
-  // kernel rows) into a ring of TR_NB buffers with cp.async and report each
-  // full buffer on its mbarrier; thread 0 waits for a full buffer, issues
-  // its MMAs and lets the tensor core report the buffer empty again, so no
-  // CTA barrier sits inside a pass.  At the end of a pass the tensor core
-  // reports the accumulator, warps 0..3 fold it into their pixels, and the
-  // CTA synchronises before the next pass overwrites it.
-  const int nch = (ks + TR_UC - 1) / TR_UC;
-  const int npass = (nuniq + 7) / 8;
-  const int ngran = TR_UC * KB * TR_N;
+  // 4. passes of up to 8 slices, one chunk per kernel row.  Producer warp
+  // 4 + b builds the chunks of ring buffer b from the bank rows in global
+  // memory (loaded one chunk ahead) and reports it full on its mbarrier;
+  // thread 0 waits for a full buffer, issues its MMAs and lets the tensor
+  // core report the buffer empty again.  At the end of a pass the tensor
+  // core reports the accumulator, warps 0..3 fold it into their pixels and
+  // meet at a named barrier before thread 0 starts the next pass.
+  const int nch = ks, npass = (nuniq + TR_SL - 1) / TR_SL, total = npass * nch;
   const uint32_t idesc = tc::idesc_bf16_f32(TR_M, TR_N);
   const uint32_t a_base = tc::smem_u32(Asm), b_base = tc::smem_u32(Bsm);
   const uint64_t a_desc0 = tc::smem_desc(a_base, LBO_A, 128);
-  const uint64_t b_desc0 = tc::smem_desc(b_base, 256, 128);
-  // this producer's granules of a chunk: (kernel row ul, K block kb, column
-  // nn), nn fastest; the same for every chunk
-  const int ptid = tid - 32;
-  uint32_t g_dst[TR_GPT];
-  int g_off[TR_GPT], g_ul[TR_GPT], g_sl[TR_GPT];
+  const uint64_t b_desc0 = tc::smem_desc(b_base, TR_N * 16, 128);
+  float outL[TR_J], outR[TR_J];
 #pragma unroll
-  for (int q = 0; q < TR_GPT; ++q) {
-    const int g = ptid + q * TR_NPROD;
-    const int nn = g & (TR_N - 1), rest = g >> 4;
-    const int kb = rest % KB, ul = rest / KB;
-    g_dst[q] = (uint32_t)ul * USTR + kb * 256 + nn * 16;
-    g_off[q] = (nn >> 3) * KP + 8 * kb;           // side row, K block
-    g_ul[q] = (ptid >= 0 && g < ngran) ? ul : TR_UC;  // TR_UC: no granule
-    g_sl[q] = nn & 7;
-  }
-  float outL = 0.f, outR = 0.f;
-  for (int pass = 0; pass < npass; ++pass) {
-    if (tid < 8) {  // element offset of each slot's flipped kernel rows
-      const int ui = pass * 8 + tid;
-      s_rowb[tid] = ui < nuniq ? ((long long)s_uniq[ui] * P.NL + lam) * ks * 2 * KP : -1;
-    }
-    __syncthreads();
-    const int c0 = pass * nch;  // global index of the pass's first chunk
-    if (warp == 0) {
-      if (lane == 0) {
-        for (int ch = 0; ch < nch; ++ch) {
-          const int c = c0 + ch, b = c % TR_NB;
-          wait_flag(&s_full[b], (uint32_t)(c / TR_NB) & 1u, err);
-          tc::fence_after_sync();
-          const int urows = min(TR_UC, ks - ch * TR_UC);
-          // the start-address field is the low 14 bits (address >> 4)
-          uint64_t ad = a_desc0 + (uint64_t)(ch * TR_UC * TR_X);  // rows of 64 B
-          uint64_t bd = b_desc0 + (uint64_t)((uint32_t)b * TR_UC * USTR >> 4);
-          for (int ul = 0; ul < urows; ++ul) {
-            uint64_t a = ad, bb = bd;
-            for (int kq = 0; kq < KP / 16; ++kq) {
-              tc::mma_bf16(tmem, a, bb, idesc, !(ch == 0 && ul == 0 && kq == 0));
-              a += (uint64_t)(2u * LBO_A >> 4);
-              bb += (uint64_t)(512u >> 4);
+  for (int i = 0; i < TR_J; ++i) outL[i] = outR[i] = 0.f;
+  if (warp >= TR_CB) {
+    // producer: task e = lane + 32 q of a chunk is (K block kb = e / 16,
+    // row ss = e % 16 = side * 8 + slot); it writes the rows (i, ss) of K
+    // block kb for the 4 shifts i from the bank words kb - 1 and kb.  A lane
+    // loads word kb of its tasks (one chunk ahead) and takes word kb - 1
+    // from the lane of task e - 16.
+    const int b = warp - TR_CB;
+    const uint32_t bdst = b_base + (uint32_t)b * BBUF;
+    const int ntask = TR_SS * KB, qwords = KP / 8;
+    uint4 cur[TR_TPL], nxt[TR_TPL];
+    auto load = [&](uint4 (&dst)[TR_TPL], int cg) {
+      const int pass = cg / nch, u = cg - pass * nch;
+#pragma unroll
+      for (int q = 0; q < TR_TPL; ++q) {
+        const int e = lane + 32 * q, kb = e >> 4, ss = e & 15;
+        const int ui = pass * TR_SL + (ss & 7);
+        dst[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (e < ntask && ui < nuniq && kb < qwords)
+          dst[q] = __ldg(reinterpret_cast<const uint4*>(
+              bp + (((long long)s_uniq[ui] * P.NL + lam) * ks + u) * 2 * KP + (ss >> 3) * KP +
+              8 * kb));
+      }
+    };
+    auto shfl4 = [&](const uint4& v) {
+      uint4 r;
+      r.x = __shfl_xor_sync(0xffffffffu, v.x, 16);
+      r.y = __shfl_xor_sync(0xffffffffu, v.y, 16);
+      r.z = __shfl_xor_sync(0xffffffffu, v.z, 16);
+      r.w = __shfl_xor_sync(0xffffffffu, v.w, 16);
+      return r;
+    };
+    if (b < total) load(cur, b);
+    for (int cg = b; cg < total; cg += TR_NB) {
+      if (cg + TR_NB < total) load(nxt, cg + TR_NB);
+      if (cg >= TR_NB)  // the MMAs of chunk cg - TR_NB read this buffer
+        wait_flag(&s_empty[b], (uint32_t)(cg / TR_NB - 1) & 1u, err);
+      const int ui_base = (cg / nch) * TR_SL;
+      uint4 other = make_uint4(0u, 0u, 0u, 0u);  // word kb of task e - 16 + 32 (q - 1)
+#pragma unroll
+      for (int q = 0; q < TR_TPL; ++q) {
+        const uint4 same = shfl4(cur[q]);  // word kb of task e + 16 or e - 16 (same q)
+        const uint4 prev = lane >= 16 ? same : other;
+        other = same;
+        const int e = lane + 32 * q, kb = e >> 4, ss = e & 15;
+        if (e < ntask && ui_base + (ss & 7) < nuniq) {
+          // elements 8 kb - i .. 8 kb - i + 7 of the row: the 16 elements of
+          // words kb - 1 and kb from position 8 - i on
+          const uint32_t c8[8] = {prev.x, prev.y, prev.z, prev.w,
+                                  cur[q].x, cur[q].y, cur[q].z, cur[q].w};
+          const uint32_t d = bdst + (uint32_t)kb * (TR_N * 16) + (uint32_t)ss * 16;
+#pragma unroll
+          for (int i = 0; i < TR_J; ++i) {
+            uint32_t g[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (i & 1)
+                g[k] = __funnelshift_r(c8[(7 - i) / 2 + k], c8[(9 - i) / 2 + k], 16);
+              else
+                g[k] = c8[(8 - i) / 2 + k];
             }
-            ad += (uint64_t)TR_X;
-            bd += (uint64_t)(USTR >> 4);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(d + i * TR_SS * 16),
+                         "r"(g[0]), "r"(g[1]), "r"(g[2]), "r"(g[3])
+                         : "memory");
+          }
+        }
+      }
+      tc::fence_async_smem();
+      tc::mbar_arrive(&s_full[b]);
+#pragma unroll
+      for (int q = 0; q < TR_TPL; ++q) cur[q] = nxt[q];
+    }
+  } else {
+    for (int pass = 0; pass < npass; ++pass) {
+      if (tid == 0) {
+        for (int ch = 0; ch < nch; ++ch) {
+          const int cg = pass * nch + ch, b = cg % TR_NB;
+          wait_flag(&s_full[b], (uint32_t)(cg / TR_NB) & 1u, err);
+          tc::fence_after_sync();
+          // the start-address field is the low 14 bits (address >> 4)
+          uint64_t ad = a_desc0 + (uint64_t)(ch * TR_CB);  // rows of 64 B
+          uint64_t bd = b_desc0 + (uint64_t)((uint32_t)b * BBUF >> 4);
+          for (int kq = 0; kq < KK / 16; ++kq) {
+            tc::mma_bf16(tmem, ad, bd, idesc, !(ch == 0 && kq == 0));
+            ad += (uint64_t)(2u * LBO_A >> 4);
+            bd += (uint64_t)(2u * TR_N * 16 >> 4);
           }
           tc::commit(&s_empty[b]);
         }
         tc::commit(&s_acc);
       }
       __syncwarp();
-    } else {
-      for (int ch = 0; ch < nch; ++ch) {
-        const int c = c0 + ch, b = c % TR_NB;
-        if (c >= TR_NB)  // the MMAs of chunk c - TR_NB read this buffer
-          wait_flag(&s_empty[b], (uint32_t)(c / TR_NB - 1) & 1u, err);
-        const uint32_t bdst = b_base + (uint32_t)b * TR_UC * USTR;
-#pragma unroll
-        for (int q = 0; q < TR_GPT; ++q) {
-          const int u = ch * TR_UC + g_ul[q];
-          const long long rb = s_rowb[g_sl[q]];
-          if (g_ul[q] < TR_UC && u < ks && rb >= 0)
-            cp16(bdst + g_dst[q], bp + rb + (long long)u * 2 * KP + g_off[q], 16);
-        }
-        cp_commit();
-        if (ch > 0) {  // the previous chunk has landed: report it
-          cp_wait<1>();
-          tc::fence_async_smem();
-          tc::mbar_arrive(&s_full[(c - 1) % TR_NB]);
-        }
-      }
-      cp_wait<0>();
-      tc::fence_async_smem();
-      tc::mbar_arrive(&s_full[(c0 + nch - 1) % TR_NB]);
-    }
-    // the pass's accumulator
-    if (warp < TR_M / 32) {
+      // the pass's accumulator
       wait_flag(&s_acc, (uint32_t)pass & 1u, err);
       tc::fence_after_sync();
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
 #pragma unroll
-      for (int sl = 0; sl < 8; ++sl) {
-        const int ui = pass * 8 + sl;
-        if (ui == idx0) {
-          outL = fmaf(w0, v[sl], outL);
-          outR = fmaf(w0, v[8 + sl], outR);
-        }
-        if (ui == idx1) {
-          outL = fmaf(w1, v[sl], outL);
-          outR = fmaf(w1, v[8 + sl], outR);
+      for (int i = 0; i < TR_J; ++i) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(i * TR_SS), v);
+#pragma unroll
+        for (int sl = 0; sl < TR_SL; ++sl) {
+          const int ui = pass * TR_SL + sl;
+          if (ui == idx0[i]) {
+            outL[i] = fmaf(w0[i], v[sl], outL[i]);
+            outR[i] = fmaf(w0[i], v[TR_SL + sl], outR[i]);
+          }
+          if (ui == idx1[i]) {
+            outL[i] = fmaf(w1[i], v[sl], outL[i]);
+            outR[i] = fmaf(w1[i], v[TR_SL + sl], outR[i]);
+          }
         }
       }
+      tc::fence_before_sync();
+      named_sync(1, TR_M);
     }
-    tc::fence_before_sync();
-    __syncthreads();
-  }
-  if (valid) {
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P.out);
-    out[(((size_t)n * 2 * P.C + c) * H + yy) * W + xx] = __float2bfloat16_rn(outL);
-    out[(((size_t)n * 2 * P.C + P.C + c) * H + yy) * W + xx] = __float2bfloat16_rn(outR);
+#pragma unroll
+    for (int i = 0; i < TR_J; ++i)
+      if (pix && yy < H && xb + i < W) {
+        out[(((size_t)n * 2 * P.C + c) * H + yy) * W + xb + i] = __float2bfloat16_rn(outL[i]);
+        out[(((size_t)n * 2 * P.C + P.C + c) * H + yy) * W + xb + i] =
+            __float2bfloat16_rn(outR[i]);
+      }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 32);
+  if (warp == 0) tc::tmem_free(tmem, TR_N);
 }
 
 }  // namespace sd
@@ -484,7 +554,7 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   if (st != SD_OK) return st;
   if (layout->dtype != SD_BF16 && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
   if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024 ||
-      (TR_Y + P.ks - 1) * (tr_kp(P.ks) / 8) > TR_SI * TR_NT)
+      (TR_Y + P.ks - 1) * (tr_kk(P.ks) / 8) > TR_SI * TR_NT || TR_SS * (tr_kk(P.ks) / 8) > 32 * TR_TPL)
     return SD_ERR_UNSUPPORTED;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
   if ((long long)N * C > 65535 || (long long)H * W > (1ll << 31) ||
@@ -518,7 +588,7 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   const size_t smem = tr_smem(P.ks);
   SD_CUDA_TRY(cudaFuncSetAttribute(render_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  dim3 grid((W + TR_X - 1) / TR_X, (H + TR_Y - 1) / TR_Y, N * C);
+  dim3 grid((W + TR_XW - 1) / TR_XW, (H + TR_Y - 1) / TR_Y, N * C);
   render_tc_kernel<<<grid, TR_NT, smem, s>>>(P, bp, err);
   return launch_status();
 }

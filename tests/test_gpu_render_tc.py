@@ -49,7 +49,8 @@ CASES = [
     (2, 1, 37, 29, 3, 4, 1, 15, False),     # ragged tiles in both directions
     (1, 2, 33, 70, 4, 5, 2, 65, False),
     (1, 1, 20, 24, 2, 1, 1, 9, False),      # single depth slice
-    (1, 3, 32, 24, 6, 8, 3, 17, True),      # 16 x 8 tiles with more than 8 slices
+    (1, 3, 32, 24, 6, 8, 3, 17, True),      # tiles with more than 8 slices
+    (1, 2, 40, 50, 5, 9, 2, 65, True),      # several passes at the largest kernel
     (1, 1, 18, 17, 2, 2, 1, 1, False),      # 1 x 1 kernel
 ]
 
