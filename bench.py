@@ -543,8 +543,22 @@ def precision_compare(sd, dev, crop=256):
         res[name] = {"ms": round(t, 3), "mpix_s": round(px / (t * 1e-3) / 1e6, 2),
                      "max_err_rel": float(np.abs(err).max() / np.abs(ref).max()),
                      "rms_err_rel": float(np.sqrt((err ** 2).mean()) / np.abs(ref).max())}
+        if dt == torch.bfloat16:
+            # the same BF16 image and bank through the tensor-core render
+            ws = torch.empty(sd.api.render_tc_workspace(lay), dtype=torch.uint8, device=dev)
+            t = _timed(lambda: sd.dp_render_tc(aif, depth, bank, lay, out=out, workspace=ws),
+                       stream, reps=3)
+            if int(ws[:4].view(torch.int32).item()) != 0:
+                raise RuntimeError("tensor-core render: a completion wait gave up")
+            got = out[0, :, :crop, :crop].float().cpu().numpy().transpose(1, 2, 0)
+            err = got.astype(np.float64) - ref
+            res["bf16_tc"] = {"ms": round(t, 3), "mpix_s": round(px / (t * 1e-3) / 1e6, 2),
+                              "max_err_rel": float(np.abs(err).max() / np.abs(ref).max()),
+                              "rms_err_rel": float(np.sqrt((err ** 2).mean()) / np.abs(ref).max())}
+            del ws
         del out, bank
     res["bf16_speedup_vs_f32"] = round(res["f32"]["ms"] / res["bf16"]["ms"], 3)
+    res["bf16_tc_speedup_vs_f32"] = round(res["f32"]["ms"] / res["bf16_tc"]["ms"], 3)
     res["bf16_bound"] = "max err <= 8 * 2^-9 of max|ref|"
     lens.free()
     return res
@@ -556,8 +570,10 @@ def pipeline_compare(sd, dev, reps=5):
     image and the bank, adjoint trace of the bank gradient.  Plain FP32 (one
     trace block per request, FP32 bank and images, eager launches) against
     the batched BF16 pipeline (persistent batched trace writing a BF16 bank,
-    BF16 images, FP32 gradients, the whole step replayed from one CUDA
-    graph), with the bank error of both against the FP64 oracle."""
+    BF16 images rendered on the tensor cores, FP32 gradients, the whole step
+    replayed from one CUDA graph), with the bank error of both against the
+    FP64 oracle, the difference of the two renders and each stage timed
+    alone (eager launches)."""
     import torch
     import oracle as O
     c = W.config_differentiation()
@@ -615,9 +631,11 @@ def pipeline_compare(sd, dev, reps=5):
                          norm=sd.SD_NORM_JOINT, dtype=torch.bfloat16)
     bt.tune(os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt"))
 
+    ws_tc = torch.empty(sd.api.render_tc_workspace(lay16), dtype=torch.uint8, device=dev)
+
     def batched():
         bank16, _ = bt.run()
-        sd.dp_render(aif16, depth, bank16, lay16, out=out16)
+        sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16, workspace=ws_tc)
         render_bwd(lay16, aif16, bank16, gaif16, gbank16, ws16)
         sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank16, max_ks=ks,
                                  max_n=c["n_grid"], grad_req=greq16)
@@ -632,6 +650,32 @@ def pipeline_compare(sd, dev, reps=5):
         batched()
     t_plain = _timed(plain, stream, reps)
     t_graph = _timed(g.replay, stream, reps)
+    torch.cuda.synchronize()
+    r32 = out32.float()
+    render_diff = float((out16.float() - r32).abs().max().item() / r32.abs().max().item())
+    bank16 = bt.out
+    stages = {
+        "f32": {
+            "trace": _timed(lambda: sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=ks,
+                                                    max_n=c["n_grid"], norm=sd.SD_NORM_JOINT,
+                                                    out=bank32, stats=st32), stream, reps),
+            "render": _timed(lambda: sd.dp_render(aif32, depth, bank32, lay32, out=out32),
+                             stream, reps),
+            "render_bwd": _timed(lambda: render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32),
+                                 stream, reps),
+            "trace_adjoint": _timed(lambda: sd.dp_psf_trace_backward(
+                lens, sensor, req_dev, n_req, gbank32, max_ks=ks, max_n=c["n_grid"],
+                grad_req=greq32), stream, reps)},
+        "bf16": {
+            "trace": _timed(lambda: bt.run(), stream, reps),
+            "render": _timed(lambda: sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16,
+                                                     workspace=ws_tc), stream, reps),
+            "render_bwd": _timed(lambda: render_bwd(lay16, aif16, bank16, gaif16, gbank16, ws16),
+                                 stream, reps),
+            "trace_adjoint": _timed(lambda: sd.dp_psf_trace_backward(
+                lens, sensor, req_dev, n_req, gbank16, max_ks=ks, max_n=c["n_grid"],
+                grad_req=greq16), stream, reps)}}
+    stages = {k: {n: round(v, 3) for n, v in d.items()} for k, d in stages.items()}
     torch.cuda.synchronize()
     # bank error of both against the FP64 oracle on 24 evenly spaced requests
     idx = np.linspace(0, n_req - 1, 24).astype(int)
@@ -651,7 +695,8 @@ def pipeline_compare(sd, dev, reps=5):
     lens.free()
     return {"requests": n_req, "rays": rays, "images": [B, 3, H, Wd],
             "plain_f32_ms": round(t_plain, 3), "batched_bf16_graph_ms": round(t_graph, 3),
-            "speedup": round(t_plain / t_graph, 3),
+            "speedup": round(t_plain / t_graph, 3), "stages_ms": stages,
+            "render_max_rel_diff_bf16_vs_f32": render_diff,
             "bank_l1_vs_oracle": {"f32": {"mean": e32[0], "max": e32[1]},
                                   "bf16": {"mean": e16[0], "max": e16[1]},
                                   "sample": "24 evenly spaced requests, FP64 oracle"}}

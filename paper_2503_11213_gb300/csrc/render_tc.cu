@@ -28,6 +28,8 @@
 // for a 128-row window (starting at row u) of a K-major BF16 matrix, K = 32
 // in two MMAs, D in tensor memory.
 
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "render_common.cuh"
@@ -127,23 +129,27 @@ inline size_t tr_bp_bytes(const RenderParams& P) {
 }
 
 // bp[key][lam][u][side][v] = bank[key][lam][side][ks-1-u][ks-1-v] (v < ks),
-// 0 for ks <= v < KP
+// 0 for ks <= v < KP.  One thread per 8-element (16-byte) piece of a row:
+// row r = (key * NL + lam, u, side), piece q.
 template <class TB>
 __global__ void tr_bank_kernel(const TB* __restrict__ bank, __nv_bfloat16* __restrict__ bp,
-                               size_t n_kl, int ks, int KP) {
-  const size_t total = n_kl * ks * 2 * KP;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int v = (int)(i % KP);
-    size_t r = i / KP;
-    const int side = (int)(r % 2);
-    r /= 2;
-    const int u = (int)(r % ks);
-    const size_t kl = r / ks;
-    float val = 0.f;
-    if (v < ks)
-      val = to_f32<TB>(bank[((kl * 2 + side) * ks + (ks - 1 - u)) * ks + (ks - 1 - v)]);
-    bp[i] = __float2bfloat16_rn(val);
+                               int n_rows, int ks, int KP) {
+  const int per_row = KP / 8, total = n_rows * per_row;  // < 2^31 - 2^24 (checked on the host)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int r = i / per_row, q = i - r * per_row;
+    const int side = r & 1, ru = r >> 1, u = ru % ks, kl = ru / ks;
+    // element v of the flipped row is src[-v]
+    const TB* src = bank + (((size_t)kl * 2 + side) * ks + (ks - 1 - u)) * ks + (ks - 1);
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int v0 = 8 * q + 2 * k, v1 = v0 + 1;
+      const float f0 = v0 < ks ? to_f32<TB>(src[-v0]) : 0.f;
+      const float f1 = v1 < ks ? to_f32<TB>(src[-v1]) : 0.f;
+      w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0)) |
+             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f1)) << 16);
+    }
+    *reinterpret_cast<uint4*>(bp + (size_t)r * KP + 8 * q) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -576,13 +582,17 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   int* err = reinterpret_cast<int*>(workspace);
   __nv_bfloat16* bp = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(workspace) + 256);
   SD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  const size_t n_kl = (size_t)P.F * P.Z * P.NL;
+  const long long n_rows = (long long)P.F * P.Z * P.NL * P.ks * 2;
+  const int kp = tr_kp(P.ks);
+  if (n_rows * (kp / 8) > 0x7f000000ll) return SD_ERR_UNSUPPORTED;
+  const int pieces = (int)(n_rows * (kp / 8));
+  const int nblk = std::min((pieces + 255) / 256, 152 * 16);
   if (layout->dtype == SD_BF16)
-    tr_bank_kernel<__nv_bfloat16><<<1024, 256, 0, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(bank), bp, n_kl, P.ks, tr_kp(P.ks));
+    tr_bank_kernel<__nv_bfloat16><<<nblk, 256, 0, s>>>(
+        reinterpret_cast<const __nv_bfloat16*>(bank), bp, (int)n_rows, P.ks, kp);
   else
-    tr_bank_kernel<float><<<1024, 256, 0, s>>>(reinterpret_cast<const float*>(bank), bp, n_kl,
-                                               P.ks, tr_kp(P.ks));
+    tr_bank_kernel<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(bank), bp,
+                                               (int)n_rows, P.ks, kp);
   st = launch_status();
   if (st != SD_OK) return st;
   const size_t smem = tr_smem(P.ks);
