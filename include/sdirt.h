@@ -308,14 +308,28 @@ sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
  * to the first/last slice.  This selection is computed in FP32 without
  * contraction: X = ((float)x - 0.5f*(W-1)) * pitch, rho = sqrtf(X*X + Y*Y),
  * q = 1.0f / depth, iq_j = 1.0f / depths_m[j].
+ *
+ * Quadrant mode (field_mode = SD_FIELD_QUADRANT): the bank holds a 2-D grid
+ * of field points of the first quadrant, [Fx = F][Fy = F][Z][NL][2][ks][ks]
+ * with both axes sampled at field_h_mm (>= 0).  A pixel takes the grid point
+ * nearest to (|X|, |Y|) on each axis separately (same rule as the radial
+ * lookup), and the flip symmetry of the DP PSF about both axes (Sec. 5.2):
+ * X < 0 mirrors the kernel's columns and exchanges L and R (the DP split is
+ * along x), Y < 0 mirrors its rows.  Removes the radial approximation of
+ * off-axis azimuths.  sd_dp_render only; the other bank entry points return
+ * SD_ERR_UNSUPPORTED for it.
  * ---------------------------------------------------------------------- */
 #define SD_MAX_BANK_FIELDS 256
 #define SD_MAX_BANK_DEPTHS 256
+#define SD_FIELD_RADIAL 0
+#define SD_FIELD_QUADRANT 1
 
 typedef struct sd_bank_layout {
   int32_t n_field, n_depth, n_lambda, ks;   /* bank [F][Z][NL][2][ks][ks] */
   int32_t dtype;                            /* SD_F32 / SD_BF16 / SD_F16 */
-  int32_t reserved;
+  int32_t field_mode;                       /* SD_FIELD_RADIAL (0) or
+                                               SD_FIELD_QUADRANT: bank
+                                               [F][F][Z][NL][2][ks][ks] */
   const float* field_h_mm;  /* host, F ascending field heights (mm) */
   const float* depths_m;    /* host, Z ascending depths (m) */
   float pitch_mm;           /* sensor pixel pitch of the rendered image */

@@ -18,7 +18,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   trace_grad       pinned by FP64 central differences of trace_functional
   render_*         pinned by the delta-PSF and constant-image identities, a
                    shift-invariant kernel against scipy correlation and brute
-                   force of the supplement's unfold/fold formulation
+                   force of the supplement's unfold/fold formulation; the
+                   quadrant bank against a per-pixel map of PSFs traced at
+                   each pixel's own signed field point
 """
 from __future__ import annotations
 
@@ -37,6 +39,9 @@ _LIB_PATH = _HERE / "_build" / "libsdirt_oracle.so"
 STATS = ("launched", "reached", "L", "R", "dp_missed", "clipped", "vignetted", "other")
 # ray states
 R_OK, R_MISS, R_CLIP, R_TIR, R_NEWTON, R_BACK = range(6)
+# bank field layouts: radial heights, or a first-quadrant grid used through
+# the PSF's flip symmetry about both axes
+FIELD_RADIAL, FIELD_QUADRANT = 0, 1
 # PSF accumulation modes and normalisations
 MODE_HARD, MODE_BILINEAR = 0, 1
 NORM_NONE, NORM_JOINT, NORM_SEPARATE, NORM_PER_RAY = 0, 1, 2, 3
@@ -80,9 +85,14 @@ def lib():
         L.or_render_select.argtypes = [i, i, pf, pf, i, pf, i, f, pd]
         L.or_render_bank_pixels.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf, f,
                                             pi, i, pd, i]
+        L.or_render_bank_mode.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf, f, i,
+                                          pd, i]
+        L.or_render_bank_pixels_mode.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf,
+                                                 f, i, pi, i, pd, i]
         for fn in ("or_lens_info", "or_trace_hits", "or_psf_bank", "or_trace_functional",
                    "or_trace_grad", "or_render_bank", "or_render_map",
-                   "or_render_bank_bwd", "or_render_select", "or_render_bank_pixels"):
+                   "or_render_bank_bwd", "or_render_select", "or_render_bank_pixels",
+                   "or_render_bank_mode", "or_render_bank_pixels_mode"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -213,34 +223,49 @@ def param_id(surface, which):
     return surface * NPAR_SURF + j
 
 
-def render_bank(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, n_threads=1):
-    """aif (N,C,H,W); depth (N,H,W) m; bank (F,Z,NL,2,ks,ks) -> (N,2C,H,W)."""
+def _bank_fields(b, field_h_mm, field_mode):
+    """Heights per axis of a bank: radial (F,Z,...) or quadrant (F*F,Z,...)."""
+    cells = b.shape[0]
+    F = len(field_h_mm)
+    if cells != (F * F if field_mode == FIELD_QUADRANT else F):
+        raise ValueError("bank field cells do not match field_h_mm and field_mode")
+    return F
+
+
+def render_bank(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, n_threads=1,
+                field_mode=0):
+    """aif (N,C,H,W); depth (N,H,W) m; bank (F,Z,NL,2,ks,ks) -> (N,2C,H,W).
+    field_mode=FIELD_QUADRANT: bank (F*F,Z,NL,2,ks,ks) over the first
+    quadrant (cell ix*F + iy), used through the PSF's flip symmetry."""
     a = _f64(aif)
     N, C, H, W = a.shape
     dm = _f32(depth_m)
     b = _f64(bank)
-    F, Z, NL, _, ks, _ = b.shape
+    _, Z, NL, _, ks, _ = b.shape
+    F = _bank_fields(b, field_h_mm, field_mode)
     out = np.zeros((N, 2 * C, H, W))
-    _check(lib().or_render_bank(_pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z, NL, ks,
-                                _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
-                                float(np.float32(pitch_mm)), _pd(out), n_threads),
-           "render_bank")
+    _check(lib().or_render_bank_mode(_pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z, NL, ks,
+                                     _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
+                                     float(np.float32(pitch_mm)), field_mode, _pd(out),
+                                     n_threads), "render_bank")
     return out
 
 
-def render_bank_pixels(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, pix, n_threads=1):
+def render_bank_pixels(aif, depth_m, bank, field_h_mm, depths_m, pitch_mm, pix, n_threads=1,
+                       field_mode=0):
     """Bank-mode render of the pixels pix (k, 3) = (n, y, x) -> (k, 2C)."""
     a = _f64(aif)
     N, C, H, W = a.shape
     dm = _f32(depth_m)
     b = _f64(bank)
-    F, Z, NL, _, ks, _ = b.shape
+    _, Z, NL, _, ks, _ = b.shape
+    F = _bank_fields(b, field_h_mm, field_mode)
     px = np.ascontiguousarray(pix, dtype=np.int32)
     out = np.zeros((len(px), 2 * C))
-    _check(lib().or_render_bank_pixels(_pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z, NL, ks,
-                                       _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
-                                       float(np.float32(pitch_mm)), _pi(px), len(px),
-                                       _pd(out), n_threads), "render_bank_pixels")
+    _check(lib().or_render_bank_pixels_mode(_pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z, NL, ks,
+                                            _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
+                                            float(np.float32(pitch_mm)), field_mode, _pi(px),
+                                            len(px), _pd(out), n_threads), "render_bank_pixels")
     return out
 
 

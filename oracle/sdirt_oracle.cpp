@@ -971,32 +971,40 @@ namespace {
 struct Sel {
   int f, z0, z1;
   double t;
+  bool mirror_x, mirror_y;  // quadrant bank: flips of the first-quadrant PSF
 };
 
+// Nearest field height to r: bracket i with fh[i] <= r < fh[i+1], then the
+// closer end (ties to the lower index); clamped at both ends.
+int nearest_height(const float* fh, int F, float r) {
+  if (r <= fh[0]) return 0;
+  if (r >= fh[F - 1]) return F - 1;
+  int i = 0;
+  while (i + 1 < F && fh[i + 1] <= r) ++i;
+  volatile float dlo = r - fh[i];
+  volatile float dhi = fh[i + 1] - r;
+  return (dhi < dlo) ? i + 1 : i;
+}
+
+// mode 0 (radial bank): f = the height nearest to the radial image height.
+// mode 1 (first-quadrant bank [F][F]): f = ix * F + iy with ix, iy the
+// heights nearest to |X| and |Y|; a pixel with X < 0 (Y < 0) uses the PSF
+// mirrored about the y (x) axis, the flip symmetry of the DP PSF (Sec. 5.2).
 Sel select_slice(int row, int col, int H, int W, float pitch, float depth,
-                 const float* fh, int F, const float* iq, int Z) {
+                 const float* fh, int F, const float* iq, int Z, int mode = 0) {
   volatile float X = ((float)col - 0.5f * (float)(W - 1)) * pitch;
   volatile float Y = ((float)row - 0.5f * (float)(H - 1)) * pitch;
-  volatile float X2 = X * X;
-  volatile float Y2 = Y * Y;
-  volatile float R2 = X2 + Y2;
-  float rho = std::sqrt((float)R2);
-  // nearest field height: bracket i with fh[i] <= rho < fh[i+1], then the
-  // closer end (ties to the lower index); clamped at both ends
-  int f;
-  if (rho <= fh[0]) {
-    f = 0;
-  } else if (rho >= fh[F - 1]) {
-    f = F - 1;
-  } else {
-    int i = 0;
-    while (i + 1 < F && fh[i + 1] <= rho) ++i;
-    volatile float dlo = rho - fh[i];
-    volatile float dhi = fh[i + 1] - rho;
-    f = (dhi < dlo) ? i + 1 : i;
-  }
   Sel s{};
-  s.f = f;
+  if (mode == 1) {
+    s.f = nearest_height(fh, F, std::fabs((float)X)) * F + nearest_height(fh, F, std::fabs((float)Y));
+    s.mirror_x = X < 0.f;
+    s.mirror_y = Y < 0.f;
+  } else {
+    volatile float X2 = X * X;
+    volatile float Y2 = Y * Y;
+    volatile float R2 = X2 + Y2;
+    s.f = nearest_height(fh, F, std::sqrt((float)R2));
+  }
   if (Z == 1) {
     s.z0 = s.z1 = 0;
     s.t = 0.0;
@@ -1030,16 +1038,29 @@ struct BankDesc {
   const float* fh;
   const float* iq;
   float pitch;
+  int mode;  // 0 radial [F], 1 first quadrant [F][F]
 };
 
-// Fills K[2][ks][ks] (unflipped) for pixel (row, col) of image n, channel c.
+// Fills K[2][ks][ks] (unflipped, rows = y, columns = x) for pixel (row, col)
+// of image n, channel c.  Quadrant bank: a mirror about the y axis reverses
+// the columns and exchanges L and R (the DP split is along x), a mirror
+// about the x axis reverses the rows.
 void pixel_kernel(const BankDesc& B, int row, int col, int H, int W, float depth,
                   int lam, double* K, Sel* sel_out) {
-  Sel s = select_slice(row, col, H, W, B.pitch, depth, B.fh, B.F, B.iq, B.Z);
-  size_t n2 = 2 * (size_t)B.ks * B.ks;
+  Sel s = select_slice(row, col, H, W, B.pitch, depth, B.fh, B.F, B.iq, B.Z, B.mode);
+  const int ks = B.ks;
+  size_t n1 = (size_t)ks * ks, n2 = 2 * n1;
   const double* k0 = B.bank + (((size_t)s.f * B.Z + s.z0) * B.NL + lam) * n2;
   const double* k1 = B.bank + (((size_t)s.f * B.Z + s.z1) * B.NL + lam) * n2;
-  for (size_t i = 0; i < n2; ++i) K[i] = (1.0 - s.t) * k0[i] + s.t * k1[i];
+  for (int side = 0; side < 2; ++side)
+    for (int a = 0; a < ks; ++a)
+      for (int b = 0; b < ks; ++b) {
+        const int side_src = s.mirror_x ? 1 - side : side;
+        const int a_src = s.mirror_y ? ks - 1 - a : a;
+        const int b_src = s.mirror_x ? ks - 1 - b : b;
+        const size_t src = side_src * n1 + (size_t)a_src * ks + b_src;
+        K[side * n1 + (size_t)a * ks + b] = (1.0 - s.t) * k0[src] + s.t * k1[src];
+      }
   if (sel_out) *sel_out = s;
 }
 
@@ -1048,16 +1069,19 @@ void pixel_kernel(const BankDesc& B, int row, int col, int H, int W, float depth
 // Bank-mode render.  aif (N,C,H,W) f64, depth_m (N,H,W) f32, bank
 // [F][Z][NL][2][ks][ks] f64, field_h_mm[F] f32 (ascending), depths_m[Z] f32
 // (ascending), out (N,2C,H,W) f64.
-int or_render_bank(const double* aif, int N, int C, int H, int W,
-                   const float* depth_m, const double* bank, int F, int Z,
-                   int NL, int ks, const float* field_h_mm,
-                   const float* depths_m, float pitch_mm, double* out,
-                   int n_threads) {
+// field_mode 0: bank [F][Z][NL][2][ks][ks] over radial heights; 1: bank
+// [F][F][Z][NL][2][ks][ks] over the first quadrant (see select_slice).
+int or_render_bank_mode(const double* aif, int N, int C, int H, int W,
+                        const float* depth_m, const double* bank, int F, int Z,
+                        int NL, int ks, const float* field_h_mm,
+                        const float* depths_m, float pitch_mm, int field_mode, double* out,
+                        int n_threads) {
   if (!aif || !depth_m || !bank || !out || ks < 1 || ks % 2 == 0) return -1;
   if (!(NL == C || NL == 1)) return -4;
+  if (field_mode != 0 && field_mode != 1) return -1;
   std::vector<float> iq(Z);
   for (int j = 0; j < Z; ++j) iq[j] = 1.0f / depths_m[j];
-  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm};
+  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm, field_mode};
   int p = (ks - 1) / 2;
   parallel_for(N * H, n_threads, [&](int nr) {
     int n = nr / H, y = nr % H;
@@ -1084,18 +1108,28 @@ int or_render_bank(const double* aif, int N, int C, int H, int W,
   return 0;
 }
 
+int or_render_bank(const double* aif, int N, int C, int H, int W,
+                   const float* depth_m, const double* bank, int F, int Z,
+                   int NL, int ks, const float* field_h_mm,
+                   const float* depths_m, float pitch_mm, double* out,
+                   int n_threads) {
+  return or_render_bank_mode(aif, N, C, H, W, depth_m, bank, F, Z, NL, ks, field_h_mm,
+                             depths_m, pitch_mm, 0, out, n_threads);
+}
+
 // Bank-mode render of selected pixels only: pix[i*3..] = (n, y, x);
 // out[i*2C + c] = L of channel c, out[i*2C + C + c] = R.
-int or_render_bank_pixels(const double* aif, int N, int C, int H, int W,
-                          const float* depth_m, const double* bank, int F, int Z,
-                          int NL, int ks, const float* field_h_mm,
-                          const float* depths_m, float pitch_mm, const int* pix,
-                          int npix, double* out, int n_threads) {
+int or_render_bank_pixels_mode(const double* aif, int N, int C, int H, int W,
+                               const float* depth_m, const double* bank, int F, int Z,
+                               int NL, int ks, const float* field_h_mm,
+                               const float* depths_m, float pitch_mm, int field_mode,
+                               const int* pix, int npix, double* out, int n_threads) {
   if (!aif || !depth_m || !bank || !pix || !out || ks < 1 || ks % 2 == 0) return -1;
   if (!(NL == C || NL == 1)) return -4;
+  if (field_mode != 0 && field_mode != 1) return -1;
   std::vector<float> iq(Z);
   for (int j = 0; j < Z; ++j) iq[j] = 1.0f / depths_m[j];
-  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm};
+  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm, field_mode};
   int p = (ks - 1) / 2;
   parallel_for(npix, n_threads, [&](int i) {
     int n = pix[3 * i], y = pix[3 * i + 1], x = pix[3 * i + 2];
@@ -1118,6 +1152,15 @@ int or_render_bank_pixels(const double* aif, int N, int C, int H, int W,
     }
   });
   return 0;
+}
+
+int or_render_bank_pixels(const double* aif, int N, int C, int H, int W,
+                          const float* depth_m, const double* bank, int F, int Z,
+                          int NL, int ks, const float* field_h_mm,
+                          const float* depths_m, float pitch_mm, const int* pix,
+                          int npix, double* out, int n_threads) {
+  return or_render_bank_pixels_mode(aif, N, C, H, W, depth_m, bank, F, Z, NL, ks, field_h_mm,
+                                    depths_m, pitch_mm, 0, pix, npix, out, n_threads);
 }
 
 // Map-mode render: psf_map (H,W,2,ks,ks) f64.

@@ -4,7 +4,7 @@ Ray trace of a lens, DP PSF binning and per-pixel DP rendering run in the
 CUDA library built from csrc/ (C ABI in include/sdirt.h); this package only
 marshals PyTorch tensors into that ABI.
 """
-from .api import (BankLayout, BatchedTrace, DPSensor, Lens, dp_psf_map, dp_psf_trace,  # noqa: F401
+from .api import (SD_FIELD_QUADRANT, SD_FIELD_RADIAL, BankLayout, BatchedTrace, DPSensor, Lens, dp_psf_map, dp_psf_trace,  # noqa: F401
                   dp_psf_trace_backward, dp_render, dp_render_backward, dp_render_map, dp_render_tc,
                   f_number_table, make_requests, render_backward_workspace, trace_hits)
 from .autograd import (DPRenderFunction, DPTraceFunction, dp_psf_trace_autograd,  # noqa: F401

@@ -49,7 +49,7 @@ class SdTraceOpts(ctypes.Structure):
 class SdBankLayout(ctypes.Structure):
     _fields_ = [("n_field", ctypes.c_int32), ("n_depth", ctypes.c_int32),
                 ("n_lambda", ctypes.c_int32), ("ks", ctypes.c_int32),
-                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("field_mode", ctypes.c_int32),
                 ("field_h_mm", ctypes.POINTER(ctypes.c_float)),
                 ("depths_m", ctypes.POINTER(ctypes.c_float)),
                 ("pitch_mm", ctypes.c_float), ("reserved2", ctypes.c_float)]

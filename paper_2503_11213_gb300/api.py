@@ -279,23 +279,32 @@ def trace_hits(lens: Lens, sensor: DPSensor, req, device="cuda"):
     return {f: rec[:, j] for j, f in enumerate(HIT_FIELDS)}
 
 
-class BankLayout:
-    """Bank [F][Z][NL][2][ks][ks] description for the renderer."""
+SD_FIELD_RADIAL, SD_FIELD_QUADRANT = 0, 1
 
-    def __init__(self, field_h_mm, depths_m, n_lambda, ks, pitch_mm, dtype=torch.float32):
+
+class BankLayout:
+    """Bank [F][Z][NL][2][ks][ks] description for the renderer; with
+    field_mode=SD_FIELD_QUADRANT a first-quadrant 2-D grid of field points,
+    [F][F][Z][NL][2][ks][ks] (x index, y index, both at field_h_mm), used
+    through the PSF's flip symmetry about both axes (sd_dp_render only)."""
+
+    def __init__(self, field_h_mm, depths_m, n_lambda, ks, pitch_mm, dtype=torch.float32,
+                 field_mode=SD_FIELD_RADIAL):
         self.fh = np.ascontiguousarray(field_h_mm, dtype=np.float32)
         self.dm = np.ascontiguousarray(depths_m, dtype=np.float32)
         self.n_lambda, self.ks, self.pitch_mm, self.dtype = n_lambda, ks, pitch_mm, dtype
+        self.field_mode = field_mode
 
     def c(self):
         return L.SdBankLayout(len(self.fh), len(self.dm), self.n_lambda, self.ks,
-                              _DT[self.dtype], 0,
+                              _DT[self.dtype], self.field_mode,
                               self.fh.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                               self.dm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                               float(self.pitch_mm), 0.0)
 
     def shape(self):
-        return (len(self.fh), len(self.dm), self.n_lambda, 2, self.ks, self.ks)
+        cells = len(self.fh) ** 2 if self.field_mode == SD_FIELD_QUADRANT else len(self.fh)
+        return (cells, len(self.dm), self.n_lambda, 2, self.ks, self.ks)
 
 
 def dp_render(aif, depth_m, bank, layout: BankLayout, out=None):

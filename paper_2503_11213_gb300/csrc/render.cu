@@ -3,7 +3,9 @@
 // out_L[n,c,y,x] = sum_{u,v} Ipad[n,c,y+u,x+v] * K_L(y,x,c)[ks-1-u][ks-1-v]
 // with Ipad the image replicate-padded by p = (ks-1)/2 (likewise R) and, in
 // bank mode, K(y,x,c) = (1-t) B[f][z0][lam] + t B[f][z0+1][lam] selected per
-// pixel from its radial image height and depth (linear in inverse depth).
+// pixel from its radial image height and depth (linear in inverse depth);
+// with a quadrant bank, from the nearest first-quadrant field point of
+// (|X|, |Y|) and the PSF's flip symmetry about both axes (Sec. 5.2).
 //
 // The render is linear in the kernel, so a pixel's output is
 // (1-t) (I * B[f][z0]) + t (I * B[f][z0+1]): a sum over bank slices with
@@ -190,9 +192,14 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
       // segment id = warp * 32 + lane of the owner thread = rb * TX + col
       const int col = sg % TX, rb = sg / TX;
       const int f = key / P.Z, z = key - f * P.Z;
-      const TB* KL = reinterpret_cast<const TB*>(P.bank) +
-                     (((size_t)f * P.Z + z) * P.NL + lam) * 2 * ks2;
-      const TB* KR = KL + ks2;
+      // quadrant bank: field cell and flips (x: mirror columns and exchange
+      // L and R; y: mirror rows); radial bank: flips = 0
+      const int flips = f / P.FC, cell = f - flips * P.FC;
+      const TB* K0 = reinterpret_cast<const TB*>(P.bank) +
+                     (((size_t)cell * P.Z + z) * P.NL + lam) * 2 * ks2;
+      const TB* KL = (flips & 1) ? K0 + ks2 : K0;
+      const TB* KR = (flips & 1) ? K0 : K0 + ks2;
+      const bool mx = flips & 1, my = flips & 2;
       // K block b covers v in [b*VB, b*VB + VB): element (u, vv, side) =
       // K_side[ks-1-u][ks-1-(b*VB+vv)] at kb[buf][(u*VB + vv)*2 + side]
       float pre[NR];
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
             int side = e & 1, uv = e >> 1, u = uv / VB, vv = uv - u * VB;
             int v_ = b * VB + vv;
             if (v_ < ks && u < ks)
-              v = ldk<TB>((side ? KR : KL) + (ks - 1 - u) * ks + (ks - 1 - v_));
+              v = ldk<TB>((side ? KR : KL) + (my ? u : ks - 1 - u) * ks + (mx ? v_ : ks - 1 - v_));
           }
           pre[r] = v;
         }
@@ -350,7 +357,9 @@ sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
-  if ((long long)P.F * P.Z > 65000) return SD_ERR_UNSUPPORTED;  // 16-bit relative keys
+  // 16-bit relative keys (quadrant keys carry 4 flip classes)
+  if ((long long)P.FC * P.Z * (P.fmode == SD_FIELD_QUADRANT ? 4 : 1) > 65000)
+    return SD_ERR_UNSUPPORTED;
   P.aif = aif;
   P.depth = depth_m;
   P.bank = bank;

@@ -546,6 +546,7 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
+  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: forward only
   if (layout->dtype != SD_F32 && layout->dtype != SD_BF16 && layout->dtype != SD_F16)
     return SD_ERR_UNSUPPORTED;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;

@@ -19,6 +19,8 @@ struct RenderParams {
   void* out;
   int N, C, H, W;
   int F, Z, NL, ks;
+  int fmode;       // SD_FIELD_RADIAL or SD_FIELD_QUADRANT
+  int FC;          // field cells of the bank: F (radial) or F * F (quadrant)
   float pitch;
   int halo_w;      // row stride of the staged tile (floats)
   int halo_h;
@@ -26,27 +28,37 @@ struct RenderParams {
   float iq[SD_MAX_BANK_DEPTHS];  // 1.0f / depth_m[j] (strictly descending)
 };
 
+// nearest of the F ascending heights fh to r (ties to the lower index),
+// clamped at both ends
+__device__ __forceinline__ int nearest_field(const float* fh, int F, float r) {
+  if (r <= fh[0]) return 0;
+  if (r >= fh[F - 1]) return F - 1;
+  int a = 0, b = F - 1;  // fh[a] <= r < fh[b]
+  while (b - a > 1) {
+    int m = (a + b) >> 1;
+    if (fh[m] <= r) a = m; else b = m;
+  }
+  float dlo = __fsub_rn(r, fh[a]);
+  float dhi = __fsub_rn(fh[a + 1], r);
+  return (dhi < dlo) ? a + 1 : a;
+}
+
 // Per-pixel bank selection in FP32 without contraction (the same sequence of
-// IEEE operations as the oracle's selection).
+// IEEE operations as the oracle's selection).  The key is f * Z + z0 with f
+// the field cell; in quadrant mode f = flips * F * F + fx * F + fy, flips =
+// (X < 0) + 2 (Y < 0), so that key + 1 is still the next depth slice.
 __device__ __forceinline__ void select_slice(const RenderParams& P, int row, int col,
                                              float depth, int* key, float* t) {
   float X = __fmul_rn(__fsub_rn((float)col, 0.5f * (float)(P.W - 1)), P.pitch);
   float Y = __fmul_rn(__fsub_rn((float)row, 0.5f * (float)(P.H - 1)), P.pitch);
-  float rho = __fsqrt_rn(__fadd_rn(__fmul_rn(X, X), __fmul_rn(Y, Y)));
   int F = P.F, f;
-  if (rho <= P.fh[0]) {
-    f = 0;
-  } else if (rho >= P.fh[F - 1]) {
-    f = F - 1;
+  if (P.fmode == SD_FIELD_QUADRANT) {
+    const int fx = nearest_field(P.fh, F, fabsf(X)), fy = nearest_field(P.fh, F, fabsf(Y));
+    const int flips = (X < 0.f ? 1 : 0) + (Y < 0.f ? 2 : 0);
+    f = flips * P.FC + fx * F + fy;
   } else {
-    int a = 0, b = F - 1;  // fh[a] <= rho < fh[b]
-    while (b - a > 1) {
-      int m = (a + b) >> 1;
-      if (P.fh[m] <= rho) a = m; else b = m;
-    }
-    float dlo = __fsub_rn(rho, P.fh[a]);
-    float dhi = __fsub_rn(P.fh[a + 1], rho);
-    f = (dhi < dlo) ? a + 1 : a;
+    float rho = __fsqrt_rn(__fadd_rn(__fmul_rn(X, X), __fmul_rn(Y, Y)));
+    f = nearest_field(P.fh, F, rho);
   }
   int Z = P.Z, z0;
   float tt;
@@ -92,7 +104,11 @@ inline sd_status check_layout(const sd_bank_layout* L, RenderParams& P) {
     P.iq[j] = 1.0f / L->depths_m[j];
     if (j && !(L->depths_m[j] > L->depths_m[j - 1])) return SD_ERR_ARG;
   }
+  if (L->field_mode != SD_FIELD_RADIAL && L->field_mode != SD_FIELD_QUADRANT) return SD_ERR_ARG;
+  if (L->field_mode == SD_FIELD_QUADRANT && !(L->field_h_mm[0] >= 0.f)) return SD_ERR_ARG;
+  P.fmode = L->field_mode;
   P.F = L->n_field;
+  P.FC = P.fmode == SD_FIELD_QUADRANT ? P.F * P.F : P.F;
   P.Z = L->n_depth;
   P.NL = L->n_lambda;
   P.ks = L->ks;

@@ -543,6 +543,7 @@ extern "C" sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, siz
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
+  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: CUDA cores only
   *bytes = 256 + tr_bp_bytes(P);
   return SD_OK;
 }
@@ -558,6 +559,7 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
+  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: CUDA cores only
   if (layout->dtype != SD_BF16 && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
   if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024 ||
       (TR_Y + P.ks - 1) * (tr_kk(P.ks) / 8) > TR_SI * TR_NT || TR_SS * (tr_kk(P.ks) / 8) > 32 * TR_TPL)
