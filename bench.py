@@ -391,6 +391,7 @@ def run_ours(args, world, rank, local, dist):
         line["differentiation_pipeline"] = pipeline_compare(sd, dev)
         line["precision"] = precision_compare(sd, dev)
         line["paper_workload"] = paper_workload(sd, dev)
+        line["quadrant_bank"] = quadrant_compare(sd, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
@@ -704,6 +705,54 @@ def pipeline_compare(sd, dev, reps=5):
 
 PAPER_TRACE_S = 801.544   # DP PSF map of 512 x 768 pixels by ray tracing (Table S3)
 PAPER_RENDER_S = 0.2      # DP image from a PSF map ("fixed cost", supplement)
+
+
+def quadrant_compare(sd, dev, reps=5):
+    """The bench render (1024x1024 RGB, 65x65 kernels, doublet-pair lens)
+    through a first-quadrant 2-D bank (16 x 16 field points up to the
+    sensor's half width, 32 depths, 3 wavelengths; other quadrants by the
+    PSF's flip symmetry) against the radial bank of the main step: trace
+    and render times, and how far apart the two renders are."""
+    import torch
+    cfg = W.config_full_forward()
+    H, Wd = cfg["sensor_hw"]
+    ps = cfg["pitch_mm"]
+    fq = np.linspace(0.0, 0.5 * Wd * ps, 16)
+    lens = sd.Lens(cfg["lens"], cfg["focus_mm"])
+    sensor = sd.DPSensor(ps)
+    stream = torch.cuda.current_stream()
+    aif = torch.tensor(W.aif_pink(1, 3, H, Wd, seed=1).astype(np.float32), device=dev)
+    depth = torch.tensor(W.depth_perlin(1, H, Wd, seed=2).astype(np.float32), device=dev)
+    dm = cfg["depths_mm"] / 1000.0
+    res = {"field_points": [16, 16], "depths": len(dm), "lambdas": 3, "ks": cfg["ks"],
+           "pupil_grid": [cfg["n_grid"]] * 2, "image": [1, 3, H, Wd]}
+    outs = {}
+    for name, fh, mode, reqs in (
+            ("radial", cfg["field_h_mm"], sd.SD_FIELD_RADIAL,
+             W.bank_grid(cfg["field_h_mm"], cfg["depths_mm"], cfg["lambdas_nm"], cfg["n_grid"],
+                         cfg["ks"])),
+            ("quadrant", fq, sd.SD_FIELD_QUADRANT,
+             W.bank_grid_quadrant(fq, cfg["depths_mm"], cfg["lambdas_nm"], cfg["n_grid"],
+                                  cfg["ks"]))):
+        req_dev, total, _ = sd.make_requests(reqs, device=dev)
+        bank = torch.empty(total, device=dev)
+        st = torch.zeros((len(reqs), 8), dtype=torch.int64, device=dev)
+        t_trace = _timed(lambda: sd.dp_psf_trace(lens, sensor, req_dev, len(reqs), total,
+                                                 max_ks=cfg["ks"], max_n=cfg["n_grid"],
+                                                 norm=sd.SD_NORM_JOINT, out=bank, stats=st),
+                         stream, reps=3)
+        lay = sd.BankLayout(fh, dm, 3, cfg["ks"], ps, field_mode=mode)
+        out = torch.empty((1, 6, H, Wd), device=dev)
+        t_render = _timed(lambda: sd.dp_render(aif, depth, bank, lay, out=out), stream, reps)
+        outs[name] = out
+        res[name] = {"psfs": len(reqs), "rays": int(st[:, 0].sum().item()),
+                     "trace_ms": round(t_trace, 3), "render_ms": round(t_render, 3)}
+        del bank
+    ref = outs["radial"]
+    res["max_rel_diff_quadrant_vs_radial"] = float(
+        ((outs["quadrant"] - ref).abs().max() / ref.abs().max()).item())
+    lens.free()
+    return res
 
 
 def paper_workload(sd, dev, reps=5):

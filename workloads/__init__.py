@@ -193,6 +193,18 @@ def bank_grid(field_h_mm, depths_mm, lambdas_nm, n_grid, ks):
     return np.array(reqs, dtype=REQ_DTYPE)
 
 
+def bank_grid_quadrant(field_h_mm, depths_mm, lambdas_nm, n_grid, ks):
+    """Requests of a first-quadrant 2-D bank, order [x height][y height]
+    [depth][wavelength], both axes sampled at field_h_mm."""
+    reqs = []
+    for hx in field_h_mm:
+        for hy in field_h_mm:
+            for d in depths_mm:
+                for lam in lambdas_nm:
+                    reqs.append((hx, d, lam, n_grid, ks, 0, hy))
+    return np.array(reqs, dtype=REQ_DTYPE)
+
+
 def inverse_uniform_depths(d_near_mm, d_far_mm, n):
     """n depths uniform in inverse depth, ascending in depth."""
     inv = np.linspace(1.0 / d_near_mm, 1.0 / d_far_mm, n)
