@@ -451,6 +451,48 @@ sd_status sd_dp_render_backward_noalloc(const float* grad_out,
 sd_status sd_dev_math_check(const float* a, const float* b, int n, float* quot,
                             float* root, void* stream);
 
+/* ------------------------------------------------------------------------
+ * DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
+ * module"; Sec. 4 implementation details): an MLP from the normalised object
+ * point p = (x_n, y_n, d_n) of a pixel to the 2*ks^2 values of its
+ * (PSF_L, PSF_R): 5 hidden layers of 512 neurons (ReLU), a linear output
+ * layer of 2*ks^2 neurons; at inference the outputs are clamped at 0 and
+ * sum-normalised jointly (sum of L + R = 1).  The paper times this on a
+ * 512 x 768 depth map with ks = 21 (0.395 s, supplement table).
+ * ---------------------------------------------------------------------- */
+#define SD_MLP_HIDDEN 512
+#define SD_MLP_MAX_KS 31
+
+/* Bytes of the packed network for kernel size ks (odd, 1..SD_MLP_MAX_KS). */
+sd_status sd_mlp_blob_bytes(int ks, size_t* bytes);
+
+/*
+ * Packs a network into blob (device memory of sd_mlp_blob_bytes(ks) bytes,
+ * 256-byte aligned; owned by the caller).  weights[l] and biases[l], l = 0..5,
+ * are host FP32, weights row-major [out][in]: 512x3, four 512x512, and
+ * (2 ks^2)x512; biases 512 (l < 5) and 2 ks^2.  The 512-wide matrices are
+ * rounded to BF16 (nearest even) and stored in the tensor cores' operand
+ * layout; layer 0 and all biases stay FP32.  Synchronous (one host-to-device
+ * copy).  SD_ERR_ARG for null pointers, a bad ks or a short blob.
+ */
+sd_status sd_mlp_pack(const float* const* weights, const float* const* biases, int ks,
+                      void* blob, size_t blob_bytes);
+
+/*
+ * The DP PSF map of a depth map predicted by the packed network: pixel (y, x)
+ * of depth_m (H, W) [metres, FP32, device] has p = (x_n, y_n, d_n) with
+ * x_n = (x - (W-1)/2) / (W/2), y_n = (y - (H-1)/2) / (H/2) (the sensor
+ * position normalised to [-1, 1]) and d_n = 2 (d - d_min) / (d_max - d_min)
+ * - 1; out (H, W, 2, ks, ks) FP32 device, the layout sd_dp_render_map takes.
+ * Tensor cores (tcgen05): BF16 operands, FP32 accumulation, hidden
+ * activations rounded to BF16 between layers.  *status (device int32) is set
+ * to 0 by the call and to 1 by the kernel if one of its bounded completion
+ * waits gave up (the map is then invalid).  H * W >= 1, d_max > d_min.
+ */
+sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, int W,
+                         float d_min_m, float d_max_m, float* out, int32_t* status,
+                         void* stream);
+
 /*
  * Test aid (the paper has no counterpart): runs the tensor-core (tcgen05)
  * path of the BF16 render on a fixed small product, D = A[u:u+128, :] B^T

@@ -16,6 +16,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                    and disparity sign; absolute PSF shapes of the aspheric lens
                    are "parity unpinned" beyond these properties
   trace_grad       pinned by FP64 central differences of trace_functional
+  mlp_psf          pinned by an independent float64 evaluation of the same
+                   network with library linear layers, and closed forms
+                   (biases only; normalised-input corners)
   render_*         pinned by the delta-PSF and constant-image identities, a
                    shift-invariant kernel against scipy correlation and brute
                    force of the supplement's unfold/fold formulation; the
@@ -307,3 +310,38 @@ def render_select(depth_m, field_h_mm, depths_m, pitch_mm):
     _check(lib().or_render_select(H, W, _pf(dm), _pf(fh), len(fh), _pf(dz), len(dz),
                                   float(np.float32(pitch_mm)), _pd(out)), "render_select")
     return out
+
+
+# --------------------------------------------------------------------------
+# DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
+# module"; Sec. 4 implementation details)
+# --------------------------------------------------------------------------
+def mlp_inputs(depth_m, d_min_m, d_max_m):
+    """Normalised object point p = (x_n, y_n, d_n) of every pixel of a depth
+    map (H, W), row-major -> (H*W, 3): the pixel's sensor position scaled to
+    [-1, 1] (the frustum's x and y at its depth, Sec. 3.3) and the depth
+    scaled linearly from [d_min, d_max] to [-1, 1]."""
+    d = np.asarray(depth_m, dtype=np.float64)
+    H, W = d.shape
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    xn = (x - 0.5 * (W - 1)) / (0.5 * W)
+    yn = (y - 0.5 * (H - 1)) / (0.5 * H)
+    dn = 2.0 * (d - d_min_m) / (d_max_m - d_min_m) - 1.0
+    return np.stack([xn, yn, dn], -1).reshape(-1, 3)
+
+
+def mlp_psf(weights, biases, p, ks):
+    """The network of Sec. 3.3 in FP64: h = ReLU(W_l h + b_l) for the input
+    layer and the hidden layers (l = 0..4, 512 neurons each), o = W_5 h + b_5
+    with 2 ks^2 outputs; at inference o is clamped at 0 and divided by its
+    sum (the sum normalisation of Sec. 3.3, joint over L and R).
+    p (n, 3) -> (n, 2, ks, ks)."""
+    h = np.asarray(p, dtype=np.float64)
+    for l in range(5):
+        h = np.maximum(h @ np.asarray(weights[l], np.float64).T + np.asarray(biases[l], np.float64),
+                       0.0)
+    o = h @ np.asarray(weights[5], np.float64).T + np.asarray(biases[5], np.float64)
+    o = np.maximum(o, 0.0)
+    s = o.sum(axis=1, keepdims=True)
+    o = np.divide(o, s, out=np.zeros_like(o), where=s > 0)
+    return o.reshape(-1, 2, ks, ks)

@@ -384,3 +384,54 @@ def dp_render_backward(grad_out, aif, depth_m, bank, layout: BankLayout, need_ai
                                           _stream()),
             "sd_dp_render_backward")
     return ga, gb
+
+
+MLP_HIDDEN = 512
+def MLP_SHAPES(ks):
+    """(out, in) of the six weight matrices for kernel size ks."""
+    return [(MLP_HIDDEN, 3)] + [(MLP_HIDDEN, MLP_HIDDEN)] * 4 + [(2 * ks * ks, MLP_HIDDEN)]
+
+
+class PsfMLP:
+    """The DP PSF prediction network (Sec. 3.3) packed on the device: weights
+    [l] (out, in) and biases[l] for l = 0..5 as float arrays of the shapes
+    MLP_SHAPES(ks) (3 -> 512, four 512 -> 512, 512 -> 2 ks^2)."""
+
+    def __init__(self, weights, biases, ks, device=None):
+        shapes = MLP_SHAPES(ks)
+        if len(weights) != 6 or len(biases) != 6:
+            raise ValueError("six weight matrices and six bias vectors")
+        self.w = [np.ascontiguousarray(w, dtype=np.float32) for w in weights]
+        self.b = [np.ascontiguousarray(b, dtype=np.float32) for b in biases]
+        for w, b, sh in zip(self.w, self.b, shapes):
+            if w.shape != sh or b.shape != (sh[0],):
+                raise ValueError(f"layer shapes must be {shapes}")
+        self.ks = ks
+        n = ctypes.c_size_t(0)
+        L.check(L.lib().sd_mlp_blob_bytes(ks, ctypes.byref(n)), "sd_mlp_blob_bytes")
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.blob = torch.empty(n.value, dtype=torch.uint8, device=dev)
+        FP = ctypes.POINTER(ctypes.c_float)
+        wp = (FP * 6)(*[w.ctypes.data_as(FP) for w in self.w])
+        bp = (FP * 6)(*[b.ctypes.data_as(FP) for b in self.b])
+        L.check(L.lib().sd_mlp_pack(wp, bp, ks, _ptr(self.blob), self.blob.numel()),
+                "sd_mlp_pack")
+
+
+def mlp_psf_map(net: PsfMLP, depth_m, d_min_m, d_max_m, out=None, status=None):
+    """Per-pixel DP PSF map (H, W, 2, ks, ks) FP32 predicted by the network
+    for a depth map (H, W) in metres (device, FP32); returns (map, status)
+    with status a device int32 (1 if a bounded wait of the kernel gave up)."""
+    H, W = depth_m.shape
+    ks = net.ks
+    if out is None:
+        out = torch.empty((H, W, 2, ks, ks), dtype=torch.float32, device=depth_m.device)
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=depth_m.device)
+    _need_cuda(depth_m, out, status, net.blob)
+    if depth_m.dtype != torch.float32:
+        raise ValueError("depth must be float32")
+    L.check(L.lib().sd_mlp_psf_map(_ptr(net.blob), ks, _ptr(depth_m), H, W, float(d_min_m),
+                                   float(d_max_m), _ptr(out), _ptr(status), _stream()),
+            "sd_mlp_psf_map")
+    return out, status

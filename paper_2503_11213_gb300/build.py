@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libsdirt.so"
 SOURCES = ["lens_trace.cu", "render.cu", "render_bwd.cu", "render_map.cu", "render_tc.cu",
-           "tune.cu", "abi.cu"]
+           "mlp.cu", "tune.cu", "abi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,347 @@
+// DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
+// module"): per pixel, an MLP maps the normalised object point p = (x_n,
+// y_n, d_n) through 5 hidden layers of 512 (ReLU) to the 2 ks^2 values of
+// (PSF_L, PSF_R); the outputs are clamped at 0 and sum-normalised.
+//
+// One CTA predicts 128 pixels (the MMA's M) with every layer on the
+// 5th-generation tensor cores:
+//   * the activations of the 128 pixels live in shared memory as the A
+//     operand (BF16, no-swizzle K-major core matrices, 128 KB);
+//   * the weights of layers 1..5 are packed on the host into 32 KB chunks of
+//     256 output rows x 64 inputs, already in the B operand layout, and one
+//     thread streams them in consumption order through a ring of three
+//     shared buffers with 1-D bulk copies (the TMA engine), completion
+//     counted in bytes on an mbarrier per buffer;
+//   * one thread issues the MMAs (M = 128, N = 256, K = 16) into a 512-column
+//     FP32 accumulator in tensor memory and commits each buffer back to the
+//     copier;
+//   * four warps (one per tensor-memory lane quarter) compute layer 0 (3
+//     inputs, CUDA cores), and after every layer read the accumulator, add
+//     the bias, apply ReLU and write the next A operand in BF16.  The output
+//     layer runs in passes of 512 columns (the accumulator's width): the
+//     passes first accumulate each pixel's sum of the clamped outputs, the
+//     last one then stores its columns normalised (re-read from tensor
+//     memory), and the earlier passes are recomputed to store theirs, so the
+//     map is written once, never read back.
+// Every wait is bounded; a wait that gives up sets *status and makes the
+// other waits of the launch give up too.
+
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace sd {
+
+constexpr int MH = SD_MLP_HIDDEN;   // hidden width
+constexpr int MM = 128;             // pixels per CTA
+constexpr int MKC = 64;             // inputs per weight chunk
+constexpr int MNC = 256;            // outputs per weight chunk
+constexpr int MNB = 3;              // weight ring buffers
+constexpr uint32_t MCHUNK = MNC * MKC * 2;        // 32 KB
+constexpr uint32_t MA_BYTES = MM * MH * 2;        // 128 KB
+constexpr int MTHREADS = 192;       // warps 0-3 epilogue, 4 MMA issue, 5 copies
+constexpr uint32_t MWAIT = 1u << 22;
+
+__host__ __device__ inline int mlp_nout(int ks) { return 2 * ks * ks; }
+__host__ __device__ inline int mlp_nblk(int ks) { return (mlp_nout(ks) + MNC - 1) / MNC; }
+// chunks: 4 hidden layers of (512/256) x (512/64), the output layer nblk x 8
+__host__ __device__ inline int mlp_chunks(int ks) { return 4 * 2 * (MH / MKC) + mlp_nblk(ks) * (MH / MKC); }
+// FP32 tail: W0 [512][3], b0..b4 [512] each, b5 [nblk * 256]
+__host__ __device__ inline size_t mlp_tail_floats(int ks) {
+  return (size_t)MH * 3 + 5 * (size_t)MH + (size_t)mlp_nblk(ks) * MNC;
+}
+inline size_t mlp_bytes(int ks) { return (size_t)mlp_chunks(ks) * MCHUNK + 4 * mlp_tail_floats(ks); }
+
+struct MlpParams {
+  const unsigned char* blob;
+  const float* depth;
+  float* out;
+  int* status;
+  int ks, H, W;
+  float d_min, d_scale;  // d_n = (d - d_min) * d_scale - 1
+};
+
+__device__ __forceinline__ bool mwait(uint64_t* bar, uint32_t parity, int* err) {
+  if (tc::mbar_wait(bar, parity, MWAIT, err)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+// output pass computed by accumulator phase ph >= 4: passes 0..npass-1, then
+// 0..npass-2 again
+__device__ __forceinline__ int mlp_pass(int ph, int npass) {
+  const int j = ph - 4;
+  return j < npass ? j : j - npass;
+}
+
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+__global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* Abuf = smem;             // element (m, k) at (k/8)*2048 + m*16 + (k%8)*2
+  unsigned char* Wbuf = smem + MA_BYTES;  // MNB chunks; (n, k) at (k/8)*4096 + n*16 + (k%8)*2
+  __shared__ __align__(8) uint64_t s_full[MNB], s_empty[MNB], s_acc, s_act, s_done;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ks = P.ks, nout = mlp_nout(ks), nblk = mlp_nblk(ks), nchunk = mlp_chunks(ks);
+  const int npass = (nblk + 1) / 2;     // output passes of up to 2 x 256 columns
+  const int nphase = 4 + 2 * npass - 1; // accumulator phases (earlier passes twice)
+  const long long npix = (long long)P.H * P.W;
+  const float* tail = reinterpret_cast<const float*>(P.blob + (size_t)nchunk * MCHUNK);
+  const float* W0 = tail;                      // [512][3]
+  const float* B0 = W0 + MH * 3;               // b0, b1, ..., b4 (512 each)
+  const float* B5 = B0 + 5 * MH;               // [nblk * 256]
+
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
+  if (tid == 0) {
+    for (int b = 0; b < MNB; ++b) {
+      tc::mbar_init(&s_full[b], 1);
+      tc::mbar_init(&s_empty[b], 1);
+    }
+    tc::mbar_init(&s_acc, 1);
+    tc::mbar_init(&s_act, MM);
+    tc::mbar_init(&s_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 5) {
+    // ---- weight copier: chunks in consumption order through the ring ------
+    if (lane == 0) {
+      int last[MNB] = {-1, -1, -1};  // last copy issued into each buffer
+      int c = 0;                     // copies issued
+      bool ok = true;
+      for (int ph = 0; ph < nphase && ok; ++ph) {
+        const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
+        const int nb0 = ph < 4 ? 0 : 2 * q, nb1 = ph < 4 ? 2 : min(nb0 + 2, nblk);
+        for (int nb = nb0; nb < nb1 && ok; ++nb)
+          for (int kb = 0; kb < MH / MKC; ++kb, ++c) {
+            const int b = c % MNB;
+            if (c >= MNB && !mwait(&s_empty[b], (uint32_t)(c / MNB - 1) & 1u, P.status)) {
+              ok = false;
+              break;
+            }
+            // blob chunk: hidden layer ph + 1, or the output layer's block nb
+            const int chunk = (ph < 4 ? ph * 16 + nb * 8 : 64 + nb * 8) + kb;
+            tc::mbar_arrive_expect_tx(&s_full[b], MCHUNK);
+            tc::bulk_g2s(Wbuf + (size_t)b * MCHUNK, P.blob + (size_t)chunk * MCHUNK, MCHUNK,
+                         &s_full[b]);
+            last[b] = c;
+          }
+      }
+      // no copy may still be landing when the CTA ends (after an error the
+      // MMA thread may not have consumed them): bounded wait for each
+      for (int b = 0; b < MNB; ++b)
+        if (last[b] >= 0) tc::mbar_wait(&s_full[b], (uint32_t)(last[b] / MNB) & 1u, MWAIT);
+    }
+  } else if (warp == 4) {
+    // ---- MMA issue --------------------------------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(MM, MNC);
+      const uint32_t a0 = tc::smem_u32(Abuf), w0 = tc::smem_u32(Wbuf);
+      int c = 0;
+      bool ok = true;
+      for (int ph = 0; ph < nphase && ok; ++ph) {
+        // the epilogue has written this phase's A operand (and read the
+        // previous phase's accumulator)
+        ok = mwait(&s_act, (uint32_t)ph & 1u, P.status);
+        tc::fence_after_sync();
+        const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
+        const int nb0 = ph < 4 ? 0 : 2 * q, nb1 = ph < 4 ? 2 : min(nb0 + 2, nblk);
+        for (int nb = nb0; nb < nb1 && ok; ++nb)
+          for (int kb = 0; kb < MH / MKC && ok; ++kb, ++c) {
+            const int b = c % MNB;
+            ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status);
+            if (!ok) break;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < MKC / 16; ++s) {
+              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(kb * 8 + s * 2) * 2048u, 2048, 128);
+              const uint64_t bd =
+                  tc::smem_desc(w0 + (uint32_t)b * MCHUNK + (uint32_t)s * 2 * 4096u, 4096, 128);
+              tc::mma_bf16(tmem + (uint32_t)((nb - nb0) * MNC), ad, bd, idesc, kb > 0 || s > 0);
+            }
+            tc::commit(&s_empty[b]);
+          }
+        tc::commit(&s_acc);
+      }
+      // every MMA issued has completed before the tensor memory is freed
+      // (also after an error)
+      tc::commit(&s_done);
+      tc::mbar_wait(&s_done, 0, MWAIT);
+    }
+  } else {
+    // ---- warps 0-3: layer 0, then every accumulator -------------------------
+    const int m = tid;                       // tensor-memory lane = A row
+    const long long pix = (long long)blockIdx.x * MM + m;
+    const bool live = pix < npix;
+    const int py = live ? (int)(pix / P.W) : 0, px = live ? (int)(pix - (long long)py * P.W) : 0;
+    const float xn = live ? ((float)px - 0.5f * (float)(P.W - 1)) / (0.5f * (float)P.W) : 0.f;
+    const float yn = live ? ((float)py - 0.5f * (float)(P.H - 1)) / (0.5f * (float)P.H) : 0.f;
+    const float dn = live ? (P.depth[pix] - P.d_min) * P.d_scale - 1.f : 0.f;
+    for (int j0 = 0; j0 < MH; j0 += 8) {
+      float a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + q;
+        const float v = fmaf(__ldg(&W0[j * 3 + 0]), xn,
+                             fmaf(__ldg(&W0[j * 3 + 1]), yn,
+                                  fmaf(__ldg(&W0[j * 3 + 2]), dn, __ldg(&B0[j]))));
+        a[q] = fmaxf(v, 0.f);
+      }
+      *reinterpret_cast<uint4*>(Abuf + (size_t)(j0 / 8) * 2048 + m * 16) =
+          make_uint4(bf2(a[0], a[1]), bf2(a[2], a[3]), bf2(a[4], a[5]), bf2(a[6], a[7]));
+    }
+    tc::fence_async_smem();
+    tc::mbar_arrive(&s_act);
+    float* orow = P.out + (live ? pix : 0) * (long long)nout;
+    float sum = 0.f;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int ph = 0; ph < nphase; ++ph) {
+      // one thread per warp polls; its warp follows
+      if (lane == 0) mwait(&s_acc, (uint32_t)ph & 1u, P.status);
+      __syncwarp();
+      tc::fence_after_sync();
+      if (ph < 4) {
+        const float* bias = B0 + (size_t)(ph + 1) * MH;
+        for (int c16 = 0; c16 < MH / 16; ++c16) {
+          float v[16];
+          tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + __ldg(&bias[c16 * 16 + q]), 0.f);
+          unsigned char* dst = Abuf + (size_t)(c16 * 2) * 2048 + m * 16;
+          *reinterpret_cast<uint4*>(dst) =
+              make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
+          *reinterpret_cast<uint4*>(dst + 2048) = make_uint4(
+              bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+        }
+        tc::fence_async_smem();
+      } else {
+        const int q = mlp_pass(ph, npass), col0 = 2 * q * MNC;
+        const int nc16 = (min(2 * MNC, nout - col0) + 15) / 16;
+        const bool first = ph - 4 < npass, last = ph - 4 == npass - 1;
+        if (first) {  // accumulate the pixel's sum of clamped outputs
+          for (int c16 = 0; c16 < nc16; ++c16) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int col = col0 + c16 * 16 + k;
+              if (col < nout) sum += fmaxf(v[k] + __ldg(&B5[col]), 0.f);
+            }
+          }
+        }
+        if (last || !first) {  // store the pass's columns normalised
+          const float inv = sum > 0.f ? 1.f / sum : 0.f;
+          for (int c16 = 0; c16 < nc16; ++c16) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+              const int col = col0 + c16 * 16 + k;  // even; nout is even
+              if (live && col < nout)
+                *reinterpret_cast<float2*>(orow + col) =
+                    make_float2(fmaxf(v[k] + __ldg(&B5[col]), 0.f) * inv,
+                                fmaxf(v[k + 1] + __ldg(&B5[col + 1]), 0.f) * inv);
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&s_act);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 512);
+}
+
+// FP32 -> BF16 bits, round to nearest even (NaN kept quiet)
+inline uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+}  // namespace sd
+
+extern "C" sd_status sd_mlp_blob_bytes(int ks, size_t* bytes) {
+  using namespace sd;
+  if (!bytes || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS) return SD_ERR_ARG;
+  *bytes = mlp_bytes(ks);
+  return SD_OK;
+}
+
+extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const* biases, int ks,
+                                 void* blob, size_t blob_bytes) {
+  using namespace sd;
+  if (!weights || !biases || !blob || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS) return SD_ERR_ARG;
+  for (int l = 0; l < 6; ++l)
+    if (!weights[l] || !biases[l]) return SD_ERR_ARG;
+  if (blob_bytes < mlp_bytes(ks) || (reinterpret_cast<uintptr_t>(blob) & 255)) return SD_ERR_ARG;
+  const int nout = mlp_nout(ks), nblk = mlp_nblk(ks);
+  std::vector<unsigned char> host(mlp_bytes(ks), 0);
+  // chunk (layer, n block, k block): element (n, k) at (k/8)*4096 + n*16 + (k%8)*2
+  size_t c = 0;
+  for (int l = 1; l <= 5; ++l) {
+    const int rows = l < 5 ? MH : nout, nbl = l < 5 ? 2 : nblk;
+    const float* Wl = weights[l];
+    for (int nb = 0; nb < nbl; ++nb)
+      for (int kb = 0; kb < MH / MKC; ++kb, ++c) {
+        unsigned char* ch = host.data() + c * MCHUNK;
+        for (int nl = 0; nl < MNC; ++nl)
+          for (int kl = 0; kl < MKC; ++kl) {
+            const int n = nb * MNC + nl, k = kb * MKC + kl;
+            const uint16_t v = n < rows ? host_bf16(Wl[(size_t)n * MH + k]) : 0;
+            std::memcpy(ch + (kl / 8) * 4096 + nl * 16 + (kl % 8) * 2, &v, 2);
+          }
+      }
+  }
+  float* tail = reinterpret_cast<float*>(host.data() + c * MCHUNK);
+  std::memcpy(tail, weights[0], sizeof(float) * MH * 3);
+  for (int l = 0; l < 5; ++l) std::memcpy(tail + MH * 3 + l * MH, biases[l], sizeof(float) * MH);
+  std::memcpy(tail + MH * 3 + 5 * MH, biases[5], sizeof(float) * nout);
+  SD_CUDA_TRY(cudaMemcpy(blob, host.data(), host.size(), cudaMemcpyHostToDevice));
+  return SD_OK;
+}
+
+extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, int W,
+                                    float d_min_m, float d_max_m, float* out, int32_t* status,
+                                    void* stream) {
+  using namespace sd;
+  if (!blob || !depth_m || !out || !status || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS)
+    return SD_ERR_ARG;
+  if (H < 1 || W < 1 || !(d_max_m > d_min_m)) return SD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(blob) & 255)) return SD_ERR_ARG;
+  const long long npix = (long long)H * W;
+  if ((npix + MM - 1) / MM > 0x7fffffffll) return SD_ERR_UNSUPPORTED;
+  MlpParams P;
+  P.blob = reinterpret_cast<const unsigned char*>(blob);
+  P.depth = depth_m;
+  P.out = out;
+  P.status = reinterpret_cast<int*>(status);
+  P.ks = ks;
+  P.H = H;
+  P.W = W;
+  P.d_min = d_min_m;
+  P.d_scale = 2.f / (d_max_m - d_min_m);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SD_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+  const size_t smem = MA_BYTES + (size_t)MNB * MCHUNK;
+  SD_CUDA_TRY(cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  mlp_kernel<<<(unsigned)((npix + MM - 1) / MM), MTHREADS, smem, s>>>(P);
+  return launch_status();
+}
