@@ -15,8 +15,9 @@
 //   * one thread issues the MMAs (M = 128, N = 256, K = 16) into a 512-column
 //     FP32 accumulator in tensor memory and commits each buffer back to the
 //     copier;
-//   * four warps (one per tensor-memory lane quarter) compute layer 0 (3
-//     inputs, CUDA cores), and after every layer read the accumulator, add
+//   * eight warps (two per tensor-memory lane quarter, one per half of the
+//     columns) compute layer 0 (3 inputs, CUDA cores), and after every layer
+//     read the accumulator, add
 //     the bias, apply ReLU and write the next A operand in BF16.  The output
 //     layer runs in passes of 512 columns (the accumulator's width): the
 //     passes first accumulate each pixel's sum of the clamped outputs, the
@@ -43,7 +44,8 @@ constexpr int MNC = 256;            // outputs per weight chunk
 constexpr int MNB = 3;              // weight ring buffers
 constexpr uint32_t MCHUNK = MNC * MKC * 2;        // 32 KB
 constexpr uint32_t MA_BYTES = MM * MH * 2;        // 128 KB
-constexpr int MTHREADS = 192;       // warps 0-3 epilogue, 4 MMA issue, 5 copies
+constexpr int MEPI = 256;           // epilogue threads: warps 0-7
+constexpr int MTHREADS = MEPI + 64;  // + warp 8 MMA issue, warp 9 copies
 constexpr uint32_t MWAIT = 1u << 22;
 
 __host__ __device__ inline int mlp_nout(int ks) { return 2 * ks * ks; }
@@ -78,6 +80,10 @@ __device__ __forceinline__ int mlp_pass(int ph, int npass) {
   return j < npass ? j : j - npass;
 }
 
+__device__ __forceinline__ void named_sync_m(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       tc::mbar_init(&s_empty[b], 1);
     }
     tc::mbar_init(&s_acc, 1);
-    tc::mbar_init(&s_act, MM);
+    tc::mbar_init(&s_act, MEPI);
     tc::mbar_init(&s_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
 
-  if (warp == 5) {
+  if (warp == 9) {
     // ---- weight copier: chunks in consumption order through the ring ------
     if (lane == 0) {
       int last[MNB] = {-1, -1, -1};  // last copy issued into each buffer
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       for (int b = 0; b < MNB; ++b)
         if (last[b] >= 0) tc::mbar_wait(&s_full[b], (uint32_t)(last[b] / MNB) & 1u, MWAIT);
     }
-  } else if (warp == 4) {
+  } else if (warp == 8) {
     // ---- MMA issue --------------------------------------------------------
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(MM, MNC);
@@ -181,15 +187,17 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       tc::mbar_wait(&s_done, 0, MWAIT);
     }
   } else {
-    // ---- warps 0-3: layer 0, then every accumulator -------------------------
-    const int m = tid;                       // tensor-memory lane = A row
+    // ---- warps 0-7: layer 0, then every accumulator -------------------------
+    __shared__ float s_sum[2][MM];
+    const int m = 32 * (warp & 3) + lane;    // tensor-memory lane = A row
+    const int half = warp >> 2;              // columns [256 half, 256 half + 256)
     const long long pix = (long long)blockIdx.x * MM + m;
     const bool live = pix < npix;
     const int py = live ? (int)(pix / P.W) : 0, px = live ? (int)(pix - (long long)py * P.W) : 0;
     const float xn = live ? ((float)px - 0.5f * (float)(P.W - 1)) / (0.5f * (float)P.W) : 0.f;
     const float yn = live ? ((float)py - 0.5f * (float)(P.H - 1)) / (0.5f * (float)P.H) : 0.f;
     const float dn = live ? (P.depth[pix] - P.d_min) * P.d_scale - 1.f : 0.f;
-    for (int j0 = 0; j0 < MH; j0 += 8) {
+    for (int j0 = half * MNC; j0 < half * MNC + MNC; j0 += 8) {
       float a[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -205,21 +213,23 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
     tc::fence_async_smem();
     tc::mbar_arrive(&s_act);
     float* orow = P.out + (live ? pix : 0) * (long long)nout;
-    float sum = 0.f;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    float part = 0.f, sum = 0.f;
+    const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * MNC);
     for (int ph = 0; ph < nphase; ++ph) {
       // one thread per warp polls; its warp follows
       if (lane == 0) mwait(&s_acc, (uint32_t)ph & 1u, P.status);
       __syncwarp();
       tc::fence_after_sync();
       if (ph < 4) {
-        const float* bias = B0 + (size_t)(ph + 1) * MH;
-        for (int c16 = 0; c16 < MH / 16; ++c16) {
-          float v[16];
-          tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+        const float* bias = B0 + (size_t)(ph + 1) * MH + half * MNC;
+        for (int c16 = 0; c16 < MNC / 16; ++c16) {
+          float bb[16], v[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + __ldg(&bias[c16 * 16 + q]), 0.f);
-          unsigned char* dst = Abuf + (size_t)(c16 * 2) * 2048 + m * 16;
+          for (int q = 0; q < 16; ++q) bb[q] = __ldg(&bias[c16 * 16 + q]);
+          tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bb[q], 0.f);
+          unsigned char* dst = Abuf + (size_t)((half * MNC) / 8 + c16 * 2) * 2048 + m * 16;
           *reinterpret_cast<uint4*>(dst) =
               make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
           *reinterpret_cast<uint4*>(dst + 2048) = make_uint4(
@@ -227,25 +237,30 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
         }
         tc::fence_async_smem();
       } else {
-        const int q = mlp_pass(ph, npass), col0 = 2 * q * MNC;
-        const int nc16 = (min(2 * MNC, nout - col0) + 15) / 16;
+        const int q = mlp_pass(ph, npass), col0 = 2 * q * MNC + half * MNC;
+        const int nc16 = max(0, (min(MNC, nout - col0) + 15) / 16);
         const bool first = ph - 4 < npass, last = ph - 4 == npass - 1;
-        if (first) {  // accumulate the pixel's sum of clamped outputs
+        if (first) {  // accumulate this half's sum of clamped outputs
           for (int c16 = 0; c16 < nc16; ++c16) {
             float v[16];
-            tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+            tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
               const int col = col0 + c16 * 16 + k;
-              if (col < nout) sum += fmaxf(v[k] + __ldg(&B5[col]), 0.f);
+              if (col < nout) part += fmaxf(v[k] + __ldg(&B5[col]), 0.f);
             }
+          }
+          if (last) {  // the pixel's total: the two halves added in order
+            s_sum[half][m] = part;
+            named_sync_m(1, MEPI);
+            sum = s_sum[0][m] + s_sum[1][m];
           }
         }
         if (last || !first) {  // store the pass's columns normalised
           const float inv = sum > 0.f ? 1.f / sum : 0.f;
           for (int c16 = 0; c16 < nc16; ++c16) {
             float v[16];
-            tc::tmem_ld16(lane_base + (uint32_t)(c16 * 16), v);
+            tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
               const int col = col0 + c16 * 16 + k;  // even; nout is even
