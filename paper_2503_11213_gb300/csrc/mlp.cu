@@ -39,19 +39,24 @@ namespace sd {
 
 constexpr int MH = SD_MLP_HIDDEN;   // hidden width
 constexpr int MM = 128;             // pixels per CTA
-constexpr int MKC = 64;             // inputs per weight chunk
+constexpr int MKC = 32;             // inputs per weight chunk
 constexpr int MNC = 256;            // outputs per weight chunk
-constexpr int MNB = 3;              // weight ring buffers
-constexpr uint32_t MCHUNK = MNC * MKC * 2;        // 32 KB
+constexpr int MNB = 5;              // weight ring buffers
+constexpr uint32_t MCHUNK = MNC * MKC * 2;        // 16 KB
+constexpr int MKPB = MH / MKC;      // chunks per 256-row block of a layer
 constexpr uint32_t MA_BYTES = MM * MH * 2;        // 128 KB
 constexpr int MEPI = 256;           // epilogue threads: warps 0-7
 constexpr int MTHREADS = MEPI + 64;  // + warp 8 MMA issue, warp 9 copies
+// per epilogue warp: 32 pixels x 16 outputs staged for coalesced stores
+// (rows of 18 floats: conflict-free 8-byte accesses)
+constexpr int MSROW = 18;
+constexpr uint32_t MSTAGE = (MEPI / 32) * 32 * MSROW * 4;
 constexpr uint32_t MWAIT = 1u << 22;
 
 __host__ __device__ inline int mlp_nout(int ks) { return 2 * ks * ks; }
 __host__ __device__ inline int mlp_nblk(int ks) { return (mlp_nout(ks) + MNC - 1) / MNC; }
 // chunks: 4 hidden layers of (512/256) x (512/64), the output layer nblk x 8
-__host__ __device__ inline int mlp_chunks(int ks) { return 4 * 2 * (MH / MKC) + mlp_nblk(ks) * (MH / MKC); }
+__host__ __device__ inline int mlp_chunks(int ks) { return 4 * 2 * MKPB + mlp_nblk(ks) * MKPB; }
 // FP32 tail: W0 [512][3], b0..b4 [512] each, b5 [nblk * 256]
 __host__ __device__ inline size_t mlp_tail_floats(int ks) {
   return (size_t)MH * 3 + 5 * (size_t)MH + (size_t)mlp_nblk(ks) * MNC;
@@ -93,6 +98,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* Abuf = smem;             // element (m, k) at (k/8)*2048 + m*16 + (k%8)*2
   unsigned char* Wbuf = smem + MA_BYTES;  // MNB chunks; (n, k) at (k/8)*4096 + n*16 + (k%8)*2
+  float* stage = reinterpret_cast<float*>(Wbuf + (size_t)MNB * MCHUNK);  // MSTAGE bytes
   __shared__ __align__(8) uint64_t s_full[MNB], s_empty[MNB], s_acc, s_act, s_done;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -124,21 +130,22 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
   if (warp == 9) {
     // ---- weight copier: chunks in consumption order through the ring ------
     if (lane == 0) {
-      int last[MNB] = {-1, -1, -1};  // last copy issued into each buffer
+      int last[MNB];  // last copy issued into each buffer
+      for (int b = 0; b < MNB; ++b) last[b] = -1;
       int c = 0;                     // copies issued
       bool ok = true;
       for (int ph = 0; ph < nphase && ok; ++ph) {
         const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
         const int nb0 = ph < 4 ? 0 : 2 * q, nb1 = ph < 4 ? 2 : min(nb0 + 2, nblk);
         for (int nb = nb0; nb < nb1 && ok; ++nb)
-          for (int kb = 0; kb < MH / MKC; ++kb, ++c) {
+          for (int kb = 0; kb < MKPB; ++kb, ++c) {
             const int b = c % MNB;
             if (c >= MNB && !mwait(&s_empty[b], (uint32_t)(c / MNB - 1) & 1u, P.status)) {
               ok = false;
               break;
             }
             // blob chunk: hidden layer ph + 1, or the output layer's block nb
-            const int chunk = (ph < 4 ? ph * 16 + nb * 8 : 64 + nb * 8) + kb;
+            const int chunk = (ph < 4 ? (ph * 2 + nb) * MKPB : (8 + nb) * MKPB) + kb;
             tc::mbar_arrive_expect_tx(&s_full[b], MCHUNK);
             tc::bulk_g2s(Wbuf + (size_t)b * MCHUNK, P.blob + (size_t)chunk * MCHUNK, MCHUNK,
                          &s_full[b]);
@@ -165,14 +172,15 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
         const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
         const int nb0 = ph < 4 ? 0 : 2 * q, nb1 = ph < 4 ? 2 : min(nb0 + 2, nblk);
         for (int nb = nb0; nb < nb1 && ok; ++nb)
-          for (int kb = 0; kb < MH / MKC && ok; ++kb, ++c) {
+          for (int kb = 0; kb < MKPB && ok; ++kb, ++c) {
             const int b = c % MNB;
             ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status);
             if (!ok) break;
             tc::fence_after_sync();
 #pragma unroll
             for (int s = 0; s < MKC / 16; ++s) {
-              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(kb * 8 + s * 2) * 2048u, 2048, 128);
+              const uint64_t ad =
+                  tc::smem_desc(a0 + (uint32_t)(kb * (MKC / 8) + s * 2) * 2048u, 2048, 128);
               const uint64_t bd =
                   tc::smem_desc(w0 + (uint32_t)b * MCHUNK + (uint32_t)s * 2 * 4096u, 4096, 128);
               tc::mma_bf16(tmem + (uint32_t)((nb - nb0) * MNC), ad, bd, idesc, kb > 0 || s > 0);
@@ -188,7 +196,8 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
     }
   } else {
     // ---- warps 0-7: layer 0, then every accumulator -------------------------
-    __shared__ float s_sum[2][MM];
+    // the two halves' sums, in the staging area (free until the first store)
+    float* s_sum = stage;  // [2][MM]
     const int m = 32 * (warp & 3) + lane;    // tensor-memory lane = A row
     const int half = warp >> 2;              // columns [256 half, 256 half + 256)
     const long long pix = (long long)blockIdx.x * MM + m;
@@ -212,7 +221,6 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
     }
     tc::fence_async_smem();
     tc::mbar_arrive(&s_act);
-    float* orow = P.out + (live ? pix : 0) * (long long)nout;
     float part = 0.f, sum = 0.f;
     const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * MNC);
     for (int ph = 0; ph < nphase; ++ph) {
@@ -251,24 +259,39 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
             }
           }
           if (last) {  // the pixel's total: the two halves added in order
-            s_sum[half][m] = part;
+            s_sum[half * MM + m] = part;
             named_sync_m(1, MEPI);
-            sum = s_sum[0][m] + s_sum[1][m];
+            sum = s_sum[m] + s_sum[MM + m];
           }
         }
         if (last || !first) {  // store the pass's columns normalised
           const float inv = sum > 0.f ? 1.f / sum : 0.f;
+          float* st = stage + (size_t)warp * 32 * MSROW;  // this warp's 32 pixels
+          const long long wpix0 = (long long)blockIdx.x * MM + 32 * (warp & 3);
+          if (last) named_sync_m(1, MEPI);  // every half has read s_sum
           for (int c16 = 0; c16 < nc16; ++c16) {
             float v[16];
             tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
-              const int col = col0 + c16 * 16 + k;  // even; nout is even
-              if (live && col < nout)
-                *reinterpret_cast<float2*>(orow + col) =
-                    make_float2(fmaxf(v[k] + __ldg(&B5[col]), 0.f) * inv,
-                                fmaxf(v[k + 1] + __ldg(&B5[col + 1]), 0.f) * inv);
+              const int col = col0 + c16 * 16 + k;
+              const float b0 = col < nout ? __ldg(&B5[col]) : 0.f;
+              const float b1 = col < nout ? __ldg(&B5[col + 1]) : 0.f;
+              *reinterpret_cast<float2*>(st + lane * MSROW + k) =
+                  make_float2(fmaxf(v[k] + b0, 0.f) * inv, fmaxf(v[k + 1] + b1, 0.f) * inv);
             }
+            __syncwarp();
+            // 4 pixels x 16 outputs per store: 8 lanes write one pixel's 64 bytes
+            const int colc = col0 + c16 * 16 + 2 * (lane & 7);  // even; nout is even
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const int pl = 4 * r + (lane >> 3);
+              const long long gp = wpix0 + pl;
+              if (gp < npix && colc < nout)
+                *reinterpret_cast<float2*>(P.out + gp * (long long)nout + colc) =
+                    *reinterpret_cast<const float2*>(st + pl * MSROW + 2 * (lane & 7));
+            }
+            __syncwarp();
           }
         }
       }
@@ -314,7 +337,7 @@ extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const
     const int rows = l < 5 ? MH : nout, nbl = l < 5 ? 2 : nblk;
     const float* Wl = weights[l];
     for (int nb = 0; nb < nbl; ++nb)
-      for (int kb = 0; kb < MH / MKC; ++kb, ++c) {
+      for (int kb = 0; kb < MKPB; ++kb, ++c) {
         unsigned char* ch = host.data() + c * MCHUNK;
         for (int nl = 0; nl < MNC; ++nl)
           for (int kl = 0; kl < MKC; ++kl) {
@@ -354,7 +377,7 @@ extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth
   P.d_scale = 2.f / (d_max_m - d_min_m);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SD_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
-  const size_t smem = MA_BYTES + (size_t)MNB * MCHUNK;
+  const size_t smem = MA_BYTES + (size_t)MNB * MCHUNK + MSTAGE;
   SD_CUDA_TRY(cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   mlp_kernel<<<(unsigned)((npix + MM - 1) / MM), MTHREADS, smem, s>>>(P);
