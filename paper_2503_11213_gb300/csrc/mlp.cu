@@ -99,7 +99,12 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
   unsigned char* Abuf = smem;             // element (m, k) at (k/8)*2048 + m*16 + (k%8)*2
   unsigned char* Wbuf = smem + MA_BYTES;  // MNB chunks; (n, k) at (k/8)*4096 + n*16 + (k%8)*2
   float* stage = reinterpret_cast<float*>(Wbuf + (size_t)MNB * MCHUNK);  // MSTAGE bytes
-  __shared__ __align__(8) uint64_t s_full[MNB], s_empty[MNB], s_acc, s_act, s_done;
+  // s_acc[h]: half h of the accumulator (n block 2q + h of the phase) is
+  // complete; s_k0: the second half's MMAs over inputs 0..255 are done (the
+  // first half's epilogue may then overwrite those inputs); s_epi[h]: the
+  // epilogue of half h has read its accumulator and, for a hidden layer,
+  // written inputs 256 h .. 256 h + 255 of the next layer
+  __shared__ __align__(8) uint64_t s_full[MNB], s_empty[MNB], s_acc[2], s_k0, s_epi[2], s_done;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ks = P.ks, nout = mlp_nout(ks), nblk = mlp_nblk(ks), nchunk = mlp_chunks(ks);
@@ -117,8 +122,11 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       tc::mbar_init(&s_full[b], 1);
       tc::mbar_init(&s_empty[b], 1);
     }
-    tc::mbar_init(&s_acc, 1);
-    tc::mbar_init(&s_act, MEPI);
+    for (int h = 0; h < 2; ++h) {
+      tc::mbar_init(&s_acc[h], 1);
+      tc::mbar_init(&s_epi[h], MEPI / 2);
+    }
+    tc::mbar_init(&s_k0, 1);
     tc::mbar_init(&s_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -164,30 +172,41 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       const uint32_t a0 = tc::smem_u32(Abuf), w0 = tc::smem_u32(Wbuf);
       int c = 0;
       bool ok = true;
-      for (int ph = 0; ph < nphase && ok; ++ph) {
-        // the epilogue has written this phase's A operand (and read the
-        // previous phase's accumulator)
-        ok = mwait(&s_act, (uint32_t)ph & 1u, P.status);
-        tc::fence_after_sync();
-        const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
-        const int nb0 = ph < 4 ? 0 : 2 * q, nb1 = ph < 4 ? 2 : min(nb0 + 2, nblk);
-        for (int nb = nb0; nb < nb1 && ok; ++nb)
-          for (int kb = 0; kb < MKPB && ok; ++kb, ++c) {
-            const int b = c % MNB;
-            ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status);
-            if (!ok) break;
-            tc::fence_after_sync();
+      // per phase: half 0 over inputs 0..255, (wait for inputs 256..511)
+      // half 0 over 256..511, half 1 over 0..255, half 1 over 256..511, so
+      // that each half's epilogue runs during the other half's MMAs
+      auto run = [&](int ph, int nb, int h, int kb0, int kb1) {
+        for (int kb = kb0; kb < kb1 && ok; ++kb, ++c) {
+          const int b = c % MNB;
+          ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status);
+          if (!ok) break;
+          tc::fence_after_sync();
 #pragma unroll
-            for (int s = 0; s < MKC / 16; ++s) {
-              const uint64_t ad =
-                  tc::smem_desc(a0 + (uint32_t)(kb * (MKC / 8) + s * 2) * 2048u, 2048, 128);
-              const uint64_t bd =
-                  tc::smem_desc(w0 + (uint32_t)b * MCHUNK + (uint32_t)s * 2 * 4096u, 4096, 128);
-              tc::mma_bf16(tmem + (uint32_t)((nb - nb0) * MNC), ad, bd, idesc, kb > 0 || s > 0);
-            }
-            tc::commit(&s_empty[b]);
+          for (int s = 0; s < MKC / 16; ++s) {
+            const uint64_t ad =
+                tc::smem_desc(a0 + (uint32_t)(kb * (MKC / 8) + s * 2) * 2048u, 2048, 128);
+            const uint64_t bd =
+                tc::smem_desc(w0 + (uint32_t)b * MCHUNK + (uint32_t)s * 2 * 4096u, 4096, 128);
+            tc::mma_bf16(tmem + (uint32_t)(h * MNC), ad, bd, idesc, kb > 0 || s > 0);
           }
-        tc::commit(&s_acc);
+          tc::commit(&s_empty[b]);
+        }
+      };
+      for (int ph = 0; ph < nphase && ok; ++ph) {
+        const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
+        const int nb0 = ph < 4 ? 0 : 2 * q;
+        const bool two = ph < 4 || nb0 + 1 < nblk;
+        ok = ok && mwait(&s_epi[0], (uint32_t)ph & 1u, P.status);
+        tc::fence_after_sync();
+        run(ph, nb0, 0, 0, MKPB / 2);
+        ok = ok && mwait(&s_epi[1], (uint32_t)ph & 1u, P.status);
+        tc::fence_after_sync();
+        run(ph, nb0, 0, MKPB / 2, MKPB);
+        tc::commit(&s_acc[0]);
+        if (two) run(ph, nb0 + 1, 1, 0, MKPB / 2);
+        tc::commit(&s_k0);
+        if (two) run(ph, nb0 + 1, 1, MKPB / 2, MKPB);
+        tc::commit(&s_acc[1]);
       }
       // every MMA issued has completed before the tensor memory is freed
       // (also after an error)
@@ -220,12 +239,16 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
           make_uint4(bf2(a[0], a[1]), bf2(a[2], a[3]), bf2(a[4], a[5]), bf2(a[6], a[7]));
     }
     tc::fence_async_smem();
-    tc::mbar_arrive(&s_act);
+    tc::mbar_arrive(&s_epi[half]);
     float part = 0.f, sum = 0.f;
     const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * MNC);
     for (int ph = 0; ph < nphase; ++ph) {
-      // one thread per warp polls; its warp follows
-      if (lane == 0) mwait(&s_acc, (uint32_t)ph & 1u, P.status);
+      // one thread per warp polls; its warp follows.  Half 0 of a hidden
+      // layer also waits until no MMA reads inputs 0..255 any more.
+      if (lane == 0) {
+        mwait(&s_acc[half], (uint32_t)ph & 1u, P.status);
+        if (half == 0 && ph < 4) mwait(&s_k0, (uint32_t)ph & 1u, P.status);
+      }
       __syncwarp();
       tc::fence_after_sync();
       if (ph < 4) {
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
         }
       }
       tc::fence_before_sync();
-      tc::mbar_arrive(&s_act);
+      tc::mbar_arrive(&s_epi[half]);
     }
   }
   tc::fence_before_sync();
