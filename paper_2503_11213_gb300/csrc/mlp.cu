@@ -57,9 +57,10 @@ __host__ __device__ inline int mlp_nout(int ks) { return 2 * ks * ks; }
 __host__ __device__ inline int mlp_nblk(int ks) { return (mlp_nout(ks) + MNC - 1) / MNC; }
 // chunks: 4 hidden layers of (512/256) x (512/64), the output layer nblk x 8
 __host__ __device__ inline int mlp_chunks(int ks) { return 4 * 2 * MKPB + mlp_nblk(ks) * MKPB; }
-// FP32 tail: W0 [512][3], b0..b4 [512] each, b5 [nblk * 256]
+// FP32 tail: layer 0 as [512] x {w_x, w_y, w_d, b0} (one 16-byte load per
+// neuron), b1..b4 [512] each, b5 [nblk * 256]
 __host__ __device__ inline size_t mlp_tail_floats(int ks) {
-  return (size_t)MH * 3 + 5 * (size_t)MH + (size_t)mlp_nblk(ks) * MNC;
+  return (size_t)MH * 4 + 4 * (size_t)MH + (size_t)mlp_nblk(ks) * MNC;
 }
 inline size_t mlp_bytes(int ks) { return (size_t)mlp_chunks(ks) * MCHUNK + 4 * mlp_tail_floats(ks); }
 
@@ -112,9 +113,9 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
   const int nphase = 4 + 2 * npass - 1; // accumulator phases (earlier passes twice)
   const long long npix = (long long)P.H * P.W;
   const float* tail = reinterpret_cast<const float*>(P.blob + (size_t)nchunk * MCHUNK);
-  const float* W0 = tail;                      // [512][3]
-  const float* B0 = W0 + MH * 3;               // b0, b1, ..., b4 (512 each)
-  const float* B5 = B0 + 5 * MH;               // [nblk * 256]
+  const float4* WB0 = reinterpret_cast<const float4*>(tail);  // [512] {w, b0}
+  const float* B1 = tail + MH * 4;             // b1, ..., b4 (512 each)
+  const float* B5 = B1 + 4 * MH;               // [nblk * 256]
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
   if (tid == 0) {
@@ -230,9 +231,8 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int j = j0 + q;
-        const float v = fmaf(__ldg(&W0[j * 3 + 0]), xn,
-                             fmaf(__ldg(&W0[j * 3 + 1]), yn,
-                                  fmaf(__ldg(&W0[j * 3 + 2]), dn, __ldg(&B0[j]))));
+        const float4 wb = __ldg(&WB0[j]);
+        const float v = fmaf(wb.x, xn, fmaf(wb.y, yn, fmaf(wb.z, dn, wb.w)));
         a[q] = fmaxf(v, 0.f);
       }
       *reinterpret_cast<uint4*>(Abuf + (size_t)(j0 / 8) * 2048 + m * 16) =
@@ -252,11 +252,17 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       __syncwarp();
       tc::fence_after_sync();
       if (ph < 4) {
-        const float* bias = B0 + (size_t)(ph + 1) * MH + half * MNC;
+        const float4* bias = reinterpret_cast<const float4*>(B1 + (size_t)ph * MH + half * MNC);
         for (int c16 = 0; c16 < MNC / 16; ++c16) {
           float bb[16], v[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) bb[q] = __ldg(&bias[c16 * 16 + q]);
+          for (int q = 0; q < 4; ++q) {
+            const float4 t = __ldg(&bias[c16 * 4 + q]);
+            bb[4 * q] = t.x;
+            bb[4 * q + 1] = t.y;
+            bb[4 * q + 2] = t.z;
+            bb[4 * q + 3] = t.w;
+          }
           tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
 #pragma unroll
           for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bb[q], 0.f);
@@ -371,9 +377,12 @@ extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const
       }
   }
   float* tail = reinterpret_cast<float*>(host.data() + c * MCHUNK);
-  std::memcpy(tail, weights[0], sizeof(float) * MH * 3);
-  for (int l = 0; l < 5; ++l) std::memcpy(tail + MH * 3 + l * MH, biases[l], sizeof(float) * MH);
-  std::memcpy(tail + MH * 3 + 5 * MH, biases[5], sizeof(float) * nout);
+  for (int j = 0; j < MH; ++j) {
+    for (int i = 0; i < 3; ++i) tail[4 * j + i] = weights[0][3 * j + i];
+    tail[4 * j + 3] = biases[0][j];
+  }
+  for (int l = 1; l < 5; ++l) std::memcpy(tail + MH * 4 + (l - 1) * MH, biases[l], sizeof(float) * MH);
+  std::memcpy(tail + MH * 8, biases[5], sizeof(float) * nout);
   SD_CUDA_TRY(cudaMemcpy(blob, host.data(), host.size(), cudaMemcpyHostToDevice));
   return SD_OK;
 }
