@@ -91,8 +91,8 @@ __device__ __forceinline__ void named_sync_m(int id, int n) {
 }
 
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
@@ -253,39 +253,45 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       tc::fence_after_sync();
       if (ph < 4) {
         const float4* bias = reinterpret_cast<const float4*>(B1 + (size_t)ph * MH + half * MNC);
-        for (int c16 = 0; c16 < MNC / 16; ++c16) {
-          float bb[16], v[16];
+        for (int c32 = 0; c32 < MNC / 32; ++c32) {
+          float bb[32], v[32];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 t = __ldg(&bias[c16 * 4 + q]);
+          for (int q = 0; q < 8; ++q) {
+            const float4 t = __ldg(&bias[c32 * 8 + q]);
             bb[4 * q] = t.x;
             bb[4 * q + 1] = t.y;
             bb[4 * q + 2] = t.z;
             bb[4 * q + 3] = t.w;
           }
-          tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+          tc::tmem_ld32(tbase + (uint32_t)(c32 * 32), v);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bb[q], 0.f);
-          unsigned char* dst = Abuf + (size_t)((half * MNC) / 8 + c16 * 2) * 2048 + m * 16;
-          *reinterpret_cast<uint4*>(dst) =
-              make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
-          *reinterpret_cast<uint4*>(dst + 2048) = make_uint4(
-              bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+          for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + bb[q], 0.f);
+          unsigned char* dst = Abuf + (size_t)((half * MNC) / 8 + c32 * 4) * 2048 + m * 16;
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            *reinterpret_cast<uint4*>(dst + g * 2048) =
+                make_uint4(bf2(v[8 * g], v[8 * g + 1]), bf2(v[8 * g + 2], v[8 * g + 3]),
+                           bf2(v[8 * g + 4], v[8 * g + 5]), bf2(v[8 * g + 6], v[8 * g + 7]));
         }
         tc::fence_async_smem();
       } else {
         const int q = mlp_pass(ph, npass), col0 = 2 * q * MNC + half * MNC;
-        const int nc16 = max(0, (min(MNC, nout - col0) + 15) / 16);
+        // columns of this half that exist (the padded rows of the output
+        // layer and their biases are 0, so their outputs are exactly 0)
+        const int nc32 = col0 < nout ? MNC / 32 : 0;
+        const float4* bias = reinterpret_cast<const float4*>(B5 + col0);
         const bool first = ph - 4 < npass, last = ph - 4 == npass - 1;
         if (first) {  // accumulate this half's sum of clamped outputs
-          for (int c16 = 0; c16 < nc16; ++c16) {
-            float v[16];
-            tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+          for (int c32 = 0; c32 < nc32; ++c32) {
+            float v[32];
+            float4 bq[8];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int col = col0 + c16 * 16 + k;
-              if (col < nout) part += fmaxf(v[k] + __ldg(&B5[col]), 0.f);
-            }
+            for (int g = 0; g < 8; ++g) bq[g] = __ldg(&bias[c32 * 8 + g]);
+            tc::tmem_ld32(tbase + (uint32_t)(c32 * 32), v);
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+              part += (fmaxf(v[4 * g] + bq[g].x, 0.f) + fmaxf(v[4 * g + 1] + bq[g].y, 0.f)) +
+                      (fmaxf(v[4 * g + 2] + bq[g].z, 0.f) + fmaxf(v[4 * g + 3] + bq[g].w, 0.f));
           }
           if (last) {  // the pixel's total: the two halves added in order
             s_sum[half * MM + m] = part;
@@ -298,29 +304,36 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
           float* st = stage + (size_t)warp * 32 * MSROW;  // this warp's 32 pixels
           const long long wpix0 = (long long)blockIdx.x * MM + 32 * (warp & 3);
           if (last) named_sync_m(1, MEPI);  // every half has read s_sum
-          for (int c16 = 0; c16 < nc16; ++c16) {
-            float v[16];
-            tc::tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+          for (int c32 = 0; c32 < nc32; ++c32) {
+            float v[32];
+            float4 bq[8];
 #pragma unroll
-            for (int k = 0; k < 16; k += 2) {
-              const int col = col0 + c16 * 16 + k;
-              const float b0 = col < nout ? __ldg(&B5[col]) : 0.f;
-              const float b1 = col < nout ? __ldg(&B5[col + 1]) : 0.f;
-              *reinterpret_cast<float2*>(st + lane * MSROW + k) =
-                  make_float2(fmaxf(v[k] + b0, 0.f) * inv, fmaxf(v[k + 1] + b1, 0.f) * inv);
-            }
-            __syncwarp();
-            // 4 pixels x 16 outputs per store: 8 lanes write one pixel's 64 bytes
-            const int colc = col0 + c16 * 16 + 2 * (lane & 7);  // even; nout is even
+            for (int g = 0; g < 8; ++g) bq[g] = __ldg(&bias[c32 * 8 + g]);
+            tc::tmem_ld32(tbase + (uint32_t)(c32 * 32), v);
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-              const int pl = 4 * r + (lane >> 3);
-              const long long gp = wpix0 + pl;
-              if (gp < npix && colc < nout)
-                *reinterpret_cast<float2*>(P.out + gp * (long long)nout + colc) =
-                    *reinterpret_cast<const float2*>(st + pl * MSROW + 2 * (lane & 7));
+            for (int h16 = 0; h16 < 2; ++h16) {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const float4 bb = bq[h16 * 4 + g];
+                const float* vv = v + h16 * 16 + 4 * g;
+                *reinterpret_cast<float2*>(st + lane * MSROW + 4 * g) =
+                    make_float2(fmaxf(vv[0] + bb.x, 0.f) * inv, fmaxf(vv[1] + bb.y, 0.f) * inv);
+                *reinterpret_cast<float2*>(st + lane * MSROW + 4 * g + 2) =
+                    make_float2(fmaxf(vv[2] + bb.z, 0.f) * inv, fmaxf(vv[3] + bb.w, 0.f) * inv);
+              }
+              __syncwarp();
+              // 4 pixels x 16 outputs per store: 8 lanes write one pixel's 64 bytes
+              const int colc = col0 + c32 * 32 + h16 * 16 + 2 * (lane & 7);  // even
+#pragma unroll
+              for (int r = 0; r < 8; ++r) {
+                const int pl = 4 * r + (lane >> 3);
+                const long long gp = wpix0 + pl;
+                if (gp < npix && colc < nout)
+                  *reinterpret_cast<float2*>(P.out + gp * (long long)nout + colc) =
+                      *reinterpret_cast<const float2*>(st + pl * MSROW + 2 * (lane & 7));
+              }
+              __syncwarp();
             }
-            __syncwarp();
           }
         }
       }
