@@ -483,15 +483,16 @@ sd_status sd_mlp_pack(const float* const* weights, const float* const* biases, i
  * of depth_m (H, W) [metres, FP32, device] has p = (x_n, y_n, d_n) with
  * x_n = (x - (W-1)/2) / (W/2), y_n = (y - (H-1)/2) / (H/2) (the sensor
  * position normalised to [-1, 1]) and d_n = 2 (d - d_min) / (d_max - d_min)
- * - 1; out (H, W, 2, ks, ks) FP32 device, the layout sd_dp_render_map takes.
+ * - 1; out (H, W, 2, ks, ks) device in out_dtype (SD_F32 or SD_BF16), the
+ * layout and dtypes sd_dp_render_map takes.
  * Tensor cores (tcgen05): BF16 operands, FP32 accumulation, hidden
  * activations rounded to BF16 between layers.  *status (device int32) is set
  * to 0 by the call and to 1 by the kernel if one of its bounded completion
  * waits gave up (the map is then invalid).  H * W >= 1, d_max > d_min.
  */
 sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, int W,
-                         float d_min_m, float d_max_m, float* out, int32_t* status,
-                         void* stream);
+                         float d_min_m, float d_max_m, void* out, int out_dtype,
+                         int32_t* status, void* stream);
 
 /*
  * Test aid (the paper has no counterpart): runs the tensor-core (tcgen05)

@@ -141,7 +141,7 @@ def lib():
     fl = ctypes.c_float
     L.sd_mlp_blob_bytes.argtypes = [i32, P(ctypes.c_size_t)]
     L.sd_mlp_pack.argtypes = [P(P(fl)), P(P(fl)), i32, vp, ctypes.c_size_t]
-    L.sd_mlp_psf_map.argtypes = [vp, i32, vp, i32, i32, fl, fl, vp, vp, vp]
+    L.sd_mlp_psf_map.argtypes = [vp, i32, vp, i32, i32, fl, fl, vp, i32, vp, vp]
     L.sd_status_string.argtypes = [i32]
     L.sd_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:

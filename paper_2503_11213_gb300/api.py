@@ -418,20 +418,22 @@ class PsfMLP:
                 "sd_mlp_pack")
 
 
-def mlp_psf_map(net: PsfMLP, depth_m, d_min_m, d_max_m, out=None, status=None):
-    """Per-pixel DP PSF map (H, W, 2, ks, ks) FP32 predicted by the network
-    for a depth map (H, W) in metres (device, FP32); returns (map, status)
-    with status a device int32 (1 if a bounded wait of the kernel gave up)."""
+def mlp_psf_map(net: PsfMLP, depth_m, d_min_m, d_max_m, out=None, status=None,
+                dtype=torch.float32):
+    """Per-pixel DP PSF map (H, W, 2, ks, ks) in dtype (float32 or bfloat16)
+    predicted by the network for a depth map (H, W) in metres (device,
+    FP32); returns (map, status) with status a device int32 (1 if a bounded
+    wait of the kernel gave up)."""
     H, W = depth_m.shape
     ks = net.ks
     if out is None:
-        out = torch.empty((H, W, 2, ks, ks), dtype=torch.float32, device=depth_m.device)
+        out = torch.empty((H, W, 2, ks, ks), dtype=dtype, device=depth_m.device)
     if status is None:
         status = torch.empty(1, dtype=torch.int32, device=depth_m.device)
     _need_cuda(depth_m, out, status, net.blob)
     if depth_m.dtype != torch.float32:
         raise ValueError("depth must be float32")
     L.check(L.lib().sd_mlp_psf_map(_ptr(net.blob), ks, _ptr(depth_m), H, W, float(d_min_m),
-                                   float(d_max_m), _ptr(out), _ptr(status), _stream()),
-            "sd_mlp_psf_map")
+                                   float(d_max_m), _ptr(out), _DT[out.dtype], _ptr(status),
+                                   _stream()), "sd_mlp_psf_map")
     return out, status

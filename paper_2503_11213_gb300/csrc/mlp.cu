@@ -67,7 +67,8 @@ inline size_t mlp_bytes(int ks) { return (size_t)mlp_chunks(ks) * MCHUNK + 4 * m
 struct MlpParams {
   const unsigned char* blob;
   const float* depth;
-  float* out;
+  void* out;       // FP32 or BF16 map
+  int out_bf16;
   int* status;
   int ks, H, W;
   float d_min, d_scale;  // d_n = (d - d_min) * d_scale - 1
@@ -328,9 +329,14 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
               for (int r = 0; r < 8; ++r) {
                 const int pl = 4 * r + (lane >> 3);
                 const long long gp = wpix0 + pl;
-                if (gp < npix && colc < nout)
-                  *reinterpret_cast<float2*>(P.out + gp * (long long)nout + colc) =
-                      *reinterpret_cast<const float2*>(st + pl * MSROW + 2 * (lane & 7));
+                if (gp < npix && colc < nout) {
+                  const float2 o = *reinterpret_cast<const float2*>(st + pl * MSROW + 2 * (lane & 7));
+                  const long long e = gp * (long long)nout + colc;
+                  if (P.out_bf16)
+                    reinterpret_cast<uint32_t*>(P.out)[e >> 1] = bf2(o.x, o.y);
+                  else
+                    *reinterpret_cast<float2*>(reinterpret_cast<float*>(P.out) + e) = o;
+                }
               }
               __syncwarp();
             }
@@ -401,12 +407,13 @@ extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const
 }
 
 extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, int W,
-                                    float d_min_m, float d_max_m, float* out, int32_t* status,
-                                    void* stream) {
+                                    float d_min_m, float d_max_m, void* out, int out_dtype,
+                                    int32_t* status, void* stream) {
   using namespace sd;
   if (!blob || !depth_m || !out || !status || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS)
     return SD_ERR_ARG;
   if (H < 1 || W < 1 || !(d_max_m > d_min_m)) return SD_ERR_ARG;
+  if (out_dtype != SD_F32 && out_dtype != SD_BF16) return SD_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(blob) & 255)) return SD_ERR_ARG;
   const long long npix = (long long)H * W;
   if ((npix + MM - 1) / MM > 0x7fffffffll) return SD_ERR_UNSUPPORTED;
@@ -414,6 +421,7 @@ extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth
   P.blob = reinterpret_cast<const unsigned char*>(blob);
   P.depth = depth_m;
   P.out = out;
+  P.out_bf16 = out_dtype == SD_BF16;
   P.status = reinterpret_cast<int*>(status);
   P.ks = ks;
   P.H = H;

@@ -10,7 +10,7 @@
   accumulates in FP32.  Bound per pixel: max|err| <= 2^-5 max|ref| of that
   pixel, mean over pixels of max|err| / max|ref| <= 2^-7.
 * Full 512 x 768 map with ks = 21 (the paper's timed size): sampled pixels,
-  deterministic, status clear."""
+  deterministic, status clear; the BF16 map equals the FP32 map rounded."""
 import numpy as np
 import pytest
 import torch
@@ -120,4 +120,22 @@ def test_mlp_validation(sdlib):
     with pytest.raises(sd.SdError):
         sd.mlp_psf_map(net, d, 2.0, 1.0)
     with pytest.raises(sd.SdError):
+        sd.mlp_psf_map(net, d, 0.5, 20.0, dtype=torch.float16)
+    with pytest.raises(sd.SdError):
         n2 = sd.PsfMLP(*he_net(rng, 33), 33)
+
+
+def test_mlp_bf16_map(sdlib):
+    """The BF16 map is the FP32 map rounded to BF16 (nearest even)."""
+    sd = sdlib
+    ks = 21
+    rng = np.random.default_rng(5)
+    w, b = he_net(rng, ks)
+    depth = W.depth_perlin(1, 40, 70, seed=5, d_near_m=0.5, d_far_m=20.0)[0].astype(np.float32)
+    net = sd.PsfMLP(w, b, ks)
+    d = torch.tensor(depth, device="cuda")
+    m32, s1 = sd.mlp_psf_map(net, d, 0.5, 20.0)
+    m16, s2 = sd.mlp_psf_map(net, d, 0.5, 20.0, dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    assert int(s1.item()) == 0 and int(s2.item()) == 0 and m16.dtype == torch.bfloat16
+    assert torch.equal(m16, m32.to(torch.bfloat16))
