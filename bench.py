@@ -705,6 +705,7 @@ def pipeline_compare(sd, dev, reps=5):
 
 PAPER_TRACE_S = 801.544   # DP PSF map of 512 x 768 pixels by ray tracing (Table S3)
 PAPER_RENDER_S = 0.2      # DP image from a PSF map ("fixed cost", supplement)
+PAPER_MLP_S = 0.395       # DP PSF map of 512 x 768 pixels by the MLP (supplement table)
 
 
 def quadrant_compare(sd, dev, reps=5):
@@ -797,6 +798,39 @@ def paper_workload(sd, dev, reps=5):
     peaks = load_peaks()
     if peaks.get("hbm_gbs"):
         res["render_hbm_frac_f32"] = round(res["f32"]["render_gbs"] / peaks["hbm_gbs"], 3)
+    # the paper's render-time PSF source: the MLP of Sec. 3.3 (5 x 512, 2 ks^2
+    # outputs) for every pixel, He-initialised (no trained weights here),
+    # then the same render from its map
+    rng = np.random.default_rng(0)
+    shapes = sd.MLP_SHAPES(ks)
+    net = sd.PsfMLP([rng.normal(0, np.sqrt(2.0 / sh[1]), size=sh).astype(np.float32)
+                     for sh in shapes],
+                    [rng.normal(0, 0.05, size=sh[0]).astype(np.float32) for sh in shapes], ks)
+    flops = 2.0 * H * Wd * sum(a * b for a, b in shapes)
+    mlp = {"network": "3 -> 5 x 512 (ReLU) -> 2 ks^2, He-initialised", "paper_mlp_s": PAPER_MLP_S,
+           "flops_per_map": flops}
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    for name, dt in (("f32_map", torch.float32), ("bf16_map", torch.bfloat16)):
+        pmap = torch.empty((H, Wd, 2, ks, ks), dtype=dt, device=dev)
+        img = aif if dt == torch.float32 else aif.to(dt)
+        out = torch.empty((1, 6, H, Wd), dtype=dt, device=dev)
+        t_m = _timed(lambda: sd.mlp_psf_map(net, depth, c["d_near_m"], c["d_far_m"], out=pmap,
+                                            status=st), stream, reps)
+        if int(st.item()) != 0:
+            raise RuntimeError("MLP kernel: a completion wait gave up")
+
+        def both():
+            sd.mlp_psf_map(net, depth, c["d_near_m"], c["d_far_m"], out=pmap, status=st)
+            sd.dp_render_map(img, pmap, out=out)
+        t_b = _timed(both, stream, reps)
+        tf = flops / (t_m * 1e-3) / 1e12
+        mlp[name] = {"mlp_map_ms": round(t_m, 3), "mlp_map_plus_render_ms": round(t_b, 3),
+                     "tflops": round(tf, 1),
+                     "frac_of_bf16_peak": round(tf / peaks["bf16_tflops"], 3)
+                     if peaks.get("bf16_tflops") else None,
+                     "speedup_vs_paper_mlp": round(PAPER_MLP_S / (t_m * 1e-3), 1)}
+        del pmap, out
+    res["mlp"] = mlp
     lens.free()
     return res
 
