@@ -124,28 +124,40 @@ __host__ __device__ inline size_t tr_b_bytes(int ks) { return (size_t)(tr_kk(ks)
 __host__ __device__ inline size_t tr_smem(int ks) {
   return tr_a_bytes(ks) + (size_t)TR_NB * tr_b_bytes(ks);
 }
+// slices of the re-laid-out bank: every key the selection can produce (a
+// quadrant bank's keys carry 4 flip classes)
+inline size_t tr_slices(const RenderParams& P) {
+  return (size_t)P.FC * P.Z * (P.fmode == SD_FIELD_QUADRANT ? 4 : 1);
+}
 inline size_t tr_bp_bytes(const RenderParams& P) {
-  return (size_t)P.F * P.Z * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
+  return tr_slices(P) * P.NL * P.ks * 2 * tr_kp(P.ks) * 2;
 }
 
 // bp[key][lam][u][side][v] = bank[key][lam][side][ks-1-u][ks-1-v] (v < ks),
-// 0 for ks <= v < KP.  One thread per 8-element (16-byte) piece of a row:
-// row r = (key * NL + lam, u, side), piece q.
+// 0 for ks <= v < KP.  Quadrant bank: key = flips * n_cells + cell (see
+// select_slice), and the slice of flip class x (bit 0) reads the other side
+// with its columns reversed, of class y (bit 1) its rows reversed.  One
+// thread per 8-element (16-byte) piece of a row: row r = (key * NL + lam,
+// u, side), piece q; n_kl = slices of the stored bank x NL.
 template <class TB>
 __global__ void tr_bank_kernel(const TB* __restrict__ bank, __nv_bfloat16* __restrict__ bp,
-                               int n_rows, int ks, int KP) {
+                               int n_rows, int ks, int KP, int n_kl) {
   const int per_row = KP / 8, total = n_rows * per_row;  // < 2^31 - 2^24 (checked on the host)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int r = i / per_row, q = i - r * per_row;
-    const int side = r & 1, ru = r >> 1, u = ru % ks, kl = ru / ks;
-    // element v of the flipped row is src[-v]
-    const TB* src = bank + (((size_t)kl * 2 + side) * ks + (ks - 1 - u)) * ks + (ks - 1);
+    const int side = r & 1, ru = r >> 1, u = ru % ks, klf = ru / ks;
+    const int flips = klf / n_kl, kl = klf - flips * n_kl;
+    const bool mx = flips & 1, my = flips & 2;
+    const int sside = mx ? 1 - side : side, row = my ? u : ks - 1 - u;
+    // element v of the flipped row: src[-v] (src[+v] for a column mirror)
+    const TB* src = bank + (((size_t)kl * 2 + sside) * ks + row) * ks + (mx ? 0 : ks - 1);
+    const int dir = mx ? 1 : -1;
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int v0 = 8 * q + 2 * k, v1 = v0 + 1;
-      const float f0 = v0 < ks ? to_f32<TB>(src[-v0]) : 0.f;
-      const float f1 = v1 < ks ? to_f32<TB>(src[-v1]) : 0.f;
+      const float f0 = v0 < ks ? to_f32<TB>(src[dir * v0]) : 0.f;
+      const float f1 = v1 < ks ? to_f32<TB>(src[dir * v1]) : 0.f;
       w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0)) |
              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f1)) << 16);
     }
@@ -543,7 +555,6 @@ extern "C" sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, siz
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
-  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: CUDA cores only
   *bytes = 256 + tr_bp_bytes(P);
   return SD_OK;
 }
@@ -559,7 +570,6 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
-  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: CUDA cores only
   if (layout->dtype != SD_BF16 && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
   if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024 ||
       (TR_Y + P.ks - 1) * (tr_kk(P.ks) / 8) > TR_SI * TR_NT || TR_SS * (tr_kk(P.ks) / 8) > 32 * TR_TPL)
@@ -584,17 +594,18 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   int* err = reinterpret_cast<int*>(workspace);
   __nv_bfloat16* bp = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(workspace) + 256);
   SD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  const long long n_rows = (long long)P.F * P.Z * P.NL * P.ks * 2;
+  const long long n_rows = (long long)tr_slices(P) * P.NL * P.ks * 2;
+  const int n_kl = P.FC * P.Z * P.NL;  // slices x wavelengths of the stored bank
   const int kp = tr_kp(P.ks);
   if (n_rows * (kp / 8) > 0x7f000000ll) return SD_ERR_UNSUPPORTED;
   const int pieces = (int)(n_rows * (kp / 8));
   const int nblk = std::min((pieces + 255) / 256, 152 * 16);
   if (layout->dtype == SD_BF16)
     tr_bank_kernel<__nv_bfloat16><<<nblk, 256, 0, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(bank), bp, (int)n_rows, P.ks, kp);
+        reinterpret_cast<const __nv_bfloat16*>(bank), bp, (int)n_rows, P.ks, kp, n_kl);
   else
     tr_bank_kernel<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(bank), bp,
-                                               (int)n_rows, P.ks, kp);
+                                               (int)n_rows, P.ks, kp, n_kl);
   st = launch_status();
   if (st != SD_OK) return st;
   const size_t smem = tr_smem(P.ks);

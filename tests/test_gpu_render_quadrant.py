@@ -3,7 +3,8 @@
 against the oracle: FP32 storage max|err| <= 1e-4 max|ref|, BF16 storage on
 the rounded inputs <= 8 * 2^-9 max|ref|; odd and even image sizes (centre
 row / column on an axis), one and several depth slices, ks 1 to 65; the
-entry points without quadrant support reject it."""
+tensor-core render on the rounded inputs <= 8 * 2^-9 max|ref|; the render
+backward rejects it."""
 import numpy as np
 import pytest
 import torch
@@ -84,6 +85,26 @@ def test_quadrant_render_bf16_and_full_size(sdlib):
     assert np.abs(got - ref).max() <= 8 * 2.0 ** -9 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("case", [(1, 3, 40, 37, 4, 3, 3, 31), (1, 1, 33, 48, 3, 4, 1, 65)])
+def test_quadrant_render_tensor_cores(sdlib, case):
+    """The tensor-core render with a quadrant bank (flip classes re-laid out
+    per call) against the oracle on the BF16-rounded inputs."""
+    sd = sdlib
+    N, C, H, Wd, F, Z, NL, ks = case
+    aif, depth, fh, dm, bank = scene(hash(case) % 2**32, *case)
+    lay = sd.BankLayout(fh, dm, NL, ks, 0.002, dtype=torch.bfloat16,
+                        field_mode=sd.SD_FIELD_QUADRANT)
+    a = torch.tensor(aif, device="cuda").to(torch.bfloat16)
+    b = torch.tensor(bank, dtype=torch.float32, device="cuda").to(torch.bfloat16).reshape(-1)
+    ws = torch.empty(sd.api.render_tc_workspace(lay), dtype=torch.uint8, device="cuda")
+    got = sd.dp_render_tc(a, torch.tensor(depth, device="cuda"), b, lay, workspace=ws)
+    torch.cuda.synchronize()
+    assert int(ws[:4].view(torch.int32).item()) == 0
+    ref = O.render_bank(a.float().cpu().numpy(), depth, b.float().cpu().numpy().reshape(bank.shape),
+                        fh, dm, 0.002, n_threads=8, field_mode=O.FIELD_QUADRANT)
+    assert np.abs(got.float().cpu().numpy() - ref).max() <= 8 * 2.0 ** -9 * np.abs(ref).max()
+
+
 def test_quadrant_bank_rejected_where_unsupported(sdlib):
     sd = sdlib
     aif, depth, fh, dm, bank = scene(3, 1, 1, 16, 16, 2, 2, 1, 9)
@@ -93,9 +114,6 @@ def test_quadrant_bank_rejected_where_unsupported(sdlib):
     b = torch.tensor(bank, dtype=torch.float32, device="cuda").reshape(-1)
     with pytest.raises(sd.SdError):
         sd.dp_render_backward(torch.zeros((1, 2, 16, 16), device="cuda"), a, d, b, lay)
-    with pytest.raises(sd.SdError):
-        sd.api.render_tc_workspace(sd.BankLayout(fh, dm, 1, 9, 0.002, dtype=torch.bfloat16,
-                                                 field_mode=sd.SD_FIELD_QUADRANT))
     bad = sd.BankLayout(fh, dm, 1, 9, 0.002, field_mode=7)
     with pytest.raises(sd.SdError):
         sd.dp_render(a, d, b, bad)
