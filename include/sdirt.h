@@ -316,9 +316,10 @@ sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
  * lookup), and the flip symmetry of the DP PSF about both axes (Sec. 5.2):
  * X < 0 mirrors the kernel's columns and exchanges L and R (the DP split is
  * along x), Y < 0 mirrors its rows.  Removes the radial approximation of
- * off-axis azimuths.  sd_dp_render and sd_dp_render_tc (whose workspace then
- * holds the four flip classes); the render backward returns
- * SD_ERR_UNSUPPORTED for it.
+ * off-axis azimuths.  All render entry points take it: sd_dp_render_tc's
+ * workspace then holds the four flip classes, and the backward's partial
+ * banks one gradient slab per key (flip class), folded onto the stored
+ * quadrant in a fixed order.
  * ---------------------------------------------------------------------- */
 #define SD_MAX_BANK_FIELDS 256
 #define SD_MAX_BANK_DEPTHS 256

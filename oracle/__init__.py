@@ -88,6 +88,8 @@ def lib():
         L.or_render_select.argtypes = [i, i, pf, pf, i, pf, i, f, pd]
         L.or_render_bank_pixels.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf, f,
                                             pi, i, pd, i]
+        L.or_render_bank_bwd_mode.argtypes = [pd, pd, i, i, i, i, pf, pd, i, i, i, i,
+                                              pf, pf, f, i, pd, pd]
         L.or_render_bank_mode.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf, f, i,
                                           pd, i]
         L.or_render_bank_pixels_mode.argtypes = [pd, i, i, i, i, pf, pd, i, i, i, i, pf, pf,
@@ -95,7 +97,8 @@ def lib():
         for fn in ("or_lens_info", "or_trace_hits", "or_psf_bank", "or_trace_functional",
                    "or_trace_grad", "or_render_bank", "or_render_map",
                    "or_render_bank_bwd", "or_render_select", "or_render_bank_pixels",
-                   "or_render_bank_mode", "or_render_bank_pixels_mode"):
+                   "or_render_bank_mode", "or_render_bank_pixels_mode",
+                   "or_render_bank_bwd_mode"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -283,20 +286,22 @@ def render_map(aif, psf_map):
     return out
 
 
-def render_bank_bwd(grad_out, aif, depth_m, bank, field_h_mm, depths_m, pitch_mm):
+def render_bank_bwd(grad_out, aif, depth_m, bank, field_h_mm, depths_m, pitch_mm,
+                    field_mode=0):
     """Adjoint of render_bank: (grad_aif, grad_bank)."""
     g = _f64(grad_out)
     a = _f64(aif)
     N, C, H, W = a.shape
     dm = _f32(depth_m)
     b = _f64(bank)
-    F, Z, NL, _, ks, _ = b.shape
+    _, Z, NL, _, ks, _ = b.shape
+    F = _bank_fields(b, field_h_mm, field_mode)
     ga = np.zeros_like(a)
     gb = np.zeros_like(b)
-    _check(lib().or_render_bank_bwd(_pd(g), _pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z,
-                                    NL, ks, _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
-                                    float(np.float32(pitch_mm)), _pd(ga), _pd(gb)),
-           "render_bank_bwd")
+    _check(lib().or_render_bank_bwd_mode(_pd(g), _pd(a), N, C, H, W, _pf(dm), _pd(b), F, Z,
+                                         NL, ks, _pf(_f32(field_h_mm)), _pf(_f32(depths_m)),
+                                         float(np.float32(pitch_mm)), field_mode, _pd(ga),
+                                         _pd(gb)), "render_bank_bwd")
     return ga, gb
 
 

@@ -1193,21 +1193,23 @@ int or_render_map(const double* aif, int N, int C, int H, int W,
 // Adjoint of or_render_bank with respect to the image and the bank:
 // grad_aif (N,C,H,W) and grad_bank (same layout as bank) are overwritten.
 // Replicate padding is adjoined by accumulating into the clamped source.
-int or_render_bank_bwd(const double* grad_out, const double* aif, int N, int C,
-                       int H, int W, const float* depth_m, const double* bank,
-                       int F, int Z, int NL, int ks, const float* field_h_mm,
-                       const float* depths_m, float pitch_mm, double* grad_aif,
-                       double* grad_bank) {
+int or_render_bank_bwd_mode(const double* grad_out, const double* aif, int N, int C,
+                            int H, int W, const float* depth_m, const double* bank,
+                            int F, int Z, int NL, int ks, const float* field_h_mm,
+                            const float* depths_m, float pitch_mm, int field_mode,
+                            double* grad_aif, double* grad_bank) {
   if (!grad_out || !aif || !depth_m || !bank || !grad_aif || !grad_bank)
     return -1;
   if (!(NL == C || NL == 1) || ks < 1 || ks % 2 == 0) return -4;
+  if (field_mode != 0 && field_mode != 1) return -1;
   std::vector<float> iq(Z);
   for (int j = 0; j < Z; ++j) iq[j] = 1.0f / depths_m[j];
-  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm};
+  BankDesc B{bank, F, Z, NL, ks, field_h_mm, iq.data(), pitch_mm, field_mode};
+  const int cells = field_mode == 1 ? F * F : F;
   int p = (ks - 1) / 2;
   size_t n2 = (size_t)ks * ks;
   std::fill(grad_aif, grad_aif + (size_t)N * C * H * W, 0.0);
-  std::fill(grad_bank, grad_bank + (size_t)F * Z * NL * 2 * n2, 0.0);
+  std::fill(grad_bank, grad_bank + (size_t)cells * Z * NL * 2 * n2, 0.0);
   std::vector<double> K(2 * n2), dK(2 * n2);
   for (int n = 0; n < N; ++n)
     for (int c = 0; c < C; ++c) {
@@ -1230,15 +1232,33 @@ int or_render_bank_bwd(const double* grad_out, const double* aif, int N, int C,
               dK[kk] = gL * img[src];
               dK[n2 + kk] = gR * img[src];
             }
+          // dK is the gradient of the pixel's kernel; each of its elements
+          // is a stored element (mirrored for a quadrant bank's flips)
           double* b0 = grad_bank + (((size_t)s.f * Z + s.z0) * NL + lam) * 2 * n2;
           double* b1 = grad_bank + (((size_t)s.f * Z + s.z1) * NL + lam) * 2 * n2;
-          for (size_t i = 0; i < 2 * n2; ++i) {
-            b0[i] += (1.0 - s.t) * dK[i];
-            b1[i] += s.t * dK[i];
-          }
+          for (int side = 0; side < 2; ++side)
+            for (int a = 0; a < ks; ++a)
+              for (int b = 0; b < ks; ++b) {
+                const int side_src = s.mirror_x ? 1 - side : side;
+                const int a_src = s.mirror_y ? ks - 1 - a : a;
+                const int b_src = s.mirror_x ? ks - 1 - b : b;
+                const size_t src = side_src * n2 + (size_t)a_src * ks + b_src;
+                const double g = dK[side * n2 + (size_t)a * ks + b];
+                b0[src] += (1.0 - s.t) * g;
+                b1[src] += s.t * g;
+              }
         }
     }
   return 0;
+}
+
+int or_render_bank_bwd(const double* grad_out, const double* aif, int N, int C,
+                       int H, int W, const float* depth_m, const double* bank,
+                       int F, int Z, int NL, int ks, const float* field_h_mm,
+                       const float* depths_m, float pitch_mm, double* grad_aif,
+                       double* grad_bank) {
+  return or_render_bank_bwd_mode(grad_out, aif, N, C, H, W, depth_m, bank, F, Z, NL, ks,
+                                 field_h_mm, depths_m, pitch_mm, 0, grad_aif, grad_bank);
 }
 
 // Per-pixel bank selection as the renderer takes it (for tests):

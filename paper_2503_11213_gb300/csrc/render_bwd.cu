@@ -33,7 +33,7 @@ namespace sd {
 constexpr int TXB = 64;            // tile width of the bitmap / bank-gradient pass
 constexpr int NT_BM = 256;         // threads of the bitmap kernel (= TXB*RT_Y/SEG)
 
-inline size_t bitmap_words(int F, int Z) { return ((size_t)F * Z + 31) / 32; }
+inline size_t bitmap_words(int nkeys) { return ((size_t)nkeys + 31) / 32; }
 
 inline void bwd_tiles(int H, int W, int* tx, int* ty) {
   *tx = (W + TXB - 1) / TXB;
@@ -233,9 +233,14 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
         GR[j] = w * gR[pix];
       }
       const int f = key / P.Z, z = key - f * P.Z;
-      const TB* KL = reinterpret_cast<const TB*>(P.bank) +
-                     (((size_t)f * P.Z + z) * P.NL + lam) * 2 * ks2;
-      const TB* KR = KL + ks2;
+      // quadrant bank: field cell and flips (x: mirror columns and exchange
+      // L and R; y: mirror rows); radial bank: flips = 0
+      const int flips = f / P.FC, cell = f - flips * P.FC;
+      const TB* K0 = reinterpret_cast<const TB*>(P.bank) +
+                     (((size_t)cell * P.Z + z) * P.NL + lam) * 2 * ks2;
+      const TB* KL = (flips & 1) ? K0 + ks2 : K0;
+      const TB* KR = (flips & 1) ? K0 : K0 + ks2;
+      const bool mx = flips & 1, my = flips & 2;
       float pre[NR];
       auto fetch = [&](int b) {
 #pragma unroll
@@ -246,7 +251,8 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
             int side = e & 1, uv = e >> 1, u = uv / VB, vv = uv - u * VB;
             int v_ = b * VB + vv;
             if (v_ < ks && u < ks)
-              v = to_f32<TB>(__ldg((side ? KR : KL) + (ks - 1 - u) * ks + (ks - 1 - v_)));
+              v = to_f32<TB>(__ldg((side ? KR : KL) + (my ? u : ks - 1 - u) * ks +
+                                   (mx ? v_ : ks - 1 - v_)));
           }
           pre[r] = v;
         }
@@ -484,6 +490,28 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
   }
 }
 
+// Quadrant bank: grad_bank = for each stored element, the sum over the four
+// flip classes (class x: other side, column mirrored; class y: row mirrored)
+// and the part slabs of the per-key gradients, in a fixed order
+// (deterministic).  n = stored elements, n_kl = stored slices x wavelengths.
+__global__ void bank_fold_quadrant(const float* __restrict__ parts_buf, size_t n, int parts,
+                                   int n_kl, int ks, float* __restrict__ gbank) {
+  const size_t ks2 = (size_t)ks * ks, nv = 4 * n;  // elements of one part slab
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t kl = i / (2 * ks2), rem = i - kl * 2 * ks2;
+    const int side = (int)(rem / ks2), e = (int)(rem - side * ks2), a = e / ks, b = e - a * ks;
+    float acc = 0.f;
+    for (int f = 0; f < 4; ++f) {
+      const bool mx = f & 1, my = f & 2;
+      const int vs = mx ? 1 - side : side, va = my ? ks - 1 - a : a, vb = mx ? ks - 1 - b : b;
+      const size_t vi = (((size_t)f * n_kl + kl) * 2 + vs) * ks2 + (size_t)va * ks + vb;
+      for (int q = 0; q < parts; ++q) acc += parts_buf[(size_t)q * nv + vi];
+    }
+    gbank[i] = acc;
+  }
+}
+
 // grad_bank = sum of the part slabs, added in part order (deterministic)
 __global__ void bank_parts_reduce(const float* __restrict__ parts_buf, size_t n, int parts,
                                   float* __restrict__ gbank) {
@@ -504,11 +532,20 @@ sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsign
                 (size_t)(TXB * RT_Y / SEG) * 4;
   auto k = render_bwd_bank_kernel<NT, SPT, TI>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(P.F * P.Z, P.NL, parts);
-  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 ? parts_buf : gbank, parts);
+  dim3 grid(n_keys(P), P.NL, parts);
+  // a quadrant bank's gradients are per key (flip class) first, then folded
+  const bool quad = P.fmode == SD_FIELD_QUADRANT;
+  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 || quad ? parts_buf : gbank,
+                           parts);
   sd_status st = launch_status();
-  if (st != SD_OK || parts == 1) return st;
-  size_t n = (size_t)P.F * P.Z * P.NL * 2 * ks * ks;
+  if (st != SD_OK) return st;
+  if (quad) {
+    const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
+    bank_fold_quadrant<<<1024, 256, 0, s>>>(parts_buf, n, parts, P.FC * P.Z * P.NL, ks, gbank);
+    return launch_status();
+  }
+  if (parts == 1) return st;
+  size_t n = (size_t)n_keys(P) * P.NL * 2 * ks * ks;
   bank_parts_reduce<<<1024, 256, 0, s>>>(parts_buf, n, parts, gbank);
   return launch_status();
 }
@@ -532,11 +569,12 @@ constexpr size_t SMEM_CAP_B = 227 * 1024;
 // tail of the launch); fewer parts with a smaller workspace.
 constexpr int BANK_PARTS = 2;
 
-inline size_t bitmap_bytes(int N, int tx, int ty, int F, int Z) {
-  return ((size_t)N * tx * ty * bitmap_words(F, Z) * 4 + 255) & ~(size_t)255;
+inline size_t bitmap_bytes(int N, int tx, int ty, int nkeys) {
+  return ((size_t)N * tx * ty * bitmap_words(nkeys) * 4 + 255) & ~(size_t)255;
 }
+// one partial bank: a slab per key (a quadrant bank's keys carry 4 flip classes)
 inline size_t bank_bytes(const RenderParams& P) {
-  return (size_t)P.F * P.Z * P.NL * 2 * P.ks * P.ks * 4;
+  return (size_t)n_keys(P) * P.NL * 2 * P.ks * P.ks * 4;
 }
 
 sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
@@ -546,11 +584,10 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
-  if (P.fmode != SD_FIELD_RADIAL) return SD_ERR_UNSUPPORTED;  // quadrant banks: forward only
   if (layout->dtype != SD_F32 && layout->dtype != SD_BF16 && layout->dtype != SD_F16)
     return SD_ERR_UNSUPPORTED;
   if (!(P.NL == C || P.NL == 1)) return SD_ERR_ARG;
-  if ((long long)P.F * P.Z > 65000) return SD_ERR_UNSUPPORTED;
+  if ((long long)n_keys(P) > 65000) return SD_ERR_UNSUPPORTED;
   P.N = N;
   P.C = C;
   P.H = H;
@@ -593,7 +630,7 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   if (st != SD_OK) return st;
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
-  *bytes = bitmap_bytes(N, tx, ty, P.F, P.Z) + (size_t)BANK_PARTS * bank_bytes(P);
+  *bytes = bitmap_bytes(N, tx, ty, n_keys(P)) + (size_t)BANK_PARTS * bank_bytes(P);
   return SD_OK;
 }
 
@@ -613,7 +650,7 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
   P.depth = depth_m;
   P.bank = bank;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  size_t bank_elems = (size_t)P.F * P.Z * P.NL * 2 * P.ks * P.ks;
+  size_t bank_elems = (size_t)P.FC * P.Z * P.NL * 2 * P.ks * P.ks;  // stored bank
   if (N == 0 || H == 0 || W == 0) {
     if (grad_bank) SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
     return SD_OK;
@@ -630,9 +667,11 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
   if (grad_bank) {
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
-    size_t words = bitmap_words(P.F, P.Z);
-    size_t need = bitmap_bytes(N, tx, ty, P.F, P.Z);
-    if (!workspace || workspace_bytes < need) return SD_ERR_ARG;
+    size_t words = bitmap_words(n_keys(P));
+    size_t need = bitmap_bytes(N, tx, ty, n_keys(P));
+    // a quadrant bank needs at least one partial bank to fold
+    const size_t need_min = need + (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
+    if (!workspace || workspace_bytes < need_min) return SD_ERR_ARG;
     unsigned* bm = reinterpret_cast<unsigned*>(workspace);
     int parts = 1;
     for (int q = BANK_PARTS; q > 1; q >>= 1)
@@ -710,7 +749,8 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
     if (st != SD_OK) return st;
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
-    need = bitmap_bytes(N, tx, ty, P.F, P.Z);
+    need = bitmap_bytes(N, tx, ty, n_keys(P)) +
+           (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
     if (need > NOALLOC_SCRATCH_BYTES) return SD_ERR_CAPACITY;
     st = noalloc_scratch(&ws);
     if (st != SD_OK) return st;

@@ -87,6 +87,12 @@ __device__ __forceinline__ void select_slice(const RenderParams& P, int row, int
   *t = tt;
 }
 
+// Keys select_slice can produce: field cells x depths, times 4 flip classes
+// for a quadrant bank.
+inline int n_keys(const RenderParams& P) {
+  return P.FC * P.Z * (P.fmode == SD_FIELD_QUADRANT ? 4 : 1);
+}
+
 inline sd_status check_layout(const sd_bank_layout* L, RenderParams& P) {
   if (!L || !L->field_h_mm || !L->depths_m) return SD_ERR_ARG;
   if (L->n_field < 1 || L->n_field > SD_MAX_BANK_FIELDS || L->n_depth < 1 ||

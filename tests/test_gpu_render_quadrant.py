@@ -4,7 +4,7 @@ against the oracle: FP32 storage max|err| <= 1e-4 max|ref|, BF16 storage on
 the rounded inputs <= 8 * 2^-9 max|ref|; odd and even image sizes (centre
 row / column on an axis), one and several depth slices, ks 1 to 65; the
 tensor-core render on the rounded inputs <= 8 * 2^-9 max|ref|; the render
-backward rejects it."""
+backward (both gradients) <= 1e-4 max|ref|."""
 import numpy as np
 import pytest
 import torch
@@ -105,15 +105,34 @@ def test_quadrant_render_tensor_cores(sdlib, case):
     assert np.abs(got.float().cpu().numpy() - ref).max() <= 8 * 2.0 ** -9 * np.abs(ref).max()
 
 
-def test_quadrant_bank_rejected_where_unsupported(sdlib):
+@pytest.mark.parametrize("case", [(1, 2, 24, 37, 3, 3, 2, 15), (2, 1, 33, 20, 4, 2, 1, 31)])
+def test_quadrant_render_backward(sdlib, case):
+    """The adjoint with a quadrant bank (per-key gradients folded onto the
+    stored quadrant) against the oracle's adjoint: max|err| <= 1e-4 max|ref|
+    for both gradients."""
+    sd = sdlib
+    N, C, H, Wd, F, Z, NL, ks = case
+    aif, depth, fh, dm, bank = scene(hash(case) % 2**32, *case)
+    rng = np.random.default_rng(1)
+    g = rng.normal(size=(N, 2 * C, H, Wd)).astype(np.float32)
+    lay = sd.BankLayout(fh, dm, NL, ks, 0.002, field_mode=sd.SD_FIELD_QUADRANT)
+    ga, gb = sd.dp_render_backward(torch.tensor(g, device="cuda"), torch.tensor(aif, device="cuda"),
+                                   torch.tensor(depth, device="cuda"),
+                                   torch.tensor(bank, dtype=torch.float32, device="cuda").reshape(-1),
+                                   lay)
+    torch.cuda.synchronize()
+    ra, rb = O.render_bank_bwd(g, aif, depth, bank, fh, dm, 0.002, field_mode=O.FIELD_QUADRANT)
+    assert np.abs(ga.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+    gbn = gb.cpu().numpy().reshape(bank.shape)
+    assert np.abs(gbn - rb).max() <= 1e-4 * np.abs(rb).max()
+
+
+def test_quadrant_bank_invalid_mode(sdlib):
     sd = sdlib
     aif, depth, fh, dm, bank = scene(3, 1, 1, 16, 16, 2, 2, 1, 9)
-    lay = sd.BankLayout(fh, dm, 1, 9, 0.002, field_mode=sd.SD_FIELD_QUADRANT)
     a = torch.tensor(aif, device="cuda")
     d = torch.tensor(depth, device="cuda")
     b = torch.tensor(bank, dtype=torch.float32, device="cuda").reshape(-1)
-    with pytest.raises(sd.SdError):
-        sd.dp_render_backward(torch.zeros((1, 2, 16, 16), device="cuda"), a, d, b, lay)
     bad = sd.BankLayout(fh, dm, 1, 9, 0.002, field_mode=7)
     with pytest.raises(sd.SdError):
         sd.dp_render(a, d, b, bad)

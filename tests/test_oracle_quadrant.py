@@ -76,3 +76,22 @@ def test_quadrant_render_equals_map_of_signed_field_points():
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
     # and the radial reading differs off the axes (the quadrant bank matters)
     assert not np.allclose(psf_map[0, 0], psf_map[0, -1])
+
+
+def test_quadrant_render_adjoint_identity():
+    """<g, render(I, B)> = <grad_I, I> and, the render being linear in the
+    bank, = <grad_B, B>: the quadrant adjoint folds every flipped use back
+    onto the stored element."""
+    rng = np.random.default_rng(6)
+    F, Z, NL, ks, H, Wd = 3, 2, 1, 5, 9, 12
+    fh = np.array([0.0, 0.006, 0.012], dtype=np.float32)
+    dm = np.array([0.5, 2.0], dtype=np.float32)
+    bank = rng.uniform(0, 1, size=(F * F, Z, NL, 2, ks, ks))
+    aif = rng.uniform(0, 1, size=(1, 2, H, Wd))
+    depth = rng.uniform(0.4, 2.5, size=(1, H, Wd)).astype(np.float32)
+    g = rng.normal(size=(1, 4, H, Wd))
+    out = O.render_bank(aif, depth, bank, fh, dm, 0.002, field_mode=O.FIELD_QUADRANT)
+    ga, gb = O.render_bank_bwd(g, aif, depth, bank, fh, dm, 0.002, field_mode=O.FIELD_QUADRANT)
+    lhs = float((g * out).sum())
+    np.testing.assert_allclose((ga * aif).sum(), lhs, rtol=1e-12)
+    np.testing.assert_allclose((gb * bank).sum(), lhs, rtol=1e-12)
