@@ -139,3 +139,23 @@ def test_mlp_bf16_map(sdlib):
     torch.cuda.synchronize()
     assert int(s1.item()) == 0 and int(s2.item()) == 0 and m16.dtype == torch.bfloat16
     assert torch.equal(m16, m32.to(torch.bfloat16))
+
+
+def test_mlp_map_render_pipeline(sdlib):
+    """The paper's render path end to end: network map, then the listing's
+    per-pixel render (sd_dp_render_map), against the oracle's network and
+    listing render on the same BF16-rounded weights; the bound adds the map
+    bound (2^-5 of each pixel's max) to the render's FP32 accumulation."""
+    sd = sdlib
+    ks, H, Wd = 21, 30, 44
+    rng = np.random.default_rng(9)
+    w, b = he_net(rng, ks)
+    depth = W.depth_perlin(1, H, Wd, seed=9, d_near_m=0.5, d_far_m=20.0)[0].astype(np.float32)
+    aif = rng.uniform(0, 1, size=(1, 3, H, Wd)).astype(np.float32)
+    net = sd.PsfMLP(w, b, ks)
+    m, st = sd.mlp_psf_map(net, torch.tensor(depth, device="cuda"), 0.5, 20.0)
+    out = sd.dp_render_map(torch.tensor(aif, device="cuda"), m)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = O.render_map(aif, oracle_map(w, b, depth, 0.5, 20.0, ks))
+    assert np.abs(out.cpu().numpy() - ref).max() <= 2.0 ** -5 * np.abs(ref).max()
