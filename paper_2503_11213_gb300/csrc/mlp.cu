@@ -227,12 +227,17 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
     const float xn = live ? ((float)px - 0.5f * (float)(P.W - 1)) / (0.5f * (float)P.W) : 0.f;
     const float yn = live ? ((float)py - 0.5f * (float)(P.H - 1)) / (0.5f * (float)P.H) : 0.f;
     const float dn = live ? (P.depth[pix] - P.d_min) * P.d_scale - 1.f : 0.f;
+    // layer 0's 512 {w, b} in the staging area (free until the first store):
+    // one coalesced load per thread instead of 256 dependent loads each
+    float4* s_wb0 = reinterpret_cast<float4*>(stage);
+    for (int j = tid; j < MH; j += MEPI) s_wb0[j] = __ldg(&WB0[j]);
+    named_sync_m(1, MEPI);
     for (int j0 = half * MNC; j0 < half * MNC + MNC; j0 += 8) {
       float a[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int j = j0 + q;
-        const float4 wb = __ldg(&WB0[j]);
+        const float4 wb = s_wb0[j];
         const float v = fmaf(wb.x, xn, fmaf(wb.y, yn, fmaf(wb.z, dn, wb.w)));
         a[q] = fmaxf(v, 0.f);
       }
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
     }
     tc::fence_async_smem();
     tc::mbar_arrive(&s_epi[half]);
+    named_sync_m(1, MEPI);  // s_wb0 is read by all before s_sum reuses the area
     float part = 0.f, sum = 0.f;
     const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * MNC);
     for (int ph = 0; ph < nphase; ++ph) {
