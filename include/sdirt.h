@@ -415,6 +415,24 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
                                           int C, int H, int W, size_t* bytes);
 
 /*
+ * The bank gradient of sd_dp_render_backward on the tensor cores (tcgen05),
+ * for BF16 images: grad_bank (FP32, the stored bank's shape) = the adjoint of
+ * the render with respect to the bank, with the image in BF16, the weighted
+ * output gradients w * G rounded to BF16, products exact and accumulated in
+ * FP32 in tensor memory in a fixed order (deterministic).  grad_out (N,2C,H,W)
+ * FP32, aif (N,C,H,W) BF16, depth_m (N,H,W) FP32, all device; the bank itself
+ * is not read.  Workspace from sd_dp_render_bank_grad_tc_workspace (device,
+ * 256-byte aligned; its first int32 becomes 1 if a bounded completion wait
+ * gave up).  ks <= 80.  Radial and quadrant banks.
+ */
+sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,
+                                              int H, int W, size_t* bytes);
+sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif,
+                                    const float* depth_m, const sd_bank_layout* layout,
+                                    int N, int C, int H, int W, float* grad_bank,
+                                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * sd_dp_render_backward for callers that cannot allocate device memory: code
  * that may only use the buffers it is handed (for example a plugin running
  * inside another runtime's memory pool, where a cudaMalloc would bypass the

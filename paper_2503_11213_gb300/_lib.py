@@ -74,6 +74,7 @@ EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_fre
            "sd_dp_render", "sd_dp_render_map", "sd_dp_render_tc", "sd_dp_render_tc_workspace", "sd_dp_render_backward",
            "sd_dp_render_backward_workspace", "sd_dp_render_backward_noalloc",
            "sd_mlp_blob_bytes", "sd_mlp_pack", "sd_mlp_psf_map",
+           "sd_dp_render_bank_grad_tc", "sd_dp_render_bank_grad_tc_workspace",
            "sd_dev_math_check", "sd_dev_tc_check", "sd_status_string", "sd_last_cuda_error",
            "sd_version")
 
@@ -138,6 +139,10 @@ def lib():
                                                   P(ctypes.c_size_t)]
     L.sd_dev_math_check.argtypes = [vp, vp, i32, vp, vp, vp]
     L.sd_dev_tc_check.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.sd_dp_render_bank_grad_tc_workspace.argtypes = [P(SdBankLayout), i32, i32, i32, i32,
+                                                      P(ctypes.c_size_t)]
+    L.sd_dp_render_bank_grad_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, vp,
+                                            vp, ctypes.c_size_t, vp]
     fl = ctypes.c_float
     L.sd_mlp_blob_bytes.argtypes = [i32, P(ctypes.c_size_t)]
     L.sd_mlp_pack.argtypes = [P(P(fl)), P(P(fl)), i32, vp, ctypes.c_size_t]

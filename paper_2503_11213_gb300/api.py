@@ -362,6 +362,37 @@ def render_backward_workspace(layout: BankLayout, N, C, H, W):
     return n.value
 
 
+def bank_grad_tc_workspace(layout: BankLayout, N, C, H, W):
+    n = ctypes.c_size_t(0)
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render_bank_grad_tc_workspace(ctypes.byref(lay), N, C, H, W,
+                                                        ctypes.byref(n)),
+            "sd_dp_render_bank_grad_tc_workspace")
+    return n.value
+
+
+def dp_render_bank_grad_tc(grad_out, aif, depth_m, layout: BankLayout, out=None, workspace=None):
+    """Bank gradient of dp_render on the tensor cores: grad_out (N,2C,H,W)
+    f32, aif (N,C,H,W) bf16, depth (N,H,W) f32 -> grad_bank (layout.shape())
+    f32.  The workspace's first int32 is an error flag (1 = a completion wait
+    gave up)."""
+    N, C, H, W = aif.shape
+    if aif.dtype != torch.bfloat16 or grad_out.dtype != torch.float32:
+        raise ValueError("bf16 image and float32 output gradient")
+    if out is None:
+        out = torch.empty(layout.shape(), dtype=torch.float32, device=aif.device)
+    if workspace is None:
+        workspace = torch.empty(bank_grad_tc_workspace(layout, N, C, H, W), dtype=torch.uint8,
+                                device=aif.device)
+    _need_cuda(grad_out, aif, depth_m, out, workspace)
+    lay = layout.c()
+    L.check(L.lib().sd_dp_render_bank_grad_tc(_ptr(grad_out), _ptr(aif), _ptr(depth_m),
+                                              ctypes.byref(lay), N, C, H, W, _ptr(out),
+                                              _ptr(workspace), workspace.numel(), _stream()),
+            "sd_dp_render_bank_grad_tc")
+    return out
+
+
 def dp_render_backward(grad_out, aif, depth_m, bank, layout: BankLayout, need_aif=True,
                        need_bank=True, workspace=None):
     """Adjoint of dp_render: (grad_aif or None, grad_bank or None), both FP32;

@@ -24,9 +24,11 @@
 //                           8-tap strips of the kernel and accumulate over the
 //                           tile's segments in a fixed order: deterministic.
 
+#include <algorithm>
 #include <mutex>
 
 #include "render_common.cuh"
+#include "tc.cuh"
 
 namespace sd {
 
@@ -617,6 +619,284 @@ sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const un
   return launch_bank_bwd<512, 4, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
 }
 
+
+// ---------------------------------------------------------------------------
+// 4. bank gradient on the tensor cores (BF16 image; the weighted gradients
+// w * G rounded to BF16; FP32 accumulation in tensor memory)
+//
+// Block (slice key, wavelength, part) as in pass 3.  For a tile pixel row y
+// and a group of 16 kernel rows u0..u0+15 the slice gradient is one product
+//   D[(g, r), (side, i)] += sum_x Ipad(y + u0 + g, x0 + 8r + x) Gw_side(y, x - i)
+// = dKf_side[u0 + g][8r + i]: M = 128 = 16 kernel rows x 8 column groups,
+// N = 32 = 2 sides x 16 shifts, K = the tile's 64 columns + 16.  The A
+// operand is the staged image tile read as a Hankel matrix directly from
+// its BF16 rows (core-matrix rows 16 bytes apart = 8 columns, K blocks 16
+// bytes apart, row groups one image row apart), so no shifted copies of the
+// image exist; B is the weighted gradient row at 16 shifts, built per row.
+// All kernel-row groups accumulate over every row and tile the block visits
+// (160 tensor-memory columns at ks = 65); the epilogue writes each element
+// once.  Deterministic (fixed MMA order).
+// ---------------------------------------------------------------------------
+constexpr int BG_NT = 256;
+constexpr int BG_KX = TXB + 16;              // K extent: tile columns + 16 shifts
+constexpr int BG_IW = BG_KX + 56;            // staged image columns (8 column groups)
+constexpr int BG_IWB = BG_IW * 2;            // its row stride in bytes (272)
+constexpr int BG_GW = 8 * 12;                // gradient row: 16 zeros, 64 values, 16 zeros
+constexpr int BG_N = 32;
+constexpr int BG_KB = BG_KX / 8;             // 10 K blocks
+constexpr uint32_t BG_LBO_B = BG_N * 16 + 16;  // B K-block stride, padded: conflict-free builds
+constexpr uint32_t BG_BBUF = BG_KB * BG_LBO_B;
+constexpr int BG_NB = 4;                     // B ring = producer warps 4..7
+constexpr int BG_MAXUG = 5;                  // kernel-row groups (ks <= 80)
+constexpr uint32_t BG_WAIT = 1u << 22;
+
+__host__ __device__ inline int bg_nug(int ks) { return (ks + 15) / 16; }
+__host__ __device__ inline size_t bg_img_bytes(int ks) {
+  return ((size_t)(RT_Y + 16 * bg_nug(ks)) * BG_IWB + 127) / 128 * 128;
+}
+__host__ __device__ inline size_t bg_smem(int ks) {
+  return bg_img_bytes(ks) + (size_t)2 * RT_Y * BG_GW * 2 + (size_t)BG_NB * BG_BBUF;
+}
+
+__device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err) {
+  if (tc::mbar_wait(bar, parity, BG_WAIT, err)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+__global__ void __launch_bounds__(BG_NT, 1) bank_grad_tc_kernel(
+    const RenderParams P, const float* __restrict__ gout, const unsigned* __restrict__ bm,
+    int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_full[BG_NB], s_empty[BG_NB], s_tile, s_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_rows[RT_Y], s_nrow, s_init;
+  __shared__ unsigned s_use;
+  const int ks = P.ks, p = (ks - 1) >> 1, nug = bg_nug(ks), rows_st = RT_Y + 16 * nug;
+  unsigned char* img = smem;                                       // [rows_st][BG_IW] bf16
+  unsigned short* gw = reinterpret_cast<unsigned short*>(smem + bg_img_bytes(ks));  // [2][32][96]
+  unsigned char* bring = smem + bg_img_bytes(ks) + (size_t)2 * RT_Y * BG_GW * 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int key = blockIdx.x, lam = blockIdx.y, part = blockIdx.z;
+  const bool two = P.Z > 1;
+  const int kw = key >> 5;
+  const unsigned kbit = 1u << (key & 31);
+  const int c_lo = (P.NL == P.C) ? lam : 0, c_hi = (P.NL == P.C) ? lam + 1 : P.C;
+
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 256);
+  if (tid == 0) {
+    for (int b = 0; b < BG_NB; ++b) {
+      tc::mbar_init(&s_full[b], 32);
+      tc::mbar_init(&s_empty[b], 1);
+    }
+    tc::mbar_init(&s_tile, 1);
+    tc::mbar_init(&s_done, 1);
+    s_init = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, BG_N);
+  const uint32_t img_a = tc::smem_u32(img), ring_a = tc::smem_u32(bring);
+  int c_row = 0, visits = 0;
+  unsigned inited = 0;  // kernel-row groups written (MMA thread)
+
+  for (int n = 0; n < P.N; ++n)
+    for (int ty = 0; ty < nty; ++ty)
+      for (int tx = 0; tx < ntx; ++tx) {
+        const size_t tile = ((size_t)n * nty + ty) * ntx + tx;
+        if ((int)(tile % (size_t)parts) != part) continue;
+        if (!(bm[tile * words + kw] & kbit)) continue;
+        const int x0 = tx * TXB, y0 = ty * RT_Y;
+        for (int c = c_lo; c < c_hi; ++c, ++visits) {
+          // the previous visit's MMAs have read the image, the gradients and
+          // their B rows; every producer has finished its builds
+          if (visits > 0) {
+            if (lane == 0) bg_wait(&s_tile, (uint32_t)(visits - 1) & 1u, err);
+            __syncwarp();
+          }
+          if (tid == 0) s_use = 0u;
+          __syncthreads();
+          const unsigned short* im =
+              reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
+          // 8 columns (16 bytes) per item: one vector load inside the image
+          // when aligned, clamped scalar loads at the edges
+          for (int i = tid; i < rows_st * (BG_IW / 8); i += BG_NT) {
+            const int r = i / (BG_IW / 8), q = i - r * (BG_IW / 8);
+            const size_t ro = (size_t)min(max(y0 + r - p, 0), P.H - 1) * P.W;
+            const int xa = x0 - p + 8 * q;
+            const unsigned short* src = im + ro + xa;
+            uint4 w;
+            if (xa >= 0 && xa + 8 <= P.W && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+              w = *reinterpret_cast<const uint4*>(src);
+            } else {
+              uint32_t e[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) e[k] = im[ro + min(max(xa + k, 0), P.W - 1)];
+              w = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                             e[6] | (e[7] << 16));
+            }
+            *reinterpret_cast<uint4*>(img + (size_t)r * BG_IWB + 16 * q) = w;
+          }
+          const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
+          const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
+          for (int i = tid; i < RT_Y * BG_GW; i += BG_NT) {
+            const int r = i / BG_GW, j = i - r * BG_GW, x = j - 16;
+            const int yy = y0 + r, xx = x0 + x;
+            float gl = 0.f, gr = 0.f;
+            if (x >= 0 && x < TXB && yy < P.H && xx < P.W) {
+              int k0;
+              float t;
+              select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &k0, &t);
+              const float w = (k0 == key) ? (two ? 1.f - t : 1.f)
+                                          : ((two && k0 + 1 == key) ? t : 0.f);
+              if (w != 0.f) {
+                gl = w * goL[(size_t)yy * P.W + xx];
+                gr = w * goR[(size_t)yy * P.W + xx];
+              }
+            }
+            const unsigned short bl = __bfloat16_as_ushort(__float2bfloat16_rn(gl));
+            const unsigned short br = __bfloat16_as_ushort(__float2bfloat16_rn(gr));
+            gw[r * BG_GW + j] = bl;
+            gw[RT_Y * BG_GW + r * BG_GW + j] = br;
+            if ((bl | br) & 0x7fffu) atomicOr(&s_use, 1u << r);
+          }
+          tc::fence_async_smem();  // the staged image, read by the tensor core
+          __syncthreads();
+          if (tid == 0) {  // the rows with a non-zero weighted gradient
+            int k = 0;
+            for (int r = 0; r < RT_Y; ++r)
+              if (s_use >> r & 1u) s_rows[k++] = r;
+            s_nrow = k;
+          }
+          __syncthreads();
+          const int nrow = s_nrow;
+          if (warp >= 4) {
+            // producer of ring buffer b: the rows k with (c_row + k) % 4 == b.
+            // Task t = (K block kb = t % 10, shift half ih, side): the 8 rows
+            // (side, 8 ih + i') of K block kb from gradient words q - 1, q
+            const int b = warp - 4;
+            for (int k = 0; k < nrow; ++k) {
+              const int cg = c_row + k;
+              if (cg % BG_NB != b) continue;
+              if (cg >= BG_NB) {
+                if (lane == 0) bg_wait(&s_empty[b], (uint32_t)(cg / BG_NB - 1) & 1u, err);
+                __syncwarp();
+              }
+              const int y = s_rows[k];
+              unsigned char* dstb = bring + (size_t)b * BG_BBUF;
+              for (int t = lane; t < 2 * 2 * BG_KB; t += 32) {
+                const int kb = t % BG_KB, ih = (t / BG_KB) & 1, side = t / (2 * BG_KB);
+                const int q = kb + 2 - ih;
+                const unsigned short* row = gw + (size_t)side * RT_Y * BG_GW + y * BG_GW;
+                const uint4 w0 = *reinterpret_cast<const uint4*>(row + 8 * (q - 1));
+                const uint4 w1 = *reinterpret_cast<const uint4*>(row + 8 * q);
+                const uint32_t c8[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                unsigned char* d = dstb + (size_t)kb * BG_LBO_B + (size_t)(side * 16 + 8 * ih) * 16;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  uint32_t g4[4];
+#pragma unroll
+                  for (int kk = 0; kk < 4; ++kk) {
+                    if (i & 1)
+                      g4[kk] = __funnelshift_r(c8[(7 - i) / 2 + kk], c8[(9 - i) / 2 + kk], 16);
+                    else
+                      g4[kk] = c8[(8 - i) / 2 + kk];
+                  }
+                  *reinterpret_cast<uint4*>(d + i * 16) = make_uint4(g4[0], g4[1], g4[2], g4[3]);
+                }
+              }
+              tc::fence_async_smem();
+              tc::mbar_arrive(&s_full[b]);
+            }
+          } else if (warp == 0) {
+            if (lane == 0) {
+              for (int k = 0; k < nrow; ++k) {
+                const int cg = c_row + k, b = cg % BG_NB;
+                if (!bg_wait(&s_full[b], (uint32_t)(cg / BG_NB) & 1u, err)) break;
+                tc::fence_after_sync();
+                const int y = s_rows[k];
+                for (int ug = 0; ug < nug; ++ug)
+#pragma unroll
+                  for (int s = 0; s < BG_KB / 2; ++s) {
+                    const uint64_t ad = tc::smem_desc(
+                        img_a + (uint32_t)(y + 16 * ug) * BG_IWB + (uint32_t)s * 32u, 16, BG_IWB);
+                    const uint64_t bd = tc::smem_desc(
+                        ring_a + (uint32_t)b * BG_BBUF + (uint32_t)s * 2u * BG_LBO_B, BG_LBO_B, 128);
+                    tc::mma_bf16(tmem + (uint32_t)(ug * BG_N), ad, bd, idesc,
+                                 ((inited >> ug) & 1u) || s > 0);
+                    inited |= 1u << ug;
+                  }
+                tc::commit(&s_empty[b]);
+              }
+              tc::commit(&s_tile);
+            }
+            __syncwarp();
+          }
+          c_row += nrow;
+        }
+      }
+  // every MMA has completed; the accumulator holds the block's gradient
+  if (tid == 0) {
+    tc::commit(&s_done);
+    s_init = (int)inited;
+  }
+  if (lane == 0) bg_wait(&s_done, 0, err);
+  __syncwarp();
+  __syncthreads();
+  tc::fence_after_sync();
+  float* out = gbank + ((size_t)part * gridDim.x * P.NL + (size_t)key * P.NL + lam) * 2 * ks * ks;
+  if (warp < 4) {
+    const int m = 32 * warp + lane, g = m >> 3, r = m & 7;
+    const unsigned ini = (unsigned)s_init;
+    for (int ug = 0; ug < nug; ++ug) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ug * BG_N), v);
+      const int u = 16 * ug + g;
+      if (u >= ks) continue;
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          if (i == 8 && r != 7) continue;  // column 64 comes from group 7, shift 8
+          const int vv = 8 * r + i;
+          if (vv < ks)
+            out[(size_t)side * ks * ks + (size_t)(ks - 1 - u) * ks + (ks - 1 - vv)] =
+                ((ini >> ug) & 1u) ? v[side * 16 + i] : 0.f;
+        }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+sd_status launch_bank_grad_tc(const RenderParams& P, const float* gout, const unsigned* bm,
+                              int words, int ntx, int nty, float* gbank, float* parts_buf,
+                              int parts, int* err, cudaStream_t s) {
+  const int ks = P.ks;
+  // at least 80 KB: two CTAs per SM, the tensor memory's 512 columns
+  const size_t smem = std::max(bg_smem(ks), (size_t)80 * 1024);
+  SD_CUDA_TRY(cudaFuncSetAttribute(bank_grad_tc_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool quad = P.fmode == SD_FIELD_QUADRANT;
+  dim3 grid(n_keys(P), P.NL, parts);
+  bank_grad_tc_kernel<<<grid, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty,
+                                                parts > 1 || quad ? parts_buf : gbank, parts, err);
+  sd_status st = launch_status();
+  if (st != SD_OK) return st;
+  if (quad) {
+    const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
+    bank_fold_quadrant<<<1024, 256, 0, s>>>(parts_buf, n, parts, P.FC * P.Z * P.NL, ks, gbank);
+    return launch_status();
+  }
+  if (parts == 1) return SD_OK;
+  const size_t n = (size_t)n_keys(P) * P.NL * 2 * ks * ks;
+  bank_parts_reduce<<<1024, 256, 0, s>>>(parts_buf, n, parts, gbank);
+  return launch_status();
+}
+
 }  // namespace sd
 
 extern "C" {
@@ -696,6 +976,62 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
     if (r != SD_OK) return r;
   }
   return SD_OK;
+}
+
+sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,
+                                              int H, int W, size_t* bytes) {
+  using namespace sd;
+  if (!bytes) return SD_ERR_ARG;
+  RenderParams P;
+  sd_status st = setup_bwd(layout, N, C, H, W, P);
+  if (st != SD_OK) return st;
+  int tx, ty;
+  bwd_tiles(H, W, &tx, &ty);
+  *bytes = 256 + bitmap_bytes(N, tx, ty, n_keys(P)) + (size_t)BANK_PARTS * bank_bytes(P);
+  return SD_OK;
+}
+
+sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, const float* depth_m,
+                                    const sd_bank_layout* layout, int N, int C, int H, int W,
+                                    float* grad_bank, void* workspace, size_t workspace_bytes,
+                                    void* stream) {
+  using namespace sd;
+  if (!grad_out || !aif || !depth_m || !grad_bank) return SD_ERR_ARG;
+  RenderParams P;
+  sd_status st = setup_bwd(layout, N, C, H, W, P);
+  if (st != SD_OK) return st;
+  if (P.ks > 16 * BG_MAXUG || bg_smem(P.ks) > 227 * 1024) return SD_ERR_UNSUPPORTED;
+  P.aif = aif;
+  P.depth = depth_m;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bank_elems = (size_t)P.FC * P.Z * P.NL * 2 * P.ks * P.ks;
+  int tx, ty;
+  bwd_tiles(H, W, &tx, &ty);
+  const size_t words = bitmap_words(n_keys(P));
+  const size_t need = 256 + bitmap_bytes(N, tx, ty, n_keys(P));
+  const size_t need_min = need + (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
+  if (!workspace || workspace_bytes < need_min || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return SD_ERR_ARG;
+  int* err = reinterpret_cast<int*>(workspace);
+  SD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (N == 0 || H == 0 || W == 0) {
+    SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
+    return SD_OK;
+  }
+  unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + 256);
+  int parts = 1;
+  for (int q = BANK_PARTS; q > 1; q >>= 1)
+    if (workspace_bytes >= need + (size_t)q * bank_bytes(P)) {
+      parts = q;
+      break;
+    }
+  float* parts_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+  dim3 g1(tx, ty, N);
+  slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
+  st = launch_status();
+  if (st != SD_OK) return st;
+  return launch_bank_grad_tc(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf, parts,
+                             err, s);
 }
 
 }  // extern "C"
