@@ -571,7 +571,8 @@ def pipeline_compare(sd, dev, reps=5):
     image and the bank, adjoint trace of the bank gradient.  Plain FP32 (one
     trace block per request, FP32 bank and images, eager launches) against
     the batched BF16 pipeline (persistent batched trace writing a BF16 bank,
-    BF16 images rendered on the tensor cores, FP32 gradients, the whole step
+    BF16 images rendered on the tensor cores, FP32 gradients (the bank's on the
+    tensor cores from BF16-rounded weighted output gradients), the whole step
     replayed from one CUDA graph), with the bank error of both against the
     FP64 oracle, the difference of the two renders and each stage timed
     alone (eager launches)."""
@@ -610,8 +611,13 @@ def pipeline_compare(sd, dev, reps=5):
         sd._lib.check(L.sd_dp_render_backward(
             sd.api._ptr(gout), sd.api._ptr(aif), sd.api._ptr(depth), sd.api._ptr(bank),
             sd.api.ctypes.byref(lc), B, 3, H, Wd, sd.api._DT[aif.dtype], sd.api._ptr(gaif),
-            sd.api._ptr(gbank), sd.api._ptr(ws), ws.numel(), sd.api._stream()),
-            "sd_dp_render_backward")
+            sd.api._ptr(gbank) if gbank is not None else None, sd.api._ptr(ws), ws.numel(),
+            sd.api._stream()), "sd_dp_render_backward")
+
+    def render_bwd_tc(lay, aif, bank, gaif, gbank, ws_img, ws_bank):
+        # image gradient on CUDA cores, bank gradient on the tensor cores
+        render_bwd(lay, aif, bank, gaif, None, ws_img)
+        sd.dp_render_bank_grad_tc(gout, aif, depth, lay, out=gbank, workspace=ws_bank)
 
     # plain FP32
     lay32, aif32, out32, gaif32, gbank32, ws32, greq32 = make(torch.float32)
@@ -633,11 +639,13 @@ def pipeline_compare(sd, dev, reps=5):
     bt.tune(os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt"))
 
     ws_tc = torch.empty(sd.api.render_tc_workspace(lay16), dtype=torch.uint8, device=dev)
+    ws_bg = torch.empty(sd.api.bank_grad_tc_workspace(lay16, B, 3, H, Wd), dtype=torch.uint8,
+                        device=dev)
 
     def batched():
         bank16, _ = bt.run()
         sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16, workspace=ws_tc)
-        render_bwd(lay16, aif16, bank16, gaif16, gbank16, ws16)
+        render_bwd_tc(lay16, aif16, bank16, gaif16, gbank16, ws16, ws_bg)
         sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank16, max_ks=ks,
                                  max_n=c["n_grid"], grad_req=greq16)
 
@@ -671,8 +679,8 @@ def pipeline_compare(sd, dev, reps=5):
             "trace": _timed(lambda: bt.run(), stream, reps),
             "render": _timed(lambda: sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16,
                                                      workspace=ws_tc), stream, reps),
-            "render_bwd": _timed(lambda: render_bwd(lay16, aif16, bank16, gaif16, gbank16, ws16),
-                                 stream, reps),
+            "render_bwd": _timed(lambda: render_bwd_tc(lay16, aif16, bank16, gaif16, gbank16, ws16,
+                                                       ws_bg), stream, reps),
             "trace_adjoint": _timed(lambda: sd.dp_psf_trace_backward(
                 lens, sensor, req_dev, n_req, gbank16, max_ks=ks, max_n=c["n_grid"],
                 grad_req=greq16), stream, reps)}}
