@@ -173,6 +173,23 @@ def setup_dist(args):
     return world, rank, local, pg
 
 
+def replica_step_ms(step_ms, dist, device=None):
+    """The job's step time over N replicas: the slowest rank's (max over
+    ranks; every rank gets it)."""
+    if not dist:
+        return step_ms
+    import torch
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(rays_per_step, world, step_ms):
+    """Whole-job throughput in G rays/s: every replica traces its own bank
+    (weak scaling, no exchange between ranks)."""
+    return world * rays_per_step / (step_ms * 1e-3) / 1e9
+
+
 def build_inputs(device, n_requests=0, image=0):
     """The benchmark workload; n_requests / image shrink it for profiling
     (every k-th bank request, an image x image render) -- never used for a
@@ -289,10 +306,7 @@ def run_ours(args, world, rank, local, dist):
     t_trace, t_render, t_bimg, t_bbank, t_adj = (phase(0, 1), phase(1, 2), phase(2, 3),
                                                  phase(3, 4), phase(4, 5))
     step_ms = sum(ev[i][0].elapsed_time(ev[i][5]) for i in range(args.steps)) / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = replica_step_ms(step_ms, dist, dev)
 
     # end to end through the public API: pinned host inputs in, DP image out
     h_req = torch.from_numpy(np.frombuffer(req_dev.cpu().numpy().tobytes(), np.uint8).copy()) \
@@ -317,6 +331,7 @@ def run_ours(args, world, rank, local, dist):
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    e2e_ms = replica_step_ms(e2e_ms, dist, dev)
     h2d = h_req.numel() + h_aif.numel() * 4 + h_depth.numel() * 4
     d2h = h_out.numel() * 4  # the DP image (gradients stay on the device)
 
@@ -347,8 +362,8 @@ def run_ours(args, world, rank, local, dist):
     tflops = {k: f / (ms * 1e-3) / 1e12 for k, (f, ms) in phases.items()}
     dominant = max(phases, key=lambda k: phases[k][1])
     achieved = tflops[dominant]
-    value = world * rays_per_step / (step_ms * 1e-3) / 1e9
-    e2e_value = world * rays_per_step / (e2e_ms * 1e-3) / 1e9
+    value = replica_value(rays_per_step, world, step_ms)
+    e2e_value = replica_value(rays_per_step, world, e2e_ms)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "G rays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
