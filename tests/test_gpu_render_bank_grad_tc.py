@@ -93,3 +93,34 @@ def test_bank_grad_tc_any_depth(sdlib, case):
     print(f"any depth: max err {err.max():.3e}, max ref {np.abs(ref).max():.3e}, "
           f"max err / magnitude sum {np.max(err / np.maximum(mag, 1e-30)):.3e}")
     assert np.all(err <= 2.0 ** -8 * mag + 1e-4 * np.abs(ref).max())
+
+
+def test_bank_grad_tc_full_size(sdlib):
+    """1024 x 1024 RGB, the 32 x 32 x 3 bank shape at 65 x 65, Perlin depth:
+    against the CUDA-core bank gradient (FP32 accumulation of the same BF16
+    image; itself parity-tested against the oracle), elementwise within
+    2^-8 of the magnitude sum (the CUDA-core adjoint of |G| and |I|) plus
+    1e-4 max."""
+    sd = sdlib
+    cfg = W.config_full_forward()
+    rng = np.random.default_rng(12)
+    H = Wd = 1024
+    aif = W.aif_pink(1, 3, H, Wd, seed=1).astype(np.float32)
+    depth = W.depth_perlin(1, H, Wd, seed=2).astype(np.float32)
+    bank = rand_bank(rng, 32, 32, 3, 65)
+    fh, dm = cfg["field_h_mm"], cfg["depths_mm"] / 1000.0
+    lay = sd.BankLayout(fh, dm, 3, 65, cfg["pitch_mm"], dtype=torch.bfloat16)
+    a = torch.tensor(aif, device="cuda").to(torch.bfloat16)
+    b = torch.tensor(bank, dtype=torch.float32, device="cuda").to(torch.bfloat16).reshape(-1)
+    d = torch.tensor(depth, device="cuda")
+    g = torch.randn((1, 6, H, Wd), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    ws = torch.empty(sd.api.bank_grad_tc_workspace(lay, 1, 3, H, Wd), dtype=torch.uint8,
+                     device="cuda")
+    got = sd.dp_render_bank_grad_tc(g, a, d, lay, workspace=ws).reshape(-1)
+    _, ref = sd.dp_render_backward(g, a, d, b, lay, need_aif=False)
+    _, mag = sd.dp_render_backward(g.abs(), a.abs(), d, b, lay, need_aif=False)
+    torch.cuda.synchronize()
+    assert int(ws[:4].view(torch.int32).item()) == 0
+    ref, mag = ref.reshape(-1), mag.reshape(-1)
+    err = (got - ref).abs()
+    assert bool((err <= 2.0 ** -8 * mag + 1e-4 * ref.abs().max()).all())
