@@ -664,7 +664,7 @@ __device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err
   return false;
 }
 
-__global__ void __launch_bounds__(BG_NT, 1) bank_grad_tc_kernel(
+__global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
     const RenderParams P, const float* __restrict__ gout, const unsigned* __restrict__ bm,
     int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -683,6 +683,11 @@ __global__ void __launch_bounds__(BG_NT, 1) bank_grad_tc_kernel(
   const unsigned kbit = 1u << (key & 31);
   const int c_lo = (P.NL == P.C) ? lam : 0, c_hi = (P.NL == P.C) ? lam + 1 : P.C;
 
+  // the gradient rows' zero borders (columns j < 16 and j >= 80) once
+  for (int i = tid; i < 2 * RT_Y * 32; i += BG_NT) {
+    const int row = i >> 5, jj = i & 31;
+    gw[row * BG_GW + (jj < 16 ? jj : 64 + jj)] = 0;
+  }
   if (warp == 0) tc::tmem_alloc(&s_tmem, 256);
   if (tid == 0) {
     for (int b = 0; b < BG_NB; ++b) {
@@ -721,46 +726,79 @@ __global__ void __launch_bounds__(BG_NT, 1) bank_grad_tc_kernel(
           const unsigned short* im =
               reinterpret_cast<const unsigned short*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
           // 8 columns (16 bytes) per item: one vector load inside the image
-          // when aligned, clamped scalar loads at the edges
-          for (int i = tid; i < rows_st * (BG_IW / 8); i += BG_NT) {
-            const int r = i / (BG_IW / 8), q = i - r * (BG_IW / 8);
-            const size_t ro = (size_t)min(max(y0 + r - p, 0), P.H - 1) * P.W;
-            const int xa = x0 - p + 8 * q;
-            const unsigned short* src = im + ro + xa;
-            uint4 w;
-            if (xa >= 0 && xa + 8 <= P.W && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-              w = *reinterpret_cast<const uint4*>(src);
-            } else {
-              uint32_t e[8];
+          // when aligned, clamped scalar loads at the edges.  A thread loads
+          // four items before storing them (their latencies overlap).
+          constexpr int BG_IPR = 4;  // items per thread and round
+          const int nimg = rows_st * (BG_IW / 8);
+          for (int i0 = 0; i0 < nimg; i0 += BG_IPR * BG_NT) {
+            uint4 iv[BG_IPR];
 #pragma unroll
-              for (int k = 0; k < 8; ++k) e[k] = im[ro + min(max(xa + k, 0), P.W - 1)];
-              w = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
-                             e[6] | (e[7] << 16));
-            }
-            *reinterpret_cast<uint4*>(img + (size_t)r * BG_IWB + 16 * q) = w;
-          }
-          const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
-          const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
-          for (int i = tid; i < RT_Y * BG_GW; i += BG_NT) {
-            const int r = i / BG_GW, j = i - r * BG_GW, x = j - 16;
-            const int yy = y0 + r, xx = x0 + x;
-            float gl = 0.f, gr = 0.f;
-            if (x >= 0 && x < TXB && yy < P.H && xx < P.W) {
-              int k0;
-              float t;
-              select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &k0, &t);
-              const float w = (k0 == key) ? (two ? 1.f - t : 1.f)
-                                          : ((two && k0 + 1 == key) ? t : 0.f);
-              if (w != 0.f) {
-                gl = w * goL[(size_t)yy * P.W + xx];
-                gr = w * goR[(size_t)yy * P.W + xx];
+            for (int t = 0; t < BG_IPR; ++t) {
+              const int i = i0 + tid + t * BG_NT;
+              iv[t] = make_uint4(0u, 0u, 0u, 0u);
+              if (i < nimg) {
+                const int r = i / (BG_IW / 8), q = i - r * (BG_IW / 8);
+                const size_t ro = (size_t)min(max(y0 + r - p, 0), P.H - 1) * P.W;
+                const int xa = x0 - p + 8 * q;
+                const unsigned short* src = im + ro + xa;
+                if (xa >= 0 && xa + 8 <= P.W && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                  iv[t] = __ldg(reinterpret_cast<const uint4*>(src));
+                } else {
+                  uint32_t e[8];
+#pragma unroll
+                  for (int k = 0; k < 8; ++k) e[k] = im[ro + min(max(xa + k, 0), P.W - 1)];
+                  iv[t] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16),
+                                     e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+                }
               }
             }
-            const unsigned short bl = __bfloat16_as_ushort(__float2bfloat16_rn(gl));
-            const unsigned short br = __bfloat16_as_ushort(__float2bfloat16_rn(gr));
-            gw[r * BG_GW + j] = bl;
-            gw[RT_Y * BG_GW + r * BG_GW + j] = br;
-            if ((bl | br) & 0x7fffu) atomicOr(&s_use, 1u << r);
+#pragma unroll
+            for (int t = 0; t < BG_IPR; ++t) {
+              const int i = i0 + tid + t * BG_NT;
+              if (i < nimg) {
+                const int r = i / (BG_IW / 8), q = i - r * (BG_IW / 8);
+                *reinterpret_cast<uint4*>(img + (size_t)r * BG_IWB + 16 * q) = iv[t];
+              }
+            }
+          }
+          // the tile's 2048 pixels, 8 per thread in two rounds of 4: depths and
+          // output gradients loaded first, then the selection and the
+          // weighted BF16 values
+          const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
+          const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
+          constexpr int BG_PPR = 4;
+          for (int t0 = 0; t0 < RT_Y * TXB / BG_NT; t0 += BG_PPR) {
+            float dq[BG_PPR], gq[BG_PPR][2];
+#pragma unroll
+            for (int t = 0; t < BG_PPR; ++t) {
+              const int i = tid + (t0 + t) * BG_NT, r = i / TXB, x = i - r * TXB;
+              const int yy = y0 + r, xx = x0 + x;
+              const bool in = yy < P.H && xx < P.W;
+              const size_t o = (size_t)yy * P.W + xx;
+              dq[t] = in ? P.depth[(size_t)n * P.H * P.W + o] : 1.f;
+              gq[t][0] = in ? goL[o] : 0.f;
+              gq[t][1] = in ? goR[o] : 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < BG_PPR; ++t) {
+              const int i = tid + (t0 + t) * BG_NT, r = i / TXB, x = i - r * TXB;
+              const int yy = y0 + r, xx = x0 + x;
+              float gl = 0.f, gr = 0.f;
+              if (yy < P.H && xx < P.W) {
+                int k0;
+                float tt;
+                select_slice(P, yy, xx, dq[t], &k0, &tt);
+                const float w = (k0 == key) ? (two ? 1.f - tt : 1.f)
+                                            : ((two && k0 + 1 == key) ? tt : 0.f);
+                gl = w * gq[t][0];
+                gr = w * gq[t][1];
+              }
+              const unsigned short bl = __bfloat16_as_ushort(__float2bfloat16_rn(gl));
+              const unsigned short br = __bfloat16_as_ushort(__float2bfloat16_rn(gr));
+              gw[r * BG_GW + x + 16] = bl;
+              gw[RT_Y * BG_GW + r * BG_GW + x + 16] = br;
+              if ((bl | br) & 0x7fffu) atomicOr(&s_use, 1u << r);
+            }
           }
           tc::fence_async_smem();  // the staged image, read by the tensor core
           __syncthreads();
