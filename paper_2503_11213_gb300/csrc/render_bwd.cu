@@ -357,8 +357,35 @@ __global__ void __launch_bounds__(TX * RT_Y / SB, 1)
 // ---------------------------------------------------------------------------
 // 3. bank gradient, one block per (slice key, wavelength)
 // ---------------------------------------------------------------------------
+// The tiles t0 .. t0 + NT - 1 (of ntiles) of this block's part whose bitmap
+// holds the slice, as offsets from t0 in ascending order: one tile per
+// thread, compacted with warp ballots, so that the bitmap loads of NT tiles
+// are in flight together (a scan of one tile after the other waits for each
+// load in turn).  Every thread of the block calls it; returns the count.
+template <int NT>
+__device__ int slice_tiles(const unsigned* __restrict__ bm, int words, int kw, unsigned kbit,
+                           size_t t0, size_t ntiles, int parts, int part, int* s_list,
+                           int* s_wc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t t = t0 + tid;
+  const bool use =
+      t < ntiles && (int)(t % (size_t)parts) == part && (bm[t * words + kw] & kbit) != 0u;
+  const unsigned bal = __ballot_sync(0xffffffffu, use);
+  if (lane == 0) s_wc[warp] = __popc(bal);
+  __syncthreads();
+  int pos = __popc(bal & ((1u << lane) - 1u)), tot = 0;
+  for (int w = 0; w < NT / 32; ++w) {
+    const int c = s_wc[w];
+    pos += w < warp ? c : 0;
+    tot += c;
+  }
+  if (use) s_list[pos] = tid;
+  __syncthreads();
+  return tot;
+}
+
 template <int NT, int SPT, class TI>
-__global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams P,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(const RenderParams P,
                                                              const float* __restrict__ gout,
                                                              const unsigned* __restrict__ bm,
                                                              int words, int ntx, int nty,
@@ -391,12 +418,17 @@ __global__ void __launch_bounds__(NT) render_bwd_bank_kernel(const RenderParams 
   const int kw = key >> 5;
   const unsigned kbit = 1u << (key & 31);
   const int c_lo = (P.NL == P.C) ? lam : 0, c_hi = (P.NL == P.C) ? lam + 1 : P.C;
-  for (int n = 0; n < P.N; ++n)
-    for (int ty = 0; ty < nty; ++ty)
-      for (int tx = 0; tx < ntx; ++tx) {
-        size_t tile = ((size_t)n * nty + ty) * ntx + tx;
-        if ((int)(tile % (size_t)parts) != part) continue;
-        if (!(bm[tile * words + kw] & kbit)) continue;
+  // the tiles of this part that use the slice, in ascending order
+  __shared__ int s_list[NT], s_twc[NT / 32];
+  const size_t ntiles = (size_t)P.N * nty * ntx;
+  for (size_t t0 = 0; t0 < ntiles; t0 += NT)
+    for (int li = 0, nlist = slice_tiles<NT>(bm, words, kw, kbit, t0, ntiles, parts, part,
+                                             s_list, s_twc);
+         li < nlist; ++li) {
+        const size_t tile = t0 + s_list[li];
+        const int n = (int)(tile / ((size_t)nty * ntx));
+        const int rem = (int)(tile - (size_t)n * nty * ntx);
+        const int ty = rem / ntx, tx = rem - ty * ntx;
         const int tx0 = tx * TXB, ty0 = ty * RT_Y;
         for (int c = c_lo; c < c_hi; ++c) {
           __syncthreads();
@@ -709,12 +741,17 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   int c_row = 0, visits = 0;
   unsigned inited = 0;  // kernel-row groups written (MMA thread)
 
-  for (int n = 0; n < P.N; ++n)
-    for (int ty = 0; ty < nty; ++ty)
-      for (int tx = 0; tx < ntx; ++tx) {
-        const size_t tile = ((size_t)n * nty + ty) * ntx + tx;
-        if ((int)(tile % (size_t)parts) != part) continue;
-        if (!(bm[tile * words + kw] & kbit)) continue;
+  // the tiles of this part that use the slice, in ascending order
+  __shared__ int s_list[BG_NT], s_twc[BG_NT / 32];
+  const size_t ntiles = (size_t)P.N * nty * ntx;
+  for (size_t t0 = 0; t0 < ntiles; t0 += BG_NT)
+    for (int li = 0, nlist = slice_tiles<BG_NT>(bm, words, kw, kbit, t0, ntiles, parts, part,
+                                                s_list, s_twc);
+         li < nlist; ++li) {
+        const size_t tile = t0 + s_list[li];
+        const int n = (int)(tile / ((size_t)nty * ntx));
+        const int rem = (int)(tile - (size_t)n * nty * ntx);
+        const int ty = rem / ntx, tx = rem - ty * ntx;
         const int x0 = tx * TXB, y0 = ty * RT_Y;
         for (int c = c_lo; c < c_hi; ++c, ++visits) {
           // the previous visit's MMAs have read the image, the gradients and
