@@ -433,11 +433,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
         for (int c = c_lo; c < c_hi; ++c) {
           __syncthreads();
           const TI* img = reinterpret_cast<const TI*>(P.aif) + ((size_t)n * P.C + c) * P.H * P.W;
-          for (int i = tid; i < HH * S; i += NT) {
-            int r = i / S, cc = i - r * S;
-            int yy = min(max(ty0 + r - p, 0), P.H - 1);
-            int xx = min(max(tx0 + cc - p, 0), P.W - 1);
-            halo[i] = to_f32<TI>(img[(size_t)yy * P.W + xx]);
+          // one warp per halo row (no division by the runtime row length)
+          for (int r = tid >> 5; r < HH; r += NT / 32) {
+            const TI* src = img + (size_t)min(max(ty0 + r - p, 0), P.H - 1) * P.W;
+#pragma unroll 4
+            for (int cc = tid & 31; cc < S; cc += 32)
+              halo[r * S + cc] = to_f32<TI>(src[min(max(tx0 + cc - p, 0), P.W - 1)]);
           }
           const float* goL = gout + (((size_t)n * 2 * P.C + c) * P.H) * P.W;
           const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
