@@ -649,6 +649,11 @@ sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const un
                               int parts, cudaStream_t s) {
   int KU = (P.ks + SEG - 1) / SEG * SEG;
   int nstrip = P.ks * (KU / SEG);
+  // one strip per thread where the strips fill 512-608 threads (ks = 61..65:
+  // 6.76 -> 6.51 ms at 1024x1024x3 against 256 threads x 3 strips, of
+  // which a quarter of the slots idle)
+  if (nstrip > 512 && nstrip <= 608)
+    return launch_bank_bwd<608, 1, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
   if (nstrip <= 256 * 3)
     return launch_bank_bwd<256, 3, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
   return launch_bank_bwd<512, 4, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
