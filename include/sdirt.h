@@ -337,6 +337,15 @@ typedef struct sd_bank_layout {
   float pitch_mm;           /* sensor pixel pitch of the rendered image */
   float reserved2;
 } sd_bank_layout;
+/*
+ * Every call that takes a layout validates it on the host before any CUDA
+ * call: SD_ERR_ARG for a null layout or height/depth array, n_field outside
+ * 1..SD_MAX_BANK_FIELDS, n_depth outside 1..SD_MAX_BANK_DEPTHS, n_lambda < 1,
+ * ks < 1 or even, pitch_mm <= 0 (or NaN), field heights or depths not
+ * strictly ascending, a depth <= 0, a field_mode other than the two above,
+ * or a quadrant bank whose first height is negative; SD_ERR_UNSUPPORTED for
+ * ks > 127.
+ */
 
 /*
  * aif (N,C,H,W) and out (N,2C,H,W) in image_dtype (SD_F32 / SD_BF16 /
