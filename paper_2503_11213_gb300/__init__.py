@@ -8,6 +8,7 @@ from .api import (SD_FIELD_QUADRANT, SD_FIELD_RADIAL, BankLayout, BatchedTrace, 
                   dp_psf_trace_backward, dp_render, dp_render_backward, dp_render_map, dp_render_tc,
                   f_number_table, make_requests, render_backward_workspace, trace_hits,
                   PsfMLP, mlp_psf_map, MLP_SHAPES, dp_render_bank_grad_tc)
+from .bank_io import lens_sha256, load_bank, save_bank  # noqa: F401
 from .autograd import (DPRenderFunction, DPTraceFunction, dp_psf_trace_autograd,  # noqa: F401
                        dp_render_autograd)
 from ._lib import (SD_BF16, SD_BIN_BILINEAR, SD_BIN_HARD, SD_F16, SD_F32, SD_NORM_JOINT,  # noqa: F401
