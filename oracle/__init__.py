@@ -24,6 +24,11 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                    force of the supplement's unfold/fold formulation; the
                    quadrant bank against a per-pixel map of PSFs traced at
                    each pixel's own signed field point
+  render_bank_bwd  pinned by the adjoint identities <G, R(I, B)> =
+                   <R*_I(G), I> = <R*_B(G), B> against the forward (radial
+                   and quadrant banks) and by central differences of it
+  render_select    pinned by a brute-force nearest-height / depth-bracket
+                   search
 """
 from __future__ import annotations
 
