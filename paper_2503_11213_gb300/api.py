@@ -209,6 +209,8 @@ def f_number_table(table, f_number, lambda_nm=587.5618, focus_mm=1000.0):
 
 
 def batched_workspace_bytes(n_req, total):
+    """Device workspace bytes of the batched trace of n_req requests writing
+    total output elements (sd_dp_psf_trace_batched_workspace)."""
     n = ctypes.c_size_t(0)
     L.check(L.lib().sd_dp_psf_trace_batched_workspace(n_req, total, ctypes.byref(n)),
             "sd_dp_psf_trace_batched_workspace")
@@ -324,6 +326,8 @@ def dp_render(aif, depth_m, bank, layout: BankLayout, out=None):
 
 
 def render_tc_workspace(layout: BankLayout):
+    """Device workspace bytes of dp_render_tc for this bank layout: the error
+    flag header and the per-call BF16 re-layout of the bank."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_tc_workspace(ctypes.byref(lay), ctypes.byref(n)),
@@ -354,6 +358,8 @@ def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=Non
 
 
 def render_backward_workspace(layout: BankLayout, N, C, H, W):
+    """Device workspace bytes of dp_render_backward's bank gradient: the
+    per-tile slice bitmap and two partial banks."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_backward_workspace(ctypes.byref(lay), N, C, H, W,
@@ -363,6 +369,8 @@ def render_backward_workspace(layout: BankLayout, N, C, H, W):
 
 
 def bank_grad_tc_workspace(layout: BankLayout, N, C, H, W):
+    """Device workspace bytes of dp_render_bank_grad_tc: the error flag header,
+    the per-tile slice bitmap and two partial banks."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_bank_grad_tc_workspace(ctypes.byref(lay), N, C, H, W,

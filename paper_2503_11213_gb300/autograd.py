@@ -39,6 +39,8 @@ class DPRenderFunction(torch.autograd.Function):
 
 
 def dp_render_autograd(aif, bank, depth_m, layout: BankLayout):
+    """dp_render with gradients for aif and bank (FP32) through the render
+    adjoint of the CUDA library."""
     return DPRenderFunction.apply(aif, bank, depth_m, layout)
 
 
@@ -85,5 +87,9 @@ class DPTraceFunction(torch.autograd.Function):
 
 def dp_psf_trace_autograd(theta, lens: Lens, pids, sensor: DPSensor, req_dev, n_req, total,
                           max_ks, max_n=512, norm=L.SD_NORM_PER_RAY):
+    """Bilinear PSFs of the requests as a function of the lens parameters
+    theta (the parameter ids pids of lens), with gradients through the
+    adjoint trace; norm is per-ray or none (a joint normalisation has no
+    useful gradient)."""
     return DPTraceFunction.apply(theta, lens, pids, sensor, req_dev, n_req, total, max_ks,
                                  max_n, norm)
