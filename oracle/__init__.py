@@ -16,9 +16,13 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                    and disparity sign; absolute PSF shapes of the aspheric lens
                    are "parity unpinned" beyond these properties
   trace_grad       pinned by FP64 central differences of trace_functional
-  mlp_psf          pinned by an independent float64 evaluation of the same
-                   network with library linear layers, and closed forms
-                   (biases only; normalised-input corners)
+  mlp_psf          pinned through all five hidden layers by signed, scaled
+                   permutation networks whose outputs follow one path back
+                   to one input (a transposed weight, a dropped layer, a
+                   missing ReLU, a wrong input order, a missing clamp or a
+                   per-plane normalisation each fail a pin), by a bias chain
+                   through every layer, the biases-only closed form and the
+                   normalised-input corners
   render_*         pinned by the delta-PSF and constant-image identities, a
                    shift-invariant kernel against scipy correlation and brute
                    force of the supplement's unfold/fold formulation; the
