@@ -235,6 +235,7 @@ def run_ours(args, world, rank, local, dist):
     ws = torch.empty(max(1, sd.api.render_backward_workspace(layout, *aif.shape)),
                      dtype=torch.uint8, device=dev)
     greq = torch.empty((n_req, 32, 8), dtype=torch.float32, device=dev)
+    swept = torch.zeros((n_req, 2), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -264,7 +265,10 @@ def run_ours(args, world, rank, local, dist):
 
     def trace_bwd():
         sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, g_adj, max_ks=cfg["ks"],
-                                 max_n=cfg["n_grid"], norm=sd.SD_NORM_PER_RAY, grad_req=greq)
+                                 max_n=cfg["n_grid"], norm=sd.SD_NORM_PER_RAY, grad_req=greq,
+                                 swept=swept)
+
+    fp32 = measure_fp32_peak(sd, dev, local)
 
     for _ in range(args.warmup):
         trace()
@@ -273,6 +277,14 @@ def run_ours(args, world, rank, local, dist):
         trace_bwd()
     torch.cuda.synchronize()
     rays_per_step = int(stats[:, 0].sum().item())
+    # rays whose reverse sweep carries a contribution (non-zero splat
+    # gradient), and the thread slots that ran it, in the adjoint of the step
+    swept_rays = int(swept[:, 0].sum().item())
+    swept_slots = int(swept[:, 1].sum().item())
+    # the adjoint traces again only the requests whose gradient patch is
+    # not all zero (the others have an exactly zero gradient)
+    live = g_adj.view(n_req, -1).ne(0).any(dim=1)
+    retraced_rays = int(stats[live, 0].sum().item())
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     if dist:
@@ -339,7 +351,8 @@ def run_ours(args, world, rank, local, dist):
     peaks = load_peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    derived_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    fp32_peak_tflops = fp32["tflops"] if fp32.get("tflops") else derived_tflops
     fpr = flops_per_ray(cfg["lens"])
     tr_ms = statistics.mean(t_trace)
     rd_ms = statistics.mean(t_render)
@@ -351,13 +364,16 @@ def run_ours(args, world, rank, local, dist):
     # algorithmic work of each phase (FMA = 2 flops)
     render_flops = H * Wd * 3 * 2 * 2 * cfg["ks"] ** 2 * 2  # px, ch, L/R, 2 slices, FMA
     afr = adjoint_flops_per_ray(cfg["lens"])
+    # the adjoint: every launched ray is traced again (the forward's work),
+    # the reverse sweep counts only for the rays that carry a contribution
+    adj_flops = retraced_rays * fpr + swept_rays * (afr - fpr)
     phases = {  # kernel: (flops per launch, ms per launch measured on the stream)
         "trace_bin_kernel": (rays_per_step * fpr, tr_ms),
         "render_fwd_kernel": (render_flops, rd_ms),
         # image and bank gradients: the forward's products once each
         "render_bwd_img_kernel": (render_flops, bi_ms),
         "render_bwd_bank_kernel": (render_flops, bb_ms),
-        "trace_adj_kernel": (rays_per_step * afr, adj_ms),
+        "trace_adj_kernel": (adj_flops, adj_ms),
     }
     tflops = {k: f / (ms * 1e-3) / 1e12 for k, (f, ms) in phases.items()}
     dominant = max(phases, key=lambda k: phases[k][1])
@@ -384,9 +400,16 @@ def run_ours(args, world, rank, local, dist):
                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / fp32_peak_tflops, 4),
                      "traffic": TRAFFIC_BYTES.get(dominant),
-                     "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                    f"{sm_max_mhz:.0f} MHz (max SM clock)",
+                     "peak_source": ("measured: FMA-chain probe on this GPU in this run, "
+                                     "median of its timed launches" if fp32.get("tflops") else
+                                     f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                     f"x {sm_max_mhz:.0f} MHz (max SM clock)"),
+                     "fp32_probe": fp32,
+                     "derived_peak_at_max_clock": round(derived_tflops, 2),
                      "flops_per_ray": fpr, "adjoint_flops_per_ray": afr,
+                     "adjoint_retraced_rays": retraced_rays,
+                     "adjoint_swept_rays": swept_rays, "adjoint_swept_slots": swept_slots,
+                     "adjoint_flops": adj_flops,
                      "render_flops": render_flops,
                      "kernels": {k: {"ms": round(phases[k][1], 4), "tflops": round(v, 3),
                                      "frac": round(v / fp32_peak_tflops, 4)}
@@ -394,9 +417,10 @@ def run_ours(args, world, rank, local, dist):
         "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_ms, 4)},
-        # trace, render, bwd image, slice bitmap, bwd bank, bank parts reduce,
-        # adjoint trace, lens reduce
-        "gpu_launches": 8 * args.steps,
+        # trace; render; image gradient (selection table, bank re-layout, two
+        # strip phases); bank gradient (slice bitmap, bank pass, parts
+        # reduce); adjoint trace and lens reduce
+        "gpu_launches": 11 * args.steps,
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
     }
@@ -411,6 +435,39 @@ def run_ours(args, world, rank, local, dist):
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
     return line
+
+
+def measure_fp32_peak(sd, dev, index, reps=40):
+    """FP32 peak of this GPU: the library's FMA-chain probe (8 blocks of 256
+    threads per SM, 16 independent chains per thread) timed with CUDA events,
+    clocks sampled while it runs.  TFLOP/s = median over the timed launches;
+    flops per SM clock from the median SM clock seen."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 8 * n_sm, 1 << 15
+    sink = torch.empty(blocks * 256, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        flops = sd.fp32_peak_launch(sink, blocks, iters)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    with ClockSampler(index) as clk:
+        for a, b in ev:
+            a.record(stream)
+            sd.fp32_peak_launch(sink, blocks, iters)
+            b.record(stream)
+        torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    med = statistics.median(ms)
+    c = clk.summary()
+    res = {"tflops": round(flops / (med * 1e-3) / 1e12, 3),
+           "tflops_best": round(flops / (ms[0] * 1e-3) / 1e12, 3),
+           "ms_per_launch": round(med, 4), "flops_per_launch": flops, "launches": reps,
+           "sm_mhz": c["sm_mhz"], "clock_reasons": c["reasons"]}
+    if c["sm_mhz"]:
+        res["flops_per_sm_clock"] = round(flops / (med * 1e-3) / (c["sm_mhz"] * 1e6) / n_sm, 2)
+    return res
 
 
 def batched_compare(sd, dev, reps=5):
@@ -780,7 +837,7 @@ def quadrant_compare(sd, dev, reps=5):
 
 
 def paper_workload(sd, dev, reps=5):
-    """The paper's own timed path (Sec. 4 implementation details, Table S3):
+    """The paper's own timed path (Sec. 5.1 implementation details, Table S3):
     RF50 (Table S1) at F/4, 550 nm, focus 1 m, a DP PSF for every pixel of a
     512 x 768 depth map over 0.5-20 m (64 x 64 pupil grid = 4096 samples,
     21 x 21 patches), then the DP render of a 512 x 768 RGB image from that
@@ -821,7 +878,7 @@ def paper_workload(sd, dev, reps=5):
     peaks = load_peaks()
     if peaks.get("hbm_gbs"):
         res["render_hbm_frac_f32"] = round(res["f32"]["render_gbs"] / peaks["hbm_gbs"], 3)
-    # the paper's render-time PSF source: the MLP of Sec. 3.3 (5 x 512, 2 ks^2
+    # the paper's render-time PSF source: the MLP of Sec. 3.2 (5 x 512, 2 ks^2
     # outputs) for every pixel, He-initialised (no trained weights here),
     # then the same render from its map
     rng = np.random.default_rng(0)

@@ -49,7 +49,10 @@ enum {
   SD_ERR_LENS = 2,         /* invalid prescription (see sd_lens_load) */
   SD_ERR_UNSUPPORTED = 3,  /* valid but not supported (e.g. ks > 127) */
   SD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
-  SD_ERR_CAPACITY = 5      /* library table full (lens slots) */
+  SD_ERR_CAPACITY = 5,     /* library table full (lens slots), or a fixed
+                              device array too small for the sizes */
+  SD_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (reported by
+                              sd_sync_status from a status word) */
 };
 
 /* ------------------------------------------------------------------------
@@ -191,7 +194,7 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
                           int64_t* stats, void* stream);
 
 /*
- * Per-pixel DP PSF map (Sec. 4 implementation details; Table S3 times it):
+ * Per-pixel DP PSF map (Sec. 5.1 implementation details; Table S3 times it):
  * one PSF pair for every pixel of an H x W depth map, the object point of
  * pixel (row, col) on the paraxial chief ray through the pixel centre
  * ((col - (W-1)/2) * pitch, (row - (H-1)/2) * pitch) at that pixel's depth
@@ -219,16 +222,22 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
  * between the passes) and swept backward through the sensor propagation,
  * Snell's law, the normal and the intersection (implicit-function
  * derivative at the converged Newton root); ray generation and the discrete
- * decisions (reached, side, splat pixel) are held fixed.  The paper trains
+ * decisions (reached, side, splat pixel) are held fixed.  A request whose
+ * grad_out patch is all zero has a zero gradient and traces no ray.  The paper trains
  * no lens; this is the differentiable form of Sec. 3.1 / Eq. 3.
  * grad_req and grad_lens are device memory owned by the caller.
+ * swept (device, nullable) receives per request [n_req][2] int64: the rays
+ * whose splat gradient is non-zero (the rays whose reverse sweep carries a
+ * contribution) and the thread slots that ran the sweep (32 per warp in
+ * which any ray has a contribution); the first is the adjoint's algorithmic
+ * work, the second what the hardware executed.
  */
 sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
                                    const sd_dp_sensor* sensor,
                                    const sd_psf_request* req, int n_req,
                                    const sd_trace_opts* opts,
                                    const float* grad_out, float* grad_req,
-                                   float* grad_lens, void* stream);
+                                   float* grad_lens, int64_t* swept, void* stream);
 
 /*
  * Batched trace of uneven requests (different N, ks, wavelength, lens) in one
@@ -313,7 +322,7 @@ sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
  * of field points of the first quadrant, [Fx = F][Fy = F][Z][NL][2][ks][ks]
  * with both axes sampled at field_h_mm (>= 0).  A pixel takes the grid point
  * nearest to (|X|, |Y|) on each axis separately (same rule as the radial
- * lookup), and the flip symmetry of the DP PSF about both axes (Sec. 5.2):
+ * lookup), and the flip symmetry of the DP PSF about both axes (Sec. 5.3):
  * X < 0 mirrors the kernel's columns and exchanges L and R (the DP split is
  * along x), Y < 0 mirrors its rows.  Removes the radial approximation of
  * off-axis azimuths.  All render entry points take it: sd_dp_render_tc's
@@ -397,19 +406,23 @@ sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, size_t* bytes)
  * both overwritten; either may be null to skip it.  aif is read in
  * image_dtype and the bank in layout->dtype (the storage types sd_dp_render
  * takes); arithmetic is FP32.  Returns SD_ERR_UNSUPPORTED for another
- * image_dtype.
- *   grad_aif: each (segment, slice) item scatters its weighted gradients into
- *     a shared padded tile, folded onto the image with FP32 atomics (the
- *     result is not bitwise reproducible run to run).
+ * image_dtype.  Both gradients are bitwise reproducible (no atomics on
+ * floating-point values; every sum runs in a fixed order).
+ * The workspace (device, 256-byte aligned, sd_dp_render_backward_workspace()
+ * bytes) holds, when grad_aif is requested, first the image pass's tables
+ * (the per-pixel slice selection, the bank re-laid as FP32 kernel columns,
+ * each kernel row's non-zero column range), then the bank pass's data.
+ *   grad_aif: warps own strips of 64 source columns and 8 output rows; each
+ *     scatters its pixels' weighted gradients, slice by slice, into a
+ *     warp-private row buffer that is added to the image once; strips whose
+ *     footprints overlap run in separate launches in a fixed order.
  *   grad_bank: thread blocks per (slice, wavelength) accumulate over the
- *     tiles that use the slice in a fixed order (deterministic).  Needs a
- *     device workspace of at least the bitmap of the slices each 64x32 tile
- *     uses; with the full sd_dp_render_backward_workspace() bytes the tiles
+ *     tiles that use the slice in a fixed order.  Needs at least the bitmap
+ *     of the slices each 64x32 tile uses; with the full workspace the tiles
  *     of a slice are split over two blocks whose partial banks are then
- *     added in a fixed order (still deterministic).  Ignored when grad_bank
- *     is null.
- * Returns SD_ERR_ARG when the workspace is missing or smaller than the
- * bitmap.
+ *     added in a fixed order.  Ignored when grad_bank is null.
+ * Returns SD_ERR_ARG when the workspace is missing, misaligned (with
+ * grad_aif) or smaller than the image tables plus the bitmap.
  */
 sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
                                 const float* depth_m, const void* bank,
@@ -419,7 +432,8 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
                                 void* workspace, size_t workspace_bytes,
                                 void* stream);
 
-/* Device workspace bytes sd_dp_render_backward needs for these sizes. */
+/* Device workspace bytes sd_dp_render_backward needs for these sizes (both
+ * gradients, two partial banks). */
 sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
                                           int C, int H, int W, size_t* bytes);
 
@@ -448,23 +462,25 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif,
  * pool or is not permitted).  The paper has no counterpart; this is a
  * deployment variant of the render adjoint with the same arguments minus the
  * workspace and the image dtype (aif is FP32; the bank is read in
- * layout->dtype).
- * The bank-gradient pass keeps its slice bitmap in a 16 MiB array that this
- * library reserves statically on every device that loads it (held until the
- * process exits); when the bitmap for these sizes (see
- * sd_dp_render_backward_workspace) exceeds 16 MiB the call returns
- * SD_ERR_CAPACITY before launching anything.  No device memory is allocated
+ * layout->dtype: FP32, BF16 or FP16).
+ * The image pass's tables and the bank pass's slice bitmap live in a 16 MiB
+ * array that this library reserves statically on every device that loads
+ * it (held until the process exits); when what the requested gradients need
+ * for these sizes exceeds 16 MiB the call returns SD_ERR_CAPACITY before
+ * launching anything.  No device memory is allocated
  * or freed.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call uses the same array and it keeps
- * the last call's contents: the bitmap pass rewrites every word the bank
- * pass reads, so nothing has to start at zero, but calls that overlap on the
- * GPU (other streams or host threads) race on the array and must be
- * serialised by the caller.
+ * before any stream capture.  The address is kept for the life of the
+ * process: do not use this entry point on a device after cudaDeviceReset
+ * (the array then lives at a new address).  Every call uses the same array
+ * and it keeps the last call's contents: each call rewrites every word it
+ * reads (selection table, re-laid bank, row extents, bitmap), so nothing has
+ * to start at zero, but calls that overlap on the GPU (other streams or
+ * host threads) race on the array and must be serialised by the caller.
  */
 sd_status sd_dp_render_backward_noalloc(const float* grad_out,
                                         const float* aif, const float* depth_m,
-                                        const float* bank,
+                                        const void* bank,
                                         const sd_bank_layout* layout, int N,
                                         int C, int H, int W, float* grad_aif,
                                         float* grad_bank, void* stream);
@@ -481,8 +497,8 @@ sd_status sd_dev_math_check(const float* a, const float* b, int n, float* quot,
                             float* root, void* stream);
 
 /* ------------------------------------------------------------------------
- * DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
- * module"; Sec. 4 implementation details): an MLP from the normalised object
+ * DP PSF prediction network (Sec. 3.2, "Pixel-wise DP image rendering
+ * module"; Sec. 5.1 implementation details): an MLP from the normalised object
  * point p = (x_n, y_n, d_n) of a pixel to the 2*ks^2 values of its
  * (PSF_L, PSF_R): 5 hidden layers of 512 neurons (ReLU), a linear output
  * layer of 2*ks^2 neurons; at inference the outputs are clamped at 0 and
@@ -533,6 +549,41 @@ sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, 
  */
 sd_status sd_dev_tc_check(const void* a, const void* b, int u, float* d,
                           int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Device-side status, failure injection and hardware probes (the paper has
+ * no counterpart: these serve error reporting, tests and measurement)
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Waits for the stream and reads a device status word written by a kernel:
+ * the first int32 of the workspace of sd_dp_render_tc or
+ * sd_dp_render_bank_grad_tc, or the status buffer of sd_mlp_psf_map.
+ * Returns SD_ERR_TIMEOUT when the word is non-zero (a bounded completion wait
+ * of that call gave up: its output is invalid), SD_OK when it is zero,
+ * SD_ERR_ARG for a null pointer and SD_ERR_CUDA when the copy fails.
+ * Synchronises the stream.
+ */
+sd_status sd_sync_status(const int32_t* status_word, void* stream);
+
+/*
+ * Failure injection for tests: every bounded completion wait (mbarrier poll
+ * loop) of the tensor-core kernels launched after this call gives up after
+ * `polls` polls; polls = 0 makes the first wait of every CTA give up without
+ * polling, so that no tensor-core product or bulk copy is issued and the
+ * kernel ends through its error path (flag set, tensor memory freed).
+ * polls < 0 restores each kernel's own limit.  Process-wide; host call.
+ */
+sd_status sd_set_wait_limit(long long polls);
+
+/*
+ * FP32 throughput probe: `blocks` blocks of 256 threads, each thread running
+ * 16 independent fused multiply-add chains for `iters` iterations
+ * (blocks * 256 * iters * 32 flops).  sink (device, blocks * 256 floats) is
+ * never written for these arguments; it keeps the arithmetic alive.  Timed
+ * by the caller (CUDA events on the stream) to measure the FP32 peak.
+ */
+sd_status sd_dev_fp32_peak(float* sink, int blocks, int iters, void* stream);
 
 /* ------------------------------------------------------------------------
  * Library information

@@ -327,13 +327,13 @@ def render_select(depth_m, field_h_mm, depths_m, pitch_mm):
 
 
 # --------------------------------------------------------------------------
-# DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
-# module"; Sec. 4 implementation details)
+# DP PSF prediction network (Sec. 3.2, "Pixel-wise DP image rendering
+# module"; Sec. 5.1 implementation details)
 # --------------------------------------------------------------------------
 def mlp_inputs(depth_m, d_min_m, d_max_m):
     """Normalised object point p = (x_n, y_n, d_n) of every pixel of a depth
     map (H, W), row-major -> (H*W, 3): the pixel's sensor position scaled to
-    [-1, 1] (the frustum's x and y at its depth, Sec. 3.3) and the depth
+    [-1, 1] (the frustum's x and y at its depth, Sec. 3.2) and the depth
     scaled linearly from [d_min, d_max] to [-1, 1]."""
     d = np.asarray(depth_m, dtype=np.float64)
     H, W = d.shape
@@ -345,10 +345,10 @@ def mlp_inputs(depth_m, d_min_m, d_max_m):
 
 
 def mlp_psf(weights, biases, p, ks):
-    """The network of Sec. 3.3 in FP64: h = ReLU(W_l h + b_l) for the input
+    """The network of Sec. 3.2 in FP64: h = ReLU(W_l h + b_l) for the input
     layer and the hidden layers (l = 0..4, 512 neurons each), o = W_5 h + b_5
     with 2 ks^2 outputs; at inference o is clamped at 0 and divided by its
-    sum (the sum normalisation of Sec. 3.3, joint over L and R).
+    sum (the sum normalisation of Sec. 3.2, joint over L and R).
     p (n, 3) -> (n, 2, ks, ks)."""
     h = np.asarray(p, dtype=np.float64)
     for l in range(5):

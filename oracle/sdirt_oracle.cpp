@@ -989,7 +989,7 @@ int nearest_height(const float* fh, int F, float r) {
 // mode 0 (radial bank): f = the height nearest to the radial image height.
 // mode 1 (first-quadrant bank [F][F]): f = ix * F + iy with ix, iy the
 // heights nearest to |X| and |Y|; a pixel with X < 0 (Y < 0) uses the PSF
-// mirrored about the y (x) axis, the flip symmetry of the DP PSF (Sec. 5.2).
+// mirrored about the y (x) axis, the flip symmetry of the DP PSF (Sec. 5.3).
 Sel select_slice(int row, int col, int H, int W, float pitch, float depth,
                  const float* fh, int F, const float* iq, int Z, int mode = 0) {
   volatile float X = ((float)col - 0.5f * (float)(W - 1)) * pitch;

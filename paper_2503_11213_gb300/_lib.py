@@ -11,7 +11,8 @@ import numpy as np
 
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libsdirt.so"
 
-SD_OK, SD_ERR_ARG, SD_ERR_LENS, SD_ERR_UNSUPPORTED, SD_ERR_CUDA, SD_ERR_CAPACITY = range(6)
+(SD_OK, SD_ERR_ARG, SD_ERR_LENS, SD_ERR_UNSUPPORTED, SD_ERR_CUDA, SD_ERR_CAPACITY,
+ SD_ERR_TIMEOUT) = range(7)
 SD_SURF_REFRACT, SD_SURF_STOP = 0, 1
 SD_BIN_HARD, SD_BIN_BILINEAR = 0, 1
 SD_NORM_NONE, SD_NORM_JOINT, SD_NORM_SEPARATE, SD_NORM_PER_RAY = range(4)
@@ -76,7 +77,7 @@ EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_fre
            "sd_mlp_blob_bytes", "sd_mlp_pack", "sd_mlp_psf_map",
            "sd_dp_render_bank_grad_tc", "sd_dp_render_bank_grad_tc_workspace",
            "sd_dev_math_check", "sd_dev_tc_check", "sd_status_string", "sd_last_cuda_error",
-           "sd_version")
+           "sd_version", "sd_sync_status", "sd_set_wait_limit", "sd_dev_fp32_peak")
 
 _lib = None
 
@@ -115,7 +116,7 @@ def lib():
     L.sd_lens_free.argtypes = [vp]
     L.sd_dp_psf_trace.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts), vp, vp, vp]
     L.sd_dp_psf_trace_backward.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
-                                           vp, vp, vp, vp]
+                                           vp, vp, vp, vp, vp]
     ll = ctypes.c_longlong
     L.sd_dp_psf_trace_batched_workspace.argtypes = [i32, ll, P(ctypes.c_size_t)]
     L.sd_dp_psf_trace_batched.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
@@ -147,6 +148,9 @@ def lib():
     L.sd_mlp_blob_bytes.argtypes = [i32, P(ctypes.c_size_t)]
     L.sd_mlp_pack.argtypes = [P(P(fl)), P(P(fl)), i32, vp, ctypes.c_size_t]
     L.sd_mlp_psf_map.argtypes = [vp, i32, vp, i32, i32, fl, fl, vp, i32, vp, vp]
+    L.sd_sync_status.argtypes = [vp, vp]
+    L.sd_set_wait_limit.argtypes = [ll]
+    L.sd_dev_fp32_peak.argtypes = [vp, i32, i32, vp]
     L.sd_status_string.argtypes = [i32]
     L.sd_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -135,10 +135,13 @@ def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=
 
 
 def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, max_ks,
-                          max_n=512, norm=L.SD_NORM_PER_RAY, grad_req=None, newton_iters=0):
+                          max_n=512, norm=L.SD_NORM_PER_RAY, grad_req=None, newton_iters=0,
+                          swept=None):
     """Adjoint of the bilinear trace: per-request and per-lens gradients of
     <grad_out, PSF> with respect to the lens parameters, as
-    (grad_req (n_req, 32, 8), grad_lens (n_lenses, 32, 8))."""
+    (grad_req (n_req, 32, 8), grad_lens (n_lenses, 32, 8)).  swept, an
+    optional (n_req, 2) int64 CUDA tensor, receives per request the rays with
+    a non-zero splat gradient and the thread slots that ran the sweep."""
     lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
     handles = (ctypes.c_void_p * len(lenses))(*[l.handle.value for l in lenses])
     dev = req_dev.device
@@ -146,11 +149,16 @@ def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, ma
         grad_req = torch.empty((n_req, L.SD_MAX_SURFACES, L.NPAR_SURF), device=dev)
     grad_lens = torch.empty((len(lenses), L.SD_MAX_SURFACES, L.NPAR_SURF), device=dev)
     _need_cuda(req_dev, grad_out, grad_req)
+    if swept is not None:
+        _need_cuda(swept)
+        if swept.dtype != torch.int64 or swept.numel() < 2 * n_req:
+            raise ValueError("swept must be an int64 tensor of n_req x 2")
     opts = L.SdTraceOpts(L.SD_BIN_BILINEAR, norm, L.SD_F32, newton_iters, max_ks, max_n)
     sen = sensor.c()
     L.check(L.lib().sd_dp_psf_trace_backward(handles, len(lenses), ctypes.byref(sen),
                                              _ptr(req_dev), n_req, ctypes.byref(opts),
                                              _ptr(grad_out), _ptr(grad_req), _ptr(grad_lens),
+                                             _ptr(swept) if swept is not None else None,
                                              _stream()), "sd_dp_psf_trace_backward")
     return grad_req, grad_lens
 
@@ -358,7 +366,8 @@ def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=Non
 
 
 def render_backward_workspace(layout: BankLayout, N, C, H, W):
-    """Device workspace bytes of dp_render_backward's bank gradient: the
+    """Device workspace bytes of dp_render_backward: the image gradient's
+    selection table, re-laid bank and row extents, then the bank gradient's
     per-tile slice bitmap and two partial banks."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
@@ -409,7 +418,7 @@ def dp_render_backward(grad_out, aif, depth_m, bank, layout: BankLayout, need_ai
     dev = aif.device
     ga = torch.empty(aif.shape, dtype=torch.float32, device=dev) if need_aif else None
     gb = torch.empty(bank.shape, dtype=torch.float32, device=dev) if need_bank else None
-    if need_bank and workspace is None:
+    if (need_bank or need_aif) and workspace is None:
         nbytes = render_backward_workspace(layout, N, C, H, W)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     _need_cuda(grad_out, aif, depth_m, bank, ga, gb)
@@ -432,7 +441,7 @@ def MLP_SHAPES(ks):
 
 
 class PsfMLP:
-    """The DP PSF prediction network (Sec. 3.3) packed on the device: weights
+    """The DP PSF prediction network (Sec. 3.2) packed on the device: weights
     [l] (out, in) and biases[l] for l = 0..5 as float arrays of the shapes
     MLP_SHAPES(ks) (3 -> 512, four 512 -> 512, 512 -> 2 ks^2)."""
 
@@ -476,3 +485,31 @@ def mlp_psf_map(net: PsfMLP, depth_m, d_min_m, d_max_m, out=None, status=None,
                                    float(d_max_m), _ptr(out), _DT[out.dtype], _ptr(status),
                                    _stream()), "sd_mlp_psf_map")
     return out, status
+
+
+def sync_status(status_word):
+    """Waits for the current stream and raises SdError (SD_ERR_TIMEOUT) when
+    the device status word -- the first int32 of a tensor-core render or
+    bank-gradient workspace, or the network's status buffer -- reports that a
+    bounded completion wait gave up."""
+    _need_cuda(status_word)
+    L.check(L.lib().sd_sync_status(_ptr(status_word), _stream()), "device status")
+
+
+def set_wait_limit(polls):
+    """Failure injection for tests: every bounded completion wait of the
+    tensor-core kernels launched afterwards gives up after `polls` polls
+    (0: at the first wait, before anything asynchronous is issued); None or
+    a negative value restores each kernel's own limit."""
+    L.check(L.lib().sd_set_wait_limit(-1 if polls is None else int(polls)), "sd_set_wait_limit")
+
+
+def fp32_peak_launch(sink, blocks, iters):
+    """Launches the FP32 throughput probe on the current stream:
+    blocks * 256 threads x iters iterations x 32 flops (16 FMA chains)."""
+    _need_cuda(sink)
+    if sink.numel() < blocks * 256:
+        raise ValueError("sink must hold blocks * 256 floats")
+    L.check(L.lib().sd_dev_fp32_peak(_ptr(sink), int(blocks), int(iters), _stream()),
+            "sd_dev_fp32_peak")
+    return float(blocks) * 256 * iters * 32

@@ -1,6 +1,6 @@
 """PSF bank files: a traced bank saved with its layout, so that it can be
 reused without tracing again (the paper fits its PSF network offline to
-traced PSFs, Sec. 3.3).
+traced PSFs, Sec. 3.2).
 
 File layout (little endian):
   8 bytes   magic b"SDBANK" + format version (uint16, 1)

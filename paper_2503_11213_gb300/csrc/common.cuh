@@ -13,6 +13,10 @@ namespace sd {
 // last CUDA error seen on this host thread
 void set_cuda_error(cudaError_t e);
 
+// Poll limit of the tensor-core kernels' bounded completion waits: dflt
+// unless sd_set_wait_limit has set a process-wide override.
+uint32_t wait_limit(uint32_t dflt);
+
 #define SD_CUDA_TRY(expr)                         \
   do {                                            \
     cudaError_t _e = (expr);                      \

@@ -1310,11 +1310,13 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[NPAR_SURF], int lane
 // order: deterministic).
 template <int NT>
 __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
-                                                       float* __restrict__ greq) {
+                                                       float* __restrict__ greq,
+                                                       long long* __restrict__ swept) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ReqCtx ctx;
   __shared__ float s_acc[NW][SD_MAX_SURFACES][NPAR_SURF];
+  __shared__ int s_swept[2];  // rays with a contribution, lanes that ran the sweep
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   float* Gs = reinterpret_cast<float*>(smem + table_bytes(P.max_n));
@@ -1323,10 +1325,23 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   const sd_psf_request q = request_of(P, r);
   for (int i = threadIdx.x; i < NW * SD_MAX_SURFACES * NPAR_SURF; i += NT)
     (&s_acc[0][0][0])[i] = 0.f;
+  if (threadIdx.x < 2) s_swept[threadIdx.x] = 0;
   setup_request(P, q, ctx, prefix, lo);
   const int ks = ctx.ks, ks2 = ks * ks, pp = (ks - 1) >> 1;
-  for (int i = threadIdx.x; i < 2 * ks2; i += NT) Gs[i] = G[q.out_offset + i];
-  __syncthreads();
+  bool nz = false;
+  for (int i = threadIdx.x; i < 2 * ks2; i += NT) {
+    const float g = G[q.out_offset + i];
+    Gs[i] = g;
+    nz = nz || g != 0.f;
+  }
+  // a request whose gradient patch is zero has an exactly zero parameter
+  // gradient (every ray's splat gradient vanishes): no ray is traced again
+  if (!__syncthreads_or(nz)) {
+    for (int i = threadIdx.x; i < SD_MAX_SURFACES * NPAR_SURF; i += NT)
+      greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + i] = 0.f;
+    if (swept && threadIdx.x < 2) swept[2 * (size_t)r + threadIdx.x] = 0;
+    return;
+  }
   const SensorF S = P.sen;
   const int total = ctx.N ? ctx.total : 0;
   const float scale = (P.norm == SD_NORM_PER_RAY) ? (total > 0 ? 1.f / (float)total : 0.f) : 1.f;
@@ -1368,7 +1383,12 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
     }
     // the whole warp sweeps when any lane needs it; the others contribute
     // exact zeros (their values are selected away, never multiplied)
-    if (!__any_sync(0xffffffffu, need)) continue;
+    const unsigned need_mask = __ballot_sync(0xffffffffu, need);
+    if (!need_mask) continue;
+    if (lane == 0) {
+      atomicAdd(&s_swept[0], __popc(need_mask));
+      atomicAdd(&s_swept[1], 32);
+    }
     if (!need) {
       // a harmless state for lanes without a contribution
       sv.px = sv.py = 0.f;
@@ -1394,6 +1414,7 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
       for (int w = 0; w < NW; ++w) a += s_acc[w][s2][j2];
     greq[(size_t)r * SD_MAX_SURFACES * NPAR_SURF + i] = a;
   }
+  if (swept && threadIdx.x < 2) swept[2 * (size_t)r + threadIdx.x] = s_swept[threadIdx.x];
 }
 
 // Sums the per-request partials of each lens: four contiguous request
@@ -1421,7 +1442,8 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
                                               const sd_dp_sensor* sensor,
                                               const sd_psf_request* req, int n_req,
                                               const sd_trace_opts* opts, const float* grad_out,
-                                              float* grad_req, float* grad_lens, void* stream) {
+                                              float* grad_req, float* grad_lens,
+                                              int64_t* swept, void* stream) {
   using namespace sd;
   if (!opts || !grad_out || !grad_req || n_req < 0 || (n_req > 0 && !req)) return SD_ERR_ARG;
   TraceParams P;
@@ -1452,9 +1474,9 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
   // count fixed at compile time and the whole per-surface state in registers
   // needed 130-190 registers per thread and measured slower.
   constexpr int NT = 256;
-  void (*k)(TraceParams, const float*, float*) = trace_adj_kernel<NT>;
+  void (*k)(TraceParams, const float*, float*, long long*) = trace_adj_kernel<NT>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k<<<n_req, NT, smem, s>>>(P, grad_out, grad_req);
+  k<<<n_req, NT, smem, s>>>(P, grad_out, grad_req, reinterpret_cast<long long*>(swept));
   st = launch_status();
   if (st != SD_OK) return st;
   if (grad_lens) {

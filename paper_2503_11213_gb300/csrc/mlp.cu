@@ -1,4 +1,4 @@
-// DP PSF prediction network (Sec. 3.3, "Pixel-wise DP image rendering
+// DP PSF prediction network (Sec. 3.2, "Pixel-wise DP image rendering
 // module"): per pixel, an MLP maps the normalised object point p = (x_n,
 // y_n, d_n) through 5 hidden layers of 512 (ReLU) to the 2 ks^2 values of
 // (PSF_L, PSF_R); the outputs are clamped at 0 and sum-normalised.
@@ -72,10 +72,12 @@ struct MlpParams {
   int* status;
   int ks, H, W;
   float d_min, d_scale;  // d_n = (d - d_min) * d_scale - 1
+  uint32_t wlim;         // polls of a pipeline wait before it gives up
 };
 
-__device__ __forceinline__ bool mwait(uint64_t* bar, uint32_t parity, int* err) {
-  if (tc::mbar_wait(bar, parity, MWAIT, err)) return true;
+__device__ __forceinline__ bool mwait(uint64_t* bar, uint32_t parity, int* err,
+                                      uint32_t limit) {
+  if (tc::mbar_wait(bar, parity, limit, err)) return true;
   atomicExch(err, 1);
   return false;
 }
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
         for (int nb = nb0; nb < nb1 && ok; ++nb)
           for (int kb = 0; kb < MKPB; ++kb, ++c) {
             const int b = c % MNB;
-            if (c >= MNB && !mwait(&s_empty[b], (uint32_t)(c / MNB - 1) & 1u, P.status)) {
+            if (c >= MNB && !mwait(&s_empty[b], (uint32_t)(c / MNB - 1) & 1u, P.status, P.wlim)) {
               ok = false;
               break;
             }
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       auto run = [&](int ph, int nb, int h, int kb0, int kb1) {
         for (int kb = kb0; kb < kb1 && ok; ++kb, ++c) {
           const int b = c % MNB;
-          ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status);
+          ok = mwait(&s_full[b], (uint32_t)(c / MNB) & 1u, P.status, P.wlim);
           if (!ok) break;
           tc::fence_after_sync();
 #pragma unroll
@@ -198,10 +200,10 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
         const int q = ph < 4 ? 0 : mlp_pass(ph, npass);
         const int nb0 = ph < 4 ? 0 : 2 * q;
         const bool two = ph < 4 || nb0 + 1 < nblk;
-        ok = ok && mwait(&s_epi[0], (uint32_t)ph & 1u, P.status);
+        ok = ok && mwait(&s_epi[0], (uint32_t)ph & 1u, P.status, P.wlim);
         tc::fence_after_sync();
         run(ph, nb0, 0, 0, MKPB / 2);
-        ok = ok && mwait(&s_epi[1], (uint32_t)ph & 1u, P.status);
+        ok = ok && mwait(&s_epi[1], (uint32_t)ph & 1u, P.status, P.wlim);
         tc::fence_after_sync();
         run(ph, nb0, 0, MKPB / 2, MKPB);
         tc::commit(&s_acc[0]);
@@ -253,8 +255,8 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_kernel(const MlpParams P) {
       // one thread per warp polls; its warp follows.  Half 0 of a hidden
       // layer also waits until no MMA reads inputs 0..255 any more.
       if (lane == 0) {
-        mwait(&s_acc[half], (uint32_t)ph & 1u, P.status);
-        if (half == 0 && ph < 4) mwait(&s_k0, (uint32_t)ph & 1u, P.status);
+        mwait(&s_acc[half], (uint32_t)ph & 1u, P.status, P.wlim);
+        if (half == 0 && ph < 4) mwait(&s_k0, (uint32_t)ph & 1u, P.status, P.wlim);
       }
       __syncwarp();
       tc::fence_after_sync();
@@ -434,6 +436,7 @@ extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth
   P.W = W;
   P.d_min = d_min_m;
   P.d_scale = 2.f / (d_max_m - d_min_m);
+  P.wlim = wait_limit(MWAIT);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SD_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   const size_t smem = MA_BYTES + (size_t)MNB * MCHUNK + MSTAGE;

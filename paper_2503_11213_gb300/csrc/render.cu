@@ -5,7 +5,7 @@
 // bank mode, K(y,x,c) = (1-t) B[f][z0][lam] + t B[f][z0+1][lam] selected per
 // pixel from its radial image height and depth (linear in inverse depth);
 // with a quadrant bank, from the nearest first-quadrant field point of
-// (|X|, |Y|) and the PSF's flip symmetry about both axes (Sec. 5.2).
+// (|X|, |Y|) and the PSF's flip symmetry about both axes (Sec. 5.3).
 //
 // The render is linear in the kernel, so a pixel's output is
 // (1-t) (I * B[f][z0]) + t (I * B[f][z0+1]): a sum over bank slices with

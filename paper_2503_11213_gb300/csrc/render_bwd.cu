@@ -71,286 +71,347 @@ __global__ void __launch_bounds__(NT_BM) slice_bitmap_kernel(const RenderParams 
 }
 
 // ---------------------------------------------------------------------------
-// 2. image gradient.  Each lane owns a vertical segment of SB pixels; every
-// shared-memory atomic carries 2*SB FMAs.
+// 2. image gradient, deterministic.  A thread block owns a strip of IG_SW
+// source columns of one channel and one 8-row block of output rows (image
+// rows 8i .. 8i+7; the first and last blocks also take the padded rows that
+// the replicate padding folds onto image rows 0 and H-1).  The 8-row source
+// blocks within reach are dealt to its warps in turn; a warp stages a source
+// block's selection and output gradients, finds the slices the block uses
+// (ascending), and for each slice lets each lane take one source column that
+// uses it: for every kernel
+// column v the lane's 8 weighted gradients (both sides) meet the 15 kernel
+// rows that connect its 8 source rows to the 8 output rows,
+//   dIpad[T0 + j][x + v] += sum_a w_k G_s(8 sb + a, x) Kf_{k,s}[d + j - a][v],
+// d = T0 + p - 8 sb, and the lane adds its 8 sums to its column of a
+// warp-private row buffer (one plain read-modify-write per row: the lanes of
+// a pass own distinct columns, and the warp's steps run in program order).
+// The buffers cover the strip's footprint (IG_SW + ks - 1 columns); at the
+// end they are added in warp order and the sum is added to the image once.  Strips whose footprints overlap run
+// in different launches (phases), so no two warps of a launch write the
+// same image element and every element receives its phase contributions in
+// a fixed order: bitwise reproducible, no atomics.
+//   Taps come from a per-call re-layout of the bank: per (slice key,
+// wavelength) and flipped-kernel column v, the column's rows (both sides
+// interleaved, zero-padded above and below) as 16-byte aligned runs, so the
+// 15 rows of a band are 8 broadcast 16-byte loads; a table of each row's
+// non-zero column range bounds the kernel columns a band visits.
 // ---------------------------------------------------------------------------
-template <int TX, int VB, int SB>
-struct BwdImgSmem {
-  static constexpr int NT = TX * RT_Y / SB, NW = NT / 32, NPX = TX * RT_Y, MW = NT / 32;
-  __host__ __device__ static int ku(int ks) { return (ks + SB - 1) / SB * SB; }
-  __host__ __device__ static size_t kbuf_words(int ks) { return (size_t)2 * (2 * ku(ks) * VB); }
-  __host__ __device__ static size_t pad_words(int ks) {
-    return (size_t)(TX + ks - 1) * (RT_Y + ks - 1 + SB);
-  }
-  static size_t bytes(int ks) {
-    size_t w = pad_words(ks) + NW * kbuf_words(ks) + 3 * (size_t)NPX  // dIpad, K, gL/gR, t
-               + (size_t)RK * MW + (RK + 1) + MAX_CHUNKS + NPX / 2;
-    return 4 * w;
-  }
+constexpr int IG_SW = 64;   // source columns per warp (two per lane)
+constexpr int IG_NW = 4;    // warps per block (one item, private buffers)
+constexpr unsigned short IG_EMPTY = 0x00ffu;  // row extent of an all-zero row
+
+struct ImgLayout {
+  int padu;    // zero rows above kernel row 0 in a re-laid column
+  int rcol;    // rows per re-laid column (even)
+  int nphase;  // launches of non-overlapping strips
+  size_t sel_bytes, kcol_bytes, ext_bytes, total;
 };
 
-template <int TX, int VB, int KSMAX, int SB, class TB>
-__global__ void __launch_bounds__(TX * RT_Y / SB, 1)
-    render_bwd_img_kernel(const RenderParams P, const float* __restrict__ gout,
-                          float* __restrict__ gaif) {
-  using SM = BwdImgSmem<TX, VB, SB>;
-  constexpr int NT = SM::NT, NW = SM::NW, NPX = SM::NPX, MW = SM::MW;
-  constexpr int NR = (2 * ((KSMAX + SB - 1) / SB * SB) * VB + 31) / 32;
+inline ImgLayout img_layout(const RenderParams& P) {
+  ImgLayout L;
+  const int ks = P.ks, p = (ks - 1) / 2;
+  // bands start at row d - 7 with d = p (mod 8) and d in [-7, ks + 6]: the
+  // padding keeps every band inside its column and 16-byte aligned
+  L.padu = (p & 1) ? 14 : 15;
+  L.rcol = (ks + 15 + L.padu + 1) & ~1;
+  L.nphase = 1 + (2 * p + IG_SW - 1) / IG_SW;
+  const size_t kl = (size_t)n_keys(P) * P.NL;
+  L.sel_bytes = ((size_t)P.N * P.H * P.W * 8 + 255) & ~(size_t)255;
+  L.kcol_bytes = (kl * ks * L.rcol * 8 + 255) & ~(size_t)255;
+  L.ext_bytes = (kl * ks * 2 + 255) & ~(size_t)255;
+  L.total = L.sel_bytes + L.kcol_bytes + L.ext_bytes;
+  return L;
+}
+
+// Per-pixel selection (key, t) of every pixel, once per call.
+__global__ void select_table_kernel(const RenderParams P, int2* __restrict__ sel) {
+  const size_t npx = (size_t)P.N * P.H * P.W;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npx;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % P.W);
+    const size_t r = i / P.W;
+    const int y = (int)(r % P.H);
+    int key;
+    float t;
+    select_slice(P, y, x, P.depth[i], &key, &t);
+    sel[i] = make_int2(key, __float_as_int(t));
+  }
+}
+
+// Re-layout of one (slice key, wavelength) per block: the flipped kernel
+// Kf_s[u][v] (quadrant banks: the key's flip class, see select_slice) as
+// kcol[kl][v][padu + u][s], zero outside 0 <= u < ks, and each row's
+// non-zero column range ext[kl][u] = vlo | vhi << 8 (IG_EMPTY if none).
+template <class TB>
+__global__ void __launch_bounds__(256) kernel_columns_kernel(const RenderParams P,
+                                                             ImgLayout IL,
+                                                             float* __restrict__ kcol,
+                                                             unsigned short* __restrict__ ext) {
+  extern __shared__ __align__(16) float kf[];  // [2][ks][ks]
+  const int ks = P.ks, ks2 = ks * ks, kl = blockIdx.x;
+  const int n_kl = P.FC * P.Z * P.NL;  // slices x wavelengths of the stored bank
+  const int flips = kl / n_kl, kls = kl - flips * n_kl;
+  const bool mx = flips & 1, my = flips & 2;
+  const TB* src = reinterpret_cast<const TB*>(P.bank) + (size_t)kls * 2 * ks2;
+  for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) {
+    const int s = i / ks2, r = i - s * ks2, row = r / ks, col = r - row * ks;
+    // stored (side s, row, col) is flipped element (u, v) of side s' below
+    const int u = my ? row : ks - 1 - row, v = mx ? col : ks - 1 - col;
+    const int sf = mx ? 1 - s : s;
+    kf[(sf * ks + u) * ks + v] = to_f32<TB>(src[i]);
+  }
+  __syncthreads();
+  float* dst = kcol + (size_t)kl * ks * IL.rcol * 2;
+  for (int i = threadIdx.x; i < ks * IL.rcol * 2; i += blockDim.x) {
+    const int v = i / (IL.rcol * 2), q = i - v * IL.rcol * 2, rho = q >> 1, s = q & 1;
+    const int u = rho - IL.padu;
+    dst[i] = (u >= 0 && u < ks) ? kf[(s * ks + u) * ks + v] : 0.f;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int u = warp; u < ks; u += blockDim.x / 32) {
+    unsigned lo = 255u, hi = 0u;
+    for (int v = lane; v < ks; v += 32)
+      if (kf[u * ks + v] != 0.f || kf[(ks + u) * ks + v] != 0.f) {
+        lo = min(lo, (unsigned)v);
+        hi = max(hi, (unsigned)v);
+      }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) ext[(size_t)kl * ks + u] = (unsigned short)(lo > hi ? IG_EMPTY : lo | (hi << 8));
+  }
+}
+
+// position of the idx-th (0-based) set bit of m (idx < popc(m))
+__device__ __forceinline__ int nth_set_bit(unsigned m, int idx) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));
+    if (idx >= c) {
+      idx -= c;
+      m >>= s;
+      pos += s;
+    }
+  }
+  return pos;
+}
+
+template <int BWMAX>
+__global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
+    const RenderParams P, ImgLayout IL, const float* __restrict__ gout,
+    const int2* __restrict__ sel, const float* __restrict__ kcol,
+    const unsigned short* __restrict__ ext, int phase, int nr_phase, int nrb,
+    float* __restrict__ gaif) {
+  // per warp: the staged source block (gL, gR, t, key) and the row buffer
   extern __shared__ __align__(16) unsigned char smem[];
-  const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
-  const int S = P.halo_w;
-  float* dpad = reinterpret_cast<float*>(smem);
-  float* kbuf = dpad + SM::pad_words(ks);
-  float* gL = kbuf + NW * SM::kbuf_words(ks);
-  float* gR = gL + NPX;
-  float* pt = gR + NPX;
-  unsigned* mask = reinterpret_cast<unsigned*>(pt + NPX);
-  int* kpre = reinterpret_cast<int*>(mask + RK * MW);
-  int* chunks = kpre + RK + 1;
-  unsigned short* prel = reinterpret_cast<unsigned short*>(chunks + MAX_CHUNKS);
-  __shared__ int s_kmin, s_kmax, s_nchunks, s_next;
-
-  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * RT_Y;
-  const int n = blockIdx.z / P.C, c = blockIdx.z - n * P.C;
+  float4 (*s_src)[8][IG_SW] = reinterpret_cast<float4 (*)[8][IG_SW]>(smem);
+  float (*s_buf)[8][BWMAX] =
+      reinterpret_cast<float (*)[8][BWMAX]>(smem + (size_t)IG_NW * 8 * IG_SW * 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one item (strip of source columns, 8 output rows) per block
+  const long long item = blockIdx.x;
+  const int rr = (int)(item % nr_phase);
+  const long long rest = item / nr_phase;
+  const int rb = (int)(rest % nrb);
+  const int nc = (int)(rest / nrb);
+  const int n = nc / P.C, c = nc - n * P.C;
   const int lam = (P.NL == P.C) ? c : 0;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int H = P.H, W = P.W;
-  const bool two = (P.Z > 1);
+  const int H = P.H, W = P.W, ks = P.ks, p = (ks - 1) >> 1;
+  const int x0 = (phase + IL.nphase * rr) * IG_SW;
+  const int BW = IG_SW + ks - 1;
+  const bool two = P.Z > 1;
+  float (*buf)[BWMAX] = s_buf[warp];
+  float4 (*src)[IG_SW] = s_src[warp];
+  for (int i = lane; i < 8 * BWMAX; i += 32) (&buf[0][0])[i] = 0.f;
 
-  const int seg_col = tid % TX, seg_rb = tid / TX;
-  int kmin_t = 0x7fffffff, kmax_t = -1;
-  int key_j[SB];
-  float t_j[SB];
   const float* goL = gout + (((size_t)n * 2 * P.C + c) * H) * W;
   const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * H) * W;
-#pragma unroll
-  for (int j = 0; j < SB; ++j) {
-    int yy = ty0 + seg_rb * SB + j, xx = tx0 + seg_col;
-    int pix = (seg_rb * SB + j) * TX + seg_col;
-    key_j[j] = -1;
-    t_j[j] = 0.f;
-    float a = 0.f, b = 0.f;
-    if (yy < H && xx < W) {
-      float d = P.depth[((size_t)n * H + yy) * W + xx];
-      select_slice(P, yy, xx, d, &key_j[j], &t_j[j]);
-      kmin_t = min(kmin_t, key_j[j]);
-      kmax_t = max(kmax_t, key_j[j] + (two ? 1 : 0));
-      a = goL[(size_t)yy * W + xx];
-      b = goR[(size_t)yy * W + xx];
-    }
-    pt[pix] = t_j[j];
-    gL[pix] = a;
-    gR[pix] = b;
-  }
-  if (tid == 0) {
-    s_kmin = 0x7fffffff;
-    s_kmax = -1;
-  }
-  for (int i = tid; i < (int)SM::pad_words(ks); i += NT) dpad[i] = 0.f;
-  __syncthreads();
-  atomicMin(&s_kmin, kmin_t);
-  atomicMax(&s_kmax, kmax_t);
-  __syncthreads();
-  const int kmin = s_kmin, kmax = s_kmax;
-#pragma unroll
-  for (int j = 0; j < SB; ++j)
-    prel[(seg_rb * SB + j) * TX + seg_col] =
-        (unsigned short)(key_j[j] >= 0 ? key_j[j] - kmin : 0xffff);
+  const int2* selp = sel + (size_t)n * H * W;
+  const int nsb = (H + 7) >> 3;
+  const int r0 = 8 * rb;
+  // virtual output row groups T0 = r0 + 8 g: rows above the image fold onto
+  // row 0 (first block), rows below onto row H - 1 (last block)
+  const int g_lo = rb == 0 ? -((p + 7) >> 3) : 0;
+  const int g_hi = r0 + 8 >= H ? (H - 1 + p - r0) >> 3 : 0;
+  const size_t col_stride = (size_t)IL.rcol * 2;  // floats per re-laid column
+  const int fold_lo = -r0, fold_hi = H - 1 - r0;  // buffer rows of clamped rows
 
-  float* kb = kbuf + warp * SM::kbuf_words(ks);
-  const int nblk = (ks + VB - 1) / VB;
-  const int KU = SM::ku(ks);
-  const int kb_elems = 2 * KU * VB;
-
-  for (int wbase = kmin; wbase <= kmax; wbase += RK) {
-    for (int i = tid; i < RK * MW; i += NT) mask[i] = 0u;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < SB; ++j) {
-      int k0 = key_j[j];
-      if (k0 < 0) continue;
-      float t = t_j[j];
-      if ((!two || t < 1.f) && k0 >= wbase && k0 < wbase + RK)
-        atomicOr(&mask[(k0 - wbase) * MW + warp], 1u << lane);
-      if (two && t > 0.f && k0 + 1 >= wbase && k0 + 1 < wbase + RK)
-        atomicOr(&mask[(k0 + 1 - wbase) * MW + warp], 1u << lane);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      int carry = 0;
-      for (int k0 = 0; k0 < RK; k0 += 32) {
-        int k = k0 + lane;
-        int cnt = 0;
-        for (int w = 0; w < MW; ++w) cnt += __popc(mask[k * MW + w]);
-        int nch = (cnt + 31) >> 5;
-        int v = nch;
-        for (int o = 1; o < 32; o <<= 1) {
-          int u = __shfl_up_sync(0xffffffffu, v, o);
-          if (lane >= o) v += u;
-        }
-        kpre[k] = carry + v - nch;
-        carry += __shfl_sync(0xffffffffu, v, 31);
-      }
-      if (lane == 0) {
-        kpre[RK] = carry;
-        s_nchunks = carry;
-      }
-    }
-    __syncthreads();
-    const int nchunks = s_nchunks;
-    for (int k = tid; k < RK; k += NT)
-      for (int q = kpre[k]; q < kpre[k + 1]; ++q) chunks[q] = (k << 8) | (q - kpre[k]);
-    if (tid == 0) s_next = NW;
-    __syncthreads();
-
-    for (int ch = warp; ch < nchunks;) {
-      const int rel = chunks[ch] >> 8, sub = chunks[ch] & 0xff;
-      const int key = wbase + rel;
-      int want = sub * 32 + lane, seg = -1;
-      for (int w = 0; w < MW; ++w) {
-        unsigned m = mask[rel * MW + w];
-        int pc = __popc(m);
-        if (seg < 0 && want >= 0 && want < pc) {
-          for (int q = 0; q < want; ++q) m &= m - 1;
-          seg = w * 32 + __ffs(m) - 1;
-        }
-        want -= pc;
-      }
-      const bool act = seg >= 0;
-      const int sg = act ? seg : 0;
-      const int col = sg % TX, rb = sg / TX;
-      // weighted gradients of the segment's pixels for this slice
-      float GL[SB], GR[SB];
-#pragma unroll
-      for (int j = 0; j < SB; ++j) {
-        int pix = (rb * SB + j) * TX + col;
-        unsigned short r16 = prel[pix];
-        float w = 0.f;
-        if (act && r16 != 0xffff) {
-          int k0 = kmin + (int)r16;
-          float t = pt[pix];
-          w = (k0 == key) ? (two ? 1.f - t : 1.f) : ((two && k0 + 1 == key) ? t : 0.f);
-        }
-        GL[j] = w * gL[pix];
-        GR[j] = w * gR[pix];
-      }
-      const int f = key / P.Z, z = key - f * P.Z;
-      // quadrant bank: field cell and flips (x: mirror columns and exchange
-      // L and R; y: mirror rows); radial bank: flips = 0
-      const int flips = f / P.FC, cell = f - flips * P.FC;
-      const TB* K0 = reinterpret_cast<const TB*>(P.bank) +
-                     (((size_t)cell * P.Z + z) * P.NL + lam) * 2 * ks2;
-      const TB* KL = (flips & 1) ? K0 + ks2 : K0;
-      const TB* KR = (flips & 1) ? K0 : K0 + ks2;
-      const bool mx = flips & 1, my = flips & 2;
-      float pre[NR];
-      auto fetch = [&](int b) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          int e = lane + 32 * r;
-          float v = 0.f;
-          if (e < kb_elems) {
-            int side = e & 1, uv = e >> 1, u = uv / VB, vv = uv - u * VB;
-            int v_ = b * VB + vv;
-            if (v_ < ks && u < ks)
-              v = to_f32<TB>(__ldg((side ? KR : KL) + (my ? u : ks - 1 - u) * ks +
-                                   (mx ? v_ : ks - 1 - v_)));
-          }
-          pre[r] = v;
-        }
-      };
-      auto commit = [&](float* dst) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          int e = lane + 32 * r;
-          if (e < kb_elems) dst[e] = pre[r];
-        }
-      };
-      // rows [ulo, uhi] of the fetched block holding a non-zero tap
-      auto extent = [&](int& ulo, int& uhi) {
-        unsigned lo_l = 0xffffffffu, hi_l = 0u;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          int e = lane + 32 * r;
-          if (e < kb_elems && pre[r] != 0.f) {
-            unsigned u = (unsigned)((e >> 1) / VB);
-            lo_l = min(lo_l, u);
-            hi_l = max(hi_l, u + 1u);
-          }
-        }
-        ulo = (int)__reduce_min_sync(0xffffffffu, lo_l);
-        uhi = (int)__reduce_max_sync(0xffffffffu, hi_l) - 1;
-      };
-      int ulo_n, uhi_n;
-      fetch(0);
-      extent(ulo_n, uhi_n);
-      commit(kb);
+  // the (group, source block) pairs of the item, dealt to the warps in turn
+  int pair = 0;
+  for (int g = g_lo; g <= g_hi; ++g) {
+    const int T0 = r0 + 8 * g;
+    const bool plain = T0 == r0 && r0 + 8 <= H;  // no row folds
+    // source blocks within reach: rows T0 - p .. T0 + 7 + p
+    const int sb_lo = max(0, (T0 - p) >> 3);  // arithmetic shift: floor division
+    const int sb_hi = min(nsb - 1, (T0 + 7 + p) >> 3);
+    for (int sb = sb_lo; sb <= sb_hi; ++sb, ++pair) {
+      if (pair % IG_NW != warp) continue;
+      const int d = T0 + p - 8 * sb;  // kernel row of (j, a) = d + j - a
+      // stage the source block: lane owns columns lane and lane + 32
       __syncwarp();
-      float* base = dpad + (rb * SB) * S + col;
-      for (int b = 0; b < nblk; ++b) {
-        const float* kcur = kb + (b & 1) * kb_elems;
-        const int ulo = ulo_n, uhi = uhi_n;
-        if (b + 1 < nblk) fetch(b + 1);
-        // taps outside rows [ulo, uhi] are zero: padded rows r in
-        // [r_begin, uhi + SB) are the only ones that can receive anything
-        const int r_begin = (ulo / SB) * SB;
-        const int vmax = uhi < 0 ? 0 : min(VB, ks - b * VB);
-        for (int vv = 0; vv < vmax; ++vv) {
-          float* colp = base + b * VB + vv;
-          const float2* kp = reinterpret_cast<const float2*>(kcur) + vv;
-          // ring of the taps u = r-SB+1 .. r of column v (zero outside [0, ks))
-          float kl[SB], kr[SB];
 #pragma unroll
-          for (int j = 0; j < SB; ++j) kl[j] = kr[j] = 0.f;
-          // contribution to padded row rb*SB + r: sum_j G_j Kf[r-j].  Rows
-          // r < KU: every tap row exists and every padded row is in the tile
-          // (KU <= ks + SB - 1); rows KU .. KU+SB-1 only drain the ring into
-          // the rows below ks + SB - 1.
-          const float2* kq = kp + r_begin * VB;
-          float* dq = colp + r_begin * S;
-          for (int r0 = r_begin; r0 < uhi + SB; r0 += SB) {
-            const bool tail = r0 >= KU;
+      for (int a = 0; a < 8; ++a) {
+        const int y = 8 * sb + a;
 #pragma unroll
-            for (int q = 0; q < SB; ++q) {
-              const float2 w2 = tail ? make_float2(0.f, 0.f) : kq[q * VB];
-              kl[q] = w2.x;
-              kr[q] = w2.y;
-              float a4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int h = 0; h < 2; ++h) {
+          const int col = lane + 32 * h, x = x0 + col;
+          float4 e = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+          if (y < H && x < W) {
+            const size_t o = (size_t)y * W + x;
+            const int2 sv = selp[o];
+            e = make_float4(goL[o], goR[o], __int_as_float(sv.y), __int_as_float(sv.x));
+          }
+          src[a][col] = e;
+        }
+      }
+      __syncwarp();
+      // the block's slices in ascending order; a pixel (key k0, weight t)
+      // uses k0 unless t == 1 and k0 + 1 when t > 0 (one slice: k0 only)
+      int last = -1;
+      while (true) {
+        int m = 0x7fffffff;
 #pragma unroll
-              for (int jj = 0; jj < SB; ++jj) {
-                a4[jj & 3] = fmaf(GL[jj], kl[(q - jj + SB) % SB], a4[jj & 3]);
-                a4[jj & 3] = fmaf(GR[jj], kr[(q - jj + SB) % SB], a4[jj & 3]);
-              }
-              // zero taps are common (the L and R halves of a blur disc),
-              // and skipping their atomics is what sets this loop's speed
-              const float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-              if ((!tail || r0 + q < ks + SB - 1) && acc != 0.f) atomicAdd(dq + q * S, acc);
-            }
-            kq += SB * VB;
-            dq += SB * S;
+        for (int q = 0; q < 16; ++q) {
+          const float4 e = src[q >> 1][lane + 32 * (q & 1)];
+          const int k0 = __float_as_int(e.w);
+          if (k0 >= 0) {
+            if ((!two || e.z < 1.f) && k0 > last) m = min(m, k0);
+            if (two && e.z > 0.f && k0 + 1 > last) m = min(m, k0 + 1);
           }
         }
-        if (b + 1 < nblk) {
-          extent(ulo_n, uhi_n);
-          commit(kb + ((b + 1) & 1) * kb_elems);
+        const int k = __reduce_min_sync(0xffffffffu, m);
+        if (k == 0x7fffffff) break;
+        last = k;
+        const int kl = k * P.NL + lam;
+        // kernel columns holding a non-zero tap in rows d - 7 .. d + 7
+        unsigned lo = 255u, hi = 0u;
+        if (lane < 15) {
+          const int u = d - 7 + lane;
+          if (u >= 0 && u < ks) {
+            const unsigned e = ext[(size_t)kl * ks + u];
+            lo = e & 0xffu;
+            hi = e >> 8;
+          }
         }
-        __syncwarp();
+        const int vlo = (int)__reduce_min_sync(0xffffffffu, lo);
+        const int vhi = (int)__reduce_max_sync(0xffffffffu, hi);
+        if (vlo > vhi) continue;
+        // the lane's columns that use slice k
+        bool f0 = false, f1 = false;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float4 e = src[q >> 1][lane + 32 * (q & 1)];
+          const int k0 = __float_as_int(e.w);
+          const bool use = k0 >= 0 && (((!two || e.z < 1.f) && k0 == k) ||
+                                       (two && e.z > 0.f && k0 + 1 == k));
+          if (q & 1) f1 = f1 || use; else f0 = f0 || use;
+        }
+        const unsigned m0 = __ballot_sync(0xffffffffu, f0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, f1);
+        const int n0 = __popc(m0), ncand = n0 + __popc(m1);
+        const float* kb0 = kcol + ((size_t)kl * ks + vlo) * col_stride + 2 * (d - 7 + IL.padu);
+        for (int q0 = 0; q0 < ncand; q0 += 32) {
+          const int idx = q0 + lane;
+          const bool act = idx < ncand;
+          const int col = !act ? 0 : (idx < n0 ? nth_set_bit(m0, idx) : 32 + nth_set_bit(m1, idx - n0));
+          float GL[8], GR[8];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            const float4 e = src[a][col];
+            const int k0 = __float_as_int(e.w);
+            const float w = !act || k0 < 0 ? 0.f
+                            : (k0 == k ? (two ? 1.f - e.z : 1.f) : ((two && k0 + 1 == k) ? e.z : 0.f));
+            GL[a] = w * e.x;
+            GR[a] = w * e.y;
+          }
+          const float4* kb = reinterpret_cast<const float4*>(kb0);
+          const size_t cs4 = col_stride / 4;
+          float* bcol = &buf[0][col];
+          // taps of column v: rows d - 7 .. d + 8, (L, R) interleaved; the
+          // next column's are loaded while this one is used
+          float4 tn[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
+          for (int v = vlo; v <= vhi; ++v) {
+            float T[32];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              T[4 * q] = tn[q].x;
+              T[4 * q + 1] = tn[q].y;
+              T[4 * q + 2] = tn[q].z;
+              T[4 * q + 3] = tn[q].w;
+            }
+            kb += cs4;
+            if (v < vhi) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
+            }
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float sl = 0.f, sr = 0.f;
+#pragma unroll
+              for (int a = 0; a < 8; ++a) {
+                sl = fmaf(GL[a], T[2 * (j - a + 7)], sl);
+                sr = fmaf(GR[a], T[2 * (j - a + 7) + 1], sr);
+              }
+              acc[j] = sl + sr;
+            }
+            if (act) {
+              if (plain) {  // distinct rows: loads, adds and stores batch
+                float old8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) old8[j] = bcol[j * BWMAX + v];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) bcol[j * BWMAX + v] = old8[j] + acc[j];
+              } else {  // folded rows may repeat: in order, one at a time
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const int tr = min(max(T0 - r0 + j, fold_lo), fold_hi);
+                  bcol[tr * BWMAX + v] += acc[j];
+                }
+              }
+            }
+            __syncwarp();
+          }
+        }
       }
-      int nxt = 0;
-      if (lane == 0) nxt = atomicAdd(&s_next, 1);
-      ch = __shfl_sync(0xffffffffu, nxt, 0);
     }
-    __syncthreads();
   }
-  // fold the padded tile onto the image (replicate padding adjoint)
+  __syncthreads();
+  // the warps' buffers added in warp order into warp 0's
+  float* b0 = &s_buf[0][0][0];
+  for (int i = threadIdx.x; i < 8 * BWMAX; i += IG_NW * 32) {
+    float s = b0[i];
+#pragma unroll
+    for (int w = 1; w < IG_NW; ++w) s += (&s_buf[w][0][0])[i];
+    b0[i] = s;
+  }
+  __syncthreads();
+  // columns outside the image fold onto its first / last column (fixed order)
+  const int cl = p - x0;            // buffer column of image column 0
+  const int cr = W - 1 - x0 + p;    // buffer column of image column W - 1
+  if (threadIdx.x < 8) {
+    const int j = threadIdx.x;
+    if (cl > 0) {
+      float s = 0.f;
+      for (int cc = 0; cc <= cl; ++cc) s += s_buf[0][j][cc];
+      s_buf[0][j][cl] = s;
+    }
+    if (cr < BW - 1) {
+      float s = s_buf[0][j][cr];
+      for (int cc = cr + 1; cc < BW; ++cc) s += s_buf[0][j][cc];
+      s_buf[0][j][cr] = s;
+    }
+  }
+  __syncthreads();
   float* ga = gaif + ((size_t)n * P.C + c) * H * W;
-  for (int i = tid; i < P.halo_h * S; i += NT) {
-    float v = dpad[i];
-    if (v == 0.f) continue;
-    int r = i / S, cc = i - r * S;
-    int yy = min(max(ty0 + r - p, 0), H - 1);
-    int xx = min(max(tx0 + cc - p, 0), W - 1);
-    atomicAdd(&ga[(size_t)yy * W + xx], v);
+  const int nrow = min(8, H - r0);
+  const int c_lo = max(0, cl), c_hi = min(BW - 1, cr);
+  const int ncol = c_hi - c_lo + 1;
+  for (int i = threadIdx.x; i < nrow * ncol; i += IG_NW * 32) {
+    const int j = i / ncol, cc = c_lo + (i - j * ncol);
+    ga[(size_t)(r0 + j) * W + (x0 - p + cc)] += s_buf[0][j][cc];
   }
 }
 
@@ -585,19 +646,6 @@ sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsign
   return launch_status();
 }
 
-template <int TX, int VB, int KSMAX, int SB, class TB>
-sd_status launch_img_bwd(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
-  using SM = BwdImgSmem<TX, VB, SB>;
-  P.halo_w = TX + P.ks - 1;
-  P.halo_h = RT_Y + P.ks - 1 + SB;
-  size_t smem = SM::bytes(P.ks);
-  auto k = render_bwd_img_kernel<TX, VB, KSMAX, SB, TB>;
-  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((P.W + TX - 1) / TX, (P.H + RT_Y - 1) / RT_Y, P.N * P.C);
-  k<<<grid, SM::NT, smem, s>>>(P, gout, gaif);
-  return launch_status();
-}
-
 constexpr size_t SMEM_CAP_B = 227 * 1024;
 // The bank gradient splits every slice's tiles over BANK_PARTS blocks when the
 // workspace holds that many partial banks (heavy slices otherwise set the
@@ -630,17 +678,43 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   return SD_OK;
 }
 
-// 8-pixel segments: 16-pixel segments halve the shared atomics per FMA but
-// need ~240 registers (8 warps per SM) and measured slower
+// The image gradient: selection table, bank re-layout, then one launch per
+// phase of non-overlapping strips (phase order fixed: deterministic).
 template <class TB>
-sd_status launch_img_bwd_any(RenderParams& P, const float* gout, float* gaif, cudaStream_t s) {
-  // one kernel column per fetch up to ks = 65 (as in the forward: 2.5 %
-  // faster with an FP32 bank, 9 % with a BF16 bank, than four columns)
-  if (P.ks <= 65 && BwdImgSmem<128, 1, 8>::bytes(P.ks) <= SMEM_CAP_B)
-    return launch_img_bwd<128, 1, 65, 8, TB>(P, gout, gaif, s);
-  if (BwdImgSmem<64, 4, 8>::bytes(P.ks) <= SMEM_CAP_B)
-    return launch_img_bwd<64, 4, 127, 8, TB>(P, gout, gaif, s);
-  return launch_img_bwd<64, 2, 127, 8, TB>(P, gout, gaif, s);
+sd_status launch_img_bwd(const RenderParams& P, const float* gout, float* gaif, void* ws,
+                         cudaStream_t s) {
+  const ImgLayout IL = img_layout(P);
+  char* base = reinterpret_cast<char*>(ws);
+  int2* sel = reinterpret_cast<int2*>(base);
+  float* kcol = reinterpret_cast<float*>(base + IL.sel_bytes);
+  unsigned short* ext = reinterpret_cast<unsigned short*>(base + IL.sel_bytes + IL.kcol_bytes);
+  const size_t npx = (size_t)P.N * P.H * P.W;
+  const int sblocks = (int)std::min<size_t>((npx + 255) / 256, (size_t)152 * 16);
+  select_table_kernel<<<sblocks, 256, 0, s>>>(P, sel);
+  sd_status st = launch_status();
+  if (st != SD_OK) return st;
+  const int n_kl = n_keys(P) * P.NL;
+  const size_t ksm = (size_t)2 * P.ks * P.ks * 4;
+  SD_CUDA_TRY(cudaFuncSetAttribute(kernel_columns_kernel<TB>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
+  kernel_columns_kernel<TB><<<n_kl, 256, ksm, s>>>(P, IL, kcol, ext);
+  st = launch_status();
+  if (st != SD_OK) return st;
+  const int nrange = (P.W + IG_SW - 1) / IG_SW, nrb = (P.H + 7) / 8;
+  const bool wide = P.ks > 65;
+  const size_t smem = (size_t)IG_NW * (8 * IG_SW * 16 + 8 * (wide ? 192 : 128) * 4);
+  auto k = wide ? render_bwd_img_kernel<192> : render_bwd_img_kernel<128>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int phase = 0; phase < IL.nphase && phase < nrange; ++phase) {
+    const int nr_phase = (nrange - phase + IL.nphase - 1) / IL.nphase;
+    const long long grid = (long long)nr_phase * nrb * P.N * P.C;  // one item per block
+    if (grid > 0x7fffffffll) return SD_ERR_UNSUPPORTED;
+    k<<<(unsigned)grid, IG_NW * 32, smem, s>>>(P, IL, gout, sel, kcol, ext, phase, nr_phase,
+                                               nrb, gaif);
+    st = launch_status();
+    if (st != SD_OK) return st;
+  }
+  return SD_OK;
 }
 
 template <class TI>
@@ -689,6 +763,7 @@ constexpr uint32_t BG_BBUF = BG_KB * BG_LBO_B;
 constexpr int BG_NB = 4;                     // B ring = producer warps 4..7
 constexpr int BG_MAXUG = 5;                  // kernel-row groups (ks <= 80)
 constexpr uint32_t BG_WAIT = 1u << 22;
+constexpr uint32_t BG_DRAIN = 1u << 24;  // final wait for the CTA's own products
 
 __host__ __device__ inline int bg_nug(int ks) { return (ks + 15) / 16; }
 __host__ __device__ inline size_t bg_img_bytes(int ks) {
@@ -698,15 +773,16 @@ __host__ __device__ inline size_t bg_smem(int ks) {
   return bg_img_bytes(ks) + (size_t)2 * RT_Y * BG_GW * 2 + (size_t)BG_NB * BG_BBUF;
 }
 
-__device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err) {
-  if (tc::mbar_wait(bar, parity, BG_WAIT, err)) return true;
+__device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err,
+                                        uint32_t limit) {
+  if (tc::mbar_wait(bar, parity, limit, err)) return true;
   atomicExch(err, 1);
   return false;
 }
 
 __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
     const RenderParams P, const float* __restrict__ gout, const unsigned* __restrict__ bm,
-    int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err) {
+    int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err, uint32_t wlim) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[BG_NB], s_empty[BG_NB], s_tile, s_done;
   __shared__ uint32_t s_tmem;
@@ -746,6 +822,7 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   const uint32_t img_a = tc::smem_u32(img), ring_a = tc::smem_u32(bring);
   int c_row = 0, visits = 0;
   unsigned inited = 0;  // kernel-row groups written (MMA thread)
+  bool issuing = true;  // MMA thread: false from the first wait that gave up
 
   // the tiles of this part that use the slice, in ascending order
   __shared__ int s_list[BG_NT], s_twc[BG_NT / 32];
@@ -763,7 +840,7 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
           // the previous visit's MMAs have read the image, the gradients and
           // their B rows; every producer has finished its builds
           if (visits > 0) {
-            if (lane == 0) bg_wait(&s_tile, (uint32_t)(visits - 1) & 1u, err);
+            if (lane == 0) bg_wait(&s_tile, (uint32_t)(visits - 1) & 1u, err, wlim);
             __syncwarp();
           }
           if (tid == 0) s_use = 0u;
@@ -864,7 +941,7 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
               const int cg = c_row + k;
               if (cg % BG_NB != b) continue;
               if (cg >= BG_NB) {
-                if (lane == 0) bg_wait(&s_empty[b], (uint32_t)(cg / BG_NB - 1) & 1u, err);
+                if (lane == 0) bg_wait(&s_empty[b], (uint32_t)(cg / BG_NB - 1) & 1u, err, wlim);
                 __syncwarp();
               }
               const int y = s_rows[k];
@@ -895,9 +972,10 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
             }
           } else if (warp == 0) {
             if (lane == 0) {
-              for (int k = 0; k < nrow; ++k) {
+              for (int k = 0; k < nrow && issuing; ++k) {
                 const int cg = c_row + k, b = cg % BG_NB;
-                if (!bg_wait(&s_full[b], (uint32_t)(cg / BG_NB) & 1u, err)) break;
+                issuing = bg_wait(&s_full[b], (uint32_t)(cg / BG_NB) & 1u, err, wlim);
+                if (!issuing) break;
                 tc::fence_after_sync();
                 const int y = s_rows[k];
                 for (int ug = 0; ug < nug; ++ug)
@@ -920,12 +998,14 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
           c_row += nrow;
         }
       }
-  // every MMA has completed; the accumulator holds the block's gradient
+  // every MMA has completed; the accumulator holds the block's gradient.
+  // This drain is bounded but not cut short by the error flag, so that no
+  // product is still running when the tensor memory is read and freed.
   if (tid == 0) {
     tc::commit(&s_done);
     s_init = (int)inited;
   }
-  if (lane == 0) bg_wait(&s_done, 0, err);
+  if (lane == 0 && !tc::mbar_wait(&s_done, 0, BG_DRAIN)) atomicExch(err, 1);
   __syncwarp();
   __syncthreads();
   tc::fence_after_sync();
@@ -966,7 +1046,8 @@ sd_status launch_bank_grad_tc(const RenderParams& P, const float* gout, const un
   const bool quad = P.fmode == SD_FIELD_QUADRANT;
   dim3 grid(n_keys(P), P.NL, parts);
   bank_grad_tc_kernel<<<grid, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty,
-                                                parts > 1 || quad ? parts_buf : gbank, parts, err);
+                                                parts > 1 || quad ? parts_buf : gbank, parts, err,
+                                                wait_limit(BG_WAIT));
   sd_status st = launch_status();
   if (st != SD_OK) return st;
   if (quad) {
@@ -993,7 +1074,8 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   if (st != SD_OK) return st;
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
-  *bytes = bitmap_bytes(N, tx, ty, n_keys(P)) + (size_t)BANK_PARTS * bank_bytes(P);
+  *bytes = img_layout(P).total + bitmap_bytes(N, tx, ty, n_keys(P)) +
+           (size_t)BANK_PARTS * bank_bytes(P);
   return SD_OK;
 }
 
@@ -1018,14 +1100,22 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
     if (grad_bank) SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
     return SD_OK;
   }
+  // the image pass's part of the workspace comes first
+  const size_t img_bytes = grad_aif ? img_layout(P).total : 0;
   if (grad_aif) {
+    if (!workspace || workspace_bytes < img_bytes ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+      return SD_ERR_ARG;
     SD_CUDA_TRY(cudaMemsetAsync(grad_aif, 0, (size_t)N * C * H * W * 4, s));
-    // the image pass reads the bank in its storage type
+    // the re-layout reads the bank in its storage type
     const int bt = layout->dtype;
-    sd_status r = bt == SD_F32    ? launch_img_bwd_any<float>(P, grad_out, grad_aif, s)
-                  : bt == SD_BF16 ? launch_img_bwd_any<__nv_bfloat16>(P, grad_out, grad_aif, s)
-                                  : launch_img_bwd_any<__half>(P, grad_out, grad_aif, s);
+    sd_status r = bt == SD_F32 ? launch_img_bwd<float>(P, grad_out, grad_aif, workspace, s)
+                  : bt == SD_BF16
+                      ? launch_img_bwd<__nv_bfloat16>(P, grad_out, grad_aif, workspace, s)
+                      : launch_img_bwd<__half>(P, grad_out, grad_aif, workspace, s);
     if (r != SD_OK) return r;
+    workspace = reinterpret_cast<char*>(workspace) + img_bytes;
+    workspace_bytes -= img_bytes;
   }
   if (grad_bank) {
     int tx, ty;
@@ -1136,7 +1226,8 @@ void* g_noalloc_ptr[64];  // device address of g_noalloc_scratch, per device
 
 // Device address of the scratch array on the current device; the first call
 // on a device looks it up (host code cannot use the array's name as a
-// device pointer).
+// device pointer).  Kept for the process's life: a cudaDeviceReset would
+// move the array, which the header excludes.
 sd_status noalloc_scratch(void** ptr) {
   int dev = 0;
   SD_CUDA_TRY(cudaGetDevice(&dev));
@@ -1154,22 +1245,25 @@ sd_status noalloc_scratch(void** ptr) {
 }  // namespace sd
 
 extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const float* aif,
-                                                   const float* depth_m, const float* bank,
+                                                   const float* depth_m, const void* bank,
                                                    const sd_bank_layout* layout, int N, int C,
                                                    int H, int W, float* grad_aif,
                                                    float* grad_bank, void* stream) {
   using namespace sd;
   void* ws = nullptr;
   size_t need = 0;
-  if (grad_bank) {
-    // the bitmap must fit; partial banks are used as far as the array allows
+  if (grad_aif || grad_bank) {
+    // the image pass's tables and the bank pass's bitmap must fit; partial
+    // banks are used as far as the array allows
     RenderParams P;
     sd_status st = setup_bwd(layout, N, C, H, W, P);
     if (st != SD_OK) return st;
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
-    need = bitmap_bytes(N, tx, ty, n_keys(P)) +
-           (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
+    if (grad_aif) need += img_layout(P).total;
+    if (grad_bank)
+      need += bitmap_bytes(N, tx, ty, n_keys(P)) +
+              (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
     if (need > NOALLOC_SCRATCH_BYTES) return SD_ERR_CAPACITY;
     st = noalloc_scratch(&ws);
     if (st != SD_OK) return st;

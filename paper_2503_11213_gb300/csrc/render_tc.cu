@@ -106,6 +106,7 @@ constexpr int TR_SI = 4;              // staged (row, K block) items per thread
 constexpr int TR_TPL = 5;             // B tasks per producer lane and kernel row (16 KB <= 160)
 constexpr int TR_WIN = 4096;          // slice keys of a tile as bits above its smallest
 constexpr uint32_t TR_WAIT = 1u << 20;  // completion polls before giving up
+constexpr uint32_t TR_DRAIN = 1u << 24;  // final wait for the CTA's own products
 
 // bank rows: flipped kernel rows padded to a multiple of 16 elements
 __host__ __device__ inline int tr_kp(int ks) { return (ks + 15) / 16 * 16; }
@@ -167,8 +168,9 @@ __global__ void tr_bank_kernel(const TB* __restrict__ bank, __nv_bfloat16* __res
 
 // Bounded completion wait; a wait that gives up raises the launch's error
 // flag at once, which makes every other wait of the launch give up too.
-__device__ __forceinline__ bool wait_flag(uint64_t* bar, uint32_t parity, int* err) {
-  if (tc::mbar_wait(bar, parity, TR_WAIT, err)) return true;
+__device__ __forceinline__ bool wait_flag(uint64_t* bar, uint32_t parity, int* err,
+                                          uint32_t limit) {
+  if (tc::mbar_wait(bar, parity, limit, err)) return true;
   atomicExch(err, 1);
   return false;
 }
@@ -187,13 +189,14 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 // rows: its row (i, side, slot) is the kernel row shifted right by i.
 __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams P,
                                                              const __nv_bfloat16* __restrict__ bp,
-                                                             int* __restrict__ err) {
+                                                             int* __restrict__ err,
+                                                             uint32_t wlim) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_uniq[TR_MAXK], s_wcnt[TR_NT / 32], s_nuniq;
   __shared__ unsigned s_bits[TR_WIN / 32];
   __shared__ int s_wpre[TR_WIN / 32], s_kmin, s_over;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_full[TR_NB], s_empty[TR_NB], s_acc;
+  __shared__ __align__(8) uint64_t s_full[TR_NB], s_empty[TR_NB], s_acc, s_fin;
   const int ks = P.ks, p = (ks - 1) >> 1, KP = tr_kp(ks), KK = tr_kk(ks), KB = KK / 8,
             R = TR_Y + ks - 1;
   const uint32_t LBO_A = tr_lbo_a(ks), BBUF = (uint32_t)tr_b_bytes(ks);
@@ -300,6 +303,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       tc::mbar_init(&s_empty[b], 1);
     }
     tc::mbar_init(&s_acc, 1);
+    tc::mbar_init(&s_fin, 1);
   }
   tc::fence_async_smem();  // the staged tile, read by the tensor core
   tc::fence_before_sync();
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
     for (int cg = b; cg < total; cg += TR_NB) {
       if (cg + TR_NB < total) load(nxt, cg + TR_NB);
       if (cg >= TR_NB)  // the MMAs of chunk cg - TR_NB read this buffer
-        wait_flag(&s_empty[b], (uint32_t)(cg / TR_NB - 1) & 1u, err);
+        wait_flag(&s_empty[b], (uint32_t)(cg / TR_NB - 1) & 1u, err, wlim);
       const int ui_base = (cg / nch) * TR_SL;
       uint4 other = make_uint4(0u, 0u, 0u, 0u);  // word kb of task e - 16 + 32 (q - 1)
 #pragma unroll
@@ -490,11 +494,15 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       for (int q = 0; q < TR_TPL; ++q) cur[q] = nxt[q];
     }
   } else {
+    // thread 0 stops issuing products at the first wait that gives up (the
+    // launch's error flag is then set and its output invalid)
+    bool issuing = true;
     for (int pass = 0; pass < npass; ++pass) {
       if (tid == 0) {
-        for (int ch = 0; ch < nch; ++ch) {
+        for (int ch = 0; ch < nch && issuing; ++ch) {
           const int cg = pass * nch + ch, b = cg % TR_NB;
-          wait_flag(&s_full[b], (uint32_t)(cg / TR_NB) & 1u, err);
+          issuing = wait_flag(&s_full[b], (uint32_t)(cg / TR_NB) & 1u, err, wlim);
+          if (!issuing) break;
           tc::fence_after_sync();
           // the start-address field is the low 14 bits (address >> 4)
           uint64_t ad = a_desc0 + (uint64_t)(ch * TR_CB);  // rows of 64 B
@@ -506,14 +514,16 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
           }
           tc::commit(&s_empty[b]);
         }
-        tc::commit(&s_acc);
+        if (issuing) tc::commit(&s_acc);
       }
       __syncwarp();
-      // the pass's accumulator
-      wait_flag(&s_acc, (uint32_t)pass & 1u, err);
+      // the pass's accumulator; a warp reads tensor memory only when every
+      // lane saw it complete (the loads are warp-collective)
+      const bool got =
+          __all_sync(0xffffffffu, wait_flag(&s_acc, (uint32_t)pass & 1u, err, wlim));
       tc::fence_after_sync();
 #pragma unroll
-      for (int i = 0; i < TR_J; ++i) {
+      for (int i = 0; i < TR_J && got; ++i) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(i * TR_SS), v);
 #pragma unroll
@@ -540,6 +550,13 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
         out[(((size_t)n * 2 * P.C + P.C + c) * H + yy) * W + xb + i] =
             __float2bfloat16_rn(outR[i]);
       }
+    // every product this CTA issued has completed before its tensor memory
+    // is freed, also when a wait gave up (a commit tracks all of them; the
+    // drain is bounded but not cut short by the error flag)
+    if (tid == 0) {
+      tc::commit(&s_fin);
+      if (!tc::mbar_wait(&s_fin, 0, TR_DRAIN)) atomicExch(err, 1);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -612,7 +629,7 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   SD_CUDA_TRY(cudaFuncSetAttribute(render_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   dim3 grid((W + TR_XW - 1) / TR_XW, (H + TR_Y - 1) / TR_Y, N * C);
-  render_tc_kernel<<<grid, TR_NT, smem, s>>>(P, bp, err);
+  render_tc_kernel<<<grid, TR_NT, smem, s>>>(P, bp, err, wait_limit(TR_WAIT));
   return launch_status();
 }
 

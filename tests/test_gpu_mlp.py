@@ -1,4 +1,4 @@
-"""The DP PSF network (Sec. 3.3) on the tensor cores against the oracle.
+"""The DP PSF network (Sec. 3.2) on the tensor cores against the oracle.
 
 * Exactness of the operand layouts: a network whose values are exact in BF16
   (layer 0 from biases only, permutation matrices, one-hot output rows) gives

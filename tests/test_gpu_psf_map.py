@@ -1,4 +1,4 @@
-"""The paper's own workload form (Sec. 4 implementation details, Table S3):
+"""The paper's own workload form (Sec. 5.1 implementation details, Table S3):
 2-D field points, the per-pixel DP PSF map of a depth map, and the render
 from a PSF map (the supplement's listing), against the oracle."""
 import numpy as np

@@ -1,6 +1,10 @@
 """GPU render backward against the oracle's adjoint (grad of the image and of
-the bank), the adjoint identities at full size, and determinism of the bank
-gradient.  Tolerance: max|err| <= 1e-4 max|ref| (FP32 accumulation)."""
+the bank), the adjoint identities at full size, and bitwise determinism of
+both gradients.  The image gradient's strip decomposition is also checked on
+shapes where its folding and phases matter (one pixel, images smaller than
+the kernel, fewer rows than a row block, ragged row blocks, a 1 x 1 kernel,
+the largest kernel).  Tolerance: max|err| <= 1e-4 max|ref| (FP32
+accumulation)."""
 import numpy as np
 import pytest
 import torch
@@ -93,6 +97,49 @@ def test_bank_gradient_deterministic_and_workspace_checked(sdlib):
         sd.dp_render_backward(*args, lay, need_aif=False, workspace=small)
 
 
+EDGE = [
+    # N, C, H, W, F, Z, NL, ks
+    (1, 1, 1, 1, 2, 2, 1, 5),        # one pixel: every tap folds onto it
+    (1, 2, 3, 5, 2, 3, 2, 9),        # image smaller than the kernel
+    (1, 1, 7, 200, 3, 3, 1, 31),     # fewer rows than a row block, four strips
+    (2, 1, 130, 17, 2, 4, 1, 65),    # narrow and tall, ragged last row block
+    (1, 1, 16, 64, 2, 2, 1, 1),      # 1 x 1 kernel: a single phase
+    (1, 1, 21, 300, 2, 3, 1, 127),   # largest kernel: three phases
+]
+
+
+@pytest.mark.parametrize("case", EDGE)
+def test_image_gradient_edge_shapes(sdlib, case):
+    sd = sdlib
+    aif, depth, fh, dm, pitch, bank, G = setup(case, 100 + case[-1])
+    lay = sd.BankLayout(fh, dm, bank.shape[2], bank.shape[-1], pitch)
+    ga, _ = sd.dp_render_backward(torch.tensor(G, device="cuda"),
+                                  torch.tensor(aif, device="cuda"),
+                                  torch.tensor(depth, device="cuda"),
+                                  torch.tensor(bank, device="cuda").reshape(-1), lay,
+                                  need_bank=False)
+    torch.cuda.synchronize()
+    ref_a, _ = O.render_bank_bwd(G, aif, depth, bank.astype(np.float64), fh, dm, pitch)
+    assert np.abs(ga.cpu().numpy() - ref_a).max() <= 1e-4 * np.abs(ref_a).max()
+
+
+def test_image_gradient_needs_aligned_workspace(sdlib):
+    sd = sdlib
+    aif, depth, fh, dm, pitch, bank, G = setup(CASES[0], 8)
+    lay = sd.BankLayout(fh, dm, 3, 15, pitch)
+    args = (torch.tensor(G, device="cuda"), torch.tensor(aif, device="cuda"),
+            torch.tensor(depth, device="cuda"), torch.tensor(bank, device="cuda").reshape(-1))
+    n = sd.render_backward_workspace(lay, *aif.shape)
+    ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sd.SdError):   # too small for the image tables
+        sd.dp_render_backward(*args, lay, need_bank=False, workspace=ws[:64])
+    with pytest.raises(sd.SdError):   # not 256-byte aligned
+        sd.dp_render_backward(*args, lay, need_bank=False, workspace=ws[8:])
+    ga, _ = sd.dp_render_backward(*args, lay, need_bank=False, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ga).all()
+
+
 def test_full_size_adjoint_identities(sdlib):
     """Batch of 8 RGB 512 x 512 images, the 32 x 32 x 3 bank of 65 x 65 PSFs:
     <R(I), G> = <I, dI(G)> and <R(B), G> = <B, dB(G)> (the render is linear
@@ -112,3 +159,7 @@ def test_full_size_adjoint_identities(sdlib):
     # FP32 accumulations over 6.3 M pixels x 8450 taps: relative 1e-4
     assert (aif.double() * ga.double()).sum().item() == pytest.approx(lhs, rel=1e-4)
     assert (bank.double() * gb.double()).sum().item() == pytest.approx(lhs, rel=1e-4)
+    # both gradients are bitwise reproducible
+    ga2, gb2 = sd.dp_render_backward(G, aif, depth, bank, lay)
+    torch.cuda.synchronize()
+    assert torch.equal(ga, ga2) and torch.equal(gb, gb2)

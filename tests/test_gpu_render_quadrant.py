@@ -1,5 +1,5 @@
 """Render through a first-quadrant 2-D bank (field points on a grid of
-(x, y) heights, other quadrants by the PSF's flip symmetry, Sec. 5.2)
+(x, y) heights, other quadrants by the PSF's flip symmetry, Sec. 5.3)
 against the oracle: FP32 storage max|err| <= 1e-4 max|ref|, BF16 storage on
 the rounded inputs <= 8 * 2^-9 max|ref|; odd and even image sizes (centre
 row / column on an axis), one and several depth slices, ks 1 to 65; the

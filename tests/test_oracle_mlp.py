@@ -1,4 +1,4 @@
-"""Pins of the oracle's DP PSF network (Sec. 3.3: five hidden layers of 512
+"""Pins of the oracle's DP PSF network (Sec. 3.2: five hidden layers of 512
 ReLU neurons, 2 ks^2 linear outputs, clamped and sum-normalised jointly at
 inference).
 

@@ -1,5 +1,5 @@
 """Pins of the first-quadrant (2-D) bank: the flip symmetry of the DP PSF
-about both axes (Sec. 5.2) checked on the oracle's own trace, and the
+about both axes (Sec. 5.3) checked on the oracle's own trace, and the
 oracle's quadrant-bank render checked against the listing render of a map of
 PSFs traced at every pixel's own signed field point (no flips there)."""
 import numpy as np

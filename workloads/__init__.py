@@ -302,7 +302,7 @@ def map_requests(depth_m, rows, cols, pitch_mm, lambda_nm, n_grid, ks):
 
 
 def config_paper_rf50():
-    """The paper's own timed workload (Sec. 4 implementation details, Table
+    """The paper's own timed workload (Sec. 5.1 implementation details, Table
     S3): Canon RF50mm (Table S1) stopped down to F/4, 550 nm, focus 1 m, a
     24 x 36 mm DP sensor of 512 x 768 pixels, a DP PSF for every pixel of a
     depth map over 0.5-20 m, a 64 x 64 pupil grid (4096 samples) and 21 x 21
