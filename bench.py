@@ -642,12 +642,13 @@ def pipeline_compare(sd, dev, reps=5):
     samples, render a batch of 8 RGB 512x512 images, render backward to the
     image and the bank, adjoint trace of the bank gradient.  Plain FP32 (one
     trace block per request, FP32 bank and images, eager launches) against
-    the batched BF16 pipeline (persistent batched trace writing a BF16 bank,
-    BF16 images rendered on the tensor cores, FP32 gradients (the bank's on the
-    tensor cores from BF16-rounded weighted output gradients), the whole step
-    replayed from one CUDA graph), with the bank error of both against the
-    FP64 oracle, the difference of the two renders and each stage timed
-    alone (eager launches)."""
+    the batched 16-bit pipelines, BF16 and FP16 (persistent batched trace
+    writing a 16-bit bank, 16-bit images rendered on the tensor cores, FP32
+    gradients: the image's on CUDA cores, the bank's on the tensor cores from
+    weighted output gradients rounded to the 16-bit type; the whole step
+    replayed from one CUDA graph).  Reported: each pipeline's time and
+    stages, each bank's L1 error against the FP64 oracle, each 16-bit
+    render's difference from the FP32 render."""
     import torch
     import oracle as O
     c = W.config_differentiation()
@@ -664,6 +665,7 @@ def pipeline_compare(sd, dev, reps=5):
     fh, dm = c["field_h_mm"], c["depths_mm"] / 1000.0
     stream = torch.cuda.current_stream()
     ks = c["ks"]
+    L = sd.lib()
 
     def make(dt):
         lay = sd.BankLayout(fh, dm, 3, ks, c["pitch_mm"], dtype=dt)
@@ -676,8 +678,6 @@ def pipeline_compare(sd, dev, reps=5):
         greq = torch.empty((n_req, 32, 8), device=dev)
         return lay, aif, out, gaif, gbank, ws, greq
 
-    L = sd.lib()
-
     def render_bwd(lay, aif, bank, gaif, gbank, ws):
         lc = lay.c()
         sd._lib.check(L.sd_dp_render_backward(
@@ -686,106 +686,107 @@ def pipeline_compare(sd, dev, reps=5):
             sd.api._ptr(gbank) if gbank is not None else None, sd.api._ptr(ws), ws.numel(),
             sd.api._stream()), "sd_dp_render_backward")
 
-    def render_bwd_tc(lay, aif, bank, gaif, gbank, ws_img, ws_bank):
-        # image gradient on CUDA cores, bank gradient on the tensor cores
-        render_bwd(lay, aif, bank, gaif, None, ws_img)
-        sd.dp_render_bank_grad_tc(gout, aif, depth, lay, out=gbank, workspace=ws_bank)
-
     # plain FP32
     lay32, aif32, out32, gaif32, gbank32, ws32, greq32 = make(torch.float32)
     bank32 = torch.empty(total, device=dev)
     st32 = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
 
-    def plain():
+    def trace32():
         sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
                         norm=sd.SD_NORM_JOINT, out=bank32, stats=st32)
+
+    def adj(gb, greq):
+        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gb, max_ks=ks, max_n=c["n_grid"],
+                                 grad_req=greq)
+
+    def plain():
+        trace32()
         sd.dp_render(aif32, depth, bank32, lay32, out=out32)
         render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32)
-        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank32, max_ks=ks,
-                                 max_n=c["n_grid"], grad_req=greq32)
+        adj(gbank32, greq32)
 
-    # batched BF16 under one CUDA graph
-    lay16, aif16, out16, gaif16, gbank16, ws16, greq16 = make(torch.bfloat16)
-    bt = sd.BatchedTrace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
-                         norm=sd.SD_NORM_JOINT, dtype=torch.bfloat16)
-    bt.tune(os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt"))
-
-    ws_tc = torch.empty(sd.api.render_tc_workspace(lay16), dtype=torch.uint8, device=dev)
-    ws_bg = torch.empty(sd.api.bank_grad_tc_workspace(lay16, B, 3, H, Wd), dtype=torch.uint8,
-                        device=dev)
-
-    def batched():
-        bank16, _ = bt.run()
-        sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16, workspace=ws_tc)
-        render_bwd_tc(lay16, aif16, bank16, gaif16, gbank16, ws16, ws_bg)
-        sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gbank16, max_ks=ks,
-                                 max_n=c["n_grid"], grad_req=greq16)
-
-    s2 = torch.cuda.Stream()
-    s2.wait_stream(stream)
-    with torch.cuda.stream(s2):
-        batched()
-    stream.wait_stream(s2)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        batched()
     t_plain = _timed(plain, stream, reps)
-    t_graph = _timed(g.replay, stream, reps)
+    stages = {"f32": {
+        "trace": _timed(trace32, stream, reps),
+        "render": _timed(lambda: sd.dp_render(aif32, depth, bank32, lay32, out=out32), stream,
+                         reps),
+        "render_bwd": _timed(lambda: render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32),
+                             stream, reps),
+        "trace_adjoint": _timed(lambda: adj(gbank32, greq32), stream, reps)}}
     torch.cuda.synchronize()
     r32 = out32.float()
-    render_diff = float((out16.float() - r32).abs().max().item() / r32.abs().max().item())
-    bank16 = bt.out
-    stages = {
-        "f32": {
-            "trace": _timed(lambda: sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=ks,
-                                                    max_n=c["n_grid"], norm=sd.SD_NORM_JOINT,
-                                                    out=bank32, stats=st32), stream, reps),
-            "render": _timed(lambda: sd.dp_render(aif32, depth, bank32, lay32, out=out32),
-                             stream, reps),
-            "render_bwd": _timed(lambda: render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32),
-                                 stream, reps),
-            "trace_adjoint": _timed(lambda: sd.dp_psf_trace_backward(
-                lens, sensor, req_dev, n_req, gbank32, max_ks=ks, max_n=c["n_grid"],
-                grad_req=greq32), stream, reps)},
-        "bf16": {
+    banks = {"f32": bank32.cpu().numpy()}
+    res = {"requests": n_req, "rays": int(st32[:, 0].sum().item()), "images": [B, 3, H, Wd],
+           "plain_f32_ms": round(t_plain, 3)}
+    tune_cache = os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt")
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        lay16, aif16, out16, gaif16, gbank16, ws16, greq16 = make(dt)
+        bt = sd.BatchedTrace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
+                             norm=sd.SD_NORM_JOINT, dtype=dt)
+        bt.tune(tune_cache)
+        ws_tc = torch.empty(sd.api.render_tc_workspace(lay16), dtype=torch.uint8, device=dev)
+        ws_bg = torch.empty(sd.api.bank_grad_tc_workspace(lay16, B, 3, H, Wd),
+                            dtype=torch.uint8, device=dev)
+
+        def render_bwd_tc():
+            # image gradient on CUDA cores, bank gradient on the tensor cores
+            render_bwd(lay16, aif16, bt.out, gaif16, None, ws16)
+            sd.dp_render_bank_grad_tc(gout, aif16, depth, lay16, out=gbank16, workspace=ws_bg)
+
+        def batched():
+            bt.run()
+            sd.dp_render_tc(aif16, depth, bt.out, lay16, out=out16, workspace=ws_tc)
+            render_bwd_tc()
+            adj(gbank16, greq16)
+
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            batched()
+        stream.wait_stream(s2)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            batched()
+        t_graph = _timed(g.replay, stream, reps)
+        torch.cuda.synchronize()
+        sd.sync_status(ws_tc[:4].view(torch.int32))
+        sd.sync_status(ws_bg[:4].view(torch.int32))
+        stages[name] = {
             "trace": _timed(lambda: bt.run(), stream, reps),
-            "render": _timed(lambda: sd.dp_render_tc(aif16, depth, bank16, lay16, out=out16,
+            "render": _timed(lambda: sd.dp_render_tc(aif16, depth, bt.out, lay16, out=out16,
                                                      workspace=ws_tc), stream, reps),
-            "render_bwd": _timed(lambda: render_bwd_tc(lay16, aif16, bank16, gaif16, gbank16, ws16,
-                                                       ws_bg), stream, reps),
-            "trace_adjoint": _timed(lambda: sd.dp_psf_trace_backward(
-                lens, sensor, req_dev, n_req, gbank16, max_ks=ks, max_n=c["n_grid"],
-                grad_req=greq16), stream, reps)}}
-    stages = {k: {n: round(v, 3) for n, v in d.items()} for k, d in stages.items()}
-    torch.cuda.synchronize()
-    # bank error of both against the FP64 oracle on 24 evenly spaced requests
+            "render_bwd": _timed(render_bwd_tc, stream, reps),
+            "trace_adjoint": _timed(lambda: adj(gbank16, greq16), stream, reps)}
+        torch.cuda.synchronize()
+        res[f"batched_{name}_graph_ms"] = round(t_graph, 3)
+        res[f"speedup_{name}"] = round(t_plain / t_graph, 3)
+        res[f"render_max_rel_diff_{name}_vs_f32"] = float(
+            (out16.float() - r32).abs().max().item() / r32.abs().max().item())
+        banks[name] = bt.out.float().cpu().numpy()
+        del g, bt, ws_tc, ws_bg, ws16, out16
+    res["stages_ms"] = {k: {n: round(v, 3) for n, v in d.items()} for k, d in stages.items()}
+    # bank error of every pipeline against the FP64 oracle on 24 evenly
+    # spaced requests
     idx = np.linspace(0, n_req - 1, 24).astype(int)
     S = dict(ps=c["pitch_mm"], h=W.DP_H * c["pitch_mm"], f=W.DP_F * c["pitch_mm"],
              w=W.DP_W * c["pitch_mm"], r=W.DP_R * c["pitch_mm"])
     ref, _ = O.psf_bank(c["lens"], c["focus_mm"], reqs[idx], S, n_threads=cpu_threads())
-    b32 = bank32.cpu().numpy()
-    b16 = bt.out.float().cpu().numpy()
 
     def l1(b):
         e = [np.abs(b[off[i]:off[i] + 2 * ks * ks] - r.ravel()).sum() / np.abs(r).sum()
              for i, r in zip(idx, ref)]
-        return float(np.mean(e)), float(np.max(e))
+        return {"mean": float(np.mean(e)), "max": float(np.max(e))}
 
-    e32, e16 = l1(b32), l1(b16)
-    rays = int(st32[:, 0].sum().item())
+    res["bank_l1_vs_oracle"] = {k: l1(v) for k, v in banks.items()}
+    res["bank_l1_vs_oracle"]["sample"] = "24 evenly spaced requests, FP64 oracle"
     lens.free()
-    return {"requests": n_req, "rays": rays, "images": [B, 3, H, Wd],
-            "plain_f32_ms": round(t_plain, 3), "batched_bf16_graph_ms": round(t_graph, 3),
-            "speedup": round(t_plain / t_graph, 3), "stages_ms": stages,
-            "render_max_rel_diff_bf16_vs_f32": render_diff,
-            "bank_l1_vs_oracle": {"f32": {"mean": e32[0], "max": e32[1]},
-                                  "bf16": {"mean": e16[0], "max": e16[1]},
-                                  "sample": "24 evenly spaced requests, FP64 oracle"}}
+    return res
 
 
 PAPER_TRACE_S = 801.544   # DP PSF map of 512 x 768 pixels by ray tracing (Table S3)
 PAPER_RENDER_S = 0.2      # DP image from a PSF map ("fixed cost", supplement)
 PAPER_MLP_S = 0.395       # DP PSF map of 512 x 768 pixels by the MLP (supplement table)
+MLP_FIT_ITERS = 20000     # Adam steps of the network fit in the paper-workload leg
 
 
 def quadrant_compare(sd, dev, reps=5):
@@ -874,21 +875,28 @@ def paper_workload(sd, dev, reps=5):
                      "render_gbs": round((map_bytes + io_bytes) / (t_rd * 1e-3) / 1e9, 1),
                      "trace_speedup_vs_paper": round(PAPER_TRACE_S / (t_tr * 1e-3), 1),
                      "render_speedup_vs_paper": round(PAPER_RENDER_S / (t_rd * 1e-3), 1)}
+        if dt == torch.float32:
+            traced_map = pmap   # the reference of the fitted network below
         del pmap, out
     peaks = load_peaks()
     if peaks.get("hbm_gbs"):
         res["render_hbm_frac_f32"] = round(res["f32"]["render_gbs"] / peaks["hbm_gbs"], 3)
-    # the paper's render-time PSF source: the MLP of Sec. 3.2 (5 x 512, 2 ks^2
-    # outputs) for every pixel, He-initialised (no trained weights here),
-    # then the same render from its map
-    rng = np.random.default_rng(0)
+    # the paper's render-time PSF source: the network of Sec. 3.2 (5 x 512,
+    # 2 ks^2 outputs) fitted to PSFs traced at random points of the region
+    # (max-normalised targets, Eq. 4 loss; seeded), its tensor-core map of
+    # every pixel, then the same render from that map
+    from paper_2503_11213_gb300 import psf_net as PN
+    ws, bs, info = PN.fit(lens, sensor, (H, Wd), c["pitch_mm"], c["d_near_m"], c["d_far_m"],
+                          c["lambda_nm"], n, ks, iters=MLP_FIT_ITERS, batch=1024, pool=1 << 17,
+                          seed=0, device=dev)
+    net = sd.PsfMLP(ws, bs, ks)
     shapes = sd.MLP_SHAPES(ks)
-    net = sd.PsfMLP([rng.normal(0, np.sqrt(2.0 / sh[1]), size=sh).astype(np.float32)
-                     for sh in shapes],
-                    [rng.normal(0, 0.05, size=sh[0]).astype(np.float32) for sh in shapes], ks)
     flops = 2.0 * H * Wd * sum(a * b for a, b in shapes)
-    mlp = {"network": "3 -> 5 x 512 (ReLU) -> 2 ks^2, He-initialised", "paper_mlp_s": PAPER_MLP_S,
-           "flops_per_map": flops}
+    mlp = {"network": "3 -> 5 x 512 (ReLU) -> 2 ks^2, fitted to traced PSFs",
+           "fit": {"iters": info["iters"], "batch": info["batch"], "pool_points": info["pool"],
+                   "pool_trace_s": round(info["trace_s"], 3), "train_s": round(info["train_s"], 2),
+                   "final_loss": info["final_loss"], "seed": info["seed"]},
+           "paper_mlp_s": PAPER_MLP_S, "flops_per_map": flops}
     st = torch.empty(1, dtype=torch.int32, device=dev)
     for name, dt in (("f32_map", torch.float32), ("bf16_map", torch.bfloat16)):
         pmap = torch.empty((H, Wd, 2, ks, ks), dtype=dt, device=dev)
@@ -896,8 +904,7 @@ def paper_workload(sd, dev, reps=5):
         out = torch.empty((1, 6, H, Wd), dtype=dt, device=dev)
         t_m = _timed(lambda: sd.mlp_psf_map(net, depth, c["d_near_m"], c["d_far_m"], out=pmap,
                                             status=st), stream, reps)
-        if int(st.item()) != 0:
-            raise RuntimeError("MLP kernel: a completion wait gave up")
+        sd.sync_status(st)
 
         def both():
             sd.mlp_psf_map(net, depth, c["d_near_m"], c["d_far_m"], out=pmap, status=st)
@@ -909,7 +916,31 @@ def paper_workload(sd, dev, reps=5):
                      "frac_of_bf16_peak": round(tf / peaks["bf16_tflops"], 3)
                      if peaks.get("bf16_tflops") else None,
                      "speedup_vs_paper_mlp": round(PAPER_MLP_S / (t_m * 1e-3), 1)}
+        if dt == torch.float32:
+            # accuracy of the predicted map against the traced map of the same
+            # depth map (per element of the sum-normalised PSFs), split into
+            # the fit (the FP32 network) and the kernel's BF16 activations
+            yy, xx = torch.meshgrid(torch.arange(H, device=dev), torch.arange(Wd, device=dev),
+                                    indexing="ij")
+            pin = torch.stack([(xx - 0.5 * (Wd - 1)) / (0.5 * Wd),
+                               (yy - 0.5 * (H - 1)) / (0.5 * H),
+                               2 * (depth - c["d_near_m"]) / (c["d_far_m"] - c["d_near_m"]) - 1],
+                              -1).reshape(-1, 3).float()
+            prm = [torch.tensor(a, device=dev) for pair in zip(ws, bs) for a in pair]
+            with torch.no_grad():
+                f32net = torch.cat([PN.sum_normalised(PN.forward(prm, pin[i:i + 65536]))
+                                    for i in range(0, pin.shape[0], 65536)]).view(pmap.shape)
+            mlp["accuracy_vs_traced_map"] = {
+                "kernel_map": PN.map_errors(pmap, traced_map),
+                "fp32_network": PN.map_errors(f32net, traced_map),
+                "kernel_vs_fp32_network": PN.map_errors(pmap, f32net),
+                "definition": "per element of the sum-normalised 2 x 21 x 21 PSFs of all "
+                              "512 x 768 pixels: l1 = mean |err|, l2 = mean err^2",
+                "paper_table_s3": {"l1": 6.887e-5, "l2": 6.830e-8,
+                                   "note": "50 depths and positions, RTX 3090; context"}}
+            del f32net
         del pmap, out
+    del traced_map
     res["mlp"] = mlp
     lens.free()
     return res

@@ -382,19 +382,20 @@ sd_status sd_dp_render_map(const void* aif, const void* psf_map, int N, int C,
                            void* out, void* stream);
 
 /*
- * sd_dp_render for BF16 images on the tensor cores (tcgen05, FP32
- * accumulation in tensor memory): aif (N,C,H,W) and out (N,2C,H,W) BF16,
- * depth_m (N,H,W) FP32, bank in layout->dtype (SD_BF16, or SD_F32 rounded to
- * BF16), all device.  Same selection, padding and output layout as
- * sd_dp_render.  Needs a device workspace of sd_dp_render_tc_workspace()
- * bytes, 256-byte aligned (a BF16 re-layout of the bank written by the call
- * and, in its first word, an error flag set to 1 if a tensor-core completion
- * wait ever gave up).  Supports ks <= 65 (SD_ERR_UNSUPPORTED otherwise).
- * Deterministic.
+ * sd_dp_render for 16-bit images on the tensor cores (tcgen05, FP32
+ * accumulation in tensor memory): aif (N,C,H,W) and out (N,2C,H,W) in
+ * image_dtype (SD_BF16 or SD_F16: both operands of a product share the
+ * type), depth_m (N,H,W) FP32, bank in layout->dtype (the image's type, or
+ * SD_F32 rounded to it), all device.  Same selection, padding and output
+ * layout as sd_dp_render.  Needs a device workspace of
+ * sd_dp_render_tc_workspace() bytes, 256-byte aligned (a 16-bit re-layout of
+ * the bank written by the call and, in its first word, an error flag set to
+ * 1 if a tensor-core completion wait ever gave up; sd_sync_status reads it).
+ * Supports ks <= 65 (SD_ERR_UNSUPPORTED otherwise).  Deterministic.
  */
 sd_status sd_dp_render_tc(const void* aif, const float* depth_m, const void* bank,
                           const sd_bank_layout* layout, int N, int C, int H,
-                          int W, void* out, void* workspace,
+                          int W, int image_dtype, void* out, void* workspace,
                           size_t workspace_bytes, void* stream);
 
 /* Workspace bytes of sd_dp_render_tc for this bank layout. */
@@ -439,21 +440,24 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
 
 /*
  * The bank gradient of sd_dp_render_backward on the tensor cores (tcgen05),
- * for BF16 images: grad_bank (FP32, the stored bank's shape) = the adjoint of
- * the render with respect to the bank, with the image in BF16, the weighted
- * output gradients w * G rounded to BF16, products exact and accumulated in
- * FP32 in tensor memory in a fixed order (deterministic).  grad_out (N,2C,H,W)
- * FP32, aif (N,C,H,W) BF16, depth_m (N,H,W) FP32, all device; the bank itself
- * is not read.  Workspace from sd_dp_render_bank_grad_tc_workspace (device,
- * 256-byte aligned; its first int32 becomes 1 if a bounded completion wait
- * gave up).  ks <= 80.  Radial and quadrant banks.
+ * for 16-bit images: grad_bank (FP32, the stored bank's shape) = the adjoint
+ * of the render with respect to the bank, with the image in image_dtype
+ * (SD_BF16 or SD_F16), the weighted output gradients w * G rounded to the
+ * same type (SD_F16: |w * G| must stay below 65504), products exact and
+ * accumulated in FP32 in tensor memory in a fixed order (deterministic).
+ * grad_out (N,2C,H,W) FP32, aif (N,C,H,W), depth_m (N,H,W) FP32, all device;
+ * the bank itself is not read.  Workspace from
+ * sd_dp_render_bank_grad_tc_workspace (device, 256-byte aligned; its first
+ * int32 becomes 1 if a bounded completion wait gave up).  ks <= 80.  Radial
+ * and quadrant banks.
  */
 sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,
                                               int H, int W, size_t* bytes);
 sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif,
                                     const float* depth_m, const sd_bank_layout* layout,
-                                    int N, int C, int H, int W, float* grad_bank,
-                                    void* workspace, size_t workspace_bytes, void* stream);
+                                    int N, int C, int H, int W, int image_dtype,
+                                    float* grad_bank, void* workspace, size_t workspace_bytes,
+                                    void* stream);
 
 /*
  * sd_dp_render_backward for callers that cannot allocate device memory: code

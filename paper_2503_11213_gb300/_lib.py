@@ -127,7 +127,7 @@ def lib():
     L.sd_dp_trace_hits.argtypes = [vp, P(SdSensor), vp, P(SdTraceOpts), vp, i32, vp, vp]
     L.sd_dp_psf_map.argtypes = [vp, P(SdSensor), vp, i32, i32, dbl, i32, i32, P(SdTraceOpts),
                                 vp, vp, vp]
-    L.sd_dp_render_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, vp, vp,
+    L.sd_dp_render_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp,
                                   ctypes.c_size_t, vp]
     L.sd_dp_render_tc_workspace.argtypes = [P(SdBankLayout), P(ctypes.c_size_t)]
     L.sd_dp_render_map.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp]
@@ -142,8 +142,8 @@ def lib():
     L.sd_dev_tc_check.argtypes = [vp, vp, i32, vp, vp, vp]
     L.sd_dp_render_bank_grad_tc_workspace.argtypes = [P(SdBankLayout), i32, i32, i32, i32,
                                                       P(ctypes.c_size_t)]
-    L.sd_dp_render_bank_grad_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, vp,
-                                            vp, ctypes.c_size_t, vp]
+    L.sd_dp_render_bank_grad_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32,
+                                            vp, vp, ctypes.c_size_t, vp]
     fl = ctypes.c_float
     L.sd_mlp_blob_bytes.argtypes = [i32, P(ctypes.c_size_t)]
     L.sd_mlp_pack.argtypes = [P(P(fl)), P(P(fl)), i32, vp, ctypes.c_size_t]

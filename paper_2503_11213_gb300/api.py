@@ -344,15 +344,15 @@ def render_tc_workspace(layout: BankLayout):
 
 
 def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=None):
-    """dp_render of a BF16 image on the tensor cores: aif (N,C,H,W) bf16,
-    depth (N,H,W) f32, bank bf16 (or f32, rounded) -> (N,2C,H,W) bf16.
-    The workspace's first int32 is an error flag (1 = a completion wait
-    gave up)."""
+    """dp_render of a 16-bit image on the tensor cores: aif (N,C,H,W) bf16
+    or f16, depth (N,H,W) f32, bank in aif's dtype (or f32, rounded) ->
+    (N,2C,H,W) in aif's dtype.  The workspace's first int32 is an error flag
+    (1 = a completion wait gave up)."""
     N, C, H, W = aif.shape
-    if aif.dtype != torch.bfloat16:
-        raise ValueError("the tensor-core render takes a bfloat16 image")
+    if aif.dtype not in (torch.bfloat16, torch.float16):
+        raise ValueError("the tensor-core render takes a bfloat16 or float16 image")
     if out is None:
-        out = torch.empty((N, 2 * C, H, W), dtype=torch.bfloat16, device=aif.device)
+        out = torch.empty((N, 2 * C, H, W), dtype=aif.dtype, device=aif.device)
     if workspace is None:
         workspace = torch.empty(render_tc_workspace(layout), dtype=torch.uint8, device=aif.device)
     _need_cuda(aif, depth_m, bank, out, workspace)
@@ -360,8 +360,8 @@ def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=Non
         raise ValueError("bank dtype must match the layout; depth must be float32")
     lay = layout.c()
     L.check(L.lib().sd_dp_render_tc(_ptr(aif), _ptr(depth_m), _ptr(bank), ctypes.byref(lay),
-                                    N, C, H, W, _ptr(out), _ptr(workspace), workspace.numel(),
-                                    _stream()), "sd_dp_render_tc")
+                                    N, C, H, W, _DT[aif.dtype], _ptr(out), _ptr(workspace),
+                                    workspace.numel(), _stream()), "sd_dp_render_tc")
     return out
 
 
@@ -390,12 +390,12 @@ def bank_grad_tc_workspace(layout: BankLayout, N, C, H, W):
 
 def dp_render_bank_grad_tc(grad_out, aif, depth_m, layout: BankLayout, out=None, workspace=None):
     """Bank gradient of dp_render on the tensor cores: grad_out (N,2C,H,W)
-    f32, aif (N,C,H,W) bf16, depth (N,H,W) f32 -> grad_bank (layout.shape())
-    f32.  The workspace's first int32 is an error flag (1 = a completion wait
-    gave up)."""
+    f32, aif (N,C,H,W) bf16 or f16, depth (N,H,W) f32 -> grad_bank
+    (layout.shape()) f32.  The workspace's first int32 is an error flag (1 =
+    a completion wait gave up)."""
     N, C, H, W = aif.shape
-    if aif.dtype != torch.bfloat16 or grad_out.dtype != torch.float32:
-        raise ValueError("bf16 image and float32 output gradient")
+    if aif.dtype not in (torch.bfloat16, torch.float16) or grad_out.dtype != torch.float32:
+        raise ValueError("bf16 or f16 image and float32 output gradient")
     if out is None:
         out = torch.empty(layout.shape(), dtype=torch.float32, device=aif.device)
     if workspace is None:
@@ -404,7 +404,8 @@ def dp_render_bank_grad_tc(grad_out, aif, depth_m, layout: BankLayout, out=None,
     _need_cuda(grad_out, aif, depth_m, out, workspace)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_bank_grad_tc(_ptr(grad_out), _ptr(aif), _ptr(depth_m),
-                                              ctypes.byref(lay), N, C, H, W, _ptr(out),
+                                              ctypes.byref(lay), N, C, H, W, _DT[aif.dtype],
+                                              _ptr(out),
                                               _ptr(workspace), workspace.numel(), _stream()),
             "sd_dp_render_bank_grad_tc")
     return out

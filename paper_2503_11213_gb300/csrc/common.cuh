@@ -6,9 +6,22 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sdirt.h"
 
 namespace sd {
+
+// A named NVTX range around each compute entry point of the C ABI, so that
+// a profiler's timeline groups the launches of one call under its name (a
+// no-op unless a profiling tool is attached).
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange&) = delete;
+  ApiRange& operator=(const ApiRange&) = delete;
+};
+#define SD_API_RANGE(name) ::sd::ApiRange sd_api_range_(name)
 
 // last CUDA error seen on this host thread
 void set_cuda_error(cudaError_t e);

@@ -219,6 +219,7 @@ extern "C" {
 
 sd_status sd_lens_load(const sd_surface* surfs, int n, double focus_mm,
                        sd_lens** out) {
+  SD_API_RANGE("sd_lens_load");
   using namespace sd;
   if (!surfs || !out || n < 1 || n > SD_MAX_SURFACES) return SD_ERR_ARG;
   if (!std::isfinite(focus_mm)) return SD_ERR_ARG;
@@ -967,6 +968,7 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
                           const sd_dp_sensor* sensor, const sd_psf_request* req,
                           int n_req, const sd_trace_opts* opts, void* out,
                           int64_t* stats, void* stream) {
+  SD_API_RANGE("sd_dp_psf_trace");
   using namespace sd;
   if (!opts || !out || (n_req > 0 && !req) || n_req < 0) return SD_ERR_ARG;
   if (n_req == 0) return SD_OK;
@@ -1013,6 +1015,7 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
                         const float* depth_m, int H, int W, double lambda_nm,
                         int n_grid, int ks, const sd_trace_opts* opts, void* out,
                         int64_t* stats, void* stream) {
+  SD_API_RANGE("sd_dp_psf_map");
   using namespace sd;
   if (!lens || !opts || !out || !depth_m || H < 0 || W < 0) return SD_ERR_ARG;
   if ((long long)H * W > 0x7fffffffLL) return SD_ERR_UNSUPPORTED;
@@ -1444,6 +1447,7 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
                                               const sd_trace_opts* opts, const float* grad_out,
                                               float* grad_req, float* grad_lens,
                                               int64_t* swept, void* stream) {
+  SD_API_RANGE("sd_dp_psf_trace_backward");
   using namespace sd;
   if (!opts || !grad_out || !grad_req || n_req < 0 || (n_req > 0 && !req)) return SD_ERR_ARG;
   TraceParams P;
@@ -1797,6 +1801,7 @@ sd_status sd_dp_psf_trace_batched(const sd_lens* const* lenses, int n_lenses,
                                   const sd_batch_config* cfg, void* out, long long total_elems,
                                   int64_t* stats, void* workspace, size_t workspace_bytes,
                                   void* stream) {
+  SD_API_RANGE("sd_dp_psf_trace_batched");
   using namespace sd;
   if (!opts || !out || n_req < 0 || (n_req > 0 && !req) || total_elems < 0) return SD_ERR_ARG;
   if (n_req == 0) return SD_OK;

@@ -380,6 +380,7 @@ extern "C" sd_status sd_mlp_blob_bytes(int ks, size_t* bytes) {
 
 extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const* biases, int ks,
                                  void* blob, size_t blob_bytes) {
+  SD_API_RANGE("sd_mlp_pack");
   using namespace sd;
   if (!weights || !biases || !blob || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS) return SD_ERR_ARG;
   for (int l = 0; l < 6; ++l)
@@ -417,6 +418,7 @@ extern "C" sd_status sd_mlp_pack(const float* const* weights, const float* const
 extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth_m, int H, int W,
                                     float d_min_m, float d_max_m, void* out, int out_dtype,
                                     int32_t* status, void* stream) {
+  SD_API_RANGE("sd_mlp_psf_map");
   using namespace sd;
   if (!blob || !depth_m || !out || !status || ks < 1 || !(ks & 1) || ks > SD_MLP_MAX_KS)
     return SD_ERR_ARG;

@@ -351,6 +351,7 @@ extern "C" {
 sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
                        const sd_bank_layout* layout, int N, int C, int H, int W,
                        int image_dtype, void* out, void* stream) {
+  SD_API_RANGE("sd_dp_render");
   using namespace sd;
   if (!aif || !depth_m || !bank || !out) return SD_ERR_ARG;
   if (N < 0 || C < 1 || H < 0 || W < 0) return SD_ERR_ARG;

@@ -735,8 +735,9 @@ sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const un
 
 
 // ---------------------------------------------------------------------------
-// 4. bank gradient on the tensor cores (BF16 image; the weighted gradients
-// w * G rounded to BF16; FP32 accumulation in tensor memory)
+// 4. bank gradient on the tensor cores (BF16 or FP16 image; the weighted
+// gradients w * G rounded to the image's type; FP32 accumulation in tensor
+// memory)
 //
 // Block (slice key, wavelength, part) as in pass 3.  For a tile pixel row y
 // and a group of 16 kernel rows u0..u0+15 the slice gradient is one product
@@ -780,6 +781,7 @@ __device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err
   return false;
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
     const RenderParams P, const float* __restrict__ gout, const unsigned* __restrict__ bm,
     int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err, uint32_t wlim) {
@@ -818,7 +820,7 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = tc::idesc_bf16_f32(128, BG_N);
+  const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, BG_N) : tc::idesc_bf16_f32(128, BG_N);
   const uint32_t img_a = tc::smem_u32(img), ring_a = tc::smem_u32(bring);
   int c_row = 0, visits = 0;
   unsigned inited = 0;  // kernel-row groups written (MMA thread)
@@ -915,8 +917,8 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
                 gl = w * gq[t][0];
                 gr = w * gq[t][1];
               }
-              const unsigned short bl = __bfloat16_as_ushort(__float2bfloat16_rn(gl));
-              const unsigned short br = __bfloat16_as_ushort(__float2bfloat16_rn(gr));
+              const unsigned short bl = tc::to_op16(gl, F16);
+              const unsigned short br = tc::to_op16(gr, F16);
               gw[r * BG_GW + x + 16] = bl;
               gw[RT_Y * BG_GW + r * BG_GW + x + 16] = br;
               if ((bl | br) & 0x7fffu) atomicOr(&s_use, 1u << r);
@@ -1037,17 +1039,16 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
 
 sd_status launch_bank_grad_tc(const RenderParams& P, const float* gout, const unsigned* bm,
                               int words, int ntx, int nty, float* gbank, float* parts_buf,
-                              int parts, int* err, cudaStream_t s) {
+                              int parts, int* err, bool f16, cudaStream_t s) {
   const int ks = P.ks;
   // at least 80 KB: two CTAs per SM, the tensor memory's 512 columns
   const size_t smem = std::max(bg_smem(ks), (size_t)80 * 1024);
-  SD_CUDA_TRY(cudaFuncSetAttribute(bank_grad_tc_kernel,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto k = f16 ? bank_grad_tc_kernel<true> : bank_grad_tc_kernel<false>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const bool quad = P.fmode == SD_FIELD_QUADRANT;
   dim3 grid(n_keys(P), P.NL, parts);
-  bank_grad_tc_kernel<<<grid, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty,
-                                                parts > 1 || quad ? parts_buf : gbank, parts, err,
-                                                wait_limit(BG_WAIT));
+  k<<<grid, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 || quad ? parts_buf : gbank,
+                              parts, err, wait_limit(BG_WAIT));
   sd_status st = launch_status();
   if (st != SD_OK) return st;
   if (quad) {
@@ -1084,6 +1085,7 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
                                 int H, int W, int image_dtype, float* grad_aif,
                                 float* grad_bank, void* workspace, size_t workspace_bytes,
                                 void* stream) {
+  SD_API_RANGE("sd_dp_render_backward");
   using namespace sd;
   if (!grad_out || !aif || !depth_m || !bank) return SD_ERR_ARG;
   if (image_dtype != SD_F32 && image_dtype != SD_BF16 && image_dtype != SD_F16)
@@ -1166,13 +1168,15 @@ sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int 
 
 sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, const float* depth_m,
                                     const sd_bank_layout* layout, int N, int C, int H, int W,
-                                    float* grad_bank, void* workspace, size_t workspace_bytes,
-                                    void* stream) {
+                                    int image_dtype, float* grad_bank, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
+  SD_API_RANGE("sd_dp_render_bank_grad_tc");
   using namespace sd;
   if (!grad_out || !aif || !depth_m || !grad_bank) return SD_ERR_ARG;
   RenderParams P;
   sd_status st = setup_bwd(layout, N, C, H, W, P);
   if (st != SD_OK) return st;
+  if (image_dtype != SD_BF16 && image_dtype != SD_F16) return SD_ERR_UNSUPPORTED;
   if (P.ks > 16 * BG_MAXUG || bg_smem(P.ks) > 227 * 1024) return SD_ERR_UNSUPPORTED;
   P.aif = aif;
   P.depth = depth_m;
@@ -1204,7 +1208,7 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
   st = launch_status();
   if (st != SD_OK) return st;
   return launch_bank_grad_tc(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf, parts,
-                             err, s);
+                             err, image_dtype == SD_F16, s);
 }
 
 }  // extern "C"
@@ -1249,6 +1253,7 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
                                                    const sd_bank_layout* layout, int N, int C,
                                                    int H, int W, float* grad_aif,
                                                    float* grad_bank, void* stream) {
+  SD_API_RANGE("sd_dp_render_backward_noalloc");
   using namespace sd;
   void* ws = nullptr;
   size_t need = 0;

@@ -52,8 +52,16 @@ __host__ __device__ inline size_t map_smem_bytes(int ks, int cw) {
   return (size_t)cw * S * R * 4 + (size_t)ks * ks * 4;
 }
 
+// 16-bit map values are held in registers as raw pairs and widened on use
+__device__ __forceinline__ float half16(uint32_t w, int hi, __nv_bfloat16*) {
+  return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+}
+__device__ __forceinline__ float half16(uint32_t w, int hi, __half*) {
+  return __half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xffffu))));
+}
+
 template <class TI, class TM, int CW>
-__global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
+__global__ void __launch_bounds__(MAP_NT, 4) render_map_kernel(const MapParams P) {
   using V = typename Vec<CW>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks, S = P.S, R = MT_Y + ks - 1;
@@ -93,21 +101,36 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
   const int E = 2 * ks2;
   const TM* mrow = reinterpret_cast<const TM*>(P.map) + ((size_t)y * P.W + x0) * E;
   const int xmax = min(MT_X, P.W - x0);
-  // the row's kernels as a stream of (pixel, tap chunk) items of 32*NTAP
+  // the row's kernels as a stream of (pixel, tap chunk) items of 32*NT
   // taps (L and R values of each); the next item is loaded while the current
-  // one is used
-  const int nch = (ks2 + 32 * NTAP - 1) / (32 * NTAP), items = xmax * nch;
-  float curL[NTAP], curR[NTAP], nxtL[NTAP], nxtR[NTAP];
-  auto load = [&](float* dl, float* dr, int it) {
+  // one is used.  A 16-bit map moves half the bytes per load, so an item has
+  // twice the taps (the same bytes in flight), kept as raw pairs.
+  constexpr bool W16 = sizeof(TM) == 2;
+  constexpr int NT = W16 ? 2 * NTAP : NTAP;
+  constexpr int NR = W16 ? NT / 2 : NT;  // registers per plane and item
+  const int nch = (ks2 + 32 * NT - 1) / (32 * NT), items = xmax * nch;
+  uint32_t curL[NR], curR[NR], nxtL[NR], nxtR[NR];
+  auto load = [&](uint32_t* dl, uint32_t* dr, int it) {
     const int px = it / nch, ch = it - px * nch;
     const TM* K = mrow + (size_t)px * E;
 #pragma unroll
-    for (int j = 0; j < NTAP; ++j) {
-      const int e = ch * 32 * NTAP + lane + 32 * j;
+    for (int j = 0; j < NT; ++j) {
+      const int e = ch * 32 * NT + lane + 32 * j;
       const bool in = e < ks2;
-      dl[j] = in ? to_f32<TM>(__ldg(K + e)) : 0.f;
-      dr[j] = in ? to_f32<TM>(__ldg(K + ks2 + e)) : 0.f;
+      if (W16) {
+        const uint32_t l = in ? __ldg(reinterpret_cast<const unsigned short*>(K) + e) : 0u;
+        const uint32_t r = in ? __ldg(reinterpret_cast<const unsigned short*>(K) + ks2 + e) : 0u;
+        dl[j >> 1] = (j & 1) ? (dl[j >> 1] | (l << 16)) : l;
+        dr[j >> 1] = (j & 1) ? (dr[j >> 1] | (r << 16)) : r;
+      } else {
+        dl[j] = __float_as_uint(in ? to_f32<TM>(__ldg(K + e)) : 0.f);
+        dr[j] = __float_as_uint(in ? to_f32<TM>(__ldg(K + ks2 + e)) : 0.f);
+      }
     }
+  };
+  auto val = [&](const uint32_t* d, int j) {
+    if constexpr (W16) return half16(d[j >> 1], j & 1, (TM*)nullptr);
+    else return __uint_as_float(d[j]);
   };
   float aL[CW], aR[CW];
 #pragma unroll
@@ -118,14 +141,15 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
     const int px = it / nch, ch = it - px * nch;
     const int base = warp * S + px;
 #pragma unroll
-    for (int j = 0; j < NTAP; ++j) {
-      const int e = ch * 32 * NTAP + lane + 32 * j;
+    for (int j = 0; j < NT; ++j) {
+      const int e = ch * 32 * NT + lane + 32 * j;
       if (e < ks2) {
         const V v = vtile[base + offs[e]];
+        const float kl = val(curL, j), kr = val(curR, j);
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-          aL[c] = fmaf(comp(v, c), curL[j], aL[c]);
-          aR[c] = fmaf(comp(v, c), curR[j], aR[c]);
+          aL[c] = fmaf(comp(v, c), kl, aL[c]);
+          aR[c] = fmaf(comp(v, c), kr, aR[c]);
         }
       }
     }
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < NTAP; ++j) {
+    for (int j = 0; j < NR; ++j) {
       curL[j] = nxtL[j];
       curR[j] = nxtR[j];
     }
@@ -194,6 +218,7 @@ sd_status launch_map(MapParams& P, cudaStream_t s) {
 extern "C" sd_status sd_dp_render_map(const void* aif, const void* psf_map, int N, int C,
                                       int H, int W, int ks, int image_dtype, int map_dtype,
                                       void* out, void* stream) {
+  SD_API_RANGE("sd_dp_render_map");
   using namespace sd;
   if (!aif || !psf_map || !out) return SD_ERR_ARG;
   if (N < 0 || C < 1 || H < 0 || W < 0 || ks < 1 || !(ks & 1)) return SD_ERR_ARG;

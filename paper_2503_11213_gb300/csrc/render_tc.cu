@@ -1,6 +1,6 @@
-// Per-pixel DP render (supplement, "Local DP PSF convolution") of BF16
-// images through a BF16 bank on the 5th-generation tensor cores (tcgen05),
-// FP32 accumulation in tensor memory.
+// Per-pixel DP render (supplement, "Local DP PSF convolution") of BF16 or
+// FP16 images through a bank in the same type on the 5th-generation tensor
+// cores (tcgen05), FP32 accumulation in tensor memory.
 //
 // A CTA renders a tile of 32 rows x 16 columns of one channel as 4 column
 // blocks of 4 pixels.  For kernel row u the tile's outputs are a product
@@ -141,8 +141,8 @@ inline size_t tr_bp_bytes(const RenderParams& P) {
 // thread per 8-element (16-byte) piece of a row: row r = (key * NL + lam,
 // u, side), piece q; n_kl = slices of the stored bank x NL.
 template <class TB>
-__global__ void tr_bank_kernel(const TB* __restrict__ bank, __nv_bfloat16* __restrict__ bp,
-                               int n_rows, int ks, int KP, int n_kl) {
+__global__ void tr_bank_kernel(const TB* __restrict__ bank, unsigned short* __restrict__ bp,
+                               int n_rows, int ks, int KP, int n_kl, bool f16) {
   const int per_row = KP / 8, total = n_rows * per_row;  // < 2^31 - 2^24 (checked on the host)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int r = i / per_row, q = i - r * per_row;
@@ -159,8 +159,7 @@ __global__ void tr_bank_kernel(const TB* __restrict__ bank, __nv_bfloat16* __res
       const int v0 = 8 * q + 2 * k, v1 = v0 + 1;
       const float f0 = v0 < ks ? to_f32<TB>(src[dir * v0]) : 0.f;
       const float f1 = v1 < ks ? to_f32<TB>(src[dir * v1]) : 0.f;
-      w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0)) |
-             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f1)) << 16);
+      w[k] = (uint32_t)tc::to_op16(f0, f16) | ((uint32_t)tc::to_op16(f1, f16) << 16);
     }
     *reinterpret_cast<uint4*>(bp + (size_t)r * KP + 8 * q) = make_uint4(w[0], w[1], w[2], w[3]);
   }
@@ -187,8 +186,9 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 // consecutive 16-byte rows (the operand of row u is the same buffer moved by
 // u image rows); B (64 x K) is built per kernel row from the flipped bank
 // rows: its row (i, side, slot) is the kernel row shifted right by i.
+template <bool F16>
 __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams P,
-                                                             const __nv_bfloat16* __restrict__ bp,
+                                                             const unsigned short* __restrict__ bp,
                                                              int* __restrict__ err,
                                                              uint32_t wlim) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
   // core reports the accumulator, warps 0..3 fold it into their pixels and
   // meet at a named barrier before thread 0 starts the next pass.
   const int nch = ks, npass = (nuniq + TR_SL - 1) / TR_SL, total = npass * nch;
-  const uint32_t idesc = tc::idesc_bf16_f32(TR_M, TR_N);
+  const uint32_t idesc = F16 ? tc::idesc_f16_f32(TR_M, TR_N) : tc::idesc_bf16_f32(TR_M, TR_N);
   const uint32_t a_base = tc::smem_u32(Asm), b_base = tc::smem_u32(Bsm);
   const uint64_t a_desc0 = tc::smem_desc(a_base, LBO_A, 128);
   const uint64_t b_desc0 = tc::smem_desc(b_base, TR_N * 16, 128);
@@ -542,13 +542,13 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       tc::fence_before_sync();
       named_sync(1, TR_M);
     }
-    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P.out);
+    unsigned short* out = reinterpret_cast<unsigned short*>(P.out);
 #pragma unroll
     for (int i = 0; i < TR_J; ++i)
       if (pix && yy < H && xb + i < W) {
-        out[(((size_t)n * 2 * P.C + c) * H + yy) * W + xb + i] = __float2bfloat16_rn(outL[i]);
+        out[(((size_t)n * 2 * P.C + c) * H + yy) * W + xb + i] = tc::to_op16(outL[i], F16);
         out[(((size_t)n * 2 * P.C + P.C + c) * H + yy) * W + xb + i] =
-            __float2bfloat16_rn(outR[i]);
+            tc::to_op16(outR[i], F16);
       }
     // every product this CTA issued has completed before its tensor memory
     // is freed, also when a wait gave up (a commit tracks all of them; the
@@ -578,8 +578,9 @@ extern "C" sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, siz
 
 extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, const void* bank,
                                      const sd_bank_layout* layout, int N, int C, int H, int W,
-                                     void* out, void* workspace, size_t workspace_bytes,
-                                     void* stream) {
+                                     int image_dtype, void* out, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  SD_API_RANGE("sd_dp_render_tc");
   using namespace sd;
   if (!aif || !depth_m || !bank || !out) return SD_ERR_ARG;
   if (N < 0 || C < 1 || H < 0 || W < 0) return SD_ERR_ARG;
@@ -587,7 +588,10 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   std::memset(&P, 0, sizeof P);
   sd_status st = check_layout(layout, P);
   if (st != SD_OK) return st;
-  if (layout->dtype != SD_BF16 && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
+  if (image_dtype != SD_BF16 && image_dtype != SD_F16) return SD_ERR_UNSUPPORTED;
+  const bool f16 = image_dtype == SD_F16;
+  // the bank in the image's type, or FP32 (rounded to it by the re-layout)
+  if (layout->dtype != image_dtype && layout->dtype != SD_F32) return SD_ERR_UNSUPPORTED;
   if (P.ks > 65 || tr_smem(P.ks) > 227 * 1024 ||
       (TR_Y + P.ks - 1) * (tr_kk(P.ks) / 8) > TR_SI * TR_NT || TR_SS * (tr_kk(P.ks) / 8) > 32 * TR_TPL)
     return SD_ERR_UNSUPPORTED;
@@ -609,7 +613,7 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   P.W = W;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int* err = reinterpret_cast<int*>(workspace);
-  __nv_bfloat16* bp = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(workspace) + 256);
+  unsigned short* bp = reinterpret_cast<unsigned short*>(reinterpret_cast<char*>(workspace) + 256);
   SD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   const long long n_rows = (long long)tr_slices(P) * P.NL * P.ks * 2;
   const int n_kl = P.FC * P.Z * P.NL;  // slices x wavelengths of the stored bank
@@ -619,17 +623,20 @@ extern "C" sd_status sd_dp_render_tc(const void* aif, const float* depth_m, cons
   const int nblk = std::min((pieces + 255) / 256, 152 * 16);
   if (layout->dtype == SD_BF16)
     tr_bank_kernel<__nv_bfloat16><<<nblk, 256, 0, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(bank), bp, (int)n_rows, P.ks, kp, n_kl);
+        reinterpret_cast<const __nv_bfloat16*>(bank), bp, (int)n_rows, P.ks, kp, n_kl, false);
+  else if (layout->dtype == SD_F16)
+    tr_bank_kernel<__half><<<nblk, 256, 0, s>>>(reinterpret_cast<const __half*>(bank), bp,
+                                                (int)n_rows, P.ks, kp, n_kl, true);
   else
     tr_bank_kernel<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(bank), bp,
-                                               (int)n_rows, P.ks, kp, n_kl);
+                                               (int)n_rows, P.ks, kp, n_kl, f16);
   st = launch_status();
   if (st != SD_OK) return st;
   const size_t smem = tr_smem(P.ks);
-  SD_CUDA_TRY(cudaFuncSetAttribute(render_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  auto k = f16 ? render_tc_kernel<true> : render_tc_kernel<false>;
+  SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((W + TR_XW - 1) / TR_XW, (H + TR_Y - 1) / TR_Y, N * C);
-  render_tc_kernel<<<grid, TR_NT, smem, s>>>(P, bp, err, wait_limit(TR_WAIT));
+  k<<<grid, TR_NT, smem, s>>>(P, bp, err, wait_limit(TR_WAIT));
   return launch_status();
 }
 

@@ -6,6 +6,9 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace sd {
 namespace tc {
 
@@ -34,6 +37,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with FP16 A and B (format 0 in bits 7-9 and 10-12): kind::f16
+// runs both 16-bit types at one rate; A and B always share the type.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Round to the 16-bit operand type (FP16 when f16, else BF16); raw bits.
+__device__ __forceinline__ unsigned short to_op16(float v, bool f16) {
+  return f16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
 // Tensor memory: ncols (power of two >= 32) columns for this CTA; one warp

@@ -59,6 +59,7 @@ extern "C" sd_status sd_dp_psf_trace_batched_tune(
     const sd_psf_request* req, int n_req, const sd_trace_opts* opts, void* out,
     long long total_elems, int64_t* stats, void* workspace, size_t workspace_bytes,
     void* stream, const char* cache_path, sd_batch_config* best) {
+  SD_API_RANGE("sd_dp_psf_trace_batched_tune");
   using namespace sd;
   if (!opts || !best) return SD_ERR_ARG;
   const std::string key = tune_key(n_req, total_elems, opts, n_lenses);

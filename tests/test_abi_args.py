@@ -73,20 +73,32 @@ def test_render_tc_args(lib):
     assert lib.sd_dp_render_tc_workspace(ctypes.byref(lay), ctypes.byref(n)) == L.SD_OK
     f = lib.sd_dp_render_tc
     ws = n.value
+    BF = L.SD_BF16
     # the workspace: missing, short or not 256-byte aligned
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, PTR, None, ws, None) == L.SD_ERR_ARG
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, PTR, ALIGNED, ws - 1, None) == \
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, BF, PTR, None, ws, None) == L.SD_ERR_ARG
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, BF, PTR, ALIGNED, ws - 1, None) == \
         L.SD_ERR_ARG
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, PTR, MIS, ws, None) == L.SD_ERR_ARG
-    # ks above 65 and FP16 banks are not supported on the tensor cores
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, BF, PTR, MIS, ws, None) == L.SD_ERR_ARG
+    # ks above 65, an FP32 image and a bank of the other 16-bit type are not
+    # supported on the tensor cores (both operands of a product share a type)
     lay67, keep67 = layout(ks=67, dtype=L.SD_BF16)
-    assert f(PTR, PTR, PTR, ctypes.byref(lay67), 1, 3, 8, 8, PTR, ALIGNED, 1 << 40, None) == \
+    assert f(PTR, PTR, PTR, ctypes.byref(lay67), 1, 3, 8, 8, BF, PTR, ALIGNED, 1 << 40, None) == \
         L.SD_ERR_UNSUPPORTED
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, L.SD_F32, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_ERR_UNSUPPORTED
     lay16, keep16 = layout(dtype=L.SD_F16)
-    assert f(PTR, PTR, PTR, ctypes.byref(lay16), 1, 3, 8, 8, PTR, ALIGNED, 1 << 40, None) == \
+    assert f(PTR, PTR, PTR, ctypes.byref(lay16), 1, 3, 8, 8, BF, PTR, ALIGNED, 1 << 40, None) == \
         L.SD_ERR_UNSUPPORTED
-    # empty inputs after a valid workspace: nothing to do
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 0, 3, 8, 8, PTR, ALIGNED, ws, None) == L.SD_OK
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 8, 8, L.SD_F16, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_ERR_UNSUPPORTED
+    # empty inputs after a valid workspace: nothing to do (BF16, FP16, and
+    # an FP32 bank rounded to either)
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 0, 3, 8, 8, BF, PTR, ALIGNED, ws, None) == L.SD_OK
+    assert f(PTR, PTR, PTR, ctypes.byref(lay16), 0, 3, 8, 8, L.SD_F16, PTR, ALIGNED, ws,
+             None) == L.SD_OK
+    lay32, keep32 = layout(dtype=L.SD_F32)
+    assert f(PTR, PTR, PTR, ctypes.byref(lay32), 0, 3, 8, 8, L.SD_F16, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_OK
 
 
 def test_render_backward_args(lib):
@@ -100,6 +112,11 @@ def test_render_backward_args(lib):
     # the bank gradient needs at least the tile bitmap in the workspace
     assert f(*args(L.SD_F32, None, PTR, None, 0)) == L.SD_ERR_ARG
     assert f(*args(L.SD_F32, None, PTR, PTR, 4)) == L.SD_ERR_ARG
+    # the image gradient needs its tables (selection, re-laid bank, row
+    # extents) in a 256-byte aligned workspace
+    assert f(*args(L.SD_F32, PTR, None, None, 0)) == L.SD_ERR_ARG
+    assert f(*args(L.SD_F32, PTR, None, ALIGNED, 4096)) == L.SD_ERR_ARG
+    assert f(*args(L.SD_F32, PTR, None, MIS, 1 << 40)) == L.SD_ERR_ARG
 
 
 def test_bank_grad_tc_args(lib):
@@ -108,15 +125,18 @@ def test_bank_grad_tc_args(lib):
     assert lib.sd_dp_render_bank_grad_tc_workspace(ctypes.byref(lay), 1, 3, 64, 64,
                                                    ctypes.byref(n)) == L.SD_OK
     f = lib.sd_dp_render_bank_grad_tc
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, None, ALIGNED, n.value, None) == \
+    BF = L.SD_BF16
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, BF, None, ALIGNED, n.value, None) == \
         L.SD_ERR_ARG                                                     # no grad_bank
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, PTR, MIS, n.value, None) == \
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, BF, PTR, MIS, n.value, None) == \
         L.SD_ERR_ARG                                                     # misaligned
-    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, PTR, ALIGNED, 16, None) == \
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, BF, PTR, ALIGNED, 16, None) == \
         L.SD_ERR_ARG                                                     # short
     lay81, keep81 = layout(ks=81, dtype=L.SD_BF16)
-    assert f(PTR, PTR, PTR, ctypes.byref(lay81), 1, 3, 64, 64, PTR, ALIGNED, 1 << 40, None) == \
-        L.SD_ERR_UNSUPPORTED                                             # ks > 80
+    assert f(PTR, PTR, PTR, ctypes.byref(lay81), 1, 3, 64, 64, BF, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_ERR_UNSUPPORTED                               # ks > 80
+    assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, L.SD_F32, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_ERR_UNSUPPORTED                               # FP32 image
 
 
 def test_mlp_map_args(lib):
