@@ -448,7 +448,7 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
  * grad_out (N,2C,H,W) FP32, aif (N,C,H,W), depth_m (N,H,W) FP32, all device;
  * the bank itself is not read.  Workspace from
  * sd_dp_render_bank_grad_tc_workspace (device, 256-byte aligned; its first
- * int32 becomes 1 if a bounded completion wait gave up).  ks <= 80.  Radial
+ * int32 becomes 1 if a bounded completion wait gave up).  ks <= 65.  Radial
  * and quadrant banks.
  */
 sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,

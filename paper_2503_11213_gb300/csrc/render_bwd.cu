@@ -1177,7 +1177,9 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
   sd_status st = setup_bwd(layout, N, C, H, W, P);
   if (st != SD_OK) return st;
   if (image_dtype != SD_BF16 && image_dtype != SD_F16) return SD_ERR_UNSUPPORTED;
-  if (P.ks > 16 * BG_MAXUG || bg_smem(P.ks) > 227 * 1024) return SD_ERR_UNSUPPORTED;
+  // the epilogue maps kernel columns 0..64 (8 column groups x 8 shifts and
+  // one more): ks <= 65
+  if (P.ks > 65 || bg_smem(P.ks) > 227 * 1024) return SD_ERR_UNSUPPORTED;
   P.aif = aif;
   P.depth = depth_m;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

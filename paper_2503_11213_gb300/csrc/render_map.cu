@@ -61,7 +61,7 @@ __device__ __forceinline__ float half16(uint32_t w, int hi, __half*) {
 }
 
 template <class TI, class TM, int CW>
-__global__ void __launch_bounds__(MAP_NT, 4) render_map_kernel(const MapParams P) {
+__global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
   using V = typename Vec<CW>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks, S = P.S, R = MT_Y + ks - 1;

@@ -16,7 +16,8 @@ valid range to [-1, 1]) through 5 hidden layers of 512 ReLU neurons to the
   library's tensor-core kernel (sd_mlp_psf_map) on the packed weights.
 
 Training is a one-off fit, off the rendering path: it runs as ordinary
-PyTorch layers with autograd and Adam on the GPU.  Points are drawn uniformly
+PyTorch layers with autograd and Adam on the GPU, one step captured in a
+CUDA graph and replayed.  Points are drawn uniformly
 in the normalised coordinates of the region (the paper samples "random
 points within the valid imaging region"); a pool of them is traced once and
 minibatches are drawn from the pool.
@@ -104,12 +105,16 @@ def fit(lens, sensor, sensor_hw, pitch_mm, d_min_m, d_max_m, lambda_nm, n_grid, 
         log_every=0):
     """Fits the network to traced PSFs.  Returns (weights, biases, info) with
     float32 numpy arrays in the layout PsfMLP takes and info holding the
-    training time, the final loss and the loss curve."""
+    training time, the final loss and the loss curve.  One optimisation step
+    (forward, Eq. 4 loss, backward, Adam with a cosine-decayed learning rate)
+    is captured once in a CUDA graph and replayed, the minibatch indices
+    drawn beforehand from a seeded generator."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     p, x_mm, y_mm, d_mm = sample_points(rng, pool, sensor_hw, pitch_mm, d_min_m, d_max_m)
     gt = traced_psfs(lens, sensor, requests_at(x_mm, y_mm, d_mm, lambda_nm, n_grid, ks), device)
     target = max_normalised(gt).flatten(1)
+    del gt
     pts = torch.tensor(p, dtype=torch.float32, device=device)
     t_trace = time.perf_counter() - t0
     w, b = he_init(rng, ks)
@@ -117,36 +122,59 @@ def fit(lens, sensor, sensor_hw, pitch_mm, d_min_m, d_max_m, lambda_nm, n_grid, 
     for wl, bl in zip(w, b):
         params += [torch.tensor(wl, device=device, requires_grad=True),
                    torch.tensor(bl, device=device, requires_grad=True)]
-    opt = torch.optim.Adam(params, lr=lr)
+    lr_t = torch.tensor(lr, dtype=torch.float32, device=device)
+    opt = torch.optim.Adam(params, lr=lr_t, capturable=True)
     gen = torch.Generator(device=device).manual_seed(seed)
-    curve = []
+    all_idx = torch.randint(0, pool, (iters, batch), device=device, generator=gen)
+    idx = all_idx[0].clone()
+    half = target.shape[1] // 2
+
+    def step():
+        opt.zero_grad(set_to_none=False)
+        out = forward(params, pts[idx])
+        tgt = target[idx]
+        # Eq. 4: L2 of the L plane plus L2 of the R plane
+        loss = ((out[:, :half] - tgt[:, :half]) ** 2).mean() + \
+            ((out[:, half:] - tgt[:, half:]) ** 2).mean()
+        loss.backward()
+        opt.step()
+        return loss
+
     prev_tf32 = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = True
+    curve = []
     try:
-        for it in range(iters):
-            # cosine decay from lr to lr_end
-            for gr in opt.param_groups:
-                gr["lr"] = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / iters))
-            idx = torch.randint(0, pool, (batch,), device=device, generator=gen)
-            out = forward(params, pts[idx])
-            tgt = target[idx]
-            half = out.shape[1] // 2
-            # Eq. 4: L2 of the L plane plus L2 of the R plane
-            loss = ((out[:, :half] - tgt[:, :half]) ** 2).mean() + \
-                ((out[:, half:] - tgt[:, half:]) ** 2).mean()
-            opt.zero_grad(set_to_none=True)
-            loss.backward()
-            opt.step()
+        # warm-up steps on a side stream (they are real steps of the fit),
+        # then one step captured and replayed
+        warm = min(3, iters)
+        side = torch.cuda.Stream(device=device)
+        side.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(side):
+            for it in range(warm):
+                lr_t.fill_(lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / iters)))
+                idx.copy_(all_idx[it])
+                loss = step()
+                if it == 0:
+                    first = float(loss.item())
+        torch.cuda.current_stream(device).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            static_loss = step()
+        for it in range(warm, iters):
+            lr_t.fill_(lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / iters)))
+            idx.copy_(all_idx[it])
+            graph.replay()
             if log_every and (it % log_every == 0 or it == iters - 1):
-                curve.append((it, float(loss.item())))
-        final = float(loss.item())
+                curve.append((it, float(static_loss.item())))
+        final = float(static_loss.item()) if iters > warm else float(loss.item())
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev_tf32
     torch.cuda.synchronize()
     ws = [params[2 * l].detach().cpu().numpy() for l in range(6)]
     bs = [params[2 * l + 1].detach().cpu().numpy() for l in range(6)]
     info = {"trace_s": t_trace, "train_s": time.perf_counter() - t0 - t_trace,
-            "final_loss": final, "curve": curve, "iters": iters, "batch": batch,
+            "first_loss": first, "final_loss": final, "curve": curve, "iters": iters,
+            "batch": batch,
             "pool": pool, "seed": seed}
     return ws, bs, info
 
