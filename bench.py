@@ -42,7 +42,14 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel, None until a capture of this build exists.  Must be re-measured
 # whenever the kernel changes.
-TRAFFIC_BYTES = {"trace_adj_kernel": 106.2e6}
+TRAFFIC_BYTES = {
+    # every request's gradient patch read once (also the zero patches it then
+    # skips): 104.6 MB read + 1.1 MB written; independent of the image size
+    "trace_adj_kernel": 105.7e6,
+    # the image-gradient call as the phase times it: selection table 4.2 MB,
+    # bank re-layout 103.9 + 91.8 MB, the two strip launches 74.1 + 82.8 MB
+    "render_bwd_img_kernel": 357.4e6,
+}
 
 # ---------------------------------------------------------------------------
 # Algorithmic FP32 work per ray (add/sub/mul/div/sqrt = 1 flop, fused

@@ -102,12 +102,39 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
     s_kmin = 0x7fffffff;
     s_kmax = -1;
   }
+  // the tile and its halo, one warp per row: 16-byte loads of EPV columns
+  // wherever such a group lies inside the image row at a 16-byte aligned
+  // address, clamped single loads at the image edges (replicate padding)
   const TI* img = reinterpret_cast<const TI*>(P.aif) + ((size_t)n * P.C + c) * H * W;
-  for (int i = tid; i < P.halo_h * S; i += NT) {
-    int r = i / S, cc = i - r * S;
-    int yy = min(max(ty0 + r - p, 0), H - 1);
-    int xx = min(max(tx0 + cc - p, 0), W - 1);
-    halo[i] = to_f32<TI>(img[(size_t)yy * W + xx]);
+  {
+    constexpr int EPV = 16 / (int)sizeof(TI);
+    const int x_lo = tx0 - p;  // image column of halo column 0
+    for (int r = warp; r < P.halo_h; r += NW) {
+      const size_t rowoff = (size_t)min(max(ty0 + r - p, 0), H - 1) * W;
+      const TI* src = img + rowoff;
+      // first column at or left of x_lo whose address is 16-byte aligned
+      const int mis = (int)((reinterpret_cast<uintptr_t>(src) / sizeof(TI) + (size_t)(x_lo + 4 * EPV)) % EPV);
+      const int xa = x_lo - mis;
+      const int ng = (S + mis + EPV - 1) / EPV;
+      for (int g = lane; g < ng; g += 32) {
+        const int x = xa + g * EPV;
+        float v[EPV];
+        if (x >= 0 && x + EPV <= W) {
+          const uint4 q = __ldg(reinterpret_cast<const uint4*>(src + x));
+          const TI* e = reinterpret_cast<const TI*>(&q);
+#pragma unroll
+          for (int k = 0; k < EPV; ++k) v[k] = to_f32<TI>(e[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < EPV; ++k) v[k] = to_f32<TI>(src[min(max(x + k, 0), W - 1)]);
+        }
+#pragma unroll
+        for (int k = 0; k < EPV; ++k) {
+          const int cc = x + k - x_lo;
+          if (cc >= 0 && cc < S) halo[r * S + cc] = v[k];
+        }
+      }
+    }
   }
   for (int i = tid; i < NPX; i += NT) {
     accL[i] = 0.f;
