@@ -410,9 +410,11 @@ sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, size_t* bytes)
  * image_dtype.  Both gradients are bitwise reproducible (no atomics on
  * floating-point values; every sum runs in a fixed order).
  * The workspace (device, 256-byte aligned, sd_dp_render_backward_workspace()
- * bytes) holds, when grad_aif is requested, first the image pass's tables
- * (the per-pixel slice selection, the bank re-laid as FP32 kernel columns,
- * each kernel row's non-zero column range), then the bank pass's data.
+ * bytes) holds first the per-pixel slice selection (key and interpolation
+ * weight, 8 bytes a pixel, written once and read by both passes), then,
+ * when grad_aif is requested, the image pass's tables (the bank re-laid as
+ * FP32 kernel columns, each kernel row's non-zero column range), then the
+ * bank pass's data.
  *   grad_aif: warps own strips of 64 source columns and 8 output rows; each
  *     scatters its pixels' weighted gradients, slice by slice, into a
  *     warp-private row buffer that is added to the image once; strips whose
@@ -422,8 +424,9 @@ sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, size_t* bytes)
  *     of the slices each 64x32 tile uses; with the full workspace the tiles
  *     of a slice are split over two blocks whose partial banks are then
  *     added in a fixed order.  Ignored when grad_bank is null.
- * Returns SD_ERR_ARG when the workspace is missing, misaligned (with
- * grad_aif) or smaller than the image tables plus the bitmap.
+ * Returns SD_ERR_ARG when a gradient is requested and the workspace is
+ * missing, misaligned or smaller than the selection table plus the image
+ * tables plus the bitmap (plus one partial bank for a quadrant bank).
  */
 sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
                                 const float* depth_m, const void* bank,
@@ -448,8 +451,9 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
  * grad_out (N,2C,H,W) FP32, aif (N,C,H,W), depth_m (N,H,W) FP32, all device;
  * the bank itself is not read.  Workspace from
  * sd_dp_render_bank_grad_tc_workspace (device, 256-byte aligned; its first
- * int32 becomes 1 if a bounded completion wait gave up).  ks <= 65.  Radial
- * and quadrant banks.
+ * int32 becomes 1 if a bounded completion wait gave up; then the per-pixel
+ * slice selection, the tile bitmap and the partial banks).  ks <= 65.
+ * Radial and quadrant banks.
  */
 sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,
                                               int H, int W, size_t* bytes);
@@ -467,7 +471,8 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif,
  * deployment variant of the render adjoint with the same arguments minus the
  * workspace and the image dtype (aif is FP32; the bank is read in
  * layout->dtype: FP32, BF16 or FP16).
- * The image pass's tables and the bank pass's slice bitmap live in a 16 MiB
+ * The per-pixel selection table (8 bytes a pixel), the image pass's tables
+ * and the bank pass's slice bitmap live in a 16 MiB
  * array that this library reserves statically on every device that loads
  * it (held until the process exits); when what the requested gradients need
  * for these sizes exceeds 16 MiB the call returns SD_ERR_CAPACITY before

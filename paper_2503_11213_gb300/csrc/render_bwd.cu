@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(NT_BM) slice_bitmap_kernel(const RenderParams 
     if (yy >= P.H || xx >= P.W) continue;
     int key;
     float t;
-    select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &key, &t);
+    selected(P, n, yy, xx, &key, &t);
     if (!two || t < 1.f) atomicOr(&sb[key >> 5], 1u << (key & 31));
     if (two && t > 0.f) atomicOr(&sb[(key + 1) >> 5], 1u << ((key + 1) & 31));
   }
@@ -104,8 +104,14 @@ struct ImgLayout {
   int padu;    // zero rows above kernel row 0 in a re-laid column
   int rcol;    // rows per re-laid column (even)
   int nphase;  // launches of non-overlapping strips
-  size_t sel_bytes, kcol_bytes, ext_bytes, total;
+  size_t kcol_bytes, ext_bytes, total;
 };
+
+// Bytes of the per-pixel selection table (first in every backward
+// workspace: both gradient passes and the bitmap read it).
+inline size_t sel_table_bytes(const RenderParams& P) {
+  return ((size_t)P.N * P.H * P.W * 8 + 255) & ~(size_t)255;
+}
 
 inline ImgLayout img_layout(const RenderParams& P) {
   ImgLayout L;
@@ -116,10 +122,9 @@ inline ImgLayout img_layout(const RenderParams& P) {
   L.rcol = (ks + 15 + L.padu + 1) & ~1;
   L.nphase = 1 + (2 * p + IG_SW - 1) / IG_SW;
   const size_t kl = (size_t)n_keys(P) * P.NL;
-  L.sel_bytes = ((size_t)P.N * P.H * P.W * 8 + 255) & ~(size_t)255;
   L.kcol_bytes = (kl * ks * L.rcol * 8 + 255) & ~(size_t)255;
   L.ext_bytes = (kl * ks * 2 + 255) & ~(size_t)255;
-  L.total = L.sel_bytes + L.kcol_bytes + L.ext_bytes;
+  L.total = L.kcol_bytes + L.ext_bytes;
   return L;
 }
 
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
               if (yy < P.H && xx < P.W) {
                 int k0;
                 float t;
-                select_slice(P, yy, xx, P.depth[((size_t)n * P.H + yy) * P.W + xx], &k0, &t);
+                selected(P, n, yy, xx, &k0, &t);
                 float w = (k0 == key) ? (two ? 1.f - t : 1.f)
                                       : ((two && k0 + 1 == key) ? t : 0.f);
                 if (w != 0.f) {
@@ -678,21 +683,25 @@ sd_status setup_bwd(const sd_bank_layout* layout, int N, int C, int H, int W,
   return SD_OK;
 }
 
-// The image gradient: selection table, bank re-layout, then one launch per
+// The per-pixel selection table of the call, written once.
+inline sd_status launch_select_table(const RenderParams& P, int2* sel, cudaStream_t s) {
+  const size_t npx = (size_t)P.N * P.H * P.W;
+  const int blocks = (int)std::min<size_t>((npx + 255) / 256, (size_t)152 * 16);
+  select_table_kernel<<<blocks, 256, 0, s>>>(P, sel);
+  return launch_status();
+}
+
+// The image gradient: bank re-layout, then one launch per
 // phase of non-overlapping strips (phase order fixed: deterministic).
 template <class TB>
 sd_status launch_img_bwd(const RenderParams& P, const float* gout, float* gaif, void* ws,
                          cudaStream_t s) {
   const ImgLayout IL = img_layout(P);
   char* base = reinterpret_cast<char*>(ws);
-  int2* sel = reinterpret_cast<int2*>(base);
-  float* kcol = reinterpret_cast<float*>(base + IL.sel_bytes);
-  unsigned short* ext = reinterpret_cast<unsigned short*>(base + IL.sel_bytes + IL.kcol_bytes);
-  const size_t npx = (size_t)P.N * P.H * P.W;
-  const int sblocks = (int)std::min<size_t>((npx + 255) / 256, (size_t)152 * 16);
-  select_table_kernel<<<sblocks, 256, 0, s>>>(P, sel);
-  sd_status st = launch_status();
-  if (st != SD_OK) return st;
+  const int2* sel = P.sel;
+  float* kcol = reinterpret_cast<float*>(base);
+  unsigned short* ext = reinterpret_cast<unsigned short*>(base + IL.kcol_bytes);
+  sd_status st;
   const int n_kl = n_keys(P) * P.NL;
   const size_t ksm = (size_t)2 * P.ks * P.ks * 4;
   SD_CUDA_TRY(cudaFuncSetAttribute(kernel_columns_kernel<TB>,
@@ -892,14 +901,15 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
           const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * P.H) * P.W;
           constexpr int BG_PPR = 4;
           for (int t0 = 0; t0 < RT_Y * TXB / BG_NT; t0 += BG_PPR) {
-            float dq[BG_PPR], gq[BG_PPR][2];
+            int2 sq[BG_PPR];
+            float gq[BG_PPR][2];
 #pragma unroll
             for (int t = 0; t < BG_PPR; ++t) {
               const int i = tid + (t0 + t) * BG_NT, r = i / TXB, x = i - r * TXB;
               const int yy = y0 + r, xx = x0 + x;
               const bool in = yy < P.H && xx < P.W;
               const size_t o = (size_t)yy * P.W + xx;
-              dq[t] = in ? P.depth[(size_t)n * P.H * P.W + o] : 1.f;
+              sq[t] = in ? P.sel[(size_t)n * P.H * P.W + o] : make_int2(-1, 0);
               gq[t][0] = in ? goL[o] : 0.f;
               gq[t][1] = in ? goR[o] : 0.f;
             }
@@ -909,9 +919,8 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
               const int yy = y0 + r, xx = x0 + x;
               float gl = 0.f, gr = 0.f;
               if (yy < P.H && xx < P.W) {
-                int k0;
-                float tt;
-                select_slice(P, yy, xx, dq[t], &k0, &tt);
+                const int k0 = sq[t].x;
+                const float tt = __int_as_float(sq[t].y);
                 const float w = (k0 == key) ? (two ? 1.f - tt : 1.f)
                                             : ((two && k0 + 1 == key) ? tt : 0.f);
                 gl = w * gq[t][0];
@@ -1075,7 +1084,7 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   if (st != SD_OK) return st;
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
-  *bytes = img_layout(P).total + bitmap_bytes(N, tx, ty, n_keys(P)) +
+  *bytes = sel_table_bytes(P) + img_layout(P).total + bitmap_bytes(N, tx, ty, n_keys(P)) +
            (size_t)BANK_PARTS * bank_bytes(P);
   return SD_OK;
 }
@@ -1102,12 +1111,30 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
     if (grad_bank) SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
     return SD_OK;
   }
-  // the image pass's part of the workspace comes first
+  if (!grad_aif && !grad_bank) return SD_OK;
+  // the selection table comes first; both passes read it
+  const size_t sel_bytes = sel_table_bytes(P);
+  if (!workspace || workspace_bytes < sel_bytes ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return SD_ERR_ARG;
+  int2* sel = reinterpret_cast<int2*>(workspace);
+  P.sel = sel;
+  workspace = reinterpret_cast<char*>(workspace) + sel_bytes;
+  workspace_bytes -= sel_bytes;
+  // then the image pass's tables
   const size_t img_bytes = grad_aif ? img_layout(P).total : 0;
+  if (grad_aif && workspace_bytes < img_bytes) return SD_ERR_ARG;
+  if (grad_bank) {
+    // a quadrant bank needs at least one partial bank to fold
+    int tx, ty;
+    bwd_tiles(H, W, &tx, &ty);
+    const size_t need_min = img_bytes + bitmap_bytes(N, tx, ty, n_keys(P)) +
+                            (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
+    if (workspace_bytes < need_min) return SD_ERR_ARG;
+  }
+  st = launch_select_table(P, sel, s);
+  if (st != SD_OK) return st;
   if (grad_aif) {
-    if (!workspace || workspace_bytes < img_bytes ||
-        (reinterpret_cast<uintptr_t>(workspace) & 255))
-      return SD_ERR_ARG;
     SD_CUDA_TRY(cudaMemsetAsync(grad_aif, 0, (size_t)N * C * H * W * 4, s));
     // the re-layout reads the bank in its storage type
     const int bt = layout->dtype;
@@ -1124,9 +1151,6 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
     bwd_tiles(H, W, &tx, &ty);
     size_t words = bitmap_words(n_keys(P));
     size_t need = bitmap_bytes(N, tx, ty, n_keys(P));
-    // a quadrant bank needs at least one partial bank to fold
-    const size_t need_min = need + (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
-    if (!workspace || workspace_bytes < need_min) return SD_ERR_ARG;
     unsigned* bm = reinterpret_cast<unsigned*>(workspace);
     int parts = 1;
     for (int q = BANK_PARTS; q > 1; q >>= 1)
@@ -1162,7 +1186,8 @@ sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int 
   if (st != SD_OK) return st;
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
-  *bytes = 256 + bitmap_bytes(N, tx, ty, n_keys(P)) + (size_t)BANK_PARTS * bank_bytes(P);
+  *bytes = 256 + sel_table_bytes(P) + bitmap_bytes(N, tx, ty, n_keys(P)) +
+           (size_t)BANK_PARTS * bank_bytes(P);
   return SD_OK;
 }
 
@@ -1187,7 +1212,8 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
   const size_t words = bitmap_words(n_keys(P));
-  const size_t need = 256 + bitmap_bytes(N, tx, ty, n_keys(P));
+  const size_t sel_bytes = sel_table_bytes(P);
+  const size_t need = 256 + sel_bytes + bitmap_bytes(N, tx, ty, n_keys(P));
   const size_t need_min = need + (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
   if (!workspace || workspace_bytes < need_min || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return SD_ERR_ARG;
@@ -1197,7 +1223,9 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
     SD_CUDA_TRY(cudaMemsetAsync(grad_bank, 0, bank_elems * 4, s));
     return SD_OK;
   }
-  unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + 256);
+  int2* sel = reinterpret_cast<int2*>(reinterpret_cast<char*>(workspace) + 256);
+  P.sel = sel;
+  unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + 256 + sel_bytes);
   int parts = 1;
   for (int q = BANK_PARTS; q > 1; q >>= 1)
     if (workspace_bytes >= need + (size_t)q * bank_bytes(P)) {
@@ -1205,6 +1233,8 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
       break;
     }
   float* parts_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+  st = launch_select_table(P, sel, s);
+  if (st != SD_OK) return st;
   dim3 g1(tx, ty, N);
   slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
   st = launch_status();
@@ -1260,13 +1290,14 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
   void* ws = nullptr;
   size_t need = 0;
   if (grad_aif || grad_bank) {
-    // the image pass's tables and the bank pass's bitmap must fit; partial
-    // banks are used as far as the array allows
+    // the selection table, the image pass's tables and the bank pass's
+    // bitmap must fit; partial banks are used as far as the array allows
     RenderParams P;
     sd_status st = setup_bwd(layout, N, C, H, W, P);
     if (st != SD_OK) return st;
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
+    need = sel_table_bytes(P);
     if (grad_aif) need += img_layout(P).total;
     if (grad_bank)
       need += bitmap_bytes(N, tx, ty, n_keys(P)) +

@@ -17,6 +17,7 @@ struct RenderParams {
   const float* depth;
   const void* bank;
   void* out;
+  const int2* sel;  // backward passes: per-pixel (key, t bits), [N][H][W]
   int N, C, H, W;
   int F, Z, NL, ks;
   int fmode;       // SD_FIELD_RADIAL or SD_FIELD_QUADRANT
@@ -85,6 +86,15 @@ __device__ __forceinline__ void select_slice(const RenderParams& P, int row, int
   }
   *key = f * Z + z0;
   *t = tt;
+}
+
+// The selection of pixel (n, row, col) from the per-pixel table that the
+// backward passes build once per call (select_slice's result, bit for bit).
+__device__ __forceinline__ void selected(const RenderParams& P, int n, int row, int col,
+                                         int* key, float* t) {
+  const int2 v = P.sel[((size_t)n * P.H + row) * P.W + col];
+  *key = v.x;
+  *t = __int_as_float(v.y);
 }
 
 // Keys select_slice can produce: field cells x depths, times 4 flip classes

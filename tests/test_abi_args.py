@@ -109,11 +109,12 @@ def test_render_backward_args(lib):
     assert f(None, PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, L.SD_F32, PTR, PTR, PTR, 0,
              None) == L.SD_ERR_ARG
     assert f(*args(7, PTR, None, None, 0)) == L.SD_ERR_UNSUPPORTED      # image dtype
-    # the bank gradient needs at least the tile bitmap in the workspace
+    # the bank gradient needs at least the selection table and the tile
+    # bitmap in the workspace
     assert f(*args(L.SD_F32, None, PTR, None, 0)) == L.SD_ERR_ARG
     assert f(*args(L.SD_F32, None, PTR, PTR, 4)) == L.SD_ERR_ARG
-    # the image gradient needs its tables (selection, re-laid bank, row
-    # extents) in a 256-byte aligned workspace
+    # the image gradient needs the selection table and its own (re-laid
+    # bank, row extents) in a 256-byte aligned workspace
     assert f(*args(L.SD_F32, PTR, None, None, 0)) == L.SD_ERR_ARG
     assert f(*args(L.SD_F32, PTR, None, ALIGNED, 4096)) == L.SD_ERR_ARG
     assert f(*args(L.SD_F32, PTR, None, MIS, 1 << 40)) == L.SD_ERR_ARG
@@ -132,9 +133,9 @@ def test_bank_grad_tc_args(lib):
         L.SD_ERR_ARG                                                     # misaligned
     assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, BF, PTR, ALIGNED, 16, None) == \
         L.SD_ERR_ARG                                                     # short
-    lay81, keep81 = layout(ks=81, dtype=L.SD_BF16)
-    assert f(PTR, PTR, PTR, ctypes.byref(lay81), 1, 3, 64, 64, BF, PTR, ALIGNED, 1 << 40,
-             None) == L.SD_ERR_UNSUPPORTED                               # ks > 80
+    lay67, keep67 = layout(ks=67, dtype=L.SD_BF16)
+    assert f(PTR, PTR, PTR, ctypes.byref(lay67), 1, 3, 64, 64, BF, PTR, ALIGNED, 1 << 40,
+             None) == L.SD_ERR_UNSUPPORTED                               # ks > 65
     assert f(PTR, PTR, PTR, ctypes.byref(lay), 1, 3, 64, 64, L.SD_F32, PTR, ALIGNED, 1 << 40,
              None) == L.SD_ERR_UNSUPPORTED                               # FP32 image
 

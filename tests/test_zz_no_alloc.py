@@ -71,9 +71,9 @@ def test_noalloc_rejects_oversized_bitmap(sdlib):
     # 250 x 256 slices: 2000 bitmap words per 64 x 32 tile; 60 x 80 tiles
     F, Z, ks, H, W_ = 250, 256, 1, 32 * 60, 64 * 80
     lay = sd.BankLayout(np.linspace(0.0, 1.0, F), np.linspace(0.3, 3.0, Z), 1, ks, 0.002)
-    # the workspace is the bitmap plus two partial banks; the bitmap alone
-    # exceeds the array by a wide margin
-    bitmap = sd.render_backward_workspace(lay, 1, 1, H, W_) - 2 * F * Z * 2 * ks * ks * 4
+    # the bitmap alone (one bit per key, whole 32-bit words, per 64 x 32
+    # tile) exceeds the array by a wide margin
+    bitmap = 60 * 80 * -(-F * Z // 32) * 4
     assert bitmap > 2 * SCRATCH
     aif = torch.zeros((1, 1, H, W_), device="cuda")
     depth = torch.ones((1, H, W_), device="cuda")
