@@ -424,10 +424,11 @@ def run_ours(args, world, rank, local, dist):
         "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_ms, 4)},
-        # trace; render; image gradient (selection table, bank re-layout, two
-        # strip phases); bank gradient (slice bitmap, bank pass, parts
-        # reduce); adjoint trace and lens reduce
-        "gpu_launches": 11 * args.steps,
+        # trace; render; image gradient call (selection table, bank
+        # re-layout, two strip phases); bank gradient call (selection table,
+        # slice bitmap, slice counts, slice order, bank pass); adjoint trace
+        # and lens reduce
+        "gpu_launches": 13 * args.steps,
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
     }

@@ -326,9 +326,9 @@ sd_status sd_dp_trace_hits(const sd_lens* lens, const sd_dp_sensor* sensor,
  * X < 0 mirrors the kernel's columns and exchanges L and R (the DP split is
  * along x), Y < 0 mirrors its rows.  Removes the radial approximation of
  * off-axis azimuths.  All render entry points take it: sd_dp_render_tc's
- * workspace then holds the four flip classes, and the backward's partial
- * banks one gradient slab per key (flip class), folded onto the stored
- * quadrant in a fixed order.
+ * workspace then holds the four flip classes, and the backward's bank
+ * gradient goes through one gradient slab per key (flip class) in its
+ * workspace, folded onto the stored quadrant in a fixed order.
  * ---------------------------------------------------------------------- */
 #define SD_MAX_BANK_FIELDS 256
 #define SD_MAX_BANK_DEPTHS 256
@@ -419,14 +419,22 @@ sd_status sd_dp_render_tc_workspace(const sd_bank_layout* layout, size_t* bytes)
  *     scatters its pixels' weighted gradients, slice by slice, into a
  *     warp-private row buffer that is added to the image once; strips whose
  *     footprints overlap run in separate launches in a fixed order.
- *   grad_bank: thread blocks per (slice, wavelength) accumulate over the
- *     tiles that use the slice in a fixed order.  Needs at least the bitmap
- *     of the slices each 64x32 tile uses; with the full workspace the tiles
- *     of a slice are split over two blocks whose partial banks are then
- *     added in a fixed order.  Ignored when grad_bank is null.
+ *   grad_bank: a thread block per (slice, wavelength) accumulates over the
+ *     64x32 tiles that use the slice in a fixed order and writes the slice's
+ *     gradient.  A slice with more tiles than a block's share of the launch
+ *     is split into two tile chunks while split slots remain: each chunk
+ *     block writes a partial slab and the second to finish adds the two in
+ *     chunk order.  Blocks start in order of their tile count (the most
+ *     first).  Needs the bitmap of the slices each tile uses, for a quadrant
+ *     bank a slab of per-flip-class gradients that is then folded, and a
+ *     work plan (8 bytes a slice plus the split slots' slabs); split slots
+ *     take what the workspace holds beyond that, none if it holds nothing
+ *     more (the result then differs from the full workspace's in rounding
+ *     only).  Ignored when grad_bank is null.
  * Returns SD_ERR_ARG when a gradient is requested and the workspace is
  * missing, misaligned or smaller than the selection table plus the image
- * tables plus the bitmap (plus one partial bank for a quadrant bank).
+ * tables plus the bitmap (plus the per-key slab of a quadrant bank) plus a
+ * work plan without split slots.
  */
 sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
                                 const float* depth_m, const void* bank,
@@ -437,7 +445,7 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif,
                                 void* stream);
 
 /* Device workspace bytes sd_dp_render_backward needs for these sizes (both
- * gradients, two partial banks). */
+ * gradients). */
 sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
                                           int C, int H, int W, size_t* bytes);
 
@@ -452,8 +460,10 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N,
  * the bank itself is not read.  Workspace from
  * sd_dp_render_bank_grad_tc_workspace (device, 256-byte aligned; its first
  * int32 becomes 1 if a bounded completion wait gave up; then the per-pixel
- * slice selection, the tile bitmap and the partial banks).  ks <= 65.
- * Radial and quadrant banks.
+ * slice selection, the tile bitmap, a quadrant bank's per-key slab and the
+ * work plan of sd_dp_render_backward's bank pass, whose blocks, slice
+ * splits and chunk sums this pass shares).  ks <= 65.  Radial and quadrant
+ * banks.
  */
 sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int N, int C,
                                               int H, int W, size_t* bytes);

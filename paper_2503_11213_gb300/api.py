@@ -368,8 +368,9 @@ def dp_render_tc(aif, depth_m, bank, layout: BankLayout, out=None, workspace=Non
 def render_backward_workspace(layout: BankLayout, N, C, H, W):
     """Device workspace bytes of dp_render_backward: the per-pixel slice
     selection both gradients read, the image gradient's re-laid bank and row
-    extents, then the bank gradient's per-tile slice bitmap and two partial
-    banks."""
+    extents, then the bank gradient's per-tile slice bitmap, its per-slice
+    tile counts and launch order (and a quadrant bank's per-flip-class
+    gradient slab)."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_backward_workspace(ctypes.byref(lay), N, C, H, W,
@@ -380,8 +381,8 @@ def render_backward_workspace(layout: BankLayout, N, C, H, W):
 
 def bank_grad_tc_workspace(layout: BankLayout, N, C, H, W):
     """Device workspace bytes of dp_render_bank_grad_tc: the error flag header,
-    the per-pixel slice selection, the per-tile slice bitmap and two partial
-    banks."""
+    the per-pixel slice selection, the per-tile slice bitmap, the per-slice
+    tile counts and launch order (and a quadrant bank's per-key slab)."""
     n = ctypes.c_size_t(0)
     lay = layout.c()
     L.check(L.lib().sd_dp_render_bank_grad_tc_workspace(ctypes.byref(lay), N, C, H, W,

@@ -9,20 +9,23 @@
 //                      source pixel),
 //   dB[key][s][ks-1-u][ks-1-v] += sum_{pixels using key} w(y,x) G_s(y,x)
 //                      Ipad(y+u, x+v)   with w = 1-t or t.
-// Three kernels:
+// Kernels (every sum in a fixed order: both gradients are deterministic):
+//   select_table_kernel     per pixel: its slice selection (key, t), once;
 //   slice_bitmap_kernel     per (image, tile): which bank slices the tile uses
 //                           (a bitmap in the caller's workspace);
-//   render_bwd_img_kernel   per (tile, channel): the forward's work list of
-//                           (segment, slice) items; each lane scatters its
-//                           segment's weighted gradients through a register
-//                           window of 8 taps into a shared padded tile, which
-//                           is then folded into grad_aif with global atomics
-//                           (FP32 addition order varies: not bitwise
-//                           reproducible);
-//   render_bwd_bank_kernel  per (slice, wavelength): visits, in a fixed order,
-//                           the tiles whose bitmap holds the slice; threads own
-//                           8-tap strips of the kernel and accumulate over the
-//                           tile's segments in a fixed order: deterministic.
+//   render_bwd_img_kernel   per (strip of 64 source columns, 8 output rows,
+//                           channel): warps scatter source blocks, slice by
+//                           slice, into private row buffers added in warp
+//                           order; strips whose footprints overlap run in
+//                           separate launches (section 2);
+//   slice_count_kernel,     the slices ordered by how many tiles use them
+//   slice_order_kernel      (the heaviest first);
+//   render_bwd_bank_kernel  per (slice, wavelength), in that order: visits, in
+//                           a fixed order, the tiles whose bitmap holds the
+//                           slice; threads own 8-tap strips of the kernel and
+//                           accumulate over the tile's segments in a fixed
+//                           order, then write the slice's gradient;
+//   bank_grad_tc_kernel     the bank gradient on the tensor cores (section 4).
 
 #include <algorithm>
 #include <mutex>
@@ -423,19 +426,33 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
 // ---------------------------------------------------------------------------
 // 3. bank gradient, one block per (slice key, wavelength)
 // ---------------------------------------------------------------------------
-// The tiles t0 .. t0 + NT - 1 (of ntiles) of this block's part whose bitmap
-// holds the slice, as offsets from t0 in ascending order: one tile per
-// thread, compacted with warp ballots, so that the bitmap loads of NT tiles
-// are in flight together (a scan of one tile after the other waits for each
-// load in turn).  Every thread of the block calls it; returns the count.
+// Work plan of a bank-gradient launch (built on the device by
+// slice_count_kernel and slice_order_kernel, in the caller's workspace).
+struct BankPlan {
+  const int* order;  // item of each block rank: key * 2 + chunk; -1 past the last
+  const int* slot;   // split slot of a key, -1 for a slice that is one item
+  int* tick;         // per (split slot, wavelength): chunks finished
+  float* pbuf;       // per (split slot, chunk, wavelength): a 2 ks^2 slab
+  int nkeys;
+  __device__ float* slab(int sl, int chunk, int lam, int NL, int ks2) const {
+    return pbuf + (((size_t)sl * 2 + chunk) * NL + lam) * 2 * (size_t)ks2;
+  }
+};
+
+// The tiles t0 .. t0 + NT - 1 (of ntiles) of the block's chunk (all tiles,
+// or those with index = chunk mod 2) whose bitmap holds the slice, as
+// offsets from t0 in ascending order: one tile per thread, compacted with
+// warp ballots, so that the bitmap loads of NT tiles are in flight together
+// (a scan of one tile after the other waits for each load in turn).  Every
+// thread of the block calls it; returns the count.
 template <int NT>
 __device__ int slice_tiles(const unsigned* __restrict__ bm, int words, int kw, unsigned kbit,
-                           size_t t0, size_t ntiles, int parts, int part, int* s_list,
+                           size_t t0, size_t ntiles, int nch, int chunk, int* s_list,
                            int* s_wc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t t = t0 + tid;
-  const bool use =
-      t < ntiles && (int)(t % (size_t)parts) == part && (bm[t * words + kw] & kbit) != 0u;
+  const bool use = t < ntiles && (nch == 1 || (int)(t & 1) == chunk) &&
+                   (bm[t * words + kw] & kbit) != 0u;
   const unsigned bal = __ballot_sync(0xffffffffu, use);
   if (lane == 0) s_wc[warp] = __popc(bal);
   __syncthreads();
@@ -450,13 +467,183 @@ __device__ int slice_tiles(const unsigned* __restrict__ bm, int words, int kw, u
   return tot;
 }
 
+// Tiles per key (how many tiles' bitmaps hold it): block (word, chunk of
+// 1024 tiles), counts by warp ballots, integer atomics into cnt (zeroed by
+// the caller; the sums do not depend on the order).
+__global__ void __launch_bounds__(256) slice_count_kernel(const unsigned* __restrict__ bm,
+                                                          int words, size_t ntiles, int nkeys,
+                                                          int* __restrict__ cnt) {
+  __shared__ int s_c[8][32];
+  const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t t0 = (size_t)blockIdx.y * 1024 + threadIdx.x;
+  int mine = 0;  // lane b: tiles of this warp holding bit b
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const size_t t = t0 + 256 * i;
+    const unsigned x = t < ntiles ? bm[t * words + w] : 0u;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const int c = __popc(__ballot_sync(0xffffffffu, (x >> b) & 1u));
+      mine += lane == b ? c : 0;
+    }
+  }
+  s_c[warp][lane] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += s_c[q][lane];
+    const int key = w * 32 + lane;
+    if (sum && key < nkeys) atomicAdd(cnt + key, sum);
+  }
+}
+
+// Work plan of the bank-gradient blocks (one block per item and wavelength).
+// A slice whose tile count exceeds half a block's fair share (NL x all
+// counts / the resident blocks) is split into two items, chunk c taking its
+// tiles with index = c (mod 2), as long as split slots remain (in key
+// order); every other slice is one item.  Items are ordered by descending tile
+// count per item (64 buckets of the count; ascending item id within a
+// bucket) so that the largest start first and none is left to run alone at
+// the end (longest-processing-time order).  order[i] = key * 2 + chunk, -1
+// past the last item; slot[key] = the split slot or -1.  One block of 1024
+// threads; everything it decides follows from the counts (deterministic).
+__global__ void __launch_bounds__(1024) slice_order_kernel(const int* __restrict__ cnt,
+                                                           int nkeys, int NL, int resident,
+                                                           int smax, int* __restrict__ slot,
+                                                           int* __restrict__ split_key,
+                                                           int* __restrict__ order) {
+  constexpr int NB = 64;
+  __shared__ int s_hist[NB], s_base[NB], s_tot[NB], s_wc[32][NB], s_max[32], s_n[32];
+  __shared__ long long s_sum[32];
+  __shared__ int s_run;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int m = 0;
+  long long sum = 0;
+  for (int k = tid; k < nkeys; k += 1024) {
+    m = max(m, cnt[k]);
+    sum += cnt[k];
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    s_max[warp] = m;
+    s_sum[warp] = sum;
+  }
+  if (tid < NB) s_hist[tid] = 0;
+  if (tid == 0) s_run = 0;
+  __syncthreads();
+  int mx = 0;
+  long long total = 0;
+  for (int q = 0; q < 32; ++q) {
+    mx = max(mx, s_max[q]);
+    total += s_sum[q];
+  }
+  // slices with more tiles than half a block's fair share are split (half:
+  // a tile of a heavy slice costs more than one of a light slice, since it
+  // holds more of the slice's pixel rows; at the full share the heaviest
+  // slices of an 8 x 512 x 512 RGB batch stayed whole and set the end of
+  // the launch, 9.9 ms against 5.5 ms for the tensor-core pass)
+  const long long share = (long long)NL * total / max(2 * resident, 1);
+  for (int c0 = 0; c0 < nkeys; c0 += 1024) {
+    const int k = c0 + tid;
+    const bool heavy = k < nkeys && cnt[k] >= 2 && (long long)cnt[k] > share;
+    const unsigned bal = __ballot_sync(0xffffffffu, heavy);
+    if (lane == 0) s_n[warp] = __popc(bal);
+    __syncthreads();
+    int rank = s_run + __popc(bal & lt), add = 0;
+    for (int q = 0; q < 32; ++q) {
+      rank += q < warp ? s_n[q] : 0;
+      add += s_n[q];
+    }
+    const bool split = heavy && rank < smax;
+    if (k < nkeys) slot[k] = split ? rank : -1;
+    if (split) split_key[rank] = k;
+    __syncthreads();
+    if (tid == 0) s_run += add;
+    __syncthreads();
+  }
+  const int nsplit = min(s_run, smax), nitems = nkeys + nsplit;
+  __syncthreads();  // slot and split_key written by the block are visible
+  // item id: k < nkeys is chunk 0 of key k, nkeys + r chunk 1 of split_key[r]
+  auto item_key = [&](int id) { return id < nkeys ? id : split_key[id - nkeys]; };
+  auto bucket = [&](int id) {
+    const int key = item_key(id);
+    const int nch = slot[key] >= 0 ? 2 : 1, w = (cnt[key] + nch - 1) / nch;
+    return NB - 1 - (int)((long long)w * NB / ((long long)mx + 1));  // 0: the heaviest
+  };
+  for (int id = tid; id < nitems; id += 1024) atomicAdd(&s_hist[bucket(id)], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int b = 0; b < NB; ++b) {
+      s_base[b] = run;
+      run += s_hist[b];
+    }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < nitems; c0 += 1024) {
+    const int id = c0 + tid;
+    const bool valid = id < nitems;
+    const int b = valid ? bucket(id) : NB;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(peers & lt);
+    for (int i = tid; i < 32 * NB; i += 1024) (&s_wc[0][0])[i] = 0;
+    __syncthreads();
+    if (valid && rank == 0) s_wc[warp][b] = __popc(peers);
+    __syncthreads();
+    if (tid < NB) {
+      int run = 0;
+      for (int q = 0; q < 32; ++q) {
+        const int c = s_wc[q][tid];
+        s_wc[q][tid] = run;
+        run += c;
+      }
+      s_tot[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int pos = s_base[b] + s_wc[warp][b] + rank;
+      if (pos < nitems) order[pos] = item_key(id) * 2 + (id < nkeys ? 0 : 1);
+    }
+    __syncthreads();
+    if (tid < NB) s_base[tid] += s_tot[tid];
+    __syncthreads();
+  }
+  for (int i = nitems + tid; i < nkeys + smax; i += 1024) order[i] = -1;
+}
+
+// The end of a block whose item is one of two chunks of a split slice: its
+// partial gradient is in its own slab (written by the block); after both
+// chunks have written theirs, the second block to finish adds them in
+// chunk order (the same sum whichever finishes last) into out.  Every
+// thread of the block calls it; nt = threads of the block.
+__device__ __forceinline__ void combine_chunks(const float* slab0, const float* slab1, float* out,
+                                               int n, int* tick, int nt) {
+  __shared__ int s_last;
+  __threadfence();  // this block's partial is visible device-wide
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(tick, 1) == 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < n; i += nt) out[i] = __ldcg(slab0 + i) + __ldcg(slab1 + i);
+  if (threadIdx.x == 0) *tick = 0;
+}
+
+// Block (rank * NL + lam) computes item order[rank] (a slice, or one tile
+// chunk of a split slice) at wavelength lam over its tiles that use the
+// slice, and writes the slice's gradient (split slices: through the two
+// chunks' slabs, see combine_chunks).
 template <int NT, int SPT, class TI>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(const RenderParams P,
                                                              const float* __restrict__ gout,
                                                              const unsigned* __restrict__ bm,
                                                              int words, int ntx, int nty,
-                                                             float* __restrict__ gbank,
-                                                             int parts) {
+                                                             BankPlan plan,
+                                                             float* __restrict__ gbank) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ks = P.ks, p = (ks - 1) >> 1, ks2 = ks * ks;
   const int KU = (ks + SEG - 1) / SEG * SEG;
@@ -470,8 +657,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
   int* segs = reinterpret_cast<int*>(G + NPX);            // NSEG
   __shared__ int s_nseg, s_wcnt[NSEG / 32];
 
-  // block (key, lam, part) visits the tiles with index = part (mod parts)
-  const int key = blockIdx.x, lam = blockIdx.y, part = blockIdx.z;
+  const int lam = (int)(blockIdx.x % P.NL), item = plan.order[blockIdx.x / P.NL];
+  if (item < 0 || (item >> 1) >= plan.nkeys) return;  // past the last item
+  const int key = item >> 1, chunk = item & 1, sl = plan.slot[key], nch = sl >= 0 ? 2 : 1;
   const int tid = threadIdx.x;
   const bool two = P.Z > 1;
   const int nstrip = ks * (KU / SEG);
@@ -484,12 +672,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
   const int kw = key >> 5;
   const unsigned kbit = 1u << (key & 31);
   const int c_lo = (P.NL == P.C) ? lam : 0, c_hi = (P.NL == P.C) ? lam + 1 : P.C;
-  // the tiles of this part that use the slice, in ascending order
+  // the tiles that use the slice, in ascending order
   __shared__ int s_list[NT], s_twc[NT / 32];
   const size_t ntiles = (size_t)P.N * nty * ntx;
   for (size_t t0 = 0; t0 < ntiles; t0 += NT)
-    for (int li = 0, nlist = slice_tiles<NT>(bm, words, kw, kbit, t0, ntiles, parts, part,
-                                             s_list, s_twc);
+    for (int li = 0, nlist = slice_tiles<NT>(bm, words, kw, kbit, t0, ntiles, nch, chunk, s_list,
+                                             s_twc);
          li < nlist; ++li) {
         const size_t tile = t0 + s_list[li];
         const int n = (int)(tile / ((size_t)nty * ntx));
@@ -573,8 +761,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
           }
         }
       }
-  // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v] of this part's slab
-  float* out = gbank + ((size_t)part * gridDim.x * P.NL + (size_t)key * P.NL + lam) * 2 * ks2;
+  // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v] (a split slice: the
+  // chunk's slab first)
+  float* out = gbank + ((size_t)key * P.NL + lam) * 2 * ks2;
+  float* dst = nch == 1 ? out : plan.slab(sl, chunk, lam, P.NL, ks2);
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
     int st = tid + s * NT;
@@ -585,19 +775,22 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
       int u = u0 + uu;
       if (u >= ks) continue;
       size_t o = (size_t)(ks - 1 - u) * ks + (ks - 1 - v);
-      out[o] = acc[s][uu];
-      out[ks2 + o] = acc[s][SEG + uu];
+      dst[o] = acc[s][uu];
+      dst[ks2 + o] = acc[s][SEG + uu];
     }
   }
+  if (nch == 2)
+    combine_chunks(plan.slab(sl, 0, lam, P.NL, ks2), plan.slab(sl, 1, lam, P.NL, ks2), out,
+                   2 * ks2, plan.tick + (size_t)sl * P.NL + lam, NT);
 }
 
 // Quadrant bank: grad_bank = for each stored element, the sum over the four
 // flip classes (class x: other side, column mirrored; class y: row mirrored)
-// and the part slabs of the per-key gradients, in a fixed order
-// (deterministic).  n = stored elements, n_kl = stored slices x wavelengths.
-__global__ void bank_fold_quadrant(const float* __restrict__ parts_buf, size_t n, int parts,
-                                   int n_kl, int ks, float* __restrict__ gbank) {
-  const size_t ks2 = (size_t)ks * ks, nv = 4 * n;  // elements of one part slab
+// of the per-key gradients, in a fixed order (deterministic).  n = stored
+// elements, n_kl = stored slices x wavelengths.
+__global__ void bank_fold_quadrant(const float* __restrict__ keyg, size_t n, int n_kl, int ks,
+                                   float* __restrict__ gbank) {
+  const size_t ks2 = (size_t)ks * ks;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t kl = i / (2 * ks2), rem = i - kl * 2 * ks2;
@@ -606,61 +799,131 @@ __global__ void bank_fold_quadrant(const float* __restrict__ parts_buf, size_t n
     for (int f = 0; f < 4; ++f) {
       const bool mx = f & 1, my = f & 2;
       const int vs = mx ? 1 - side : side, va = my ? ks - 1 - a : a, vb = mx ? ks - 1 - b : b;
-      const size_t vi = (((size_t)f * n_kl + kl) * 2 + vs) * ks2 + (size_t)va * ks + vb;
-      for (int q = 0; q < parts; ++q) acc += parts_buf[(size_t)q * nv + vi];
+      acc += keyg[(((size_t)f * n_kl + kl) * 2 + vs) * ks2 + (size_t)va * ks + vb];
     }
     gbank[i] = acc;
   }
 }
 
-// grad_bank = sum of the part slabs, added in part order (deterministic)
-__global__ void bank_parts_reduce(const float* __restrict__ parts_buf, size_t n, int parts,
-                                  float* __restrict__ gbank) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    float a = parts_buf[i];
-    for (int q = 1; q < parts; ++q) a += parts_buf[(size_t)q * n + i];
-    gbank[i] = a;
-  }
+// Workspace of a bank-gradient plan: counts, split slots, order, split keys,
+// tickets, then the chunk slabs of at most smax split slices (the plan is
+// the last part of a workspace and smax what the rest of it holds).
+struct PlanLayout {
+  int smax;
+  size_t cnt, slot, order, split, tick, pbuf, total;
+};
+
+inline PlanLayout plan_layout(const RenderParams& P, int smax) {
+  const int nk = n_keys(P);
+  PlanLayout L;
+  L.smax = smax;
+  size_t o = 0;
+  L.cnt = o;
+  o += (size_t)nk * 4;
+  L.slot = o;
+  o += (size_t)nk * 4;
+  L.order = o;
+  o += ((size_t)nk + smax) * 4;
+  L.split = o;
+  o += (size_t)smax * 4;
+  L.tick = o;
+  o += (size_t)smax * P.NL * 4;
+  L.pbuf = (o + 255) & ~(size_t)255;
+  o = L.pbuf + (size_t)2 * smax * P.NL * 2 * P.ks * P.ks * 4;
+  L.total = (o + 255) & ~(size_t)255;
+  return L;
+}
+
+// split slots a full workspace provides: an eighth of the keys, at least 32
+inline int plan_smax(const RenderParams& P) { return std::max(32, n_keys(P) / 8); }
+inline size_t plan_bytes(const RenderParams& P) { return plan_layout(P, plan_smax(P)).total; }
+
+// the most split slots (up to plan_smax) whose plan fits in avail bytes; -1
+// if not even a plan without splits fits
+inline int plan_smax_fit(const RenderParams& P, size_t avail) {
+  const size_t per = (size_t)2 * P.NL * 2 * P.ks * P.ks * 4 + (size_t)(2 + P.NL) * 4;
+  const size_t base = plan_layout(P, 0).total;
+  if (avail < base) return -1;
+  int sm = (int)std::min<size_t>((size_t)plan_smax(P), (avail - base) / per);
+  while (sm > 0 && plan_layout(P, sm).total > avail) --sm;
+  return sm;
+}
+
+// blocks of kernel fn (nt threads, smem bytes) resident on the whole GPU
+inline sd_status resident_blocks(const void* fn, int nt, size_t smem, int* out) {
+  int dev = 0, sms = 0, nb = 0;
+  SD_CUDA_TRY(cudaGetDevice(&dev));
+  SD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nt, smem));
+  *out = std::max(1, nb) * std::max(1, sms);
+  return SD_OK;
+}
+
+// Builds the plan in ws (plan_layout(P, smax).total bytes, 256-byte
+// aligned) for a bank kernel of which `resident` blocks run at once; returns
+// it in *plan and the number of block ranks (items) to launch in *ranks.
+inline sd_status launch_plan(const RenderParams& P, const unsigned* bm, int words, size_t ntiles,
+                             int resident, void* ws, int smax, BankPlan* plan, int* ranks,
+                             cudaStream_t s) {
+  const PlanLayout L = plan_layout(P, smax);
+  const int nk = n_keys(P);
+  char* b = reinterpret_cast<char*>(ws);
+  int* cnt = reinterpret_cast<int*>(b + L.cnt);
+  int* slot = reinterpret_cast<int*>(b + L.slot);
+  int* order = reinterpret_cast<int*>(b + L.order);
+  int* split = reinterpret_cast<int*>(b + L.split);
+  int* tick = reinterpret_cast<int*>(b + L.tick);
+  SD_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nk * 4, s));
+  if (L.smax > 0) SD_CUDA_TRY(cudaMemsetAsync(tick, 0, (size_t)L.smax * P.NL * 4, s));
+  dim3 g(words, (unsigned)((ntiles + 1023) / 1024));
+  slice_count_kernel<<<g, 256, 0, s>>>(bm, words, ntiles, nk, cnt);
+  sd_status st = launch_status();
+  if (st != SD_OK) return st;
+  slice_order_kernel<<<1, 1024, 0, s>>>(cnt, nk, P.NL, resident, L.smax, slot, split, order);
+  st = launch_status();
+  if (st != SD_OK) return st;
+  plan->order = order;
+  plan->slot = slot;
+  plan->tick = tick;
+  plan->pbuf = reinterpret_cast<float*>(b + L.pbuf);
+  plan->nkeys = nk;
+  *ranks = nk + L.smax;
+  return SD_OK;
 }
 
 template <int NT, int SPT, class TI>
 sd_status launch_bank_bwd(const RenderParams& P, const float* gout, const unsigned* bm, int words,
-                          int ntx, int nty, float* gbank, float* parts_buf, int parts,
-                          cudaStream_t s) {
+                          int ntx, int nty, void* plan_ws, int smax, float* gbank,
+                          float* quad_buf, cudaStream_t s) {
   const int ks = P.ks;
   size_t smem = (size_t)(RT_Y + ks - 1 + SEG) * (TXB + ks - 1) * 4 + (size_t)TXB * RT_Y * 8 +
                 (size_t)(TXB * RT_Y / SEG) * 4;
   auto k = render_bwd_bank_kernel<NT, SPT, TI>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(n_keys(P), P.NL, parts);
+  int resident = 0, ranks = 0;
+  sd_status st = resident_blocks(reinterpret_cast<const void*>(k), NT, smem, &resident);
+  if (st != SD_OK) return st;
+  BankPlan plan;
+  st = launch_plan(P, bm, words, (size_t)P.N * ntx * nty, resident, plan_ws, smax, &plan, &ranks,
+                   s);
+  if (st != SD_OK) return st;
   // a quadrant bank's gradients are per key (flip class) first, then folded
   const bool quad = P.fmode == SD_FIELD_QUADRANT;
-  k<<<grid, NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 || quad ? parts_buf : gbank,
-                           parts);
-  sd_status st = launch_status();
-  if (st != SD_OK) return st;
-  if (quad) {
-    const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
-    bank_fold_quadrant<<<1024, 256, 0, s>>>(parts_buf, n, parts, P.FC * P.Z * P.NL, ks, gbank);
-    return launch_status();
-  }
-  if (parts == 1) return st;
-  size_t n = (size_t)n_keys(P) * P.NL * 2 * ks * ks;
-  bank_parts_reduce<<<1024, 256, 0, s>>>(parts_buf, n, parts, gbank);
+  k<<<(unsigned)ranks * P.NL, NT, smem, s>>>(P, gout, bm, words, ntx, nty, plan,
+                                             quad ? quad_buf : gbank);
+  st = launch_status();
+  if (st != SD_OK || !quad) return st;
+  const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
+  bank_fold_quadrant<<<1024, 256, 0, s>>>(quad_buf, n, P.FC * P.Z * P.NL, ks, gbank);
   return launch_status();
 }
 
 constexpr size_t SMEM_CAP_B = 227 * 1024;
-// The bank gradient splits every slice's tiles over BANK_PARTS blocks when the
-// workspace holds that many partial banks (heavy slices otherwise set the
-// tail of the launch); fewer parts with a smaller workspace.
-constexpr int BANK_PARTS = 2;
 
 inline size_t bitmap_bytes(int N, int tx, int ty, int nkeys) {
   return ((size_t)N * tx * ty * bitmap_words(nkeys) * 4 + 255) & ~(size_t)255;
 }
-// one partial bank: a slab per key (a quadrant bank's keys carry 4 flip classes)
+// per-key gradient slab of a quadrant bank (its keys carry 4 flip classes)
 inline size_t bank_bytes(const RenderParams& P) {
   return (size_t)n_keys(P) * P.NL * 2 * P.ks * P.ks * 4;
 }
@@ -728,18 +991,21 @@ sd_status launch_img_bwd(const RenderParams& P, const float* gout, float* gaif, 
 
 template <class TI>
 sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const unsigned* bm,
-                              int words, int tx, int ty, float* gbank, float* parts_buf,
-                              int parts, cudaStream_t s) {
+                              int words, int tx, int ty, void* plan_ws, int smax,
+                              float* gbank, float* quad_buf, cudaStream_t s) {
   int KU = (P.ks + SEG - 1) / SEG * SEG;
   int nstrip = P.ks * (KU / SEG);
   // one strip per thread where the strips fill 512-608 threads (ks = 61..65:
   // 6.76 -> 6.51 ms at 1024x1024x3 against 256 threads x 3 strips, of
   // which a quarter of the slots idle)
   if (nstrip > 512 && nstrip <= 608)
-    return launch_bank_bwd<608, 1, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
+    return launch_bank_bwd<608, 1, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
+                                       s);
   if (nstrip <= 256 * 3)
-    return launch_bank_bwd<256, 3, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
-  return launch_bank_bwd<512, 4, TI>(P, gout, bm, words, tx, ty, gbank, parts_buf, parts, s);
+    return launch_bank_bwd<256, 3, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
+                                       s);
+  return launch_bank_bwd<512, 4, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
+                                       s);
 }
 
 
@@ -793,7 +1059,8 @@ __device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err
 template <bool F16>
 __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
     const RenderParams P, const float* __restrict__ gout, const unsigned* __restrict__ bm,
-    int words, int ntx, int nty, float* __restrict__ gbank, int parts, int* err, uint32_t wlim) {
+    int words, int ntx, int nty, BankPlan plan, float* __restrict__ gbank, int* err,
+    uint32_t wlim) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[BG_NB], s_empty[BG_NB], s_tile, s_done;
   __shared__ uint32_t s_tmem;
@@ -804,7 +1071,11 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   unsigned short* gw = reinterpret_cast<unsigned short*>(smem + bg_img_bytes(ks));  // [2][32][96]
   unsigned char* bring = smem + bg_img_bytes(ks) + (size_t)2 * RT_Y * BG_GW * 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int key = blockIdx.x, lam = blockIdx.y, part = blockIdx.z;
+  // block (rank * NL + lam): item order[rank] (a slice or one tile chunk of
+  // a split slice; the items with the most tiles first)
+  const int lam = (int)(blockIdx.x % P.NL), item = plan.order[blockIdx.x / P.NL];
+  if (item < 0 || (item >> 1) >= plan.nkeys) return;  // past the last item
+  const int key = item >> 1, chunk = item & 1, sl = plan.slot[key], nch = sl >= 0 ? 2 : 1;
   const bool two = P.Z > 1;
   const int kw = key >> 5;
   const unsigned kbit = 1u << (key & 31);
@@ -835,11 +1106,11 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   unsigned inited = 0;  // kernel-row groups written (MMA thread)
   bool issuing = true;  // MMA thread: false from the first wait that gave up
 
-  // the tiles of this part that use the slice, in ascending order
+  // the tiles that use the slice, in ascending order
   __shared__ int s_list[BG_NT], s_twc[BG_NT / 32];
   const size_t ntiles = (size_t)P.N * nty * ntx;
   for (size_t t0 = 0; t0 < ntiles; t0 += BG_NT)
-    for (int li = 0, nlist = slice_tiles<BG_NT>(bm, words, kw, kbit, t0, ntiles, parts, part,
+    for (int li = 0, nlist = slice_tiles<BG_NT>(bm, words, kw, kbit, t0, ntiles, nch, chunk,
                                                 s_list, s_twc);
          li < nlist; ++li) {
         const size_t tile = t0 + s_list[li];
@@ -1020,7 +1291,9 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   __syncwarp();
   __syncthreads();
   tc::fence_after_sync();
-  float* out = gbank + ((size_t)part * gridDim.x * P.NL + (size_t)key * P.NL + lam) * 2 * ks * ks;
+  const int ks2 = ks * ks;
+  float* out = gbank + ((size_t)key * P.NL + lam) * 2 * ks2;
+  float* dst = nch == 1 ? out : plan.slab(sl, chunk, lam, P.NL, ks2);
   if (warp < 4) {
     const int m = 32 * warp + lane, g = m >> 3, r = m & 7;
     const unsigned ini = (unsigned)s_init;
@@ -1036,7 +1309,7 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
           if (i == 8 && r != 7) continue;  // column 64 comes from group 7, shift 8
           const int vv = 8 * r + i;
           if (vv < ks)
-            out[(size_t)side * ks * ks + (size_t)(ks - 1 - u) * ks + (ks - 1 - vv)] =
+            dst[(size_t)side * ks2 + (size_t)(ks - 1 - u) * ks + (ks - 1 - vv)] =
                 ((ini >> ug) & 1u) ? v[side * 16 + i] : 0.f;
         }
     }
@@ -1044,30 +1317,35 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_free(tmem, 256);
+  if (nch == 2)
+    combine_chunks(plan.slab(sl, 0, lam, P.NL, ks2), plan.slab(sl, 1, lam, P.NL, ks2), out,
+                   2 * ks2, plan.tick + (size_t)sl * P.NL + lam, BG_NT);
 }
 
 sd_status launch_bank_grad_tc(const RenderParams& P, const float* gout, const unsigned* bm,
-                              int words, int ntx, int nty, float* gbank, float* parts_buf,
-                              int parts, int* err, bool f16, cudaStream_t s) {
+                              int words, int ntx, int nty, void* plan_ws, int smax,
+                              float* gbank, float* quad_buf, int* err, bool f16,
+                              cudaStream_t s) {
   const int ks = P.ks;
   // at least 80 KB: two CTAs per SM, the tensor memory's 512 columns
   const size_t smem = std::max(bg_smem(ks), (size_t)80 * 1024);
   auto k = f16 ? bank_grad_tc_kernel<true> : bank_grad_tc_kernel<false>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const bool quad = P.fmode == SD_FIELD_QUADRANT;
-  dim3 grid(n_keys(P), P.NL, parts);
-  k<<<grid, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty, parts > 1 || quad ? parts_buf : gbank,
-                              parts, err, wait_limit(BG_WAIT));
-  sd_status st = launch_status();
+  int resident = 0, ranks = 0;
+  sd_status st = resident_blocks(reinterpret_cast<const void*>(k), BG_NT, smem, &resident);
   if (st != SD_OK) return st;
-  if (quad) {
-    const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
-    bank_fold_quadrant<<<1024, 256, 0, s>>>(parts_buf, n, parts, P.FC * P.Z * P.NL, ks, gbank);
-    return launch_status();
-  }
-  if (parts == 1) return SD_OK;
-  const size_t n = (size_t)n_keys(P) * P.NL * 2 * ks * ks;
-  bank_parts_reduce<<<1024, 256, 0, s>>>(parts_buf, n, parts, gbank);
+  BankPlan plan;
+  st = launch_plan(P, bm, words, (size_t)P.N * ntx * nty, resident, plan_ws, smax, &plan, &ranks,
+                   s);
+  if (st != SD_OK) return st;
+  const bool quad = P.fmode == SD_FIELD_QUADRANT;
+  k<<<(unsigned)ranks * P.NL, BG_NT, smem, s>>>(P, gout, bm, words, ntx, nty, plan,
+                                                quad ? quad_buf : gbank, err,
+                                                wait_limit(BG_WAIT));
+  st = launch_status();
+  if (st != SD_OK || !quad) return st;
+  const size_t n = (size_t)P.FC * P.Z * P.NL * 2 * ks * ks;
+  bank_fold_quadrant<<<1024, 256, 0, s>>>(quad_buf, n, P.FC * P.Z * P.NL, ks, gbank);
   return launch_status();
 }
 
@@ -1085,7 +1363,7 @@ sd_status sd_dp_render_backward_workspace(const sd_bank_layout* layout, int N, i
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
   *bytes = sel_table_bytes(P) + img_layout(P).total + bitmap_bytes(N, tx, ty, n_keys(P)) +
-           (size_t)BANK_PARTS * bank_bytes(P);
+           (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0) + plan_bytes(P);
   return SD_OK;
 }
 
@@ -1124,13 +1402,18 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
   // then the image pass's tables
   const size_t img_bytes = grad_aif ? img_layout(P).total : 0;
   if (grad_aif && workspace_bytes < img_bytes) return SD_ERR_ARG;
+  // then the bank pass's bitmap, a quadrant bank's per-key slab (folded
+  // onto the stored quadrant) and the work plan, whose split slots take
+  // what the rest of the workspace holds
+  int smax = 0;
   if (grad_bank) {
-    // a quadrant bank needs at least one partial bank to fold
     int tx, ty;
     bwd_tiles(H, W, &tx, &ty);
-    const size_t need_min = img_bytes + bitmap_bytes(N, tx, ty, n_keys(P)) +
-                            (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
-    if (workspace_bytes < need_min) return SD_ERR_ARG;
+    const size_t fixed = img_bytes + bitmap_bytes(N, tx, ty, n_keys(P)) +
+                         (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
+    if (workspace_bytes < fixed) return SD_ERR_ARG;
+    smax = plan_smax_fit(P, workspace_bytes - fixed);
+    if (smax < 0) return SD_ERR_ARG;
   }
   st = launch_select_table(P, sel, s);
   if (st != SD_OK) return st;
@@ -1152,26 +1435,22 @@ sd_status sd_dp_render_backward(const float* grad_out, const void* aif, const fl
     size_t words = bitmap_words(n_keys(P));
     size_t need = bitmap_bytes(N, tx, ty, n_keys(P));
     unsigned* bm = reinterpret_cast<unsigned*>(workspace);
-    int parts = 1;
-    for (int q = BANK_PARTS; q > 1; q >>= 1)
-      if (workspace_bytes >= need + (size_t)q * bank_bytes(P)) {
-        parts = q;
-        break;
-      }
-    float* parts_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+    float* quad_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+    void* plan_ws = reinterpret_cast<char*>(workspace) + need +
+                    (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
     dim3 g1(tx, ty, N);
     slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
     sd_status r = launch_status();
     if (r != SD_OK) return r;
     // the bank pass reads the image in its storage type
     r = image_dtype == SD_F32
-            ? launch_bank_bwd_any<float>(P, grad_out, bm, (int)words, tx, ty, grad_bank,
-                                         parts_buf, parts, s)
+            ? launch_bank_bwd_any<float>(P, grad_out, bm, (int)words, tx, ty, plan_ws, smax,
+                                         grad_bank, quad_buf, s)
         : image_dtype == SD_BF16
-            ? launch_bank_bwd_any<__nv_bfloat16>(P, grad_out, bm, (int)words, tx, ty,
-                                                 grad_bank, parts_buf, parts, s)
-            : launch_bank_bwd_any<__half>(P, grad_out, bm, (int)words, tx, ty, grad_bank,
-                                          parts_buf, parts, s);
+            ? launch_bank_bwd_any<__nv_bfloat16>(P, grad_out, bm, (int)words, tx, ty, plan_ws,
+                                                 smax, grad_bank, quad_buf, s)
+            : launch_bank_bwd_any<__half>(P, grad_out, bm, (int)words, tx, ty, plan_ws, smax,
+                                          grad_bank, quad_buf, s);
     if (r != SD_OK) return r;
   }
   return SD_OK;
@@ -1187,7 +1466,7 @@ sd_status sd_dp_render_bank_grad_tc_workspace(const sd_bank_layout* layout, int 
   int tx, ty;
   bwd_tiles(H, W, &tx, &ty);
   *bytes = 256 + sel_table_bytes(P) + bitmap_bytes(N, tx, ty, n_keys(P)) +
-           (size_t)BANK_PARTS * bank_bytes(P);
+           (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0) + plan_bytes(P);
   return SD_OK;
 }
 
@@ -1213,10 +1492,14 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
   bwd_tiles(H, W, &tx, &ty);
   const size_t words = bitmap_words(n_keys(P));
   const size_t sel_bytes = sel_table_bytes(P);
-  const size_t need = 256 + sel_bytes + bitmap_bytes(N, tx, ty, n_keys(P));
-  const size_t need_min = need + (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
-  if (!workspace || workspace_bytes < need_min || (reinterpret_cast<uintptr_t>(workspace) & 255))
+  const int nk = n_keys(P);
+  const size_t need = 256 + sel_bytes + bitmap_bytes(N, tx, ty, nk);
+  const size_t quad_bytes = P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0;
+  if (!workspace || workspace_bytes < need + quad_bytes ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
     return SD_ERR_ARG;
+  const int smax = plan_smax_fit(P, workspace_bytes - need - quad_bytes);
+  if (smax < 0) return SD_ERR_ARG;
   int* err = reinterpret_cast<int*>(workspace);
   SD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   if (N == 0 || H == 0 || W == 0) {
@@ -1226,21 +1509,16 @@ sd_status sd_dp_render_bank_grad_tc(const float* grad_out, const void* aif, cons
   int2* sel = reinterpret_cast<int2*>(reinterpret_cast<char*>(workspace) + 256);
   P.sel = sel;
   unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + 256 + sel_bytes);
-  int parts = 1;
-  for (int q = BANK_PARTS; q > 1; q >>= 1)
-    if (workspace_bytes >= need + (size_t)q * bank_bytes(P)) {
-      parts = q;
-      break;
-    }
-  float* parts_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+  float* quad_buf = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + need);
+  void* plan_ws = reinterpret_cast<char*>(workspace) + need + quad_bytes;
   st = launch_select_table(P, sel, s);
   if (st != SD_OK) return st;
   dim3 g1(tx, ty, N);
   slice_bitmap_kernel<<<g1, NT_BM, words * 4, s>>>(P, bm, (int)words);
   st = launch_status();
   if (st != SD_OK) return st;
-  return launch_bank_grad_tc(P, grad_out, bm, (int)words, tx, ty, grad_bank, parts_buf, parts,
-                             err, image_dtype == SD_F16, s);
+  return launch_bank_grad_tc(P, grad_out, bm, (int)words, tx, ty, plan_ws, smax, grad_bank,
+                             quad_buf, err, image_dtype == SD_F16, s);
 }
 
 }  // extern "C"
@@ -1291,7 +1569,8 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
   size_t need = 0;
   if (grad_aif || grad_bank) {
     // the selection table, the image pass's tables and the bank pass's
-    // bitmap must fit; partial banks are used as far as the array allows
+    // bitmap, a quadrant bank's per-key slab and a work plan without split
+    // slots must fit (split slots take what the array holds beyond that)
     RenderParams P;
     sd_status st = setup_bwd(layout, N, C, H, W, P);
     if (st != SD_OK) return st;
@@ -1300,7 +1579,7 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
     need = sel_table_bytes(P);
     if (grad_aif) need += img_layout(P).total;
     if (grad_bank)
-      need += bitmap_bytes(N, tx, ty, n_keys(P)) +
+      need += bitmap_bytes(N, tx, ty, n_keys(P)) + plan_layout(P, 0).total +
               (P.fmode == SD_FIELD_QUADRANT ? bank_bytes(P) : 0);
     if (need > NOALLOC_SCRATCH_BYTES) return SD_ERR_CAPACITY;
     st = noalloc_scratch(&ws);

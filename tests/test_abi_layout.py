@@ -118,12 +118,14 @@ def test_tc_workspace_holds_the_bf16_relayout(lib):
         assert st == L.SD_OK and n >= 256 + keys * 3 * 2 * 65 * 65 * 2
 
 
-def test_backward_workspace_holds_image_tables_bitmap_and_two_partial_banks(lib):
+def test_backward_workspace_holds_selection_image_tables_bitmap_and_plan(lib):
     # an 8-byte selection per pixel (both passes), the image gradient's
     # tables (every key's kernel re-laid as FP32 columns of at least ks rows
     # per side, a 2-byte extent per kernel row), then the bank gradient's
-    # tile bitmaps and a partial FP32 bank for each of two blocks per slice
-    # (one slab per key)
+    # tile bitmaps, for a quadrant bank an FP32 gradient slab per key (flip
+    # class), and the work plan: 8 bytes per key (tile count, launch order)
+    # and two chunk slabs (all wavelengths) for each of max(32, keys / 8)
+    # split slices
     N, C, H, W = 2, 3, 100, 130
     for mode, cells in ((0, 3), (1, 9)):
         lay, keep = layout(mode=mode)
@@ -132,12 +134,16 @@ def test_backward_workspace_holds_image_tables_bitmap_and_two_partial_banks(lib)
         tiles = N * -(-H // 32) * -(-W // 64)
         assert st == L.SD_OK
         sel_part = N * H * W * 8
-        bank_part = 2 * keys * 3 * 2 * 65 * 65 * 4 + tiles * keys // 8
+        slab = keys * 3 * 2 * 65 * 65 * 4
+        bitmap = tiles * keys // 8
+        plan = 8 * keys + 2 * max(32, keys // 8) * 3 * 2 * 65 * 65 * 4
         img_part = keys * 3 * 65 * (65 * 2 * 4 + 2)
-        assert n >= sel_part + bank_part + img_part
-        # the tensor-core bank gradient needs the selection but no image tables
+        assert n >= sel_part + img_part + bitmap + plan + (slab if mode == 1 else 0)
+        # the tensor-core bank gradient needs the same bank-pass parts but no
+        # image tables
         st2, n2 = bg_ws(lib, lay, N, C, H, W)
-        assert st2 == L.SD_OK and sel_part + bank_part <= n2 < n
+        assert st2 == L.SD_OK and sel_part + bitmap + plan + (slab if mode == 1 else 0) <= n2
+        assert n2 < n
 
 
 def test_workspace_grows_with_the_problem(lib):

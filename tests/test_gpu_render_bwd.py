@@ -97,6 +97,43 @@ def test_bank_gradient_deterministic_and_workspace_checked(sdlib):
         sd.dp_render_backward(*args, lay, need_aif=False, workspace=small)
 
 
+def test_bank_gradient_with_fewer_split_slots(sdlib):
+    # the work plan splits slices with more than a block's share of tiles
+    # into two chunks while split slots remain; a workspace shortened by the
+    # chunk slabs leaves none (every slice one block) or a few: each result
+    # matches the oracle and repeats bitwise
+    sd = sdlib
+    case = CASES[3]
+    N, C, H, W_, F, Z, NL, ks = case
+    aif, depth, fh, dm, pitch, bank, G = setup(case, 11)
+    lay = sd.BankLayout(fh, dm, NL, ks, pitch)
+    args = (torch.tensor(G, device="cuda"), torch.tensor(aif, device="cuda"),
+            torch.tensor(depth, device="cuda"), torch.tensor(bank, device="cuda").reshape(-1))
+    _, ref = O.render_bank_bwd(G, aif, depth, bank, fh, dm, pitch)
+    full = sd.render_backward_workspace(lay, N, C, H, W_)
+    slab = 2 * NL * 2 * ks * ks * 4            # both chunks of one split slice
+    # the smallest workspace the bank gradient accepts (no split slot): the
+    # calls that are refused launch nothing
+    lo, hi = 0, full
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        try:
+            sd.dp_render_backward(*args, lay, need_aif=False,
+                                  workspace=torch.empty(mid, dtype=torch.uint8, device="cuda"))
+            hi = mid
+        except sd.SdError:
+            lo = mid
+    assert hi < full - 32 * slab
+    for nbytes in (full, hi, hi + 3 * slab + 1024):
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        _, b1 = sd.dp_render_backward(*args, lay, need_aif=False, workspace=ws)
+        _, b2 = sd.dp_render_backward(*args, lay, need_aif=False, workspace=ws)
+        torch.cuda.synchronize()
+        assert torch.equal(b1, b2)
+        got = b1.cpu().numpy().reshape(ref.shape)
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
 EDGE = [
     # N, C, H, W, F, Z, NL, ks
     (1, 1, 1, 1, 2, 2, 1, 5),        # one pixel: every tap folds onto it

@@ -2,7 +2,7 @@
 device memory, e.g. code confined to a host framework's memory pool) gives
 the same gradients as the workspace entry point, on two calls in a row, for
 a radial FP32 bank, a radial BF16 bank and a first-quadrant bank (whose
-partial bank must fit in the fixed array), and rejects sizes whose slice
+per-key gradient slab must fit in the fixed array), and rejects sizes whose slice
 bitmap exceeds its fixed 16 MiB device array.
 
 Collected last on purpose: it shares one static device array across calls,
@@ -53,7 +53,7 @@ def test_noalloc_matches_workspace_entry(sdlib, case):
     fh = np.linspace(0.0, 0.5 * max(H, W_) * 0.002, F)
     dm = W.inverse_uniform_depths(300.0, 3000.0, Z) / 1000.0
     lay = sd.BankLayout(fh, dm, NL, ks, 0.002, dtype=dt, field_mode=mode)
-    # the bitmap and (quadrant bank) one partial bank must fit in the array
+    # the tables, the bitmap and (quadrant bank) the per-key slab must fit
     assert sd.render_backward_workspace(lay, N, C, H, W_) < SCRATCH
     ref_a, ref_b = sd.dp_render_backward(G, aif, depth, bank, lay)
     for _ in range(2):
