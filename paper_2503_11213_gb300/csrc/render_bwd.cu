@@ -244,7 +244,17 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
   const size_t col_stride = (size_t)IL.rcol * 2;  // floats per re-laid column
   const int fold_lo = -r0, fold_hi = H - 1 - r0;  // buffer rows of clamped rows
 
-  // the (group, source block) pairs of the item, dealt to the warps in turn
+  // the (group, source block) pairs of the item: the first pairs are dealt
+  // to the warps in turn, the last npairs mod IG_NW are shared by all warps,
+  // each taking every IG_NW-th of the pair's slices (a fixed assignment, so
+  // the buffers' sums do not vary; without the sharing an interior item's 9
+  // pairs left one warp with 3 while the others waited at the barrier)
+  int npairs = 0;
+  for (int g = g_lo; g <= g_hi; ++g) {
+    const int T0 = r0 + 8 * g;
+    npairs += max(0, min(nsb - 1, (T0 + 7 + p) >> 3) - max(0, (T0 - p) >> 3) + 1);
+  }
+  const int dealt = npairs - npairs % IG_NW;
   int pair = 0;
   for (int g = g_lo; g <= g_hi; ++g) {
     const int T0 = r0 + 8 * g;
@@ -253,7 +263,8 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
     const int sb_lo = max(0, (T0 - p) >> 3);  // arithmetic shift: floor division
     const int sb_hi = min(nsb - 1, (T0 + 7 + p) >> 3);
     for (int sb = sb_lo; sb <= sb_hi; ++sb, ++pair) {
-      if (pair % IG_NW != warp) continue;
+      const bool shared_pair = pair >= dealt;
+      if (!shared_pair && pair % IG_NW != warp) continue;
       const int d = T0 + p - 8 * sb;  // kernel row of (j, a) = d + j - a
       // stage the source block: lane owns columns lane and lane + 32
       __syncwarp();
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
       __syncwarp();
       // the block's slices in ascending order; a pixel (key k0, weight t)
       // uses k0 unless t == 1 and k0 + 1 when t > 0 (one slice: k0 only)
-      int last = -1;
+      int last = -1, ordinal = 0;
       while (true) {
         int m = 0x7fffffff;
 #pragma unroll
@@ -290,6 +301,7 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
         const int k = __reduce_min_sync(0xffffffffu, m);
         if (k == 0x7fffffff) break;
         last = k;
+        if (shared_pair && ordinal++ % IG_NW != warp) continue;
         const int kl = k * P.NL + lam;
         // kernel columns holding a non-zero tap in rows d - 7 .. d + 7
         unsigned lo = 255u, hi = 0u;
