@@ -204,17 +204,124 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int idx) {
   return pos;
 }
 
+// A half pass: up to 16 candidate columns of one slice (the columns of the
+// staged source block whose pixels use the slice: bit c of m0 is column c,
+// bit c of m1 column 32 + c), candidates q0 .. q0 + 15 of them.  Warp-uniform.
+struct IgUnit {
+  int k;              // slice key
+  int vlo, vhi;       // kernel columns holding a non-zero tap in the band
+  unsigned m0, m1;
+  int n0, ncand, q0;  // n0 = popc(m0); ncand = candidates of the slice
+  const float* kb0;   // re-laid taps of kernel column vlo, band start
+};
+
+// One pass: lanes 0-15 take unit U0's candidates into row buffer buf0,
+// lanes 16-31 unit U1's (if valid) into buf1.  Each lane holds 8 source
+// rows of its column, weighted by the slice's interpolation weight, and
+// for every kernel column v of the union of the two units' ranges (taps
+// outside a unit's range are zero) adds the 8 output rows of the band to
+// its buffer column.  Within a half the columns are distinct, and the two
+// halves write separate buffers, so no two lanes touch one word.
 template <int BWMAX>
-__global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
+__device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0, float* buf1,
+                                        const IgUnit& U0, const IgUnit& U1, bool u1_valid,
+                                        bool two, bool plain, int jr0, int fold_lo, int fold_hi,
+                                        size_t col_stride) {
+  const int lane = threadIdx.x & 31, h = lane >> 4;
+  const bool mine_valid = h == 0 || u1_valid;
+  // this lane's unit (selected field by field: the values are warp-uniform
+  // per half)
+  const int k = h ? U1.k : U0.k;
+  const unsigned m0 = h ? U1.m0 : U0.m0, m1 = h ? U1.m1 : U0.m1;
+  const int n0 = h ? U1.n0 : U0.n0, ncand = h ? U1.ncand : U0.ncand;
+  // an idle half (no second unit) keeps the first unit's range and taps so
+  // that its loads stay inside the re-laid bank
+  const bool hu = h && u1_valid;
+  const int vlo_u = hu ? U1.vlo : U0.vlo;
+  const float* kb_u = hu ? U1.kb0 : U0.kb0;
+  const int idx = (h ? U1.q0 : U0.q0) + (lane & 15);
+  const bool act = mine_valid && idx < ncand;
+  const int col = !act ? 0 : (idx < n0 ? nth_set_bit(m0, idx) : 32 + nth_set_bit(m1, idx - n0));
+  const int vlo = u1_valid ? min(U0.vlo, U1.vlo) : U0.vlo;
+  const int vhi = u1_valid ? max(U0.vhi, U1.vhi) : U0.vhi;
+  float GL[8], GR[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const float4 e = src[a][col];
+    const int k0 = __float_as_int(e.w);
+    const float w = !act || k0 < 0 ? 0.f
+                    : (k0 == k ? (two ? 1.f - e.z : 1.f) : ((two && k0 + 1 == k) ? e.z : 0.f));
+    GL[a] = w * e.x;
+    GR[a] = w * e.y;
+  }
+  // the lane reads its own unit's taps from column vlo (of the union) on;
+  // columns before its own range are zero, so start the pointer there too
+  const size_t cs4 = col_stride / 4;
+  const float4* kb = reinterpret_cast<const float4*>(kb_u) - (ptrdiff_t)(vlo_u - vlo) * cs4;
+  float* bcol = (h ? buf1 : buf0) + col;
+  // taps of column v: rows d - 7 .. d + 8, (L, R) interleaved; the next
+  // column's are loaded while this one is used
+  float4 tn[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
+  for (int v = vlo; v <= vhi; ++v) {
+    float T[32];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      T[4 * q] = tn[q].x;
+      T[4 * q + 1] = tn[q].y;
+      T[4 * q + 2] = tn[q].z;
+      T[4 * q + 3] = tn[q].w;
+    }
+    kb += cs4;
+    if (v < vhi) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
+    }
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float sl = 0.f, sr = 0.f;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        sl = fmaf(GL[a], T[2 * (j - a + 7)], sl);
+        sr = fmaf(GR[a], T[2 * (j - a + 7) + 1], sr);
+      }
+      acc[j] = sl + sr;
+    }
+    if (act) {
+      if (plain) {  // distinct rows: loads, adds and stores batch
+        float old8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) old8[j] = bcol[j * BWMAX + v];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bcol[j * BWMAX + v] = old8[j] + acc[j];
+      } else {  // folded rows may repeat: in order, one at a time
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int tr = min(max(jr0 + j, fold_lo), fold_hi);
+          bcol[tr * BWMAX + v] += acc[j];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int BWMAX>
+__global__ void __launch_bounds__(IG_NW * 32, 3) render_bwd_img_kernel(
     const RenderParams P, ImgLayout IL, const float* __restrict__ gout,
     const int2* __restrict__ sel, const float* __restrict__ kcol,
     const unsigned short* __restrict__ ext, int phase, int nr_phase, int nrb,
     float* __restrict__ gaif) {
-  // per warp: the staged source block (gL, gR, t, key) and the row buffer
+  // per warp: the staged source block (gL, gR, t, key) and a row buffer per
+  // half-warp
   extern __shared__ __align__(16) unsigned char smem[];
   float4 (*s_src)[8][IG_SW] = reinterpret_cast<float4 (*)[8][IG_SW]>(smem);
-  float (*s_buf)[8][BWMAX] =
-      reinterpret_cast<float (*)[8][BWMAX]>(smem + (size_t)IG_NW * 8 * IG_SW * 16);
+  // buffer b = 2 * warp + half at s_buf + b * IG_BUFS: 16 floats of padding
+  // put a column's word in the two halves' buffers in different banks
+  constexpr int IG_BUFS = 8 * BWMAX + 16;
+  float* s_buf = reinterpret_cast<float*>(smem + (size_t)IG_NW * 8 * IG_SW * 16);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // one item (strip of source columns, 8 output rows) per block
   const long long item = blockIdx.x;
@@ -228,9 +335,10 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
   const int x0 = (phase + IL.nphase * rr) * IG_SW;
   const int BW = IG_SW + ks - 1;
   const bool two = P.Z > 1;
-  float (*buf)[BWMAX] = s_buf[warp];
+  float* buf0 = s_buf + (size_t)(2 * warp) * IG_BUFS;
+  float* buf1 = buf0 + IG_BUFS;
   float4 (*src)[IG_SW] = s_src[warp];
-  for (int i = lane; i < 8 * BWMAX; i += 32) (&buf[0][0])[i] = 0.f;
+  for (int i = lane; i < 2 * IG_BUFS; i += 32) buf0[i] = 0.f;  // both halves
 
   const float* goL = gout + (((size_t)n * 2 * P.C + c) * H) * W;
   const float* goR = gout + (((size_t)n * 2 * P.C + P.C + c) * H) * W;
@@ -287,6 +395,8 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
       // the block's slices in ascending order; a pixel (key k0, weight t)
       // uses k0 unless t == 1 and k0 + 1 when t > 0 (one slice: k0 only)
       int last = -1, ordinal = 0;
+      bool pending = false;  // a half pass waiting for its partner
+      IgUnit held{};
       while (true) {
         int m = 0x7fffffff;
 #pragma unroll
@@ -329,84 +439,37 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
         const unsigned m0 = __ballot_sync(0xffffffffu, f0);
         const unsigned m1 = __ballot_sync(0xffffffffu, f1);
         const int n0 = __popc(m0), ncand = n0 + __popc(m1);
-        const float* kb0 = kcol + ((size_t)kl * ks + vlo) * col_stride + 2 * (d - 7 + IL.padu);
-        for (int q0 = 0; q0 < ncand; q0 += 32) {
-          const int idx = q0 + lane;
-          const bool act = idx < ncand;
-          const int col = !act ? 0 : (idx < n0 ? nth_set_bit(m0, idx) : 32 + nth_set_bit(m1, idx - n0));
-          float GL[8], GR[8];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const float4 e = src[a][col];
-            const int k0 = __float_as_int(e.w);
-            const float w = !act || k0 < 0 ? 0.f
-                            : (k0 == k ? (two ? 1.f - e.z : 1.f) : ((two && k0 + 1 == k) ? e.z : 0.f));
-            GL[a] = w * e.x;
-            GR[a] = w * e.y;
-          }
-          const float4* kb = reinterpret_cast<const float4*>(kb0);
-          const size_t cs4 = col_stride / 4;
-          float* bcol = &buf[0][col];
-          // taps of column v: rows d - 7 .. d + 8, (L, R) interleaved; the
-          // next column's are loaded while this one is used
-          float4 tn[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
-          for (int v = vlo; v <= vhi; ++v) {
-            float T[32];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              T[4 * q] = tn[q].x;
-              T[4 * q + 1] = tn[q].y;
-              T[4 * q + 2] = tn[q].z;
-              T[4 * q + 3] = tn[q].w;
-            }
-            kb += cs4;
-            if (v < vhi) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
-            }
-            float acc[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float sl = 0.f, sr = 0.f;
-#pragma unroll
-              for (int a = 0; a < 8; ++a) {
-                sl = fmaf(GL[a], T[2 * (j - a + 7)], sl);
-                sr = fmaf(GR[a], T[2 * (j - a + 7) + 1], sr);
-              }
-              acc[j] = sl + sr;
-            }
-            if (act) {
-              if (plain) {  // distinct rows: loads, adds and stores batch
-                float old8[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) old8[j] = bcol[j * BWMAX + v];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) bcol[j * BWMAX + v] = old8[j] + acc[j];
-              } else {  // folded rows may repeat: in order, one at a time
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  const int tr = min(max(T0 - r0 + j, fold_lo), fold_hi);
-                  bcol[tr * BWMAX + v] += acc[j];
-                }
-              }
-            }
-            __syncwarp();
+        // the slice's candidates in half passes of 16, paired in order
+        const IgUnit U{k, vlo, vhi, m0, m1, n0, ncand, 0,
+                       kcol + ((size_t)kl * ks + vlo) * col_stride + 2 * (d - 7 + IL.padu)};
+        for (int q0 = 0; q0 < ncand; q0 += 16) {
+          IgUnit u = U;
+          u.q0 = q0;
+          if (!pending) {
+            held = u;
+            pending = true;
+          } else {
+            ig_pass<BWMAX>(src, buf0, buf1, held, u, true, two, plain, T0 - r0, fold_lo,
+                           fold_hi, col_stride);
+            pending = false;
           }
         }
       }
+      if (pending)
+        ig_pass<BWMAX>(src, buf0, buf1, held, held, false, two, plain, T0 - r0, fold_lo,
+                       fold_hi, col_stride);
     }
   }
   __syncthreads();
-  // the warps' buffers added in warp order into warp 0's
-  float* b0 = &s_buf[0][0][0];
+  // the buffers added in (warp, half) order into the first
+  float* b0 = s_buf;
   for (int i = threadIdx.x; i < 8 * BWMAX; i += IG_NW * 32) {
     float s = b0[i];
 #pragma unroll
-    for (int w = 1; w < IG_NW; ++w) s += (&s_buf[w][0][0])[i];
+    for (int w = 1; w < 2 * IG_NW; ++w) s += s_buf[(size_t)w * IG_BUFS + i];
     b0[i] = s;
   }
+  float (*fb)[BWMAX] = reinterpret_cast<float (*)[BWMAX]>(b0);  // [8][BWMAX]
   __syncthreads();
   // columns outside the image fold onto its first / last column (fixed order)
   const int cl = p - x0;            // buffer column of image column 0
@@ -415,13 +478,13 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
     const int j = threadIdx.x;
     if (cl > 0) {
       float s = 0.f;
-      for (int cc = 0; cc <= cl; ++cc) s += s_buf[0][j][cc];
-      s_buf[0][j][cl] = s;
+      for (int cc = 0; cc <= cl; ++cc) s += fb[j][cc];
+      fb[j][cl] = s;
     }
     if (cr < BW - 1) {
-      float s = s_buf[0][j][cr];
-      for (int cc = cr + 1; cc < BW; ++cc) s += s_buf[0][j][cc];
-      s_buf[0][j][cr] = s;
+      float s = fb[j][cr];
+      for (int cc = cr + 1; cc < BW; ++cc) s += fb[j][cc];
+      fb[j][cr] = s;
     }
   }
   __syncthreads();
@@ -431,7 +494,7 @@ __global__ void __launch_bounds__(IG_NW * 32, 4) render_bwd_img_kernel(
   const int ncol = c_hi - c_lo + 1;
   for (int i = threadIdx.x; i < nrow * ncol; i += IG_NW * 32) {
     const int j = i / ncol, cc = c_lo + (i - j * ncol);
-    ga[(size_t)(r0 + j) * W + (x0 - p + cc)] += s_buf[0][j][cc];
+    ga[(size_t)(r0 + j) * W + (x0 - p + cc)] += fb[j][cc];
   }
 }
 
@@ -986,7 +1049,8 @@ sd_status launch_img_bwd(const RenderParams& P, const float* gout, float* gaif, 
   if (st != SD_OK) return st;
   const int nrange = (P.W + IG_SW - 1) / IG_SW, nrb = (P.H + 7) / 8;
   const bool wide = P.ks > 65;
-  const size_t smem = (size_t)IG_NW * (8 * IG_SW * 16 + 8 * (wide ? 192 : 128) * 4);
+  const size_t smem =
+      (size_t)IG_NW * (8 * IG_SW * 16 + 2 * (8 * (wide ? 192 : 128) + 16) * 4);
   auto k = wide ? render_bwd_img_kernel<192> : render_bwd_img_kernel<128>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int phase = 0; phase < IL.nphase && phase < nrange; ++phase) {
