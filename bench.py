@@ -47,8 +47,12 @@ TRAFFIC_BYTES = {
     # skips): 104.6 MB read + 1.1 MB written; independent of the image size
     "trace_adj_kernel": 105.7e6,
     # the image-gradient call as the phase times it: selection table 4.2 MB,
-    # bank re-layout 103.9 + 91.8 MB, the two strip launches 74.1 + 82.8 MB
-    "render_bwd_img_kernel": 357.4e6,
+    # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.7 MB
+    "render_bwd_img_kernel": 375.6e6,
+    # the bank-gradient call as the phase times it: selection table 4.2 MB,
+    # slice bitmap 8.4 MB, work plan 0.1 MB, bank pass 46.3 MB read + 41.4 MB
+    # written (the rest of the 103.8 MB gradient bank still in L2 at its end)
+    "render_bwd_bank_kernel": 100.4e6,
 }
 
 # ---------------------------------------------------------------------------
@@ -419,7 +423,8 @@ def run_ours(args, world, rank, local, dist):
                      "adjoint_flops": adj_flops,
                      "render_flops": render_flops,
                      "kernels": {k: {"ms": round(phases[k][1], 4), "tflops": round(v, 3),
-                                     "frac": round(v / fp32_peak_tflops, 4)}
+                                     "frac": round(v / fp32_peak_tflops, 4),
+                                     "traffic": TRAFFIC_BYTES.get(k)}
                                  for k, v in tflops.items()}},
         "e2e": {"value": round(e2e_value, 4), "unit": "G rays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
