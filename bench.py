@@ -44,8 +44,9 @@ FP32_LANES_PER_SM = 128
 # whenever the kernel changes.
 TRAFFIC_BYTES = {
     # every request's gradient patch read once (also the zero patches it then
-    # skips): 104.6 MB read + 1.1 MB written; independent of the image size
-    "trace_adj_kernel": 105.7e6,
+    # skips) and the landing mask of the requests it traces again: 116.2 MB
+    # read + 1.2 MB written; independent of the image size
+    "trace_adj_kernel": 117.5e6,
     # the image-gradient call as the phase times it: selection table 4.2 MB,
     # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.7 MB
     "render_bwd_img_kernel": 375.6e6,
@@ -249,10 +250,14 @@ def run_ours(args, world, rank, local, dist):
     swept = torch.zeros((n_req, 2), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    # the forward records which rays land within a pixel of their patch; the
+    # adjoint traces only those again
+    mask = sd.land_mask(n_req, cfg["n_grid"], device=dev)
 
     def trace():
         sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=cfg["ks"],
-                        max_n=cfg["n_grid"], norm=sd.SD_NORM_JOINT, out=bank, stats=stats)
+                        max_n=cfg["n_grid"], norm=sd.SD_NORM_JOINT, out=bank, stats=stats,
+                        mask=mask)
 
     def render():
         sd.dp_render(aif, depth, bank, layout, out=out)
@@ -277,7 +282,7 @@ def run_ours(args, world, rank, local, dist):
     def trace_bwd():
         sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, g_adj, max_ks=cfg["ks"],
                                  max_n=cfg["n_grid"], norm=sd.SD_NORM_PER_RAY, grad_req=greq,
-                                 swept=swept)
+                                 swept=swept, mask=mask)
 
     fp32 = measure_fp32_peak(sd, dev, local)
 
@@ -293,9 +298,11 @@ def run_ours(args, world, rank, local, dist):
     swept_rays = int(swept[:, 0].sum().item())
     swept_slots = int(swept[:, 1].sum().item())
     # the adjoint traces again only the requests whose gradient patch is
-    # not all zero (the others have an exactly zero gradient)
+    # not all zero (the others have an exactly zero gradient), and of those
+    # only the rays the landing mask marks
     live = g_adj.view(n_req, -1).ne(0).any(dim=1)
-    retraced_rays = int(stats[live, 0].sum().item())
+    live_rays = int(stats[live, 0].sum().item())
+    retraced_rays = mask_rays(mask, stats[:, 0], live, n_req)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     if dist:
@@ -418,6 +425,7 @@ def run_ours(args, world, rank, local, dist):
                      "fp32_probe": fp32,
                      "derived_peak_at_max_clock": round(derived_tflops, 2),
                      "flops_per_ray": fpr, "adjoint_flops_per_ray": afr,
+                     "adjoint_live_request_rays": live_rays,
                      "adjoint_retraced_rays": retraced_rays,
                      "adjoint_swept_rays": swept_rays, "adjoint_swept_slots": swept_slots,
                      "adjoint_flops": adj_flops,
@@ -448,6 +456,17 @@ def run_ours(args, world, rank, local, dist):
         line["cpu_baseline"] = cpu_baseline(cfg, reqs, aif_np, depth_np, args.cpu_seconds)
     lens.free()
     return line
+
+
+def mask_rays(mask, launched, live, n_req):
+    """Set bits of a landing mask over the requests in `live`, counting only
+    each request's words that hold its launched rays."""
+    words = mask.numel() // max(n_req, 1)
+    m = mask[:n_req * words].view(n_req, words).cpu().numpy().view(np.uint32)
+    nw = (launched.cpu().numpy() + 31) // 32
+    keep = np.arange(words)[None, :] < nw[:, None]
+    keep &= live.cpu().numpy()[:, None]
+    return int(np.unpackbits(np.where(keep, m, 0).view(np.uint8)).sum())
 
 
 def measure_fp32_peak(sd, dev, index, reps=40):

@@ -167,8 +167,30 @@ typedef struct sd_trace_opts {
   int32_t max_ks;       /* required: largest ks of any request (odd, <= 127);
                            sizes the shared-memory patch */
   int32_t max_n_grid;   /* largest N of any request (0 = 512, <= 2048) */
-  int32_t reserved[2];
+  uint32_t* land_mask;  /* device, nullable: one bit per ray (see
+                           sd_dp_psf_trace_mask_bytes).  sd_dp_psf_trace
+                           writes it; sd_dp_psf_trace_backward reads it and
+                           traces again only the rays whose bit is set.  The
+                           other trace entry points ignore it. */
 } sd_trace_opts;
+
+/*
+ * Bytes of a landing mask for n_req requests with pupil grids up to
+ * max_n_grid (0 = 512): request r owns words [r * W, (r + 1) * W), W =
+ * ceil(max_n_grid^2 / 32); bit k % 32 of its word k / 32 is ray k of the
+ * request (the trace's ray order: in-pupil samples in raster order).
+ * sd_dp_psf_trace sets the bit of every ray that reaches the sensor, lands
+ * on the L or R sub-pixel (Eq. 1/2) and has its nearest pixel centre at most
+ * one pixel outside the request's ks x ks patch (the bilinear footprint of a
+ * ray can touch the patch only then), whatever the binning mode, and clears
+ * the others; words past a request's ray count are left as they are.  The
+ * adjoint takes the same decisions with the same FP32 code, so a ray with a
+ * clear bit has no splat gradient there.  A mask holds for the lenses,
+ * parameters, sensor and requests it was traced with: an adjoint given a
+ * mask takes every ray whose bit is clear to have a zero splat gradient.
+ * SD_ERR_ARG for n_req < 0, a null bytes or max_n_grid outside [0, 2048].
+ */
+sd_status sd_dp_psf_trace_mask_bytes(int n_req, int max_n_grid, size_t* bytes);
 
 /* Per-request statistics (int64 each, device, nullable). */
 enum { SD_STAT_LAUNCHED = 0, SD_STAT_REACHED, SD_STAT_L, SD_STAT_R,
@@ -231,6 +253,11 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
  * contribution) and the thread slots that ran the sweep (32 per warp in
  * which any ray has a contribution); the first is the adjoint's algorithmic
  * work, the second what the hardware executed.
+ * With opts->land_mask (written by sd_dp_psf_trace of the same lenses,
+ * sensor, requests and max_n_grid) only the rays whose bit is set are traced
+ * again, taken in ray order from a queue that keeps every warp but the
+ * request's last full: the gradient equals the maskless one up to the order
+ * of FP32 additions (deterministic either way).
  */
 sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
                                    const sd_dp_sensor* sensor,

@@ -8,7 +8,7 @@ from .api import (SD_FIELD_QUADRANT, SD_FIELD_RADIAL, BankLayout, BatchedTrace, 
                   dp_psf_trace_backward, dp_render, dp_render_backward, dp_render_map, dp_render_tc,
                   f_number_table, make_requests, render_backward_workspace, trace_hits,
                   PsfMLP, mlp_psf_map, MLP_SHAPES, dp_render_bank_grad_tc, sync_status,
-                  set_wait_limit, fp32_peak_launch)
+                  set_wait_limit, fp32_peak_launch, land_mask, land_mask_bytes)
 from .bank_io import lens_sha256, load_bank, save_bank  # noqa: F401
 from .autograd import (DPRenderFunction, DPTraceFunction, dp_psf_trace_autograd,  # noqa: F401
                        dp_render_autograd)

@@ -44,7 +44,7 @@ class SdTraceOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("norm", ctypes.c_int32),
                 ("out_dtype", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("max_ks", ctypes.c_int32), ("max_n_grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("land_mask", ctypes.c_void_p)]
 
 
 class SdBankLayout(ctypes.Structure):
@@ -69,7 +69,8 @@ assert REQUEST_DTYPE.itemsize == 56
 
 # every exported symbol of include/sdirt.h
 EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_free",
-           "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_psf_trace_batched",
+           "sd_dp_psf_trace", "sd_dp_psf_trace_backward", "sd_dp_psf_trace_mask_bytes",
+           "sd_dp_psf_trace_batched",
            "sd_dp_psf_trace_batched_workspace", "sd_dp_psf_trace_batched_tune",
            "sd_dp_trace_hits", "sd_dp_psf_map",
            "sd_dp_render", "sd_dp_render_map", "sd_dp_render_tc", "sd_dp_render_tc_workspace", "sd_dp_render_backward",
@@ -117,6 +118,7 @@ def lib():
     L.sd_dp_psf_trace.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts), vp, vp, vp]
     L.sd_dp_psf_trace_backward.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
                                            vp, vp, vp, vp, vp]
+    L.sd_dp_psf_trace_mask_bytes.argtypes = [i32, i32, P(ctypes.c_size_t)]
     ll = ctypes.c_longlong
     L.sd_dp_psf_trace_batched_workspace.argtypes = [i32, ll, P(ctypes.c_size_t)]
     L.sd_dp_psf_trace_batched.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),

@@ -115,10 +115,37 @@ def make_requests(reqs, ks_offsets=True, device="cuda"):
     return dev, total, off
 
 
+def land_mask_bytes(n_req, max_n=512):
+    """Bytes of a landing mask (sd_dp_psf_trace_mask_bytes)."""
+    n = ctypes.c_size_t(0)
+    L.check(L.lib().sd_dp_psf_trace_mask_bytes(n_req, max_n, ctypes.byref(n)),
+            "sd_dp_psf_trace_mask_bytes")
+    return n.value
+
+
+def land_mask(n_req, max_n=512, device="cuda"):
+    """An uninitialised landing mask for n_req requests (int32 words): pass
+    it to dp_psf_trace to record which rays land near the patch, then to
+    dp_psf_trace_backward of the same lenses, sensor and requests."""
+    return torch.empty(max(1, land_mask_bytes(n_req, max_n) // 4), dtype=torch.int32,
+                       device=device)
+
+
+def _mask_ptr(mask):
+    if mask is None:
+        return None
+    _need_cuda(mask)
+    if mask.dtype != torch.int32:
+        raise ValueError("the landing mask must be an int32 tensor (land_mask())")
+    return mask.data_ptr()
+
+
 def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=512,
                  mode=L.SD_BIN_HARD, norm=L.SD_NORM_JOINT, dtype=torch.float32,
-                 out=None, stats=None, newton_iters=0):
-    """Traces the requests (device array from make_requests) into a flat bank."""
+                 out=None, stats=None, newton_iters=0, mask=None):
+    """Traces the requests (device array from make_requests) into a flat bank.
+    mask (from land_mask(n_req, max_n)), if given, records for every ray
+    whether it lands within a pixel of its request's patch."""
     lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
     handles = (ctypes.c_void_p * len(lenses))(*[l.handle.value for l in lenses])
     if out is None:
@@ -126,7 +153,10 @@ def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=
     if stats is None:
         stats = torch.zeros((n_req, L.SD_N_STATS), dtype=torch.int64, device=req_dev.device)
     _need_cuda(req_dev, out, stats)
-    opts = L.SdTraceOpts(mode, norm, _DT[out.dtype], newton_iters, max_ks, max_n)
+    if mask is not None and mask.numel() * 4 < land_mask_bytes(n_req, max_n):
+        raise ValueError("the landing mask is too small for these requests")
+    opts = L.SdTraceOpts(mode, norm, _DT[out.dtype], newton_iters, max_ks, max_n,
+                         _mask_ptr(mask))
     sen = sensor.c()
     L.check(L.lib().sd_dp_psf_trace(handles, len(lenses), ctypes.byref(sen), _ptr(req_dev),
                                     n_req, ctypes.byref(opts), _ptr(out), _ptr(stats),
@@ -136,12 +166,14 @@ def dp_psf_trace(lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=
 
 def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, max_ks,
                           max_n=512, norm=L.SD_NORM_PER_RAY, grad_req=None, newton_iters=0,
-                          swept=None):
+                          swept=None, mask=None):
     """Adjoint of the bilinear trace: per-request and per-lens gradients of
     <grad_out, PSF> with respect to the lens parameters, as
     (grad_req (n_req, 32, 8), grad_lens (n_lenses, 32, 8)).  swept, an
     optional (n_req, 2) int64 CUDA tensor, receives per request the rays with
-    a non-zero splat gradient and the thread slots that ran the sweep."""
+    a non-zero splat gradient and the thread slots that ran the sweep.  mask,
+    a landing mask written by dp_psf_trace of the same lenses, sensor and
+    requests (same max_n), restricts the retrace to the rays it marks."""
     lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
     handles = (ctypes.c_void_p * len(lenses))(*[l.handle.value for l in lenses])
     dev = req_dev.device
@@ -153,7 +185,10 @@ def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, ma
         _need_cuda(swept)
         if swept.dtype != torch.int64 or swept.numel() < 2 * n_req:
             raise ValueError("swept must be an int64 tensor of n_req x 2")
-    opts = L.SdTraceOpts(L.SD_BIN_BILINEAR, norm, L.SD_F32, newton_iters, max_ks, max_n)
+    if mask is not None and mask.numel() * 4 < land_mask_bytes(n_req, max_n):
+        raise ValueError("the landing mask is too small for these requests")
+    opts = L.SdTraceOpts(L.SD_BIN_BILINEAR, norm, L.SD_F32, newton_iters, max_ks, max_n,
+                         _mask_ptr(mask))
     sen = sensor.c()
     L.check(L.lib().sd_dp_psf_trace_backward(handles, len(lenses), ctypes.byref(sen),
                                              _ptr(req_dev), n_req, ctypes.byref(opts),

@@ -375,6 +375,9 @@ struct TraceParams {
   int max_ks;
   void* out;
   long long* stats;
+  // landing mask (nullable): one bit per ray, mask_words words per request
+  unsigned* land_mask;
+  int mask_words;
   // hit dump (test path)
   float* rec;
   int max_rays;
@@ -778,6 +781,9 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
     int key = -1;
     float fx = 0.f, fy = 0.f;
     int side = 2;
+    // lands on the L or R sub-pixel with its nearest pixel centre at most one
+    // pixel outside the patch (the adjoint takes the same decisions)
+    bool land = false;
     if (k < total) {
       float x, y, z, dx, dy, dz;
       row = advance_row(prefix, k, row);
@@ -790,6 +796,7 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
         float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
         side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
         bool inpatch = af >= 0.f && af < (float)ks && bf >= 0.f && bf < (float)ks;
+        land = side != 2 && af >= -1.f && af <= (float)ks && bf >= -1.f && bf <= (float)ks;
         if (!inpatch) {
           ++c_clip;
           if (MODE == 0) side = 2;  // nothing to deposit
@@ -804,6 +811,13 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
       } else {
         ++c_other;
       }
+    }
+    if (P.land_mask) {
+      // one word per warp: rays base + 32 w .. base + 32 w + 31
+      const unsigned bits = __ballot_sync(0xffffffffu, land);
+      const int k0 = base + (threadIdx.x & ~31);
+      if (lane == 0 && k0 < total)
+        P.land_mask[(size_t)r * P.mask_words + (k0 >> 5)] = bits;
     }
     if (MODE == 0) {
       // warp-aggregated shared-memory increment of the landing bin
@@ -957,8 +971,12 @@ sd_status fill_params(TraceParams& P, const sd_lens* const* lenses, int n_lenses
   P.norm = opts ? opts->norm : SD_NORM_JOINT;
   if (P.norm < 0 || P.norm > 3) return SD_ERR_ARG;
   P.newton_max = (opts && opts->newton_iters > 0) ? opts->newton_iters : 12;
+  P.land_mask = opts ? opts->land_mask : nullptr;
   return SD_OK;
 }
+
+// words of a request's landing mask for pupil grids up to max_n
+inline int mask_words(int max_n) { return (int)(((long long)max_n * max_n + 31) / 32); }
 
 }  // namespace sd
 
@@ -988,6 +1006,7 @@ sd_status sd_dp_psf_trace(const sd_lens* const* lenses, int n_lenses,
   P.max_ks = max_ks;
   P.out = out;
   P.stats = reinterpret_cast<long long*>(stats);
+  P.mask_words = mask_words(max_n);
   size_t smem = trace_smem_bytes(max_n, max_ks);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int threads = 256;
@@ -1029,6 +1048,7 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
   const sd_lens* ls[1] = {lens};
   sd_status st = fill_params(P, ls, 1, sensor, opts);
   if (st != SD_OK) return st;
+  P.land_mask = nullptr;  // the map path writes no landing mask
   P.req = nullptr;
   P.n_req = H * W;
   P.map_depth = depth_m;
@@ -1351,8 +1371,58 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   const int n = ctx.N ? c_lens[ctx.slot].n : 0;
   AdjState sv;
   int row = 0;
-  for (int base = 0; base < total; base += NT) {
-    const int k = base + threadIdx.x;
+  // With a landing mask the rays whose bit is set are taken in ray order
+  // from a ring queue that warp 0 refills 32 mask words at a time, NT per
+  // round, so that every warp but the request's last is full; without one,
+  // every ray (NT consecutive rays per round).
+  constexpr int QCAP = 2048;  // > NT - 1 + 32 * 32: a refill never wraps onto live entries
+  __shared__ int s_q[QCAP];
+  __shared__ int s_head, s_qn, s_wpos;
+  const unsigned* mw = P.land_mask ? P.land_mask + (size_t)r * P.mask_words : nullptr;
+  const int nwords = (total + 31) >> 5;
+  if (threadIdx.x == 0) s_head = s_qn = s_wpos = 0;
+  int take = 0;  // rays handed out in the previous round
+  for (int base = 0;; base += NT) {
+    int k;
+    if (mw) {
+      __syncthreads();  // every thread has its previous ray
+      if (warp == 0) {
+        int head = (s_head + take) & (QCAP - 1), qn = s_qn - take, wpos = s_wpos;
+        while (qn < NT && wpos < nwords) {
+          const int wi = wpos + lane;
+          unsigned m = wi < nwords ? mw[wi] : 0u;
+          const int c = __popc(m);
+          int pre = c;  // inclusive prefix of the counts over the lanes
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+          }
+          const int all = __shfl_sync(0xffffffffu, pre, 31);
+          int pos = head + qn + pre - c;
+          while (m) {
+            s_q[pos & (QCAP - 1)] = (wi << 5) + __ffs(m) - 1;
+            m &= m - 1;
+            ++pos;
+          }
+          qn += all;
+          wpos += 32;
+        }
+        if (lane == 0) {
+          s_head = head;
+          s_qn = qn;
+          s_wpos = wpos;
+        }
+      }
+      __syncthreads();
+      const int qn = s_qn;
+      if (qn == 0) break;
+      take = min(qn, NT);
+      k = (int)threadIdx.x < take ? s_q[(s_head + threadIdx.x) & (QCAP - 1)] : total;
+    } else {
+      if (base >= total) break;
+      k = base + threadIdx.x;
+    }
     float x, y, z, dx = 0.f, dy = 0.f, dz = 1.f, gfx = 0.f, gfy = 0.f;
     bool need = false;
     if (k < total) {
@@ -1441,6 +1511,13 @@ __global__ void __launch_bounds__(1024) grad_lens_reduce(const float* __restrict
 
 }  // namespace sd
 
+extern "C" sd_status sd_dp_psf_trace_mask_bytes(int n_req, int max_n_grid, size_t* bytes) {
+  if (!bytes || n_req < 0 || max_n_grid < 0 || max_n_grid > 2048) return SD_ERR_ARG;
+  const int max_n = max_n_grid > 0 ? max_n_grid : 512;
+  *bytes = (size_t)n_req * sd::mask_words(max_n) * 4;
+  return SD_OK;
+}
+
 extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int n_lenses,
                                               const sd_dp_sensor* sensor,
                                               const sd_psf_request* req, int n_req,
@@ -1472,6 +1549,7 @@ extern "C" sd_status sd_dp_psf_trace_backward(const sd_lens* const* lenses, int 
   P.n_req = n_req;
   P.max_n = max_n;
   P.max_ks = max_ks;
+  P.mask_words = mask_words(max_n);
   size_t smem = table_bytes(max_n) + (size_t)2 * max_ks * max_ks * 4;
   // Surface count read at run time; the forward keeps one t per surface (a
   // local array) and the reverse sweep rebuilds the rest.  Variants with the

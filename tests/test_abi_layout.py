@@ -178,3 +178,22 @@ def test_batched_workspace(lib):
     assert lib.sd_dp_psf_trace_batched_workspace(100, 2 * 65 * 65 * 100, ctypes.byref(n)) == L.SD_OK
     # a 32-bit count per output element of every request
     assert n.value >= 4 * 2 * 65 * 65 * 100
+
+
+def test_landing_mask_bytes(lib):
+    # one bit per pupil sample of the largest grid, whole 32-bit words per
+    # request (0 = the 512 default)
+    n = ctypes.c_size_t(0)
+    assert lib.sd_dp_psf_trace_mask_bytes(3, 96, ctypes.byref(n)) == L.SD_OK
+    assert n.value == 3 * 288 * 4
+    assert lib.sd_dp_psf_trace_mask_bytes(2, 0, ctypes.byref(n)) == L.SD_OK
+    assert n.value == 2 * 512 * 512 // 8
+    assert lib.sd_dp_psf_trace_mask_bytes(5, 7, ctypes.byref(n)) == L.SD_OK
+    assert n.value == 5 * 2 * 4
+    assert lib.sd_dp_psf_trace_mask_bytes(0, 64, ctypes.byref(n)) == L.SD_OK and n.value == 0
+    assert lib.sd_dp_psf_trace_mask_bytes(-1, 64, ctypes.byref(n)) == L.SD_ERR_ARG
+    assert lib.sd_dp_psf_trace_mask_bytes(1, 4096, ctypes.byref(n)) == L.SD_ERR_ARG
+    assert lib.sd_dp_psf_trace_mask_bytes(1, 64, None) == L.SD_ERR_ARG
+    # the options struct keeps its size: the mask pointer replaced two
+    # reserved words
+    assert ctypes.sizeof(L.SdTraceOpts) == 32

@@ -133,3 +133,65 @@ def test_adjoint_matches_oracle(sdlib, n_grid):
     assert np.linalg.norm(gs - rs) <= 1e-2 * np.linalg.norm(rs)
     assert np.abs(gs - rs).max() <= 2e-2 * np.abs(rs).max()
     lens.free()
+
+
+def test_adjoint_with_landing_mask(sdlib):
+    """The landing mask written by the forward trace (hard binning) marks the
+    rays that reach the sensor on the L or R sub-pixel with their landing
+    pixel at most one pixel outside the patch (the oracle's landings:
+    mismatches only on rays within 1e-5 mm of a decision boundary); the
+    adjoint restricted to the marked
+    rays gives the unmasked adjoint's per-request gradients up to the order
+    of FP32 additions, the same contributing rays, fewer swept thread slots,
+    and repeats bitwise."""
+    sd = sdlib
+    cfg = W.config_full_forward()
+    tab, ps, focus = cfg["lens"], cfg["pitch_mm"], cfg["focus_mm"]
+    N = 96
+    reqs = np.concatenate([
+        W.bank_grid([0.0, 0.9, 1.4], [400.0, 2500.0], [W.LAMBDA_D], N, 21),
+        W.bank_grid([0.5, 1.4], [700.0], [W.LAMBDA_F], N, 65)])
+    n = len(reqs)
+    S = oracle_sensor(ps)
+    lens = sd.Lens(tab, focus)
+    sensor = sd.DPSensor(ps)
+    dev, total, off = sd.make_requests(reqs)
+    mask = sd.land_mask(n, N)
+    mask.fill_(-1)  # words past a request's rays are left as they are
+    sd.dp_psf_trace(lens, sensor, dev, n, total, max_ks=65, max_n=N, mask=mask)
+    torch.cuda.synchronize()
+    words = (N * N + 31) // 32
+    m = mask.cpu().numpy().view(np.uint32).reshape(n, words)
+    for r in range(n):
+        h = O.trace_hits(tab, focus, reqs[r], S)
+        ks = int(reqs[r]["ks"])
+        # oracle sides: 0 = L, 1 = R, 2 = neither sub-pixel
+        want = (h["state"] == O.R_OK) & (h["side"] != 2) & (h["a"] >= -1) & \
+               (h["a"] <= ks) & (h["b"] >= -1) & (h["b"] <= ks)
+        k = np.arange(len(want))
+        got = ((m[r][k >> 5] >> (k & 31).astype(np.uint32)) & 1).astype(bool)
+        bad = got != want
+        # FP32 and FP64 decide differently only next to a boundary, and few
+        # rays lie there
+        assert np.all(h["margin"][bad] < 1e-5), (r, int(bad.sum()))
+        assert bad.sum() <= 3 + 0.002 * len(want)
+        assert 0 < got.sum() < len(want)
+    rng = np.random.default_rng(5)
+    g = torch.tensor(rng.standard_normal(total), dtype=torch.float32, device="cuda")
+    sw0 = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    sw1 = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    g0, _ = sd.dp_psf_trace_backward(lens, sensor, dev, n, g, max_ks=65, max_n=N, swept=sw0)
+    g1, _ = sd.dp_psf_trace_backward(lens, sensor, dev, n, g, max_ks=65, max_n=N, swept=sw1,
+                                     mask=mask)
+    g2, _ = sd.dp_psf_trace_backward(lens, sensor, dev, n, g, max_ks=65, max_n=N, mask=mask)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    a0, a1 = g0.cpu().numpy().reshape(n, -1), g1.cpu().numpy().reshape(n, -1)
+    for r in range(n):
+        assert np.abs(a1[r] - a0[r]).max() <= 1e-4 * np.abs(a0[r]).max()
+    s0, s1 = sw0.cpu().numpy(), sw1.cpu().numpy()
+    assert np.array_equal(s0[:, 0], s1[:, 0])
+    assert s1[:, 1].sum() < s0[:, 1].sum()
+    print("swept slots without / with the mask:", s0[:, 1].sum(), s1[:, 1].sum(),
+          "rays with a contribution:", s0[:, 0].sum())
+    lens.free()
