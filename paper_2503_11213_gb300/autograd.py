@@ -10,7 +10,7 @@ import torch
 
 from . import _lib as L
 from .api import BankLayout, DPSensor, Lens, dp_psf_trace, dp_psf_trace_backward, dp_render, \
-    dp_render_backward
+    dp_render_backward, land_mask
 
 
 class DPRenderFunction(torch.autograd.Function):
@@ -66,8 +66,12 @@ class DPTraceFunction(torch.autograd.Function):
         vals = theta.detach().to("cpu", torch.float64).tolist()
         for pid, v in zip(pids, vals):
             lens.set_param(int(pid), float(v))
+        # the rays that land near their patch, so that the backward traces
+        # only those again (the lens stays as set here until then)
+        mask = land_mask(n_req, max_n, device=req_dev.device)
         out, _ = dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=max_ks, max_n=max_n,
-                              mode=L.SD_BIN_BILINEAR, norm=norm)
+                              mode=L.SD_BIN_BILINEAR, norm=norm, mask=mask)
+        ctx.mask = mask
         ctx.lens, ctx.pids, ctx.sensor = lens, list(pids), sensor
         ctx.req_dev, ctx.n_req, ctx.max_ks, ctx.max_n, ctx.norm = req_dev, n_req, max_ks, max_n, norm
         ctx.theta_meta = (theta.dtype, theta.device)
@@ -77,7 +81,8 @@ class DPTraceFunction(torch.autograd.Function):
     def backward(ctx, grad_out):
         g = grad_out.to(torch.float32).contiguous()
         _, grad_lens = dp_psf_trace_backward(ctx.lens, ctx.sensor, ctx.req_dev, ctx.n_req, g,
-                                             max_ks=ctx.max_ks, max_n=ctx.max_n, norm=ctx.norm)
+                                             max_ks=ctx.max_ks, max_n=ctx.max_n, norm=ctx.norm,
+                                             mask=ctx.mask)
         flat = grad_lens[0].reshape(-1)
         idx = torch.tensor(ctx.pids, dtype=torch.long, device=flat.device)
         dtype, device = ctx.theta_meta
