@@ -994,29 +994,36 @@ def cpu_threads():
 
 
 def cpu_baseline(cfg, reqs, aif_np, depth_np, budget_s):
-    """The FP64 oracle, as it stands, on a bounded sample of the same step:
-    every k-th bank request (threads over requests) and a set of rendered
-    pixels; each part scaled linearly to the full step."""
+    """The FP64 oracle, as it stands, on a bounded sample of each phase of
+    the same step, each phase's time scaled linearly to the full step:
+    the trace (every k-th bank request, threads over requests), the render
+    (a set of pixels, threads over pixels), the render backward (an image
+    crop, the oracle's single-threaded adjoint) and the adjoint trace
+    (evenly spaced live requests, threads over requests, forward-mode dual
+    numbers for the 22 lens parameters of the differentiation study: its
+    cost does not depend on the gradient's values)."""
     import oracle as O
     cores = cpu_threads()
     ps = cfg["pitch_mm"]
     S = dict(ps=ps, h=W.DP_H * ps, f=W.DP_F * ps, w=W.DP_W * ps, r=W.DP_R * ps)
     n_req = len(reqs)
-    # calibrate the sample on one request, then fill about budget/2 seconds
+    lens, focus = cfg["lens"], cfg["focus_mm"]
+    # trace: calibrate on one request, then fill about 0.3 of the budget
     t0 = time.perf_counter()
-    O.psf_bank(cfg["lens"], cfg["focus_mm"], reqs[:1], S, n_threads=1)
+    O.psf_bank(lens, focus, reqs[:1], S, n_threads=1)
     per_req = time.perf_counter() - t0
-    n_s = int(max(cores, min(n_req, round(0.5 * budget_s * cores / max(per_req, 1e-6)))))
+    n_s = int(max(cores, min(n_req, round(0.3 * budget_s * cores / max(per_req, 1e-6)))))
     n_s = max(cores, (n_s // cores) * cores)
     idx = np.linspace(0, n_req - 1, n_s).astype(int)
     t0 = time.perf_counter()
-    _, st = O.psf_bank(cfg["lens"], cfg["focus_mm"], reqs[idx], S, n_threads=cores)
+    _, st = O.psf_bank(lens, focus, reqs[idx], S, n_threads=cores)
     t_trace = (time.perf_counter() - t0) * n_req / n_s
     rays = int(st[:, 0].sum()) * n_req / n_s
-    # render sample
+    # render: a set of pixels
     cfgd = cfg["depths_mm"] / 1000.0
     rng = np.random.default_rng(0)
-    bank = np.full((32, 32, 3, 2, cfg["ks"], cfg["ks"]), 1.0 / (2 * cfg["ks"] ** 2))
+    nf, nz = len(cfg["field_h_mm"]), len(cfgd)
+    bank = np.full((nf, nz, 3, 2, cfg["ks"], cfg["ks"]), 1.0 / (2 * cfg["ks"] ** 2))
     H, Wd = aif_np.shape[2:]
     npx = 64 * cores
     pix = np.stack([np.zeros(npx, int), rng.integers(0, H, npx), rng.integers(0, Wd, npx)], 1)
@@ -1024,14 +1031,60 @@ def cpu_baseline(cfg, reqs, aif_np, depth_np, budget_s):
     O.render_bank_pixels(aif_np, depth_np, bank, cfg["field_h_mm"], cfgd, ps, pix,
                          n_threads=cores)
     t_render = (time.perf_counter() - t0) * (H * Wd) / npx
-    step_s = t_trace + t_render
+    # render backward: an image crop, side calibrated on 8 x 8 pixels to
+    # about 0.2 of the budget
+    def bwd_crop(side):
+        y0, x0 = (H - side) // 2, (Wd - side) // 2
+        a = aif_np[:, :, y0:y0 + side, x0:x0 + side]
+        g = rng.standard_normal((1, 6, side, side))
+        d = depth_np[:, y0:y0 + side, x0:x0 + side]
+        t0 = time.perf_counter()
+        O.render_bank_bwd(g, a, d, bank, cfg["field_h_mm"], cfgd, ps)
+        return time.perf_counter() - t0
+    t8 = bwd_crop(8)
+    side = int(np.clip(8 * np.sqrt(0.2 * budget_s / max(t8, 1e-6)), 8, min(H, Wd)))
+    t_bwd = bwd_crop(side) * (H * Wd) / (side * side)
+    # adjoint: the requests whose slice some pixel uses (the others have a
+    # zero gradient patch), sampled evenly, traced at 64 x 64 pupil samples
+    # and scaled by the rays the step's requests launch
+    sel = O.render_select(depth_np[0], cfg["field_h_mm"], cfgd, ps)
+    f, z0, t = sel[..., 0].astype(int), sel[..., 1].astype(int), sel[..., 3]
+    used = np.zeros(nf * nz, bool)
+    used[(f * nz + z0)[t < 1]] = True
+    up = (t > 0) & (z0 + 1 < nz)
+    used[(f * nz + z0 + 1)[up]] = True
+    nl = n_req // (nf * nz)
+    live = np.flatnonzero(np.repeat(used, nl))
+    pids = [O.param_id(s_, "c") for s_ in range(1, 7)] + [O.param_id(1, "k"), O.param_id(6, "k")]
+    pids += [O.param_id(s_, a_) for s_ in (1, 6) for a_ in ("a4", "a6", "a8", "a10")]
+    pids += [O.param_id(s_, "t") for s_ in range(1, 7)]
+    small = reqs.copy()
+    small["n_grid"] = 64
+    G1 = [rng.standard_normal((2, cfg["ks"], cfg["ks"]))]
+    t0 = time.perf_counter()
+    O.trace_grad(lens, focus, small[live[:1]], S, G1, pids, n_threads=1)
+    per_adj = time.perf_counter() - t0
+    n_a = int(max(cores, min(len(live), round(0.2 * budget_s * cores / max(per_adj, 1e-6)))))
+    n_a = max(1, min(len(live), (n_a // cores) * cores or cores))
+    aidx = live[np.linspace(0, len(live) - 1, n_a).astype(int)]
+    G = [rng.standard_normal((2, cfg["ks"], cfg["ks"])) for _ in range(n_a)]
+    _, st_small = O.psf_bank(lens, focus, small[aidx[:1]], S, n_threads=1)
+    t0 = time.perf_counter()
+    O.trace_grad(lens, focus, small[aidx], S, G, pids, n_threads=cores)
+    ray_scale = (int(st[:, 0].sum()) / n_s) / max(1, int(st_small[0, 0]))
+    t_adj = (time.perf_counter() - t0) * len(live) / n_a * ray_scale
+    step_s = t_trace + t_render + t_bwd + t_adj
     return {"value": round(rays / step_s / 1e9, 6), "unit": "G rays/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"{n_s} of {n_req} bank requests (evenly spaced) + {npx} of {H * Wd} "
-                      f"rendered pixels, FP64 C++ oracle on {cores} threads, each part "
-                      f"scaled linearly to the full step",
+            "sample": f"trace: {n_s} of {n_req} bank requests (evenly spaced); render: {npx} "
+                      f"of {H * Wd} pixels; render backward: a {side}x{side} crop (the "
+                      f"oracle's adjoint is single-threaded); adjoint: {n_a} of the "
+                      f"{len(live)} requests with a non-zero gradient patch at 64x64 pupil "
+                      f"samples, scaled by launched rays (x{ray_scale:.1f}); FP64 C++ oracle "
+                      f"on {cores} threads, each phase scaled linearly to the full step",
             "step_s_extrapolated": round(step_s, 3),
-            "trace_s": round(t_trace, 3), "render_s": round(t_render, 3)}
+            "trace_s": round(t_trace, 3), "render_s": round(t_render, 3),
+            "render_bwd_s": round(t_bwd, 3), "adjoint_s": round(t_adj, 3)}
 
 
 def run_reference(args, world, rank):
