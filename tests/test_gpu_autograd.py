@@ -110,12 +110,14 @@ def test_trace_autograd_matches_adjoint_and_descends(sdlib):
     l0, g, psf0 = loss_at(theta0, grad=True)
     # the forward is the plain bilinear, per-ray normalised trace (its FP32
     # shared-memory splat adds in arbitrary order: equal to rounding)
+    mask = sd.land_mask(len(reqs), 64)
     ref_psf, _ = sd.dp_psf_trace(lens, sen, dev, len(reqs), total, max_ks=65, max_n=64,
-                                 mode=sd.SD_BIN_BILINEAR, norm=sd.SD_NORM_PER_RAY)
+                                 mode=sd.SD_BIN_BILINEAR, norm=sd.SD_NORM_PER_RAY, mask=mask)
     torch.testing.assert_close(psf0, ref_psf, rtol=1e-5, atol=1e-9)
-    # autograd's gradient is the adjoint trace of dLoss/dPSF = 2 (PSF - T)
+    # autograd's gradient is the adjoint trace of dLoss/dPSF = 2 (PSF - T),
+    # restricted like autograd's to the rays the forward's landing mask marks
     _, glens = sd.dp_psf_trace_backward(lens, sen, dev, len(reqs), 2.0 * (psf0 - T), max_ks=65,
-                                        max_n=64)
+                                        max_n=64, mask=mask)
     direct = glens[0].reshape(-1).cpu().numpy()[pids].astype(np.float64)
     np.testing.assert_allclose(g, direct, rtol=1e-6, atol=1e-12 * np.abs(direct).max())
     # a step in natural units whose predicted decrease is 1 % of the loss
