@@ -631,6 +631,20 @@ sd_status sd_set_wait_limit(long long polls);
  */
 sd_status sd_dev_fp32_peak(float* sink, int blocks, int iters, void* stream);
 
+/*
+ * Bounds checks of a checked build (the library compiled with -DSD_CHECKED;
+ * the paper has no counterpart).  There, the kernels test the indices they
+ * compute before the accesses that use them (image and buffer positions,
+ * workspace slabs, shared-memory tables, output elements) and skip an access
+ * whose index is out of range, recording it.  Synchronises the device, then
+ * returns the first failing site (translation unit * 100000 + source line;
+ * 0 if none), its index and bound (low 32 bits; index and bound nullable)
+ * and the number of failed checks since the last call, and clears the
+ * records.  SD_ERR_UNSUPPORTED in the normal build, whose checks compile
+ * away; SD_ERR_ARG for a null site or count.
+ */
+sd_status sd_check_status(int32_t* site, int32_t* index, int32_t* bound, int64_t* count);
+
 /* ------------------------------------------------------------------------
  * Library information
  * ---------------------------------------------------------------------- */

@@ -5,11 +5,16 @@ Loading fails loudly when libsdirt.so is missing: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import numpy as np
 
-_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libsdirt.so"
+# the checked build (bounds-checked kernels, sd_check_status) when the
+# environment sets SDIRT_CHECKED=1
+_LIB_PATH = Path(__file__).resolve().parent / (
+    "_build_checked/libsdirt_checked.so" if os.environ.get("SDIRT_CHECKED") == "1"
+    else "_build/libsdirt.so")
 
 (SD_OK, SD_ERR_ARG, SD_ERR_LENS, SD_ERR_UNSUPPORTED, SD_ERR_CUDA, SD_ERR_CAPACITY,
  SD_ERR_TIMEOUT) = range(7)
@@ -78,7 +83,8 @@ EXPORTS = ("sd_lens_load", "sd_lens_paraxial", "sd_lens_set_param", "sd_lens_fre
            "sd_mlp_blob_bytes", "sd_mlp_pack", "sd_mlp_psf_map",
            "sd_dp_render_bank_grad_tc", "sd_dp_render_bank_grad_tc_workspace",
            "sd_dev_math_check", "sd_dev_tc_check", "sd_status_string", "sd_last_cuda_error",
-           "sd_version", "sd_sync_status", "sd_set_wait_limit", "sd_dev_fp32_peak")
+           "sd_version", "sd_sync_status", "sd_set_wait_limit", "sd_dev_fp32_peak",
+           "sd_check_status")
 
 _lib = None
 
@@ -119,6 +125,8 @@ def lib():
     L.sd_dp_psf_trace_backward.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),
                                            vp, vp, vp, vp, vp]
     L.sd_dp_psf_trace_mask_bytes.argtypes = [i32, i32, P(ctypes.c_size_t)]
+    L.sd_check_status.argtypes = [P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+                                  P(ctypes.c_int64)]
     ll = ctypes.c_longlong
     L.sd_dp_psf_trace_batched_workspace.argtypes = [i32, ll, P(ctypes.c_size_t)]
     L.sd_dp_psf_trace_batched.argtypes = [P(vp), i32, P(SdSensor), vp, i32, P(SdTraceOpts),

@@ -115,6 +115,19 @@ def make_requests(reqs, ks_offsets=True, device="cuda"):
     return dev, total, off
 
 
+def check_status():
+    """Bounds checks of the checked build (SDIRT_CHECKED=1): synchronises the
+    device, then returns and clears (site, index, bound, count): the first
+    failing check's site (translation unit * 100000 + source line; 0 if
+    none), its index and bound, and the number of failed checks.  Raises
+    SdError (SD_ERR_UNSUPPORTED) in the normal build."""
+    site, index, bound = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    count = ctypes.c_int64(0)
+    L.check(L.lib().sd_check_status(ctypes.byref(site), ctypes.byref(index), ctypes.byref(bound),
+                                    ctypes.byref(count)), "sd_check_status")
+    return site.value, index.value, bound.value, count.value
+
+
 def land_mask_bytes(n_req, max_n=512):
     """Bytes of a landing mask (sd_dp_psf_trace_mask_bytes)."""
     n = ctypes.c_size_t(0)

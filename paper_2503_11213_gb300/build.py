@@ -2,6 +2,10 @@
 
 The translation units are compiled in parallel into paper_2503_11213_gb300/_build
 and linked against the shared CUDA runtime (the one PyTorch also loads).
+build(checked=True) builds libsdirt_checked.so in _build_checked with
+-DSD_CHECKED: the kernels test the indices they compute before using them
+and record failures (sd_check_status); the binding loads it when the
+environment sets SDIRT_CHECKED=1.
 """
 from __future__ import annotations
 
@@ -14,6 +18,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libsdirt.so"
+BUILD_CHECKED = PKG / "_build_checked"
+LIB_CHECKED = BUILD_CHECKED / "libsdirt_checked.so"
 SOURCES = ["lens_trace.cu", "render.cu", "render_bwd.cu", "render_map.cu", "render_tc.cu",
            "mlp.cu", "tune.cu", "abi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -27,27 +33,28 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the sdirt CUDA library cannot be built")
 
 
-def _stale() -> bool:
-    if not LIB.exists():
+def _stale(lib: Path) -> bool:
+    if not lib.exists():
         return True
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) + \
         [PKG.parent / "include" / "sdirt.h", Path(__file__)]
     return any(d.exists() and d.stat().st_mtime > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    if not force and not _stale():
-        return LIB
-    BUILD.mkdir(parents=True, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> Path:
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if not force and not _stale(lib):
+        return lib
+    out_dir.mkdir(parents=True, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = BUILD / (Path(src).stem + ".o")
+        obj = out_dir / (Path(src).stem + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *FLAGS, "-I", str(PKG.parent / "include"), "-c", str(CSRC / src),
-               "-o", str(obj)]
+        cmd = [cc, *ARCH, *FLAGS, *(["-DSD_CHECKED"] if checked else []),
+               "-I", str(PKG.parent / "include"), "-c", str(CSRC / src), "-o", str(obj)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -60,16 +67,17 @@ def build(force: bool = False, verbose: bool = False) -> Path:
             print(out.decode(errors="replace"))
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    tmp = lib.with_suffix(f".{os.getpid()}.tmp")
     link = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", str(tmp), *map(str, objs),
             "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

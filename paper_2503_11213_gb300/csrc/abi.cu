@@ -38,6 +38,17 @@ __global__ void __launch_bounds__(256) fp32_peak_kernel(float* __restrict__ sink
 }
 }  // namespace sd
 
+#ifdef SD_CHECKED
+namespace sd {
+sd_status check_take_lens_trace(int32_t*);
+sd_status check_take_render(int32_t*);
+sd_status check_take_render_bwd(int32_t*);
+sd_status check_take_render_map(int32_t*);
+sd_status check_take_render_tc(int32_t*);
+sd_status check_take_mlp(int32_t*);
+}  // namespace sd
+#endif
+
 extern "C" {
 
 const char* sd_status_string(sd_status s) {
@@ -70,6 +81,35 @@ sd_status sd_set_wait_limit(long long polls) {
   sd::g_wait_limit.store(polls < 0 ? -1 : (polls > 0xffffffffll ? 0xffffffffll : polls),
                          std::memory_order_relaxed);
   return SD_OK;
+}
+
+sd_status sd_check_status(int32_t* site, int32_t* index, int32_t* bound, int64_t* count) {
+  if (!site || !count) return SD_ERR_ARG;
+#ifdef SD_CHECKED
+  SD_CUDA_TRY(cudaDeviceSynchronize());
+  sd_status (*const take[])(int32_t*) = {
+      sd::check_take_lens_trace, sd::check_take_render, sd::check_take_render_bwd,
+      sd::check_take_render_map, sd::check_take_render_tc, sd::check_take_mlp};
+  *site = 0;
+  *count = 0;
+  for (auto f : take) {
+    int32_t rec[4];
+    const sd_status st = f(rec);
+    if (st != SD_OK) return st;
+    if (rec[3] == 0) continue;
+    if (*site == 0) {
+      *site = rec[0];
+      if (index) *index = rec[1];
+      if (bound) *bound = rec[2];
+    }
+    *count += rec[3];
+  }
+  return SD_OK;
+#else
+  (void)index;
+  (void)bound;
+  return SD_ERR_UNSUPPORTED;
+#endif
 }
 
 sd_status sd_dev_fp32_peak(float* sink, int blocks, int iters, void* stream) {

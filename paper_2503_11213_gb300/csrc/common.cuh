@@ -30,6 +30,46 @@ void set_cuda_error(cudaError_t e);
 // unless sd_set_wait_limit has set a process-wide override.
 uint32_t wait_limit(uint32_t dflt);
 
+// ---- checked build -------------------------------------------------------
+// Built with -DSD_CHECKED, SD_CHECK(i, n) tests 0 <= i < n before an access
+// whose index the kernel computes; a failing test records, in its
+// translation unit's device record, the first failing site (SD_TU * 100000
+// + line), the index and bound (low 32 bits) and a count, and yields false
+// so that the caller skips the access.  In the normal build it is the
+// constant true.  sd_check_status reads and clears the records.
+#ifndef SD_TU
+#define SD_TU 0
+#endif
+#ifdef SD_CHECKED
+namespace {
+__device__ int g_check[4];  // one per translation unit: site, index, bound, count
+}
+__device__ __forceinline__ bool check_index(int site, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(&g_check[0], 0, site) == 0) {
+    g_check[1] = (int)i;
+    g_check[2] = (int)n;
+  }
+  atomicAdd(&g_check[3], 1);
+  return false;
+}
+#define SD_CHECK(i, n) ::sd::check_index(SD_TU * 100000 + __LINE__, (long long)(i), (long long)(n))
+// Host reader of this translation unit's record (defined once per file by
+// SD_CHECK_TU(name)): copies it to rec[4] and clears it.
+#define SD_CHECK_TU(name)                                                   \
+  namespace sd {                                                            \
+  sd_status check_take_##name(int32_t* rec) {                               \
+    SD_CUDA_TRY(cudaMemcpyFromSymbol(rec, g_check, sizeof(int) * 4));       \
+    const int zero[4] = {0, 0, 0, 0};                                       \
+    SD_CUDA_TRY(cudaMemcpyToSymbol(g_check, zero, sizeof zero));            \
+    return SD_OK;                                                           \
+  }                                                                         \
+  }
+#else
+#define SD_CHECK(i, n) true
+#define SD_CHECK_TU(name)
+#endif
+
 #define SD_CUDA_TRY(expr)                         \
   do {                                            \
     cudaError_t _e = (expr);                      \

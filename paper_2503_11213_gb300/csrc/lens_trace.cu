@@ -15,6 +15,7 @@
 // object point, refractive indices at the request wavelength) runs in FP64
 // in the block prologue; the per-ray trace is FP32.
 
+#define SD_TU 1  // translation unit id of this file's SD_CHECK sites
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -816,13 +817,14 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
       // one word per warp: rays base + 32 w .. base + 32 w + 31
       const unsigned bits = __ballot_sync(0xffffffffu, land);
       const int k0 = base + (threadIdx.x & ~31);
-      if (lane == 0 && k0 < total)
+      if (lane == 0 && k0 < total && SD_CHECK(k0 >> 5, P.mask_words))
         P.land_mask[(size_t)r * P.mask_words + (k0 >> 5)] = bits;
     }
     if (MODE == 0) {
       // warp-aggregated shared-memory increment of the landing bin
       unsigned int m = __match_any_sync(0xffffffffu, key);
-      if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&patch[key], (unsigned)__popc(m));
+      if (key >= 0 && lane == __ffs(m) - 1 && SD_CHECK(key, 2 * ks2))
+        atomicAdd(&patch[key], (unsigned)__popc(m));
     } else if (side < 2) {
       float a0f = floorf(fx), b0f = floorf(fy);
       float wx = fx - a0f, wy = fy - b0f;
@@ -1390,7 +1392,7 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
         int head = (s_head + take) & (QCAP - 1), qn = s_qn - take, wpos = s_wpos;
         while (qn < NT && wpos < nwords) {
           const int wi = wpos + lane;
-          unsigned m = wi < nwords ? mw[wi] : 0u;
+          unsigned m = wi < nwords && SD_CHECK(wi, P.mask_words) ? mw[wi] : 0u;
           const int c = __popc(m);
           int pre = c;  // inclusive prefix of the counts over the lanes
 #pragma unroll
@@ -1937,3 +1939,5 @@ sd_status sd_dp_psf_trace_batched(const sd_lens* const* lenses, int n_lenses,
 }
 
 }  // extern "C"
+
+SD_CHECK_TU(lens_trace)

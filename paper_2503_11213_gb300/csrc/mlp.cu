@@ -27,6 +27,7 @@
 // Every wait is bounded; a wait that gives up sets *status and makes the
 // other waits of the launch give up too.
 
+#define SD_TU 6  // translation unit id of this file's SD_CHECK sites
 #include <cstring>
 #include <vector>
 
@@ -447,3 +448,5 @@ extern "C" sd_status sd_mlp_psf_map(const void* blob, int ks, const float* depth
   mlp_kernel<<<(unsigned)((npix + MM - 1) / MM), MTHREADS, smem, s>>>(P);
   return launch_status();
 }
+
+SD_CHECK_TU(mlp)

@@ -28,6 +28,7 @@
 //      receives at most two non-zero contributions (its two slices), so the
 //      order of the additions cannot change the result: deterministic.
 
+#define SD_TU 2  // translation unit id of this file's SD_CHECK sites
 #include "render_common.cuh"
 
 namespace sd {
@@ -285,6 +286,10 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
         const int u_begin = (ulo / SEG) * SEG;
         const int vmax = uhi < 0 ? 0 : min(VB, ks - b * VB);
         for (int vv = 0; vv < vmax; ++vv) {
+          // the deepest halo row this column's window reaches
+          if (!SD_CHECK((size_t)(rb * SEG + (uhi / SEG) * SEG + 2 * SEG - 1) * S + col + b * VB + vv,
+                        SM::halo_words(ks)))
+            continue;
           const float* colp = base + b * VB + vv;
           float win[SEG];
 #pragma unroll
@@ -314,6 +319,7 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
 #pragma unroll
         for (int j = 0; j < SEG; ++j) {
           int pix = (rb * SEG + j) * TX + col;
+          if (!SD_CHECK(pix, SM::NPX)) continue;
           unsigned short r16 = prel[pix];
           if (r16 == 0xffff) continue;
           int k0 = kmin + (int)r16;
@@ -412,3 +418,5 @@ sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
 }
 
 }  // extern "C"
+
+SD_CHECK_TU(render)

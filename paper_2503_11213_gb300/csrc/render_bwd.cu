@@ -27,6 +27,7 @@
 //                           order, then write the slice's gradient;
 //   bank_grad_tc_kernel     the bank gradient on the tensor cores (section 4).
 
+#define SD_TU 3  // translation unit id of this file's SD_CHECK sites
 #include <algorithm>
 #include <mutex>
 
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(256) kernel_columns_kernel(const RenderParams 
   for (int i = threadIdx.x; i < ks * IL.rcol * 2; i += blockDim.x) {
     const int v = i / (IL.rcol * 2), q = i - v * IL.rcol * 2, rho = q >> 1, s = q & 1;
     const int u = rho - IL.padu;
-    dst[i] = (u >= 0 && u < ks) ? kf[(s * ks + u) * ks + v] : 0.f;
+    if (SD_CHECK((size_t)kl * ks * IL.rcol * 2 + i, IL.kcol_bytes / 4))
+      dst[i] = (u >= 0 && u < ks) ? kf[(s * ks + u) * ks + v] : 0.f;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int u = warp; u < ks; u += blockDim.x / 32) {
@@ -289,7 +291,7 @@ __device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0,
       }
       acc[j] = sl + sr;
     }
-    if (act) {
+    if (act && SD_CHECK(col + v, BWMAX)) {
       if (plain) {  // distinct rows: loads, adds and stores batch
         float old8[8];
 #pragma unroll
@@ -300,7 +302,7 @@ __device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int tr = min(max(jr0 + j, fold_lo), fold_hi);
-          bcol[tr * BWMAX + v] += acc[j];
+          if (SD_CHECK(tr, 8)) bcol[tr * BWMAX + v] += acc[j];
         }
       }
     }
@@ -439,7 +441,11 @@ __global__ void __launch_bounds__(IG_NW * 32, 3) render_bwd_img_kernel(
         const unsigned m0 = __ballot_sync(0xffffffffu, f0);
         const unsigned m1 = __ballot_sync(0xffffffffu, f1);
         const int n0 = __popc(m0), ncand = n0 + __popc(m1);
-        // the slice's candidates in half passes of 16, paired in order
+        // the slice's candidates in half passes of 16, paired in order (the
+        // band of the slice's last kernel column stays inside the re-laid bank)
+        if (!SD_CHECK(((size_t)kl * ks + ks - 1) * col_stride + 2 * (d - 7 + IL.padu) + 31,
+                      IL.kcol_bytes / 4))
+          continue;
         const IgUnit U{k, vlo, vhi, m0, m1, n0, ncand, 0,
                        kcol + ((size_t)kl * ks + vlo) * col_stride + 2 * (d - 7 + IL.padu)};
         for (int q0 = 0; q0 < ncand; q0 += 16) {
@@ -494,7 +500,8 @@ __global__ void __launch_bounds__(IG_NW * 32, 3) render_bwd_img_kernel(
   const int ncol = c_hi - c_lo + 1;
   for (int i = threadIdx.x; i < nrow * ncol; i += IG_NW * 32) {
     const int j = i / ncol, cc = c_lo + (i - j * ncol);
-    ga[(size_t)(r0 + j) * W + (x0 - p + cc)] += fb[j][cc];
+    const long long o = (long long)(r0 + j) * W + (x0 - p + cc);
+    if (SD_CHECK(o, (long long)H * W) && SD_CHECK(cc, BWMAX)) ga[o] += fb[j][cc];
   }
 }
 
@@ -509,6 +516,7 @@ struct BankPlan {
   int* tick;         // per (split slot, wavelength): chunks finished
   float* pbuf;       // per (split slot, chunk, wavelength): a 2 ks^2 slab
   int nkeys;
+  int smax;          // split slots
   __device__ float* slab(int sl, int chunk, int lam, int NL, int ks2) const {
     return pbuf + (((size_t)sl * 2 + chunk) * NL + lam) * 2 * (size_t)ks2;
   }
@@ -839,6 +847,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
   // dKf[u][v] -> B[key][lam][side][ks-1-u][ks-1-v] (a split slice: the
   // chunk's slab first)
   float* out = gbank + ((size_t)key * P.NL + lam) * 2 * ks2;
+  if (nch == 2 && !SD_CHECK(sl, plan.smax)) return;
   float* dst = nch == 1 ? out : plan.slab(sl, chunk, lam, P.NL, ks2);
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
@@ -962,6 +971,7 @@ inline sd_status launch_plan(const RenderParams& P, const unsigned* bm, int word
   plan->tick = tick;
   plan->pbuf = reinterpret_cast<float*>(b + L.pbuf);
   plan->nkeys = nk;
+  plan->smax = L.smax;
   *ranks = nk + L.smax;
   return SD_OK;
 }
@@ -1384,9 +1394,8 @@ __global__ void __launch_bounds__(BG_NT, 2) bank_grad_tc_kernel(
         for (int i = 0; i < 9; ++i) {
           if (i == 8 && r != 7) continue;  // column 64 comes from group 7, shift 8
           const int vv = 8 * r + i;
-          if (vv < ks)
-            dst[(size_t)side * ks2 + (size_t)(ks - 1 - u) * ks + (ks - 1 - vv)] =
-                ((ini >> ug) & 1u) ? v[side * 16 + i] : 0.f;
+          const long long o = (long long)side * ks2 + (long long)(ks - 1 - u) * ks + (ks - 1 - vv);
+          if (vv < ks && SD_CHECK(o, 2 * ks2)) dst[o] = ((ini >> ug) & 1u) ? v[side * 16 + i] : 0.f;
         }
     }
   }
@@ -1664,3 +1673,5 @@ extern "C" sd_status sd_dp_render_backward_noalloc(const float* grad_out, const 
   return sd_dp_render_backward(grad_out, aif, depth_m, bank, layout, N, C, H, W, SD_F32,
                                grad_aif, grad_bank, ws, NOALLOC_SCRATCH_BYTES, stream);
 }
+
+SD_CHECK_TU(render_bwd)

@@ -17,6 +17,7 @@
 // stored coalesced at the end.
 // Deterministic (fixed reduction order).
 
+#define SD_TU 4  // translation unit id of this file's SD_CHECK sites
 #include <cstring>
 
 #include "common.cuh"
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(MAP_NT) render_map_kernel(const MapParams P) {
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
       const int e = ch * 32 * NT + lane + 32 * j;
-      if (e < ks2) {
+      if (e < ks2 && SD_CHECK(base + offs[e], R * S)) {
         const V v = vtile[base + offs[e]];
         const float kl = val(curL, j), kr = val(curR, j);
 #pragma unroll
@@ -244,3 +245,5 @@ extern "C" sd_status sd_dp_render_map(const void* aif, const void* psf_map, int 
   if (image_dtype == SD_F32 && map_dtype == SD_F16) return launch_map<float, __half>(P, s);
   return SD_ERR_UNSUPPORTED;
 }
+
+SD_CHECK_TU(render_map)

@@ -28,6 +28,7 @@
 // for a 128-row window (starting at row u) of a K-major BF16 matrix, K = 32
 // in two MMAs, D in tensor memory.
 
+#define SD_TU 5  // translation unit id of this file's SD_CHECK sites
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       kmin_t = min(kmin_t, u0 ? key[i] : key[i] + 1);
     }
   }
-  if (pix) {
+  if (pix && SD_CHECK(TR_J * 2 * tid + 2 * TR_J - 1, TR_MAXK)) {
 #pragma unroll
     for (int i = 0; i < TR_J; ++i) {
       s_cand[TR_J * 2 * tid + 2 * i] = (use >> (2 * i)) & 1u ? key[i] : -1;
@@ -354,7 +355,8 @@ __global__ void __launch_bounds__(TR_NT, 2) render_tc_kernel(const RenderParams 
       while (b) {
         const int bit = __ffs(b) - 1;
         b &= b - 1;
-        s_uniq[pos++] = kmin + 32 * w + bit;
+        if (SD_CHECK(pos, TR_MAXK)) s_uniq[pos] = kmin + 32 * w + bit;
+        ++pos;
       }
     }
   } else {
@@ -649,3 +651,5 @@ extern "C" sd_status sd_dev_tc_check(const void* a, const void* b, int u, float*
                                     reinterpret_cast<const __nv_bfloat16*>(b), u, d, status);
   return launch_status();
 }
+
+SD_CHECK_TU(render_tc)

@@ -161,3 +161,14 @@ def test_mlp_map_args(lib):
     assert call(dmax=float("nan")) == L.SD_ERR_ARG
     assert call(dt=L.SD_F16) == L.SD_ERR_UNSUPPORTED
     assert call(blob=MIS) == L.SD_ERR_ARG
+
+
+def test_check_status_needs_the_checked_build(lib):
+    # the normal build compiles its bounds checks away and says so before
+    # touching the device
+    site, index, bound = ctypes.c_int32(7), ctypes.c_int32(0), ctypes.c_int32(0)
+    count = ctypes.c_int64(7)
+    assert lib.sd_check_status(ctypes.byref(site), ctypes.byref(index), ctypes.byref(bound),
+                               ctypes.byref(count)) == L.SD_ERR_UNSUPPORTED
+    assert lib.sd_check_status(None, None, None, ctypes.byref(count)) == L.SD_ERR_ARG
+    assert lib.sd_check_status(ctypes.byref(site), None, None, None) == L.SD_ERR_ARG
