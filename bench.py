@@ -723,19 +723,22 @@ def pipeline_compare(sd, dev, reps=5):
     bank32 = torch.empty(total, device=dev)
     st32 = torch.zeros((n_req, 8), dtype=torch.int64, device=dev)
 
+    # every pipeline's trace records the landing mask its adjoint reads
+    mask32 = sd.land_mask(n_req, c["n_grid"], device=dev)
+
     def trace32():
         sd.dp_psf_trace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
-                        norm=sd.SD_NORM_JOINT, out=bank32, stats=st32)
+                        norm=sd.SD_NORM_JOINT, out=bank32, stats=st32, mask=mask32)
 
-    def adj(gb, greq):
+    def adj(gb, greq, mask):
         sd.dp_psf_trace_backward(lens, sensor, req_dev, n_req, gb, max_ks=ks, max_n=c["n_grid"],
-                                 grad_req=greq)
+                                 grad_req=greq, mask=mask)
 
     def plain():
         trace32()
         sd.dp_render(aif32, depth, bank32, lay32, out=out32)
         render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32)
-        adj(gbank32, greq32)
+        adj(gbank32, greq32, mask32)
 
     t_plain = _timed(plain, stream, reps)
     stages = {"f32": {
@@ -744,7 +747,7 @@ def pipeline_compare(sd, dev, reps=5):
                          reps),
         "render_bwd": _timed(lambda: render_bwd(lay32, aif32, bank32, gaif32, gbank32, ws32),
                              stream, reps),
-        "trace_adjoint": _timed(lambda: adj(gbank32, greq32), stream, reps)}}
+        "trace_adjoint": _timed(lambda: adj(gbank32, greq32, mask32), stream, reps)}}
     torch.cuda.synchronize()
     r32 = out32.float()
     banks = {"f32": bank32.cpu().numpy()}
@@ -753,8 +756,9 @@ def pipeline_compare(sd, dev, reps=5):
     tune_cache = os.path.join(ROOT, "paper_2503_11213_gb300", "_build", "tune_cache.txt")
     for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
         lay16, aif16, out16, gaif16, gbank16, ws16, greq16 = make(dt)
+        mask16 = sd.land_mask(n_req, c["n_grid"], device=dev)
         bt = sd.BatchedTrace(lens, sensor, req_dev, n_req, total, max_ks=ks, max_n=c["n_grid"],
-                             norm=sd.SD_NORM_JOINT, dtype=dt)
+                             norm=sd.SD_NORM_JOINT, dtype=dt, mask=mask16)
         bt.tune(tune_cache)
         ws_tc = torch.empty(sd.api.render_tc_workspace(lay16), dtype=torch.uint8, device=dev)
         ws_bg = torch.empty(sd.api.bank_grad_tc_workspace(lay16, B, 3, H, Wd),
@@ -769,7 +773,7 @@ def pipeline_compare(sd, dev, reps=5):
             bt.run()
             sd.dp_render_tc(aif16, depth, bt.out, lay16, out=out16, workspace=ws_tc)
             render_bwd_tc()
-            adj(gbank16, greq16)
+            adj(gbank16, greq16, mask16)
 
         s2 = torch.cuda.Stream()
         s2.wait_stream(stream)
@@ -788,7 +792,7 @@ def pipeline_compare(sd, dev, reps=5):
             "render": _timed(lambda: sd.dp_render_tc(aif16, depth, bt.out, lay16, out=out16,
                                                      workspace=ws_tc), stream, reps),
             "render_bwd": _timed(render_bwd_tc, stream, reps),
-            "trace_adjoint": _timed(lambda: adj(gbank16, greq16), stream, reps)}
+            "trace_adjoint": _timed(lambda: adj(gbank16, greq16, mask16), stream, reps)}
         torch.cuda.synchronize()
         res[f"batched_{name}_graph_ms"] = round(t_graph, 3)
         res[f"speedup_{name}"] = round(t_plain / t_graph, 3)

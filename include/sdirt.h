@@ -169,9 +169,10 @@ typedef struct sd_trace_opts {
   int32_t max_n_grid;   /* largest N of any request (0 = 512, <= 2048) */
   uint32_t* land_mask;  /* device, nullable: one bit per ray (see
                            sd_dp_psf_trace_mask_bytes).  sd_dp_psf_trace
-                           writes it; sd_dp_psf_trace_backward reads it and
-                           traces again only the rays whose bit is set.  The
-                           other trace entry points ignore it. */
+                           and sd_dp_psf_trace_batched write it;
+                           sd_dp_psf_trace_backward reads it and traces
+                           again only the rays whose bit is set.  The map
+                           and hit-dump entry points ignore it. */
 } sd_trace_opts;
 
 /*
@@ -179,7 +180,8 @@ typedef struct sd_trace_opts {
  * max_n_grid (0 = 512): request r owns words [r * W, (r + 1) * W), W =
  * ceil(max_n_grid^2 / 32); bit k % 32 of its word k / 32 is ray k of the
  * request (the trace's ray order: in-pupil samples in raster order).
- * sd_dp_psf_trace sets the bit of every ray that reaches the sensor, lands
+ * sd_dp_psf_trace (and sd_dp_psf_trace_batched, bitwise the same) sets the
+ * bit of every ray that reaches the sensor, lands
  * on the L or R sub-pixel (Eq. 1/2) and has its nearest pixel centre at most
  * one pixel outside the request's ks x ks patch (the bilinear footprint of a
  * ray can touch the patch only then), whatever the binning mode, and clears
@@ -253,8 +255,9 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
  * contribution) and the thread slots that ran the sweep (32 per warp in
  * which any ray has a contribution); the first is the adjoint's algorithmic
  * work, the second what the hardware executed.
- * With opts->land_mask (written by sd_dp_psf_trace of the same lenses,
- * sensor, requests and max_n_grid) only the rays whose bit is set are traced
+ * With opts->land_mask (written by sd_dp_psf_trace or sd_dp_psf_trace_batched
+ * of the same lenses, sensor, requests and max_n_grid) only the rays whose
+ * bit is set are traced
  * again, taken in ray order from a queue that keeps every warp but the
  * request's last full: the gradient equals the maskless one up to the order
  * of FP32 additions (deterministic either way).

@@ -280,7 +280,7 @@ class BatchedTrace:
     nothing and can be captured in a CUDA graph."""
 
     def __init__(self, lenses, sensor: DPSensor, req_dev, n_req, total, max_ks, max_n=512,
-                 norm=L.SD_NORM_JOINT, dtype=torch.float32, config=None):
+                 norm=L.SD_NORM_JOINT, dtype=torch.float32, config=None, mask=None):
         self.lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]
         self.handles = (ctypes.c_void_p * len(self.lenses))(
             *[l.handle.value for l in self.lenses])
@@ -290,7 +290,13 @@ class BatchedTrace:
         self.stats = torch.zeros((n_req, L.SD_N_STATS), dtype=torch.int64, device=dev)
         self.ws = torch.empty(batched_workspace_bytes(n_req, total), dtype=torch.uint8, device=dev)
         self.sen = sensor.c()
-        self.opts = L.SdTraceOpts(L.SD_BIN_HARD, norm, _DT[dtype], 0, max_ks, max_n)
+        # mask (from land_mask(n_req, max_n)), if given, receives every
+        # ray's landing bit on each run, as dp_psf_trace writes it
+        if mask is not None and mask.numel() * 4 < land_mask_bytes(n_req, max_n):
+            raise ValueError("the landing mask is too small for these requests")
+        self.mask = mask
+        self.opts = L.SdTraceOpts(L.SD_BIN_HARD, norm, _DT[dtype], 0, max_ks, max_n,
+                                  _mask_ptr(mask))
         self.config = L.SdBatchConfig(*(config or (0, 0, 0)), 0)
 
     def run(self):

@@ -1646,6 +1646,10 @@ __global__ void __launch_bounds__(128) prep_kernel(TraceParams P, BatchWs W, int
   }
   if (fits)
     for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) W.counts[q.out_offset + i] = 0u;
+  // the items OR their rays' landing bits into the request's mask words
+  if (fits && P.land_mask)
+    for (int i = threadIdx.x; i < (ctx.total + 31) >> 5; i += blockDim.x)
+      if (SD_CHECK(i, P.mask_words)) P.land_mask[(size_t)r * P.mask_words + i] = 0u;
   if (P.stats && threadIdx.x < SD_N_STATS)
     P.stats[(long long)r * SD_N_STATS + threadIdx.x] =
         threadIdx.x == SD_STAT_LAUNCHED && fits ? (long long)ctx.total : 0;
@@ -1756,7 +1760,7 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
   __shared__ ReqCtx ctx;
   __shared__ unsigned s_stats[SD_N_STATS];
   __shared__ float s_red[64];
-  __shared__ int s_last, s_rows;
+  __shared__ int s_last, s_rows, s_off;
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   unsigned* patch = reinterpret_cast<unsigned*>(smem + table_bytes(P.max_n));
@@ -1814,13 +1818,28 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
         s_rows = carry;
       }
     }
+    if (threadIdx.x == 0) s_off = 0;
     __syncthreads();
     const int total = s_rows;
+    if (P.land_mask) {
+      // the request's rays before this item (its rows above row0): the
+      // item's first ray index in the request's landing mask
+      int c_above = 0;
+      for (int j = threadIdx.x; j < row0; j += blockDim.x) {
+        int c, l;
+        row_span(N, j, &c, &l);
+        c_above += c;
+      }
+      if (c_above) atomicAdd(&s_off, c_above);
+      __syncthreads();
+    }
+    const int ray0 = s_off;
     unsigned c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0, c_clip = 0;
     int row = 0;
     for (int base = 0; base < total; base += blockDim.x) {
       int k = base + threadIdx.x;
       int key = -1;
+      bool land = false;  // as in trace_bin_kernel
       if (k < total) {
         // ray k of the item (k grows within the item: advance the row)
         row = advance_row(prefix, k, row);
@@ -1839,10 +1858,23 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
           else if (side == 0) ++c_l;
           else ++c_r;
           if (inpatch && side < 2) key = side * ks2 + (int)bf * ks + (int)af;
+          land = side != 2 && af >= -1.f && af <= (float)ks && bf >= -1.f && bf <= (float)ks;
         } else if (st == ST_CLIP) {
           ++c_vign;
         } else {
           ++c_other;
+        }
+      }
+      if (P.land_mask) {
+        // the warp's 32 rays start at request ray g0, which need not be a
+        // word boundary: their bits go to words g0 / 32 and the next
+        const unsigned bits = __ballot_sync(0xffffffffu, land);
+        const int g0 = ray0 + base + (threadIdx.x & ~31), w0 = g0 >> 5, sh = g0 & 31;
+        if (lane == 0 && bits) {
+          unsigned* mr = P.land_mask + (size_t)r * P.mask_words;
+          if (SD_CHECK(w0, P.mask_words)) atomicOr(mr + w0, bits << sh);
+          const unsigned hi = sh ? bits >> (32 - sh) : 0u;
+          if (hi && SD_CHECK(w0 + 1, P.mask_words)) atomicOr(mr + w0 + 1, hi);
         }
       }
       unsigned m = __match_any_sync(0xffffffffu, key);
@@ -1908,6 +1940,7 @@ sd_status sd_dp_psf_trace_batched(const sd_lens* const* lenses, int n_lenses,
   P.n_req = n_req;
   P.max_n = max_n;
   P.max_ks = max_ks;
+  P.mask_words = mask_words(max_n);
   P.out = out;
   P.stats = reinterpret_cast<long long*>(stats);
   BatchWs W = batch_ws(workspace, n_req);  // u32 counts at the requests' output offsets

@@ -30,13 +30,25 @@ def test_batched_equals_per_request_kernel(sdlib, config, two_d):
     sd = sdlib
     lenses, reqs, dev, total, off = batch(sd, 160, seed=3, two_d=two_d)
     sensor = sd.DPSensor(0.002)
-    ref, ref_st = sd.dp_psf_trace(lenses, sensor, dev, len(reqs), total, max_ks=127, max_n=512)
+    m_ref = sd.land_mask(len(reqs), 512)
+    ref, ref_st = sd.dp_psf_trace(lenses, sensor, dev, len(reqs), total, max_ks=127, max_n=512,
+                                  mask=m_ref)
+    m_bt = sd.land_mask(len(reqs), 512)
+    m_bt.fill_(-1)  # the batched trace clears the words it owns before ORing bits in
     bt = sd.BatchedTrace(lenses, sensor, dev, len(reqs), total, max_ks=127, max_n=512,
-                         config=config)
+                         config=config, mask=m_bt)
     out, st = bt.run()
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     assert torch.equal(st, ref_st)
+    # the landing masks agree on every word that holds a request's rays (the
+    # items' rows start anywhere in a word: their bits are ORed in)
+    words = 512 * 512 // 32
+    a = m_ref.view(len(reqs), words).cpu().numpy()
+    b = m_bt.view(len(reqs), words).cpu().numpy()
+    used = (ref_st[:, 0].cpu().numpy() + 31) // 32
+    for r in range(len(reqs)):
+        assert np.array_equal(a[r, :used[r]], b[r, :used[r]]), r
     for l in lenses:
         l.free()
 
