@@ -273,9 +273,11 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
       extent(ulo_n, uhi_n);
       commit(kb);
       __syncwarp();
-      float aL[SEG], aR[SEG];
+      // (L, R) sums of the SEG pixels: one packed two-lane FMA per tap and
+      // pixel (its components round like fmaf)
+      float2 a2[SEG];
 #pragma unroll
-      for (int j = 0; j < SEG; ++j) aL[j] = aR[j] = 0.f;
+      for (int j = 0; j < SEG; ++j) a2[j] = make_float2(0.f, 0.f);
       const float* base = halo + (rb * SEG) * S + col;
       for (int b = 0; b < nblk; ++b) {
         const float* kcur = kb + (b & 1) * kb_elems;
@@ -302,8 +304,8 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
               float2 w2 = kp[u * VB];
 #pragma unroll
               for (int j = 0; j < SEG; ++j) {
-                aL[j] = fmaf(win[(q + j) % SEG], w2.x, aL[j]);
-                aR[j] = fmaf(win[(q + j) % SEG], w2.y, aR[j]);
+                const float iv = win[(q + j) % SEG];
+                a2[j] = __ffma2_rn(make_float2(iv, iv), w2, a2[j]);
               }
               win[q] = colp[(u + SEG) * S];
             }
@@ -326,8 +328,8 @@ __global__ void __launch_bounds__(4 * TX, 1) render_fwd_kernel(const RenderParam
           float t = pt[pix];
           float w = (k0 == key) ? (two ? 1.f - t : 1.f) : ((two && k0 + 1 == key) ? t : 0.f);
           if (w != 0.f) {
-            atomicAdd(&accL[pix], aL[j] * w);
-            atomicAdd(&accR[pix], aR[j] * w);
+            atomicAdd(&accL[pix], a2[j].x * w);
+            atomicAdd(&accR[pix], a2[j].y * w);
           }
         }
       }

@@ -246,15 +246,17 @@ __device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0,
   const int col = !act ? 0 : (idx < n0 ? nth_set_bit(m0, idx) : 32 + nth_set_bit(m1, idx - n0));
   const int vlo = u1_valid ? min(U0.vlo, U1.vlo) : U0.vlo;
   const int vhi = u1_valid ? max(U0.vhi, U1.vhi) : U0.vhi;
-  float GL[8], GR[8];
+  // (L, R) pairs: the weighted gradients, the re-laid taps (interleaved by
+  // side) and the sums go through the packed two-lane FMA, whose components
+  // round like fmaf (the same sums, half the FMA instructions)
+  float2 G2[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const float4 e = src[a][col];
     const int k0 = __float_as_int(e.w);
     const float w = !act || k0 < 0 ? 0.f
                     : (k0 == k ? (two ? 1.f - e.z : 1.f) : ((two && k0 + 1 == k) ? e.z : 0.f));
-    GL[a] = w * e.x;
-    GR[a] = w * e.y;
+    G2[a] = make_float2(w * e.x, w * e.y);
   }
   // the lane reads its own unit's taps from column vlo (of the union) on;
   // columns before its own range are zero, so start the pointer there too
@@ -267,13 +269,11 @@ __device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0,
 #pragma unroll
   for (int q = 0; q < 8; ++q) tn[q] = __ldg(kb + q);
   for (int v = vlo; v <= vhi; ++v) {
-    float T[32];
+    float2 T2[16];  // band row r: (L, R)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      T[4 * q] = tn[q].x;
-      T[4 * q + 1] = tn[q].y;
-      T[4 * q + 2] = tn[q].z;
-      T[4 * q + 3] = tn[q].w;
+      T2[2 * q] = make_float2(tn[q].x, tn[q].y);
+      T2[2 * q + 1] = make_float2(tn[q].z, tn[q].w);
     }
     kb += cs4;
     if (v < vhi) {
@@ -283,13 +283,10 @@ __device__ __forceinline__ void ig_pass(const float4 (*src)[IG_SW], float* buf0,
     float acc[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      float sl = 0.f, sr = 0.f;
+      float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        sl = fmaf(GL[a], T[2 * (j - a + 7)], sl);
-        sr = fmaf(GR[a], T[2 * (j - a + 7) + 1], sr);
-      }
-      acc[j] = sl + sr;
+      for (int a = 0; a < 8; ++a) s2 = __ffma2_rn(G2[a], T2[j - a + 7], s2);
+      acc[j] = s2.x + s2.y;
     }
     if (act && SD_CHECK(col + v, BWMAX)) {
       if (plain) {  // distinct rows: loads, adds and stores batch
@@ -746,11 +743,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
   const int tid = threadIdx.x;
   const bool two = P.Z > 1;
   const int nstrip = ks * (KU / SEG);
-  float acc[SPT][2 * SEG];
+  // per strip and row: (L, R) sums, one packed two-lane FMA per tap (its
+  // components round like fmaf)
+  float2 acc[SPT][SEG];
 #pragma unroll
   for (int s = 0; s < SPT; ++s)
 #pragma unroll
-    for (int i = 0; i < 2 * SEG; ++i) acc[s][i] = 0.f;
+    for (int i = 0; i < SEG; ++i) acc[s][i] = make_float2(0.f, 0.f);
 
   const int kw = key >> 5;
   const unsigned kbit = 1u << (key & 31);
@@ -836,8 +835,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
                 float2 g = G[(rb * SEG + j) * TXB + col];
 #pragma unroll
                 for (int uu = 0; uu < SEG; ++uu) {
-                  acc[s][uu] = fmaf(g.x, img[j + uu], acc[s][uu]);
-                  acc[s][SEG + uu] = fmaf(g.y, img[j + uu], acc[s][SEG + uu]);
+                  acc[s][uu] = __ffma2_rn(g, make_float2(img[j + uu], img[j + uu]), acc[s][uu]);
                 }
               }
             }
@@ -859,8 +857,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(
       int u = u0 + uu;
       if (u >= ks) continue;
       size_t o = (size_t)(ks - 1 - u) * ks + (ks - 1 - v);
-      dst[o] = acc[s][uu];
-      dst[ks2 + o] = acc[s][SEG + uu];
+      dst[o] = acc[s][uu].x;
+      dst[ks2 + o] = acc[s][uu].y;
     }
   }
   if (nch == 2)
