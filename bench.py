@@ -902,7 +902,12 @@ def paper_workload(sd, dev, reps=5):
         out = torch.empty((1, 6, H, Wd), dtype=dt, device=dev)
         t_tr = _timed(lambda: sd.dp_psf_map(lens, sensor, depth, c["lambda_nm"], n, ks,
                                             out=pmap, stats=stats), stream, reps)
-        t_rd = _timed(lambda: sd.dp_render_map(img, pmap, out=out), stream, reps)
+        # the bulk-copy form (with a status word) and the per-thread-load form
+        st_r = torch.empty(1, dtype=torch.int32, device=dev)
+        t_rd = _timed(lambda: sd.dp_render_map(img, pmap, out=out, status=st_r), stream, reps)
+        sd.sync_status(st_r)
+        t_rd_loads = _timed(lambda: sd.dp_render_map(img, pmap, out=out, status=False), stream,
+                            reps)
         rays = int(stats[:, 0].sum().item())
         map_bytes = pmap.numel() * pmap.element_size()
         io_bytes = img.numel() * img.element_size() + out.numel() * out.element_size()
@@ -910,6 +915,7 @@ def paper_workload(sd, dev, reps=5):
                      "psfs_per_s": round(H * Wd / (t_tr * 1e-3), 1),
                      "rays": rays, "grays_s": round(rays / (t_tr * 1e-3) / 1e9, 3),
                      "render_gbs": round((map_bytes + io_bytes) / (t_rd * 1e-3) / 1e9, 1),
+                     "render_ms_per_thread_loads": round(t_rd_loads, 4),
                      "trace_speedup_vs_paper": round(PAPER_TRACE_S / (t_tr * 1e-3), 1),
                      "render_speedup_vs_paper": round(PAPER_RENDER_S / (t_rd * 1e-3), 1)}
         if dt == torch.float32:
@@ -918,6 +924,7 @@ def paper_workload(sd, dev, reps=5):
     peaks = load_peaks()
     if peaks.get("hbm_gbs"):
         res["render_hbm_frac_f32"] = round(res["f32"]["render_gbs"] / peaks["hbm_gbs"], 3)
+        res["render_hbm_frac_bf16"] = round(res["bf16"]["render_gbs"] / peaks["hbm_gbs"], 3)
     # the paper's render-time PSF source: the network of Sec. 3.2 (5 x 512,
     # 2 ks^2 outputs) fitted to PSFs traced at random points of the region
     # (max-normalised targets, Eq. 4 loss; seeded), its tensor-core map of

@@ -406,10 +406,16 @@ sd_status sd_dp_render(const void* aif, const float* depth_m, const void* bank,
  * deterministic.  Storage pairs as sd_dp_render (F32/F32, F32/BF16,
  * BF16/BF16, F16/F16, F32/F16 for image/map); others return
  * SD_ERR_UNSUPPORTED, as do ks > 127.
+ * status (device int32, nullable) is zeroed by the call and becomes 1 if a
+ * bounded completion wait gave up (out is then invalid; sd_sync_status reads
+ * it).  With a status word, ks <= 21, W a multiple of 4 (16-bit map) or 2
+ * (FP32 map) and a 16-byte aligned map, the map is streamed into shared
+ * memory by bulk copies; otherwise, and always without a status word, it is
+ * read with per-thread loads.  Both forms give the same bits.
  */
 sd_status sd_dp_render_map(const void* aif, const void* psf_map, int N, int C,
                            int H, int W, int ks, int image_dtype, int map_dtype,
-                           void* out, void* stream);
+                           void* out, int32_t* status, void* stream);
 
 /*
  * sd_dp_render for 16-bit images on the tensor cores (tcgen05, FP32
@@ -607,7 +613,8 @@ sd_status sd_dev_tc_check(const void* a, const void* b, int u, float* d,
 /*
  * Waits for the stream and reads a device status word written by a kernel:
  * the first int32 of the workspace of sd_dp_render_tc or
- * sd_dp_render_bank_grad_tc, or the status buffer of sd_mlp_psf_map.
+ * sd_dp_render_bank_grad_tc, or the status word of sd_mlp_psf_map or
+ * sd_dp_render_map.
  * Returns SD_ERR_TIMEOUT when the word is non-zero (a bounded completion wait
  * of that call gave up: its output is invalid), SD_OK when it is zero,
  * SD_ERR_ARG for a null pointer and SD_ERR_CUDA when the copy fails.
@@ -617,10 +624,11 @@ sd_status sd_sync_status(const int32_t* status_word, void* stream);
 
 /*
  * Failure injection for tests: every bounded completion wait (mbarrier poll
- * loop) of the tensor-core kernels launched after this call gives up after
- * `polls` polls; polls = 0 makes the first wait of every CTA give up without
- * polling, so that no tensor-core product or bulk copy is issued and the
- * kernel ends through its error path (flag set, tensor memory freed).
+ * loop) of the tensor-core kernels and of the bulk-copy map render launched
+ * after this call gives up after `polls` polls; polls = 0 makes the first
+ * wait of every CTA give up without polling, so that no tensor-core product
+ * is issued and the kernel ends through its error path (flag set, the bulk
+ * copies already issued waited for, tensor memory freed).
  * polls < 0 restores each kernel's own limit.  Process-wide; host call.
  */
 sd_status sd_set_wait_limit(long long polls);

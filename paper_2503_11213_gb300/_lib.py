@@ -140,7 +140,7 @@ def lib():
     L.sd_dp_render_tc.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp,
                                   ctypes.c_size_t, vp]
     L.sd_dp_render_tc_workspace.argtypes = [P(SdBankLayout), P(ctypes.c_size_t)]
-    L.sd_dp_render_map.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp]
+    L.sd_dp_render_map.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp]
     L.sd_dp_render.argtypes = [vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32, i32, vp, vp]
     L.sd_dp_render_backward.argtypes = [vp, vp, vp, vp, P(SdBankLayout), i32, i32, i32, i32,
                                         i32, vp, vp, vp, ctypes.c_size_t, vp]

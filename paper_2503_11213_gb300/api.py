@@ -233,18 +233,24 @@ def dp_psf_map(lens: Lens, sensor: DPSensor, depth_m, lambda_nm, n_grid, ks,
     return out, stats
 
 
-def dp_render_map(aif, psf_map, out=None):
+def dp_render_map(aif, psf_map, out=None, status=None):
     """aif (N,C,H,W) f32/bf16/f16 and a PSF map (H,W,2,ks,ks) -> DP image
-    (N,2C,H,W) in aif's dtype (one kernel pair per pixel for all channels)."""
+    (N,2C,H,W) in aif's dtype (one kernel pair per pixel for all channels).
+    status: a device int32 word (one is made if None) that the call zeroes
+    and sets to 1 if a bounded wait of the bulk-copy form gave up; read it
+    with sync_status.  status=False takes the per-thread-load form."""
     N, C, H, W = aif.shape
     ks = psf_map.shape[-1]
     if tuple(psf_map.shape) != (H, W, 2, ks, ks):
         raise ValueError("psf_map must be (H, W, 2, ks, ks)")
     if out is None:
         out = torch.empty((N, 2 * C, H, W), dtype=aif.dtype, device=aif.device)
-    _need_cuda(aif, psf_map, out)
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=aif.device)
+    _need_cuda(aif, psf_map, out, *([status] if status is not False else []))
     L.check(L.lib().sd_dp_render_map(_ptr(aif), _ptr(psf_map), N, C, H, W, ks, _DT[aif.dtype],
-                                     _DT[psf_map.dtype], _ptr(out), _stream()),
+                                     _DT[psf_map.dtype], _ptr(out),
+                                     None if status is False else _ptr(status), _stream()),
             "sd_dp_render_map")
     return out
 

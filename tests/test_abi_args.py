@@ -40,15 +40,18 @@ def layout(ks=65, nl=3, dtype=L.SD_F32, nf=3, nz=3):
 def test_render_map_args(lib):
     f = lib.sd_dp_render_map
     F32, BF16, F16 = L.SD_F32, L.SD_BF16, L.SD_F16
-    assert f(None, PTR, 1, 3, 8, 8, 5, F32, F32, PTR, None) == L.SD_ERR_ARG
-    assert f(PTR, PTR, 1, 3, 8, 8, 4, F32, F32, PTR, None) == L.SD_ERR_ARG      # even ks
-    assert f(PTR, PTR, 1, 0, 8, 8, 5, F32, F32, PTR, None) == L.SD_ERR_ARG      # C < 1
-    assert f(PTR, PTR, -1, 3, 8, 8, 5, F32, F32, PTR, None) == L.SD_ERR_ARG
-    assert f(PTR, PTR, 1, 3, 8, 8, 129, F32, F32, PTR, None) == L.SD_ERR_UNSUPPORTED
-    assert f(PTR, PTR, 70000, 1, 8, 8, 5, F32, F32, PTR, None) == L.SD_ERR_UNSUPPORTED
+    assert f(None, PTR, 1, 3, 8, 8, 5, F32, F32, PTR, None, None) == L.SD_ERR_ARG
+    assert f(PTR, PTR, 1, 3, 8, 8, 4, F32, F32, PTR, None, None) == L.SD_ERR_ARG      # even ks
+    assert f(PTR, PTR, 1, 0, 8, 8, 5, F32, F32, PTR, None, None) == L.SD_ERR_ARG      # C < 1
+    assert f(PTR, PTR, -1, 3, 8, 8, 5, F32, F32, PTR, None, None) == L.SD_ERR_ARG
+    assert f(PTR, PTR, 1, 3, 8, 8, 129, F32, F32, PTR, None, None) == L.SD_ERR_UNSUPPORTED
+    assert f(PTR, PTR, 70000, 1, 8, 8, 5, F32, F32, PTR, None, None) == L.SD_ERR_UNSUPPORTED
+    # image / map storage pairs outside the supported set
+    assert f(PTR, PTR, 1, 3, 8, 8, 5, BF16, F32, PTR, None, None) == L.SD_ERR_UNSUPPORTED
+    assert f(PTR, PTR, 1, 3, 8, 8, 5, F16, BF16, PTR, None, None) == L.SD_ERR_UNSUPPORTED
     # empty inputs: nothing to do
-    assert f(PTR, PTR, 0, 3, 8, 8, 5, F32, F32, PTR, None) == L.SD_OK
-    assert f(PTR, PTR, 1, 3, 0, 8, 5, F32, F32, PTR, None) == L.SD_OK
+    assert f(PTR, PTR, 0, 3, 8, 8, 5, F32, F32, PTR, None, None) == L.SD_OK
+    assert f(PTR, PTR, 1, 3, 0, 8, 5, F32, F32, PTR, None, None) == L.SD_OK
 
 
 def test_render_args(lib):

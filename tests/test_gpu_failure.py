@@ -1,7 +1,7 @@
-"""Failure detection of the tensor-core kernels without a GPU fault.
+"""Failure detection of the kernels with completion waits, without a GPU fault.
 
-Every completion wait of the tensor-core render, its bank gradient and the
-PSF network is a bounded poll loop; a wait that gives up sets the launch's
+Every completion wait of the tensor-core render, its bank gradient, the
+PSF network and the bulk-copy map render is a bounded poll loop; a wait that gives up sets the launch's
 status word, the CTA stops issuing products, drains what it issued (a
 separately bounded wait), frees its tensor memory and returns.  Here the
 poll limit is set to 0 (sd_set_wait_limit), so the first wait of every CTA
@@ -101,6 +101,30 @@ def test_mlp_gives_up_and_recovers(sdlib):
     finally:
         sd.set_wait_limit(None)
     again, _ = sd.mlp_psf_map(net, depth, 0.5, 20.0, status=st)
+    sd.sync_status(st)
+    assert torch.equal(again, good)
+
+
+def test_render_map_gives_up_and_recovers(sdlib):
+    """The bulk-copy form of the map render issues its first copies before
+    its first wait: with the limit at 0 that wait gives up, the warp stops,
+    waits for the copies it issued and the block returns."""
+    sd = sdlib
+    rng = np.random.default_rng(4)
+    a = torch.tensor(rng.uniform(0, 1, size=(1, 3, 24, 64)).astype(np.float32), device="cuda")
+    k = torch.tensor(rng.uniform(0, 1, size=(24, 64, 2, 21, 21)).astype(np.float32),
+                     device="cuda").to(torch.bfloat16)
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    good = sd.dp_render_map(a, k, status=st)
+    sd.sync_status(st)
+    good = good.clone()
+    try:
+        sd.set_wait_limit(0)
+        sd.dp_render_map(a, k, status=st)
+        expect_timeout(sd, st)
+    finally:
+        sd.set_wait_limit(None)
+    again = sd.dp_render_map(a, k, status=st)
     sd.sync_status(st)
     assert torch.equal(again, good)
 

@@ -179,6 +179,43 @@ def test_render_map_full_size_and_deterministic(sdlib):
     assert np.abs(g1.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
+STAGED_CASES = [
+    # N, C, H, W, ks, image dtype, map dtype: shapes the bulk-copy form takes
+    # (W a multiple of the chunk's pixels, ks <= 21), ragged tiles and rows
+    (1, 3, 19, 44, 21, torch.float32, torch.float32),
+    (1, 3, 19, 44, 21, torch.float32, torch.bfloat16),
+    (1, 3, 19, 44, 21, torch.bfloat16, torch.bfloat16),
+    (1, 3, 19, 44, 21, torch.float16, torch.float16),
+    (2, 2, 13, 36, 9, torch.float32, torch.float32),
+    (1, 5, 17, 40, 3, torch.float32, torch.bfloat16),
+    (1, 1, 9, 4, 1, torch.float32, torch.float32),
+    (1, 3, 512, 768, 21, torch.float32, torch.bfloat16),
+]
+
+
+@pytest.mark.parametrize("case", STAGED_CASES)
+def test_render_map_staged_equals_direct(sdlib, case):
+    """The bulk-copy form (with a status word) and the per-thread-load form
+    (without) take every tap in the same lane and order: bitwise equal, and
+    the status word stays 0."""
+    sd = sdlib
+    N, C, H, Wd, ks, idt, mdt = case
+    rng = np.random.default_rng(H * Wd + ks)
+    a = torch.tensor(rng.uniform(0, 1, size=(N, C, H, Wd)).astype(np.float32),
+                     device="cuda").to(idt)
+    k = torch.tensor(rng.uniform(0, 1, size=(H, Wd, 2, ks, ks)).astype(np.float32),
+                     device="cuda").to(mdt)
+    st = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    staged = sd.dp_render_map(a, k, status=st)
+    direct = sd.dp_render_map(a, k, status=False)
+    sd.sync_status(st)
+    assert torch.equal(staged, direct)
+    if H * Wd <= 1024:
+        ref = O.render_map(a.float().cpu().numpy(), k.float().cpu().numpy())
+        tol = 1e-5 if idt == torch.float32 else 8 * 2.0 ** -9
+        assert np.abs(staged.float().cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
 def test_map_validation(sdlib):
     sd = sdlib
     a = torch.zeros((1, 3, 8, 8), device="cuda")
