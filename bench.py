@@ -48,12 +48,15 @@ TRAFFIC_BYTES = {
     # read + 1.2 MB written; independent of the image size
     "trace_adj_kernel": 117.5e6,
     # the image-gradient call as the phase times it: selection table 4.2 MB,
-    # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.7 MB
-    "render_bwd_img_kernel": 375.6e6,
+    # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.1 MB
+    "render_bwd_img_kernel": 375.1e6,
     # the bank-gradient call as the phase times it: selection table 4.2 MB,
-    # slice bitmap 8.4 MB, work plan 0.1 MB, bank pass 46.3 MB read + 41.4 MB
+    # slice bitmap 8.4 MB, work plan 0.1 MB, bank pass 46.3 MB read + 41.5 MB
     # written (the rest of the 103.8 MB gradient bank still in L2 at its end)
-    "render_bwd_bank_kernel": 100.4e6,
+    "render_bwd_bank_kernel": 100.5e6,
+    # one render launch: the bank slices its tiles use and the image, 66.0 MB
+    # read, 7.9 MB of output written
+    "render_fwd_kernel": 73.9e6,
 }
 
 # ---------------------------------------------------------------------------
