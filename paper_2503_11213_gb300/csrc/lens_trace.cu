@@ -21,6 +21,8 @@
 #include <mutex>
 #include <vector>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sd {
@@ -351,7 +353,8 @@ sd_status sd_lens_free(sd_lens* lens) {
 // ---------------------------------------------------------------------------
 namespace sd {
 
-enum { ST_OK = 0, ST_MISS = 1, ST_CLIP = 2, ST_TIR = 3, ST_NEWTON = 4, ST_BACK = 5 };
+enum { ST_OK = 0, ST_MISS = 1, ST_CLIP = 2, ST_TIR = 3, ST_NEWTON = 4, ST_BACK = 5,
+       ST_NONE = 6 };  // ST_NONE: the empty slot of a pair past the last ray
 
 struct SensorF {
   float ps, inv_ps, h, w, r2, fh;  // fh = (f - h) / f
@@ -506,22 +509,31 @@ __device__ void setup_request(const TraceParams& P, const sd_psf_request& q,
   __syncthreads();
 }
 
-// a*b + c*d with one rounding to about 1 ulp (Kahan: the rounding error of
-// c*d is recovered exactly by an FMA and added back)
-__device__ __forceinline__ float dot2(float a, float b, float c, float d) {
-  float w = c * d;
-  float e = fmaf(c, d, -w);
-  float f = fmaf(a, b, w);
-  return f + e;
-}
+// ---------------------------------------------------------------------------
+// One ray (float) or two rays (float2) through the same rounded operations.
+// The tracer below is written once over these: every FP32 operation is an
+// explicitly rounded add, multiply or fused multiply-add (no contraction left
+// to the compiler), and the float2 forms are the packed two-lane
+// instructions of sm_100 and later, whose components round exactly like the
+// scalar ones.  So a ray traced alone and the same ray traced as one of a
+// pair give the same bits, and the forward (pairs), the adjoint's recompute,
+// the batched trace and the map trace (single rays) take the same decisions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+// a - b = a + (-b) with one rounding
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// 1/sqrt(x) to about half an ulp: hardware estimate plus one Newton step
-// (unit vectors feed Snell's law, whose output direction error is
-// multiplied by the remaining path length to the sensor).
-__device__ __forceinline__ float rsqrt_refined(float x) {
-  float r = rsqrtf(x);
-  return r * fmaf(-0.5f * x * r, r, 1.5f);
-}
+template <class V> __device__ __forceinline__ V vb(float s);
+template <> __device__ __forceinline__ float vb<float>(float s) { return s; }
+template <> __device__ __forceinline__ float2 vb<float2>(float s) { return make_float2(s, s); }
 
 // Hardware reciprocal estimate (rcp.approx, about 1 ulp; denormals flushed).
 __device__ __forceinline__ float rcp_est(float b) {
@@ -529,144 +541,312 @@ __device__ __forceinline__ float rcp_est(float b) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
   return r;
 }
+__device__ __forceinline__ float2 rcp_est(float2 b) { return make_float2(rcp_est(b.x), rcp_est(b.y)); }
+__device__ __forceinline__ float rsqrt_est(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float2 rsqrt_est(float2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float2 vmax(float2 a, float b) {
+  return make_float2(fmaxf(a.x, b), fmaxf(a.y, b));
+}
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float2 fast_div(float2 a, float2 b) {
+  return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+}
+
+// Per-ray masks and statuses: bool / int for one ray, two of each for a pair.
+struct M2 {
+  bool x, y;
+};
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ M2 lt(float2 a, float b) { return {a.x < b, a.y < b}; }
+__device__ __forceinline__ bool gt(float a, float b) { return a > b; }
+__device__ __forceinline__ M2 gt(float2 a, float b) { return {a.x > b, a.y > b}; }
+__device__ __forceinline__ M2 gt(float2 a, float2 b) { return {a.x > b.x, a.y > b.y}; }
+__device__ __forceinline__ bool vnot(bool m) { return !m; }
+__device__ __forceinline__ M2 vnot(M2 m) { return {!m.x, !m.y}; }
+__device__ __forceinline__ bool vand(bool a, bool b) { return a && b; }
+__device__ __forceinline__ M2 vand(M2 a, M2 b) { return {a.x && b.x, a.y && b.y}; }
+__device__ __forceinline__ bool any_of(bool m) { return m; }
+__device__ __forceinline__ bool any_of(M2 m) { return m.x || m.y; }
+__device__ __forceinline__ float sel(bool m, float a, float b) { return m ? a : b; }
+__device__ __forceinline__ float2 sel(M2 m, float2 a, float2 b) {
+  return make_float2(m.x ? a.x : b.x, m.y ? a.y : b.y);
+}
+__device__ __forceinline__ bool small_step(float s) { return fabsf(s) < 1e-5f; }
+__device__ __forceinline__ M2 small_step(float2 s) { return {fabsf(s.x) < 1e-5f, fabsf(s.y) < 1e-5f}; }
+
+// status: the first failure of each ray stays
+__device__ __forceinline__ int fail(int st, bool m, int code) { return st == ST_OK && m ? code : st; }
+__device__ __forceinline__ int2 fail(int2 st, M2 m, int code) {
+  return make_int2(st.x == ST_OK && m.x ? code : st.x, st.y == ST_OK && m.y ? code : st.y);
+}
+__device__ __forceinline__ bool dead(int st) { return st != ST_OK; }
+__device__ __forceinline__ bool dead(int2 st) { return st.x != ST_OK && st.y != ST_OK; }
+__device__ __forceinline__ bool alive(int st) { return st == ST_OK; }
+__device__ __forceinline__ M2 alive(int2 st) { return {st.x == ST_OK, st.y == ST_OK}; }
+template <class V> struct VStat;
+template <> struct VStat<float> {
+  using S = int;
+  using M = bool;
+};
+template <> struct VStat<float2> {
+  using S = int2;
+  using M = M2;
+};
+
+// a*b + c*d with one rounding to about 1 ulp (Kahan: the rounding error of
+// c*d is recovered exactly by an FMA and added back)
+template <class V>
+__device__ __forceinline__ V dot2(V a, V b, V c, V d) {
+  const V w = vmul(c, d);
+  const V e = vfma(c, d, vneg(w));
+  const V f = vfma(a, b, w);
+  return vadd(f, e);
+}
+
+// 1/sqrt(x) to about half an ulp: hardware estimate plus one Newton step
+// (unit vectors feed Snell's law, whose output direction error is
+// multiplied by the remaining path length to the sensor).
+template <class V>
+__device__ __forceinline__ V rsqrt_refined(V x) {
+  const V r = rsqrt_est(x);
+  return vmul(r, vfma(vmul(vmul(vb<V>(-0.5f), x), r), r, vb<V>(1.5f)));
+}
 
 // a / b from the reciprocal estimate and one Newton-Raphson correction of
 // the quotient (Markstein, IBM J. Res. Dev. 34(1), 1990): the FMA residual
 // a - b q0 of q0 = a rcp(b) is exact, and q0 + residual * rcp(b) is within
 // one ulp of a / b.  Branch-free; valid for the normal-range operands of the
 // trace (lengths and cosines), b != 0.
-__device__ __forceinline__ float div_nr(float a, float b) {
-  const float r = rcp_est(b);
-  const float q = a * r;
-  return fmaf(fmaf(-b, q, a), r, q);
+template <class V>
+__device__ __forceinline__ V div_nr(V a, V b) {
+  const V r = rcp_est(b);
+  const V q = vmul(a, r);
+  return vfma(vfma(vneg(b), q, a), r, q);
 }
 
 // sqrt(x) for x >= 0 from the reciprocal square-root estimate and one
 // Newton correction on the residual x - s^2 (Markstein's method), within
 // about one ulp.  x is clamped to 1e-30 so that x = 0 yields 1e-15, not NaN.
-__device__ __forceinline__ float sqrt_nr(float x) {
-  x = fmaxf(x, 1e-30f);
-  const float r = rsqrtf(x);
-  const float s = x * r;
-  return fmaf(fmaf(-s, s, x), 0.5f * r, s);
+template <class V>
+__device__ __forceinline__ V sqrt_nr(V x) {
+  x = vmax(x, 1e-30f);
+  const V r = rsqrt_est(x);
+  const V s = vmul(x, r);
+  return vfma(vfma(vneg(s), s, x), vmul(vb<V>(0.5f), r), s);
 }
 
-// Sequential trace (FP32) of one ray in surface-0-vertex-local coordinates.
+// Constants of surface s for the tracer, derived with explicitly rounded
+// operations from the lens image and the request's refractive ratios: as
+// values (one ray) or as duplicated pairs (two rays) staged per block.
+template <class V>
+struct SurfK {
+  V c, negc, k, kk;    // curvature, its negative, conic, 1 + k
+  V nkc2, halfc;       // -(1 + k) c^2, c / 2
+  V negckk, sd2, negt; // -c (1 + k), clear semi-diameter^2, -thickness
+  V a[5], da[5];       // a4..a12 and m a_2m
+  V e, e2, om;         // eta, eta^2, 1 - eta^2
+  int kind;
+};
+
+__device__ __forceinline__ SurfK<float> surf_consts(const DevSurf& S, float eta, float omeg2) {
+  SurfK<float> K;
+  K.c = S.c;
+  K.negc = -S.c;
+  K.k = S.k;
+  K.kk = __fadd_rn(1.f, S.k);
+  K.nkc2 = -__fmul_rn(__fmul_rn(K.kk, S.c), S.c);
+  K.halfc = __fmul_rn(0.5f, S.c);
+  K.negckk = -__fmul_rn(S.c, K.kk);
+  K.sd2 = S.sd2;
+  K.negt = -S.t;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    K.a[j] = S.a[j];
+    K.da[j] = S.da[j];
+  }
+  K.e = eta;
+  K.e2 = __fmul_rn(eta, eta);
+  K.om = omeg2;
+  K.kind = S.kind;
+  return K;
+}
+
+__device__ __forceinline__ SurfK<float2> pair_consts(const SurfK<float>& K) {
+  SurfK<float2> P;
+  P.c = vb<float2>(K.c);
+  P.negc = vb<float2>(K.negc);
+  P.k = vb<float2>(K.k);
+  P.kk = vb<float2>(K.kk);
+  P.nkc2 = vb<float2>(K.nkc2);
+  P.halfc = vb<float2>(K.halfc);
+  P.negckk = vb<float2>(K.negckk);
+  P.sd2 = vb<float2>(K.sd2);
+  P.negt = vb<float2>(K.negt);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    P.a[j] = vb<float2>(K.a[j]);
+    P.da[j] = vb<float2>(K.da[j]);
+  }
+  P.e = vb<float2>(K.e);
+  P.e2 = vb<float2>(K.e2);
+  P.om = vb<float2>(K.om);
+  P.kind = K.kind;
+  return P;
+}
+
+// Sequential trace (FP32) of one ray (V = float) or two rays (V = float2)
+// in surface-0-vertex-local coordinates; KS(s) yields SurfK<V> of surface s.
 // On success (x, y) is the sensor landing point and (dx, dy, dz) the unit
 // direction.  Positions are kept relative to the current surface vertex.
-// Per-surface forward state kept for the adjoint: hit point (vertex-local),
-// direction arriving at the surface and the intersection parameter.
+// A ray of a pair that fails keeps its first status and runs on with the
+// other (its values are not used); loops end when both rays are done.
+// Per-surface forward state kept for the adjoint (one ray, SAVE): the
+// intersection parameter at every surface and the last hit point.
 struct AdjState {
   float t[SD_MAX_SURFACES];  // intersection parameter at every surface
   float px, py, pz;          // hit point at the last surface (vertex-local)
 };
 
-// NSC > 0: the lens has exactly NSC surfaces (loops fully unrolled, per-
-// surface state in registers); NSC == 0: surface count read at run time.
-template <bool SAVE, int NSC = 0>
-__device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ eta,
-                                           const float* __restrict__ omeg2, int newton_max,
-                                           float& x, float& y, float& z,
-                                           float& dx, float& dy, float& dz, AdjState* sv) {
-  const DevLens& L = c_lens[slot];
-  const int n = NSC ? NSC : L.n;
-#pragma unroll
-  for (int s = 0; s < (NSC ? NSC : n); ++s) {
-    const DevSurf& S = L.s[s];
+// A single ray returns at its first failure; a pair runs each surface to its
+// end and returns there when both rays have failed (fewer tests per ray).
+#define SD_EARLY_OUT(V, st)                          \
+  if constexpr (std::is_same<V, float>::value) {     \
+    if (dead(st)) return st;                         \
+  }
+
+template <bool SAVE, class V, class KS>
+__device__ __forceinline__ typename VStat<V>::S trace_ray_v(
+    int n, const KS& ks_of, int newton_max, typename VStat<V>::S st, V& x, V& y, V& z, V& dx,
+    V& dy, V& dz, AdjState* sv) {
+  using M = typename VStat<V>::M;
+  const V one = vb<V>(1.f), m2 = vb<V>(-2.f);
+  for (int s = 0; s < n; ++s) {
+    const SurfK<V>& S = ks_of(s);
     const int kind = S.kind;
-    float t;
+    V t;
     if (kind & K_FLAT) {
-      if (!(dz > 0.f)) return ST_BACK;
-      t = div_nr(-z, dz);
+      st = fail(st, vnot(gt(dz, 0.f)), ST_BACK);
+      SD_EARLY_OUT(V, st);
+      t = div_nr(vneg(z), dz);
     } else {
       // conic: A t^2 - 2 B t + C = 0 (|d| = 1), root nearest the vertex in
-      // the cancellation-free form t = C / (B + sqrt(B^2 - A C))
-      float kk = 1.f + S.k;
-      float A = S.c * fmaf(S.k * dz, dz, 1.f);
-      float B = dz - S.c * (x * dx + y * dy + kk * z * dz);
-      float C = S.c * (x * x + y * y + kk * z * z) - 2.f * z;
-      float disc = B * B - A * C;
-      if (disc < 0.f) return ST_MISS;
-      float den = B + sqrt_nr(disc);
-      if (!(den > 0.f)) return ST_MISS;
+      // the cancellation-free form t = C / (B + sqrt(B^2 - A C)); nA = -A
+      const V nA = vmul(S.negc, vfma(vmul(S.k, dz), dz, one));
+      const V kz = vmul(S.kk, z);
+      const V B = vfma(S.negc, vfma(kz, dz, vfma(y, dy, vmul(x, dx))), dz);
+      const V C = vfma(S.c, vfma(kz, z, vfma(y, y, vmul(x, x))), vmul(m2, z));
+      const V disc = vfma(nA, C, vmul(B, B));
+      const V den = vadd(B, sqrt_nr(disc));
+      // no real root, or the root's denominator not positive
+      st = fail(st, vnot(vand(vnot(lt(disc, 0.f)), gt(den, 0.f))), ST_MISS);
+      SD_EARLY_OUT(V, st);
       t = div_nr(C, den);
     }
     if (kind & K_ASPH) {
-      // Newton on F(t) = z + t dz - sag(rho(t)^2), started at the conic root
-      const float sc = S.c, kc2 = (1.f + S.k) * S.c * S.c;
-      const float a0 = S.a[0], a1 = S.a[1], a2 = S.a[2], a3 = S.a[3], a4 = S.a[4];
-      const float d0 = S.da[0], d1 = S.da[1], d2 = S.da[2], d3 = S.da[3], d4 = S.da[4];
+      // Newton on F(t) = z + t dz - sag(rho(t)^2), started at the conic root;
+      // a ray stops updating t once its step is below 1e-5 mm
+      M act = alive(st);
       int it = 0;
       for (; it < newton_max; ++it) {
-        float px = fmaf(t, dx, x), py = fmaf(t, dy, y);
-        float u = px * px + py * py;
-        float arg = 1.f - kc2 * u;
-        if (arg < 0.f) return ST_NEWTON;
-        float q = sqrt_nr(arg);
-        float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, a4, a3), a2), a1), a0);
-        float zs = div_nr(sc * u, 1.f + q) + u * u * poly;
-        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, d4, d3), d2), d1), d0);
-        // the derivative and the step only steer the iteration (its fixed point
-        // is the root of the exactly evaluated F): fast reciprocals suffice
-        float dzdu = (q > 0.f ? 0.5f * sc * rsqrtf(arg) : 0.f) + u * dpoly;
-        float F = fmaf(t, dz, z) - zs;
-        float dF = dz - 2.f * dzdu * (px * dx + py * dy);
-        float step = __fdividef(F, dF);
-        t -= step;
-        if (fabsf(step) < 1e-5f) break;
+        const V px = vfma(t, dx, x), py = vfma(t, dy, y);
+        const V u = vfma(py, py, vmul(px, px));
+        const V arg = vfma(S.nkc2, u, one);
+        st = fail(st, vand(act, lt(arg, 0.f)), ST_NEWTON);
+        act = vand(act, alive(st));
+        if (!any_of(act)) break;
+        const V argc = vmax(arg, 1e-30f);
+        const V r = rsqrt_est(argc);
+        // q = sqrt(arg) (sqrt_nr, sharing the estimate with the derivative)
+        const V s0 = vmul(argc, r);
+        const V q = vfma(vfma(vneg(s0), s0, argc), vmul(vb<V>(0.5f), r), s0);
+        const V poly =
+            vfma(u, vfma(u, vfma(u, vfma(u, S.a[4], S.a[3]), S.a[2]), S.a[1]), S.a[0]);
+        const V zs = vfma(vmul(u, u), poly, div_nr(vmul(S.c, u), vadd(one, q)));
+        const V dpoly =
+            vfma(u, vfma(u, vfma(u, vfma(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
+        // the derivative and the step only steer the iteration (its fixed
+        // point is the root of the exactly evaluated F): estimates suffice
+        const V dzdu = vfma(u, dpoly, vmul(S.halfc, r));
+        const V F = vsub(vfma(t, dz, z), zs);
+        const V dF = vfma(vmul(m2, dzdu), vfma(py, dy, vmul(px, dx)), dz);
+        const V step = fast_div(F, dF);
+        t = vsub(t, sel(act, step, vb<V>(0.f)));
+        act = vand(act, vnot(small_step(step)));
+        if (!any_of(act)) break;
       }
-      if (it == newton_max) return ST_NEWTON;
+      st = fail(st, act, ST_NEWTON);  // not converged in newton_max steps
+      SD_EARLY_OUT(V, st);
     }
-    if (SAVE) sv->t[s] = t;
-    x = fmaf(t, dx, x);
-    y = fmaf(t, dy, y);
-    z = fmaf(t, dz, z);
-    if (SAVE && s == n - 1) {
-      sv->px = x;
-      sv->py = y;
-      sv->pz = z;
+    if constexpr (SAVE) sv->t[s] = t;
+    x = vfma(t, dx, x);
+    y = vfma(t, dy, y);
+    z = vfma(t, dz, z);
+    if constexpr (SAVE) {
+      if (s == n - 1) {
+        sv->px = x;
+        sv->py = y;
+        sv->pz = z;
+      }
     }
-    float rho2 = x * x + y * y;
-    if (rho2 > S.sd2) return ST_CLIP;
+    const V rho2 = vfma(y, y, vmul(x, x));
+    st = fail(st, gt(rho2, S.sd2), ST_CLIP);
+    SD_EARLY_OUT(V, st);
     if (kind & K_REFRACT) {
-      float nx, ny, nz;
+      V nx, ny, nz;
       if (kind & K_ASPH) {
-        float u = rho2;
-        float q = sqrt_nr(1.f - (1.f + S.k) * S.c * S.c * u);
-        float dpoly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, S.da[4], S.da[3]), S.da[2]), S.da[1]), S.da[0]);
-        float dzdu = div_nr(0.5f * S.c, q) + u * dpoly;
-        nx = -2.f * x * dzdu;
-        ny = -2.f * y * dzdu;
-        nz = 1.f;
+        const V qq = sqrt_nr(vfma(S.nkc2, rho2, one));
+        const V dpoly = vfma(
+            rho2, vfma(rho2, vfma(rho2, vfma(rho2, S.da[4], S.da[3]), S.da[2]), S.da[1]),
+            S.da[0]);
+        const V dzdu = vfma(rho2, dpoly, div_nr(S.halfc, qq));
+        nx = vmul(vmul(m2, x), dzdu);
+        ny = vmul(vmul(m2, y), dzdu);
+        nz = one;
       } else {
         // gradient of the quadric c(x^2+y^2) + c(1+k) z^2 - 2 z, oriented +z
-        nx = -S.c * x;
-        ny = -S.c * y;
-        nz = 1.f - S.c * (1.f + S.k) * z;
+        nx = vmul(S.negc, x);
+        ny = vmul(S.negc, y);
+        nz = vfma(S.negckk, z, one);
       }
-      float inv = rsqrt_refined(nx * nx + ny * ny + nz * nz);
-      nx *= inv;
-      ny *= inv;
-      nz *= inv;
+      const V inv = rsqrt_refined(vfma(nz, nz, vfma(ny, ny, vmul(nx, nx))));
+      nx = vmul(nx, inv);
+      ny = vmul(ny, inv);
+      nz = vmul(nz, inv);
       // vector Snell's law with the normal along the propagation:
       // d' = e d + g n with g = cos(t_t) - e cos(t_i), evaluated as
-      // (1 - e^2) / (cos(t_t) + e cos(t_i)) to avoid the cancellation
-      float e = eta[s];
-      float cosi = nx * dx + ny * dy + nz * dz;
-      float k2 = 1.f - e * e * (1.f - cosi * cosi);
-      if (k2 < 0.f) return ST_TIR;
-      float g = div_nr(omeg2[s], sqrt_nr(k2) + e * cosi);
-      dx = dot2(e, dx, g, nx);
-      dy = dot2(e, dy, g, ny);
-      dz = dot2(e, dz, g, nz);
+      // (1 - e^2) / (cos(t_t) + e cos(t_i)) to avoid the cancellation;
+      // cos^2(t_t) = 1 - e^2 (1 - cos^2(t_i)) = (1 - e^2) + e^2 cos^2(t_i)
+      const V cosi = vfma(nz, dz, vfma(ny, dy, vmul(nx, dx)));
+      const V k2 = vfma(vmul(S.e2, cosi), cosi, S.om);
+      st = fail(st, lt(k2, 0.f), ST_TIR);
+      SD_EARLY_OUT(V, st);
+      const V g = div_nr(S.om, vfma(S.e, cosi, sqrt_nr(k2)));
+      dx = dot2(S.e, dx, g, nx);
+      dy = dot2(S.e, dy, g, ny);
+      dz = dot2(S.e, dz, g, nz);
     }
-    z -= S.t;  // vertex-local coordinate of the next surface (or the sensor)
+    z = vadd(z, S.negt);  // vertex-local coordinate of the next surface (or the sensor)
+    if (dead(st)) return st;
   }
-  if (!(dz > 0.f)) return ST_BACK;
-  float t = div_nr(-z, dz);
-  x = fmaf(t, dx, x);
-  y = fmaf(t, dy, y);
-  return ST_OK;
+  st = fail(st, vnot(gt(dz, 0.f)), ST_BACK);
+  if (dead(st)) return st;
+  const V t = div_nr(vneg(z), dz);
+  x = vfma(t, dx, x);
+  y = vfma(t, dy, y);
+  return st;
+}
+
+// One ray, the surface constants derived on the fly (the adjoint, the
+// batched trace, the map trace, the hit dump).
+template <bool SAVE>
+__device__ __forceinline__ int trace_ray_t(int slot, const float* __restrict__ eta,
+                                           const float* __restrict__ omeg2, int newton_max,
+                                           float& x, float& y, float& z, float& dx, float& dy,
+                                           float& dz, AdjState* sv) {
+  const DevLens& L = c_lens[slot];
+  auto ks_of = [&](int s) { return surf_consts(L.s[s], eta[s], omeg2[s]); };
+  return trace_ray_v<SAVE, float>(L.n, ks_of, newton_max, (int)ST_OK, x, y, z, dx, dy, dz, sv);
 }
 
 __device__ __forceinline__ int trace_ray(int slot, const float* __restrict__ eta,
@@ -752,10 +932,13 @@ __device__ __forceinline__ void store_out(void* out, long long idx, float v) {
 }
 
 // One block per request.  MODE 0: hard counts (u32), 1: bilinear (f32).
+// A thread traces rays k and k + blockDim.x together (packed pairs) and bins
+// each of the two sets of blockDim.x consecutive rays as one.
 template <int MODE, class OutT>
 __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ReqCtx ctx;
+  __shared__ SurfK<float2> s_surf[SD_MAX_SURFACES];
   __shared__ unsigned int s_stats[SD_N_STATS];
   __shared__ float s_red[2][32];
   int* prefix = reinterpret_cast<int*>(smem);
@@ -769,6 +952,9 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
   setup_request(P, q, ctx, prefix, lo);
   const int ks = ctx.ks, ks2 = ks * ks, p = (ks - 1) >> 1;
   for (int i = threadIdx.x; i < 2 * ks2; i += blockDim.x) patch[i] = 0u;
+  const int nsurf = ctx.N ? c_lens[ctx.slot].n : 0;
+  for (int sf = threadIdx.x; sf < nsurf; sf += blockDim.x)
+    s_surf[sf] = pair_consts(surf_consts(c_lens[ctx.slot].s[sf], ctx.eta[sf], ctx.omeg2[sf]));
   __syncthreads();
 
   const SensorF S = P.sen;
@@ -776,9 +962,10 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
   const int lane = threadIdx.x & 31;
   unsigned int c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0,
                c_clip = 0;
-  int row = 0;
-  for (int base = 0; base < total; base += blockDim.x) {
-    int k = base + threadIdx.x;
+  auto ks_of = [&](int sf) -> const SurfK<float2>& { return s_surf[sf]; };
+  // bins one ray (k, its status and landing values) of a set of blockDim.x
+  // consecutive rays; every thread of the block calls it for each set
+  auto bin = [&](int k, int st, float x, float y, float dx, float dz) {
     int key = -1;
     float fx = 0.f, fy = 0.f;
     int side = 2;
@@ -786,10 +973,6 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
     // pixel outside the patch (the adjoint takes the same decisions)
     bool land = false;
     if (k < total) {
-      float x, y, z, dx, dy, dz;
-      row = advance_row(prefix, k, row);
-      make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
-      int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
       if (st == ST_OK) {
         ++c_reached;
         fx = (x - ctx.xc) * S.inv_ps + (float)p;
@@ -814,11 +997,11 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
       }
     }
     if (P.land_mask) {
-      // one word per warp: rays base + 32 w .. base + 32 w + 31
+      // one word per warp: its 32 consecutive rays k - lane .. k - lane + 31
       const unsigned bits = __ballot_sync(0xffffffffu, land);
-      const int k0 = base + (threadIdx.x & ~31);
-      if (lane == 0 && k0 < total && SD_CHECK(k0 >> 5, P.mask_words))
-        P.land_mask[(size_t)r * P.mask_words + (k0 >> 5)] = bits;
+      const int kw = k - lane;
+      if (lane == 0 && kw < total && SD_CHECK(kw >> 5, P.mask_words))
+        P.land_mask[(size_t)r * P.mask_words + (kw >> 5)] = bits;
     }
     if (MODE == 0) {
       // warp-aggregated shared-memory increment of the landing bin
@@ -839,6 +1022,28 @@ __global__ void __launch_bounds__(256) trace_bin_kernel(TraceParams P) {
             atomicAdd(&P0[bb * ks + aa], (jx ? wx : 1.f - wx) * (jy ? wy : 1.f - wy));
         }
     }
+  };
+  const int NT = blockDim.x;
+  int row0 = 0, row1 = 0;
+  for (int base = 0; base < total; base += 2 * NT) {
+    const int k0 = base + threadIdx.x, k1 = k0 + NT;
+    float2 x = make_float2(0.f, 0.f), y = x, z = x, dx = x, dy = x,
+           dz = make_float2(1.f, 1.f);
+    int2 st = make_int2(k0 < total ? (int)ST_OK : (int)ST_NONE,
+                        k1 < total ? (int)ST_OK : (int)ST_NONE);
+    if (k0 < total) {
+      row0 = advance_row(prefix, k0, row0);
+      make_ray_row(ctx, prefix, lo, k0, row0, x.x, y.x, z.x, dx.x, dy.x, dz.x);
+    }
+    if (k1 < total) {
+      row1 = advance_row(prefix, k1, row1);
+      make_ray_row(ctx, prefix, lo, k1, row1, x.y, y.y, z.y, dx.y, dy.y, dz.y);
+    }
+    if (k0 < total)
+      st = trace_ray_v<false, float2>(nsurf, ks_of, P.newton_max, st, x, y, z, dx, dy, dz,
+                                      nullptr);
+    bin(k0, st.x, x.x, y.x, dx.x, dz.x);
+    bin(k1, st.y, x.y, y.y, dx.y, dz.y);
   }
   // block statistics
   atomicAdd(&s_stats[SD_STAT_REACHED], c_reached);
