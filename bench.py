@@ -321,7 +321,7 @@ def run_ours(args, world, rank, local, dist):
     torch.cuda.synchronize()
     rays_per_step = int(stats[:, 0].sum().item())
     # rays whose reverse sweep carries a contribution (non-zero splat
-    # gradient), and the thread slots that ran it, in the adjoint of the step
+    # gradient), and the ray slots that ran it (64 per sweeping warp), in the adjoint of the step
     swept_rays = int(swept[:, 0].sum().item())
     swept_slots = int(swept[:, 1].sum().item())
     # the adjoint traces again only the requests whose gradient patch is

@@ -252,9 +252,10 @@ sd_status sd_dp_psf_map(const sd_lens* lens, const sd_dp_sensor* sensor,
  * grad_req and grad_lens are device memory owned by the caller.
  * swept (device, nullable) receives per request [n_req][2] int64: the rays
  * whose splat gradient is non-zero (the rays whose reverse sweep carries a
- * contribution) and the thread slots that ran the sweep (32 per warp in
- * which any ray has a contribution); the first is the adjoint's algorithmic
- * work, the second what the hardware executed.
+ * contribution) and the ray slots that ran the sweep (64 per warp in which
+ * any ray has a contribution: each thread sweeps two rays as a pair); the
+ * first is the adjoint's algorithmic work, the second what the hardware
+ * executed.
  * With opts->land_mask (written by sd_dp_psf_trace or sd_dp_psf_trace_batched
  * of the same lenses, sensor, requests and max_n_grid) only the rays whose
  * bit is set are traced

@@ -184,7 +184,7 @@ def dp_psf_trace_backward(lenses, sensor: DPSensor, req_dev, n_req, grad_out, ma
     <grad_out, PSF> with respect to the lens parameters, as
     (grad_req (n_req, 32, 8), grad_lens (n_lenses, 32, 8)).  swept, an
     optional (n_req, 2) int64 CUDA tensor, receives per request the rays with
-    a non-zero splat gradient and the thread slots that ran the sweep.  mask,
+    a non-zero splat gradient and the ray slots that ran the sweep (two per thread).  mask,
     a landing mask written by dp_psf_trace of the same lenses, sensor and
     requests (same max_n), restricts the retrace to the rays it marks."""
     lenses = lenses if isinstance(lenses, (list, tuple)) else [lenses]

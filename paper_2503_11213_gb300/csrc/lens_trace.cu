@@ -646,6 +646,10 @@ struct SurfK {
   V negckk, sd2, negt; // -c (1 + k), clear semi-diameter^2, -thickness
   V a[5], da[5];       // a4..a12 and m a_2m
   V e, e2, om;         // eta, eta^2, 1 - eta^2
+  // for the adjoint's reverse sweep
+  V ie, ie2;           // 1 / eta, its square
+  V kc2, qc3, qkc3;    // (1 + k) c^2, c^3 / 4, (1 + k) c^3 / 4
+  V dda[5];            // (m - 1) m a_2m
   int kind;
 };
 
@@ -668,6 +672,13 @@ __device__ __forceinline__ SurfK<float> surf_consts(const DevSurf& S, float eta,
   K.e = eta;
   K.e2 = __fmul_rn(eta, eta);
   K.om = omeg2;
+  K.ie = div_nr(1.f, eta);
+  K.ie2 = __fmul_rn(K.ie, K.ie);
+  K.kc2 = __fmul_rn(__fmul_rn(K.kk, S.c), S.c);
+  K.qc3 = __fmul_rn(0.25f, __fmul_rn(__fmul_rn(S.c, S.c), S.c));
+  K.qkc3 = __fmul_rn(K.kk, K.qc3);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) K.dda[j] = __fmul_rn((float)(j + 1), S.da[j]);
   K.kind = S.kind;
   return K;
 }
@@ -691,6 +702,13 @@ __device__ __forceinline__ SurfK<float2> pair_consts(const SurfK<float>& K) {
   P.e = vb<float2>(K.e);
   P.e2 = vb<float2>(K.e2);
   P.om = vb<float2>(K.om);
+  P.ie = vb<float2>(K.ie);
+  P.ie2 = vb<float2>(K.ie2);
+  P.kc2 = vb<float2>(K.kc2);
+  P.qc3 = vb<float2>(K.qc3);
+  P.qkc3 = vb<float2>(K.qkc3);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) P.dda[j] = vb<float2>(K.dda[j]);
   P.kind = K.kind;
   return P;
 }
@@ -701,12 +719,14 @@ __device__ __forceinline__ SurfK<float2> pair_consts(const SurfK<float>& K) {
 // direction.  Positions are kept relative to the current surface vertex.
 // A ray of a pair that fails keeps its first status and runs on with the
 // other (its values are not used); loops end when both rays are done.
-// Per-surface forward state kept for the adjoint (one ray, SAVE): the
-// intersection parameter at every surface and the last hit point.
-struct AdjState {
-  float t[SD_MAX_SURFACES];  // intersection parameter at every surface
-  float px, py, pz;          // hit point at the last surface (vertex-local)
+// Per-surface forward state kept for the adjoint (SAVE): the intersection
+// parameter at every surface and the last hit point, of one ray or a pair.
+template <class V>
+struct AdjStateV {
+  V t[SD_MAX_SURFACES];  // intersection parameter at every surface
+  V px, py, pz;          // hit point at the last surface (vertex-local)
 };
+using AdjState = AdjStateV<float>;
 
 // A single ray returns at its first failure; a pair runs each surface to its
 // end and returns there when both rays have failed (fewer tests per ray).
@@ -718,7 +738,7 @@ struct AdjState {
 template <bool SAVE, class V, class KS>
 __device__ __forceinline__ typename VStat<V>::S trace_ray_v(
     int n, const KS& ks_of, int newton_max, typename VStat<V>::S st, V& x, V& y, V& z, V& dx,
-    V& dy, V& dz, AdjState* sv) {
+    V& dy, V& dz, AdjStateV<V>* sv) {
   using M = typename VStat<V>::M;
   const V one = vb<V>(1.f), m2 = vb<V>(-2.f);
   for (int s = 0; s < n; ++s) {
@@ -1350,7 +1370,9 @@ namespace sd {
 // ---------------------------------------------------------------------------
 constexpr int NPAR_SURF = 8;
 
-// Reverse sweep of one ray.  The forward pass kept only t at every surface
+// Reverse sweep of one ray (V = float) or of two rays (V = float2, packed
+// two-lane instructions; KS(s) yields the surface constants).  The forward
+// pass kept only t at every surface
 // and the hit point at the last one: going backwards, the incoming direction
 // at a surface follows from its outgoing one by inverting Snell's law at the
 // hit point (cos t_t = n . d_out, sin^2 t_i = sin^2 t_t / e^2, d_in =
@@ -1358,90 +1380,85 @@ constexpr int NPAR_SURF = 8;
 // thickness), so no per-surface state is stored.  `emit(s, v)` receives the
 // 8 parameter adjoints of surface s (v[7] = thickness after it) and is
 // called by every lane of the warp for s = n-1 .. 0.
-template <class Emit>
-__device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ eta,
-                                            const float* __restrict__ omeg2, const AdjState& sv,
-                                            float dfx, float dfy, float dfz, float xb, float yb,
-                                            Emit emit) {
-  const DevLens& L = c_lens[slot];
-  const int n = L.n;
-  float Px = sv.px, Py = sv.py, Pz = sv.pz;  // hit point at surface s
-  float ox = dfx, oy = dfy, oz = dfz;        // direction leaving surface s
+template <class V, class KS, class Emit>
+__device__ __forceinline__ void adjoint_ray(int n, const KS& ks_of, const AdjStateV<V>& sv,
+                                            V dfx, V dfy, V dfz, V xb, V yb, Emit emit) {
+  const V one = vb<V>(1.f), two = vb<V>(2.f), m2 = vb<V>(-2.f), mone = vb<V>(-1.f);
+  V Px = sv.px, Py = sv.py, Pz = sv.pz;  // hit point at surface s
+  V ox = dfx, oy = dfy, oz = dfz;        // direction leaving surface s
   // sensor: x_s = X + tau dx, tau = -Z / dz with Z the last hit moved to
   // sensor-local z
-  float Z = Pz - L.s[n - 1].t;
-  float tau = div_nr(-Z, dfz);
-  float taub = xb * dfx + yb * dfy;
-  float Pbx = xb, Pby = yb, Pbz = div_nr(-taub, dfz);
-  float dbx = xb * tau, dby = yb * tau, dbz = div_nr(taub * Z, dfz * dfz);
-  float tcarry = -Pbz;  // adjoint of the thickness after surface s
+  const V Z = vadd(Pz, ks_of(n - 1).negt);
+  const V tau = div_nr(vneg(Z), dfz);
+  const V taub = vfma(yb, dfy, vmul(xb, dfx));
+  V Pbx = xb, Pby = yb, Pbz = div_nr(vneg(taub), dfz);
+  V dbx = vmul(xb, tau), dby = vmul(yb, tau), dbz = div_nr(vmul(taub, Z), vmul(dfz, dfz));
+  V tcarry = vneg(Pbz);  // adjoint of the thickness after surface s
   for (int s = n - 1; s >= 0; --s) {
-    const DevSurf& S = L.s[s];
-    const float t = sv.t[s];
-    float v[NPAR_SURF];
+    const SurfK<V>& S = ks_of(s);
+    const V t = sv.t[s];
+    V v[NPAR_SURF];
 #pragma unroll
-    for (int j = 0; j < NPAR_SURF; ++j) v[j] = 0.f;
+    for (int j = 0; j < NPAR_SURF; ++j) v[j] = vb<V>(0.f);
     v[7] = tcarry;
-    float ix = ox, iy = oy, iz = oz;  // direction arriving at the surface
-    float ibx, iby, ibz;              // adjoint of the incoming direction
-    float gx = 0.f, gy = 0.f, gz = 1.f;  // grad Phi at the hit
+    V ix = ox, iy = oy, iz = oz;  // direction arriving at the surface
+    V ibx, iby, ibz;              // adjoint of the incoming direction
+    V gx = vb<V>(0.f), gy = vb<V>(0.f), gz = one;  // grad Phi at the hit
+    const V u = vfma(Py, Py, vmul(Px, Px));
     if (S.kind & K_REFRACT) {
-      const float c = S.c, kk = 1.f + S.k;
-      const float u = Px * Px + Py * Py;
-      const float q = sqrt_nr(1.f - kk * c * c * u);
-      const float iq = div_nr(1.f, q), iq3 = iq * iq * iq;
+      const V q = sqrt_nr(vfma(S.nkc2, u, one));
+      const V iq = div_nr(one, q), iq3 = vmul(vmul(iq, iq), iq);
       // S1 = dsag/du = c / (2q) + sum_j (j+2) a_j u^(j+1)
-      float up = 1.f, S1 = 0.5f * c * iq, dS1 = 0.25f * kk * c * c * c * iq3;
+      V up = one, S1 = vmul(S.halfc, iq), dS1 = vmul(S.qkc3, iq3);
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        dS1 += (float)((j + 2) * (j + 1)) * S.a[j] * up;  // u^j
-        up *= u;
-        S1 += (float)(j + 2) * S.a[j] * up;               // u^(j+1)
+        dS1 = vfma(S.dda[j], up, dS1);  // (j+2)(j+1) a_j u^j
+        up = vmul(up, u);
+        S1 = vfma(S.da[j], up, S1);     // (j+2) a_j u^(j+1)
       }
-      gx = -2.f * Px * S1;
-      gy = -2.f * Py * S1;
-      gz = 1.f;
-      const float imn = rsqrt_refined(gx * gx + gy * gy + 1.f);
-      const float nx = gx * imn, ny = gy * imn, nz = imn;
+      gx = vmul(vmul(m2, Px), S1);
+      gy = vmul(vmul(m2, Py), S1);
+      const V imn = rsqrt_refined(vfma(gy, gy, vfma(gx, gx, one)));
+      const V nx = vmul(gx, imn), ny = vmul(gy, imn), nz = imn;
       // Snell: dout = e din + g n, g = (1 - e^2) / (ct + e cosi)
-      const float e = eta[s], ie = div_nr(1.f, e);
-      const float ct = nx * ox + ny * oy + nz * oz;
-      const float cosi = sqrt_nr(1.f - (1.f - ct * ct) * ie * ie);
-      const float D = ct + e * cosi;
-      const float g = div_nr(omeg2[s], D);
-      ix = (ox - g * nx) * ie;
-      iy = (oy - g * ny) * ie;
-      iz = (oz - g * nz) * ie;
-      ibx = e * dbx;
-      iby = e * dby;
-      ibz = e * dbz;
-      const float gb = dbx * nx + dby * ny + dbz * nz;
-      float nbx = g * dbx, nby = g * dby, nbz = g * dbz;
-      const float Db = div_nr(-gb * g, D);
-      const float k2b = div_nr(Db, 2.f * ct);
-      const float cosib = Db * e + k2b * 2.f * e * e * cosi;
-      nbx += cosib * ix;
-      nby += cosib * iy;
-      nbz += cosib * iz;
-      ibx += cosib * nx;
-      iby += cosib * ny;
-      ibz += cosib * nz;
+      const V ct = vfma(nz, oz, vfma(ny, oy, vmul(nx, ox)));
+      const V cosi = sqrt_nr(vfma(vfma(ct, ct, mone), S.ie2, one));
+      const V D = vfma(S.e, cosi, ct);
+      const V g = div_nr(S.om, D), ng = vneg(g);
+      ix = vmul(vfma(ng, nx, ox), S.ie);
+      iy = vmul(vfma(ng, ny, oy), S.ie);
+      iz = vmul(vfma(ng, nz, oz), S.ie);
+      ibx = vmul(S.e, dbx);
+      iby = vmul(S.e, dby);
+      ibz = vmul(S.e, dbz);
+      const V gb = vfma(dbz, nz, vfma(dby, ny, vmul(dbx, nx)));
+      V nbx = vmul(g, dbx), nby = vmul(g, dby), nbz = vmul(g, dbz);
+      const V Db = div_nr(vmul(gb, ng), D);
+      const V k2b = div_nr(Db, vmul(two, ct));
+      const V cosib = vfma(vmul(vmul(two, S.e2), k2b), cosi, vmul(Db, S.e));
+      nbx = vfma(cosib, ix, nbx);
+      nby = vfma(cosib, iy, nby);
+      nbz = vfma(cosib, iz, nbz);
+      ibx = vfma(cosib, nx, ibx);
+      iby = vfma(cosib, ny, iby);
+      ibz = vfma(cosib, nz, ibz);
       // n = m / |m|,  m = (-2 Px S1, -2 Py S1, 1)
-      const float nd = nx * nbx + ny * nby + nz * nbz;
-      const float mbx = (nbx - nx * nd) * imn, mby = (nby - ny * nd) * imn;
-      const float S1b = -2.f * Px * mbx - 2.f * Py * mby;
-      Pbx += -2.f * S1 * mbx;
-      Pby += -2.f * S1 * mby;
-      const float ub = S1b * dS1;
-      Pbx += 2.f * Px * ub;
-      Pby += 2.f * Py * ub;
-      v[0] += S1b * (0.5f * iq + 0.5f * kk * c * c * u * iq3);
-      v[1] += S1b * (0.25f * c * c * c * u * iq3);
+      const V nnd = vneg(vfma(nz, nbz, vfma(ny, nby, vmul(nx, nbx))));
+      const V mbx = vmul(vfma(nx, nnd, nbx), imn), mby = vmul(vfma(ny, nnd, nby), imn);
+      const V S1b = vmul(m2, vfma(Py, mby, vmul(Px, mbx)));
+      const V m2S1 = vmul(m2, S1);
+      Pbx = vfma(m2S1, mbx, Pbx);
+      Pby = vfma(m2S1, mby, Pby);
+      const V ub = vmul(S1b, dS1);
+      Pbx = vfma(vmul(two, Px), ub, Pbx);
+      Pby = vfma(vmul(two, Py), ub, Pby);
+      v[0] = vfma(S1b, vmul(vb<V>(0.5f), vfma(vmul(S.kc2, u), iq3, iq)), v[0]);
+      v[1] = vfma(S1b, vmul(vmul(S.qc3, u), iq3), v[1]);
       up = u;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        v[2 + j] += S1b * (float)(j + 2) * up;  // u^(j+1)
-        up *= u;
+        v[2 + j] = vfma(vmul(S1b, vb<V>((float)(j + 2))), up, v[2 + j]);  // u^(j+1)
+        up = vmul(up, u);
       }
     } else {
       ibx = dbx;
@@ -1449,34 +1466,35 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       ibz = dbz;
     }
     // hit P = o + t din
-    float obx = Pbx, oby = Pby, obz = Pbz;
-    ibx += t * Pbx;
-    iby += t * Pby;
-    ibz += t * Pbz;
-    const float tb = Pbx * ix + Pby * iy + Pbz * iz;
+    V obx = Pbx, oby = Pby, obz = Pbz;
+    ibx = vfma(t, Pbx, ibx);
+    iby = vfma(t, Pby, iby);
+    ibz = vfma(t, Pbz, ibz);
+    const V tb = vfma(Pbz, iz, vfma(Pby, iy, vmul(Pbx, ix)));
     // implicit intersection Phi(o + t din; theta) = 0
-    const float lam = div_nr(-tb, gx * ix + gy * iy + gz * iz);
-    obx += lam * gx;
-    oby += lam * gy;
-    obz += lam * gz;
-    ibx += lam * t * gx;
-    iby += lam * t * gy;
-    ibz += lam * t * gz;
+    const V lam = div_nr(vneg(tb), vfma(gz, iz, vfma(gy, iy, vmul(gx, ix))));
+    obx = vfma(lam, gx, obx);
+    oby = vfma(lam, gy, oby);
+    obz = vfma(lam, gz, obz);
+    const V lt = vmul(lam, t);
+    ibx = vfma(lt, gx, ibx);
+    iby = vfma(lt, gy, iby);
+    ibz = vfma(lt, gz, ibz);
     if (S.kind & K_REFRACT) {
-      const float c = S.c, kk = 1.f + S.k;
-      const float u = Px * Px + Py * Py;
-      const float q = sqrt_nr(1.f - kk * c * c * u);
-      const float Sc = div_nr(c * u, 1.f + q);  // conic part of the sag
-      const float i2q = div_nr(0.5f, q);
+      const V q = sqrt_nr(vfma(S.nkc2, u, one));
+      const V Sc = div_nr(vmul(S.c, u), vadd(one, q));  // conic part of the sag
+      const V nli = vneg(div_nr(vmul(vb<V>(0.5f), lam), q));  // -lam / (2q)
       // Phi = z - sag:  dPhi/dc = -(u + (1+k) Sc^2) / (2q), dPhi/dk = -c Sc^2 / (2q),
       // dPhi/da_j = -u^(j+2)
-      v[0] += lam * (-(u + kk * Sc * Sc) * i2q);
-      v[1] += lam * (-c * Sc * Sc * i2q);
-      float up = u * u;
+      const V Sc2 = vmul(Sc, Sc);
+      v[0] = vfma(nli, vfma(S.kk, Sc2, u), v[0]);
+      v[1] = vfma(nli, vmul(S.c, Sc2), v[1]);
+      const V nlam = vneg(lam);
+      V up = vmul(u, u);
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        v[2 + j] += lam * (-up);
-        up *= u;
+        v[2 + j] = vfma(nlam, up, v[2 + j]);
+        up = vmul(up, u);
       }
     }
     emit(s, v);
@@ -1485,14 +1503,14 @@ __device__ __forceinline__ void adjoint_ray(int slot, const float* __restrict__ 
       Pbx = obx;
       Pby = oby;
       Pbz = obz;
-      tcarry = -obz;
+      tcarry = vneg(obz);
       dbx = ibx;
       dby = iby;
       dbz = ibz;
-      const float Tp = L.s[s - 1].t;
-      Px = fmaf(-t, ix, Px);
-      Py = fmaf(-t, iy, Py);
-      Pz = fmaf(-t, iz, Pz) + Tp;
+      const V nt = vneg(t);
+      Px = vfma(nt, ix, Px);
+      Py = vfma(nt, iy, Py);
+      Pz = vsub(vfma(nt, iz, Pz), ks_of(s - 1).negt);
       ox = ix;
       oy = iy;
       oz = iz;
@@ -1546,7 +1564,8 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ReqCtx ctx;
   __shared__ float s_acc[NW][SD_MAX_SURFACES][NPAR_SURF];
-  __shared__ int s_swept[2];  // rays with a contribution, lanes that ran the sweep
+  __shared__ int s_swept[2];  // rays with a contribution, ray slots that ran the sweep
+  __shared__ SurfK<float2> s_surf[SD_MAX_SURFACES];
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   float* Gs = reinterpret_cast<float*>(smem + table_bytes(P.max_n));
@@ -1576,26 +1595,33 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
   const int total = ctx.N ? ctx.total : 0;
   const float scale = (P.norm == SD_NORM_PER_RAY) ? (total > 0 ? 1.f / (float)total : 0.f) : 1.f;
   const int n = ctx.N ? c_lens[ctx.slot].n : 0;
-  AdjState sv;
-  int row = 0;
-  // With a landing mask the rays whose bit is set are taken in ray order
-  // from a ring queue that warp 0 refills 32 mask words at a time, NT per
-  // round, so that every warp but the request's last is full; without one,
-  // every ray (NT consecutive rays per round).
-  constexpr int QCAP = 2048;  // > NT - 1 + 32 * 32: a refill never wraps onto live entries
+  for (int sf = threadIdx.x; sf < n; sf += NT)
+    s_surf[sf] = pair_consts(surf_consts(c_lens[ctx.slot].s[sf], ctx.eta[sf], ctx.omeg2[sf]));
+  __syncthreads();
+  auto ks_of = [&](int sf) -> const SurfK<float2>& { return s_surf[sf]; };
+  AdjStateV<float2> sv;
+  int row0 = 0, row1 = 0;
+  // A thread takes two rays a round (k and k + NT of the round's rays) and
+  // traces and sweeps them as a packed pair.  With a landing mask the rays
+  // whose bit is set are taken in ray order from a ring queue that warp 0
+  // refills 32 mask words at a time, 2 NT per round, so that every warp but
+  // the request's last is full; without one, every ray (2 NT consecutive
+  // rays per round).
+  constexpr int QCAP = 2048;  // > 2 NT - 1 + 32 * 32: a refill never wraps onto live entries
+  static_assert(QCAP > 2 * NT - 1 + 32 * 32, "ray queue too small");
   __shared__ int s_q[QCAP];
   __shared__ int s_head, s_qn, s_wpos;
   const unsigned* mw = P.land_mask ? P.land_mask + (size_t)r * P.mask_words : nullptr;
   const int nwords = (total + 31) >> 5;
   if (threadIdx.x == 0) s_head = s_qn = s_wpos = 0;
   int take = 0;  // rays handed out in the previous round
-  for (int base = 0;; base += NT) {
-    int k;
+  for (int base = 0;; base += 2 * NT) {
+    int k0, k1;
     if (mw) {
       __syncthreads();  // every thread has its previous ray
       if (warp == 0) {
         int head = (s_head + take) & (QCAP - 1), qn = s_qn - take, wpos = s_wpos;
-        while (qn < NT && wpos < nwords) {
+        while (qn < 2 * NT && wpos < nwords) {
           const int wi = wpos + lane;
           unsigned m = wi < nwords && SD_CHECK(wi, P.mask_words) ? mw[wi] : 0u;
           const int c = __popc(m);
@@ -1624,66 +1650,89 @@ __global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const floa
       __syncthreads();
       const int qn = s_qn;
       if (qn == 0) break;
-      take = min(qn, NT);
-      k = (int)threadIdx.x < take ? s_q[(s_head + threadIdx.x) & (QCAP - 1)] : total;
+      take = min(qn, 2 * NT);
+      const int t0 = threadIdx.x, t1 = threadIdx.x + NT;
+      k0 = t0 < take ? s_q[(s_head + t0) & (QCAP - 1)] : total;
+      k1 = t1 < take ? s_q[(s_head + t1) & (QCAP - 1)] : total;
     } else {
       if (base >= total) break;
-      k = base + threadIdx.x;
+      k0 = base + threadIdx.x;
+      k1 = k0 + NT;
     }
-    float x, y, z, dx = 0.f, dy = 0.f, dz = 1.f, gfx = 0.f, gfy = 0.f;
-    bool need = false;
-    if (k < total) {
-      row = advance_row(prefix, k, row);
-      make_ray_row(ctx, prefix, lo, k, row, x, y, z, dx, dy, dz);
-      int st = trace_ray_t<true>(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz,
-                                 &sv);
-      if (st == ST_OK) {
-        float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
-        float fy = (y - ctx.yc) * S.inv_ps + (float)pp;
-        float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
-        int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dx, dz));
-        if (side != 2) {
-          float a0f = floorf(fx), b0f = floorf(fy);
-          float wx = fx - a0f, wy = fy - b0f;
-          int a0 = (int)a0f, b0 = (int)b0f;
-          const float* Gp = Gs + side * ks2;
+    float2 x = make_float2(0.f, 0.f), y = x, z = x, dx = x, dy = x,
+           dz = make_float2(1.f, 1.f);
+    int2 st = make_int2(k0 < total ? (int)ST_OK : (int)ST_NONE,
+                        k1 < total ? (int)ST_OK : (int)ST_NONE);
+    if (k0 < total) {
+      row0 = advance_row(prefix, k0, row0);
+      make_ray_row(ctx, prefix, lo, k0, row0, x.x, y.x, z.x, dx.x, dy.x, dz.x);
+    }
+    if (k1 < total) {
+      row1 = advance_row(prefix, k1, row1);
+      make_ray_row(ctx, prefix, lo, k1, row1, x.y, y.y, z.y, dx.y, dy.y, dz.y);
+    }
+    if (k0 < total)
+      st = trace_ray_v<true, float2>(n, ks_of, P.newton_max, st, x, y, z, dx, dy, dz, &sv);
+    // the splat gradient of one ray (the forward's decisions)
+    auto splat = [&](int stv, float xv, float yv, float dxv, float dzv, float& gfx, float& gfy) {
+      gfx = gfy = 0.f;
+      if (stv != ST_OK) return false;
+      float fx = (xv - ctx.xc) * S.inv_ps + (float)pp;
+      float fy = (yv - ctx.yc) * S.inv_ps + (float)pp;
+      float af = floorf(fx + 0.5f), bf = floorf(fy + 0.5f);
+      int side = dp_side(S, (fx - af) * S.ps, (fy - bf) * S.ps, tan_theta(dxv, dzv));
+      if (side == 2) return false;
+      float a0f = floorf(fx), b0f = floorf(fy);
+      float wx = fx - a0f, wy = fy - b0f;
+      int a0 = (int)a0f, b0 = (int)b0f;
+      const float* Gp = Gs + side * ks2;
 #pragma unroll
-          for (int jy = 0; jy < 2; ++jy)
+      for (int jy = 0; jy < 2; ++jy)
 #pragma unroll
-            for (int jx = 0; jx < 2; ++jx) {
-              int aa = a0 + jx, bb = b0 + jy;
-              if (aa < 0 || aa >= ks || bb < 0 || bb >= ks) continue;
-              float gv = Gp[bb * ks + aa];
-              gfx += gv * (jx ? 1.f : -1.f) * (jy ? wy : 1.f - wy);
-              gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
-            }
-          need = gfx != 0.f || gfy != 0.f;
+        for (int jx = 0; jx < 2; ++jx) {
+          int aa = a0 + jx, bb = b0 + jy;
+          if (aa < 0 || aa >= ks || bb < 0 || bb >= ks) continue;
+          float gv = Gp[bb * ks + aa];
+          gfx += gv * (jx ? 1.f : -1.f) * (jy ? wy : 1.f - wy);
+          gfy += gv * (jy ? 1.f : -1.f) * (jx ? wx : 1.f - wx);
         }
-      }
-    }
-    // the whole warp sweeps when any lane needs it; the others contribute
-    // exact zeros (their values are selected away, never multiplied)
-    const unsigned need_mask = __ballot_sync(0xffffffffu, need);
-    if (!need_mask) continue;
+      return gfx != 0.f || gfy != 0.f;
+    };
+    float gfx0, gfy0, gfx1, gfy1;
+    const bool need0 = splat(st.x, x.x, y.x, dx.x, dz.x, gfx0, gfy0);
+    const bool need1 = splat(st.y, x.y, y.y, dx.y, dz.y, gfx1, gfy1);
+    // the whole warp sweeps when any ray of it needs it; the other rays
+    // contribute exact zeros (their values are selected away, never added)
+    const unsigned nm0 = __ballot_sync(0xffffffffu, need0);
+    const unsigned nm1 = __ballot_sync(0xffffffffu, need1);
+    if (!(nm0 | nm1)) continue;
     if (lane == 0) {
-      atomicAdd(&s_swept[0], __popc(need_mask));
-      atomicAdd(&s_swept[1], 32);
+      atomicAdd(&s_swept[0], __popc(nm0) + __popc(nm1));
+      atomicAdd(&s_swept[1], 64);
     }
-    if (!need) {
-      // a harmless state for lanes without a contribution
-      sv.px = sv.py = 0.f;
-      sv.pz = 0.f;
-      for (int s2 = 0; s2 < n; ++s2) sv.t[s2] = 0.f;
-      dx = dy = 0.f;
-      dz = 1.f;
+    if (!(need0 && need1)) {
+      // a harmless state for the rays without a contribution
+      const float2 zero = make_float2(0.f, 0.f);
+      const M2 keep{need0, need1};
+      sv.px = sel(keep, sv.px, zero);
+      sv.py = sel(keep, sv.py, zero);
+      sv.pz = sel(keep, sv.pz, zero);
+      for (int s2 = 0; s2 < n; ++s2) sv.t[s2] = sel(keep, sv.t[s2], zero);
+      dx = sel(keep, dx, zero);
+      dy = sel(keep, dy, zero);
+      dz = sel(keep, dz, make_float2(1.f, 1.f));
     }
-    adjoint_ray(ctx.slot, ctx.eta, ctx.omeg2, sv, dx, dy, dz, scale * S.inv_ps * gfx,
-                scale * S.inv_ps * gfy, [&](int s2, float (&v)[NPAR_SURF]) {
+    const float gs = scale * S.inv_ps;
+    adjoint_ray<float2>(n, ks_of, sv, dx, dy, dz, make_float2(gs * gfx0, gs * gfx1),
+                        make_float2(gs * gfy0, gs * gfy1), [&](int s2, float2 (&v)[NPAR_SURF]) {
+                          // the pair's two rays added first (ray k, then k + NT)
+                          float w[NPAR_SURF];
 #pragma unroll
-                  for (int j2 = 0; j2 < NPAR_SURF; ++j2) v[j2] = need ? v[j2] : 0.f;
-                  const float tot = warp_sum8(v, lane);
-                  if ((lane & 3) == 0) s_acc[warp][s2][(lane >> 2) & 7] += tot;
-                });
+                          for (int j2 = 0; j2 < NPAR_SURF; ++j2)
+                            w[j2] = (need0 ? v[j2].x : 0.f) + (need1 ? v[j2].y : 0.f);
+                          const float tot = warp_sum8(w, lane);
+                          if ((lane & 3) == 0) s_acc[warp][s2][(lane >> 2) & 7] += tot;
+                        });
   }
   __syncthreads();
   // per-request partials: warps added in order

@@ -142,7 +142,7 @@ def test_adjoint_with_landing_mask(sdlib):
     mismatches only on rays within 1e-5 mm of a decision boundary); the
     adjoint restricted to the marked
     rays gives the unmasked adjoint's per-request gradients up to the order
-    of FP32 additions, the same contributing rays, fewer swept thread slots,
+    of FP32 additions, the same contributing rays, fewer swept ray slots,
     and repeats bitwise."""
     sd = sdlib
     cfg = W.config_full_forward()
