@@ -2015,9 +2015,11 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
   __shared__ unsigned s_stats[SD_N_STATS];
   __shared__ float s_red[64];
   __shared__ int s_last, s_rows, s_off;
+  __shared__ SurfK<float2> s_surf[SD_MAX_SURFACES];
   int* prefix = reinterpret_cast<int*>(smem);
   int* lo = prefix + (P.max_n + 1);
   unsigned* patch = reinterpret_cast<unsigned*>(smem + table_bytes(P.max_n));
+  auto ks_of = [&](int sf) -> const SurfK<float2>& { return s_surf[sf]; };
   const int M = W.item_start[n_req];
   const int G = gridDim.x, b = blockIdx.x;
   const int i0 = (int)((long long)M * b / G), i1 = (int)((long long)M * (b + 1) / G);
@@ -2041,6 +2043,9 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
       cur = r;
       items_here = 0;
       __syncthreads();
+      // the request's surface constants as pairs (read after the next barrier)
+      for (int sf = threadIdx.x; sf < c_lens[ctx.slot].n; sf += blockDim.x)
+        s_surf[sf] = pair_consts(surf_consts(c_lens[ctx.slot].s[sf], ctx.eta[sf], ctx.omeg2[sf]));
     }
     ++items_here;
     // rows of this item and their in-pupil spans
@@ -2089,17 +2094,12 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
     }
     const int ray0 = s_off;
     unsigned c_reached = 0, c_vign = 0, c_other = 0, c_l = 0, c_r = 0, c_miss = 0, c_clip = 0;
-    int row = 0;
-    for (int base = 0; base < total; base += blockDim.x) {
-      int k = base + threadIdx.x;
+    // bins ray k of the item (one of a set of blockDim.x consecutive rays,
+    // every thread calls it for each set), as trace_bin_kernel does
+    auto bin = [&](int k, int st, float x, float y, float dx, float dz) {
       int key = -1;
-      bool land = false;  // as in trace_bin_kernel
+      bool land = false;
       if (k < total) {
-        // ray k of the item (k grows within the item: advance the row)
-        row = advance_row(prefix, k, row);
-        float x, y, z, dx, dy, dz;
-        pupil_ray(ctx, lo[row] + (k - prefix[row]), row0 + row, x, y, z, dx, dy, dz);
-        int st = trace_ray(ctx.slot, ctx.eta, ctx.omeg2, P.newton_max, x, y, z, dx, dy, dz);
         if (st == ST_OK) {
           ++c_reached;
           float fx = (x - ctx.xc) * S.inv_ps + (float)pp;
@@ -2123,7 +2123,7 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
         // the warp's 32 rays start at request ray g0, which need not be a
         // word boundary: their bits go to words g0 / 32 and the next
         const unsigned bits = __ballot_sync(0xffffffffu, land);
-        const int g0 = ray0 + base + (threadIdx.x & ~31), w0 = g0 >> 5, sh = g0 & 31;
+        const int g0 = ray0 + k - lane, w0 = g0 >> 5, sh = g0 & 31;
         if (lane == 0 && bits) {
           unsigned* mr = P.land_mask + (size_t)r * P.mask_words;
           if (SD_CHECK(w0, P.mask_words)) atomicOr(mr + w0, bits << sh);
@@ -2133,6 +2133,33 @@ __global__ void __launch_bounds__(1024) batched_trace_kernel(TraceParams P, Batc
       }
       unsigned m = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&patch[key], (unsigned)__popc(m));
+    };
+    // rays k and k + blockDim.x of the item (k grows within the item: each
+    // advances its own row) traced together as a packed pair
+    const int NT = blockDim.x;
+    int rw0 = 0, rw1 = 0;
+    const int nsurf = c_lens[ctx.slot].n;
+    for (int base = 0; base < total; base += 2 * NT) {
+      const int k0 = base + threadIdx.x, k1 = k0 + NT;
+      float2 x = make_float2(0.f, 0.f), y = x, z = x, dx = x, dy = x,
+             dz = make_float2(1.f, 1.f);
+      int2 st = make_int2(k0 < total ? (int)ST_OK : (int)ST_NONE,
+                          k1 < total ? (int)ST_OK : (int)ST_NONE);
+      if (k0 < total) {
+        rw0 = advance_row(prefix, k0, rw0);
+        pupil_ray(ctx, lo[rw0] + (k0 - prefix[rw0]), row0 + rw0, x.x, y.x, z.x, dx.x, dy.x,
+                  dz.x);
+      }
+      if (k1 < total) {
+        rw1 = advance_row(prefix, k1, rw1);
+        pupil_ray(ctx, lo[rw1] + (k1 - prefix[rw1]), row0 + rw1, x.y, y.y, z.y, dx.y, dy.y,
+                  dz.y);
+      }
+      if (k0 < total)
+        st = trace_ray_v<false, float2>(nsurf, ks_of, P.newton_max, st, x, y, z, dx, dy, dz,
+                                        nullptr);
+      bin(k0, st.x, x.x, y.x, dx.x, dz.x);
+      bin(k1, st.y, x.y, y.y, dx.y, dz.y);
     }
     atomicAdd(&s_stats[SD_STAT_REACHED], c_reached);
     atomicAdd(&s_stats[SD_STAT_VIGNETTED], c_vign);
