@@ -718,7 +718,7 @@ __device__ __forceinline__ void combine_chunks(const float* slab0, const float* 
 // slice, and writes the slice's gradient (split slices: through the two
 // chunks' slabs, see combine_chunks).
 template <int NT, int SPT, class TI>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) render_bwd_bank_kernel(const RenderParams P,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : (NT <= 320 ? 2 : 1)) render_bwd_bank_kernel(const RenderParams P,
                                                              const float* __restrict__ gout,
                                                              const unsigned* __restrict__ bm,
                                                              int words, int ntx, int nty,
@@ -1079,11 +1079,12 @@ sd_status launch_bank_bwd_any(const RenderParams& P, const float* gout, const un
                               float* gbank, float* quad_buf, cudaStream_t s) {
   int KU = (P.ks + SEG - 1) / SEG * SEG;
   int nstrip = P.ks * (KU / SEG);
-  // one strip per thread where the strips fill 512-608 threads (ks = 61..65:
-  // 6.76 -> 6.51 ms at 1024x1024x3 against 256 threads x 3 strips, of
-  // which a quarter of the slots idle)
-  if (nstrip > 512 && nstrip <= 608)
-    return launch_bank_bwd<608, 1, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
+  // where the strips fill 512-640 slots (ks = 61..65): 320 threads with two
+  // strips each, two blocks per SM, so that one block's staging of a tile
+  // overlaps the other's products (608 threads x 1 strip, one block per SM,
+  // was 1.5 % slower; 256 threads x 3 strips left a quarter of the slots idle)
+  if (nstrip > 512 && nstrip <= 640)
+    return launch_bank_bwd<320, 2, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
                                        s);
   if (nstrip <= 256 * 3)
     return launch_bank_bwd<256, 3, TI>(P, gout, bm, words, tx, ty, plan_ws, smax, gbank, quad_buf,
