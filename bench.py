@@ -43,17 +43,20 @@ FP32_LANES_PER_SM = 128
 # kernel, None until a capture of this build exists.  Must be re-measured
 # whenever the kernel changes.
 TRAFFIC_BYTES = {
+    # the bank and the landing mask written (63.8 MB reached DRAM within the
+    # launch), 0.7 MB read
+    "trace_bin_kernel": 64.5e6,
     # every request's gradient patch read once (also the zero patches it then
-    # skips) and the landing mask of the requests it traces again: 116.2 MB
-    # read + 1.2 MB written; independent of the image size
-    "trace_adj_kernel": 117.5e6,
+    # skips) and the landing mask of the requests it traces again: 113.8 MB
+    # read + 2.0 MB written; independent of the image size
+    "trace_adj_kernel": 115.8e6,
     # the image-gradient call as the phase times it: selection table 4.2 MB,
     # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.1 MB
     "render_bwd_img_kernel": 375.1e6,
     # the bank-gradient call as the phase times it: selection table 4.2 MB,
-    # slice bitmap 8.4 MB, work plan 0.1 MB, bank pass 46.3 MB read + 41.5 MB
+    # slice bitmap 8.4 MB, work plan 0.1 MB, bank pass 47.6 MB read + 55.3 MB
     # written (the rest of the 103.8 MB gradient bank still in L2 at its end)
-    "render_bwd_bank_kernel": 100.5e6,
+    "render_bwd_bank_kernel": 115.6e6,
     # one render launch: the bank slices its tiles use and the image, 66.0 MB
     # read, 7.9 MB of output written
     "render_fwd_kernel": 73.9e6,
