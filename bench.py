@@ -392,17 +392,32 @@ def run_ours(args, world, rank, local, dist):
     h_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
+    # the image and depth uploads run on a copy stream during the trace (the
+    # render waits for them), the DP image's download during the backward
+    copy = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.fill_(float(i))
         e2e_ev[i][0].record(stream)
         req_dev.copy_(h_req, non_blocking=True)
-        aif.copy_(h_aif, non_blocking=True)
-        depth.copy_(h_depth, non_blocking=True)
+        copy.wait_event(e2e_ev[i][0])  # the previous step is done with aif and depth
+        with torch.cuda.stream(copy):
+            aif.copy_(h_aif, non_blocking=True)
+            depth.copy_(h_depth, non_blocking=True)
+        inputs = torch.cuda.Event()
+        inputs.record(copy)
         trace()
+        stream.wait_event(inputs)
         render()
+        rendered = torch.cuda.Event()
+        rendered.record(stream)
+        copy.wait_event(rendered)
+        with torch.cuda.stream(copy):
+            h_out.copy_(out, non_blocking=True)
+        fetched = torch.cuda.Event()
+        fetched.record(copy)
         backward()
-        h_out.copy_(out, non_blocking=True)
+        stream.wait_event(fetched)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
