@@ -221,15 +221,54 @@ constexpr int MB_PRE = ((MB_Y + 20) * (MT_X + 20) + MB_NT - 1) / MB_NT;  // tile
 constexpr uint32_t MB_WAIT = 1u << 22;   // polls of a stage wait
 constexpr uint32_t MB_DRAIN = 1u << 24;  // polls of the final drain
 
-__host__ __device__ inline size_t mb_smem_bytes(int ks, int cw) {
+// esz: bytes per staged image value (4, or 2 for a 16-bit image)
+__host__ __device__ inline size_t mb_smem_bytes(int ks, int cw, int esz) {
   const size_t S = MT_X + ks - 1, R = MB_Y + ks - 1;
-  return (size_t)MB_Y * MB_NS * 16 * ks * ks + (size_t)2 * cw * S * R * 4;
+  return (size_t)MB_Y * MB_NS * 16 * ks * ks + (size_t)2 * cw * S * R * esz;
 }
+
+// The staged image: FP32 values, or a 16-bit image's own values (widening
+// them is exact, and a tap position's CW channels take half the bytes).
+template <class TI, int CW> struct StageT {
+  using E = float;
+  using V = typename Vec<CW>::T;
+};
+template <int CW> struct Vec16;
+template <> struct Vec16<1> { using T = unsigned short; };
+template <> struct Vec16<2> { using T = ushort2; };
+template <> struct Vec16<4> { using T = ushort4; };
+template <int CW> struct StageT<__nv_bfloat16, CW> {
+  using E = unsigned short;
+  using V = typename Vec16<CW>::T;
+};
+template <int CW> struct StageT<__half, CW> {
+  using E = unsigned short;
+  using V = typename Vec16<CW>::T;
+};
+__device__ __forceinline__ unsigned short comp(unsigned short v, int) { return v; }
+__device__ __forceinline__ unsigned short comp(ushort2 v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ unsigned short comp(ushort4 v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+template <class TI> __device__ __forceinline__ float staged_f32(float v) { return v; }
+template <class TI> __device__ __forceinline__ float staged_f32(unsigned short v);
+template <> __device__ __forceinline__ float staged_f32<__nv_bfloat16>(unsigned short v) {
+  return __uint_as_float((unsigned)v << 16);
+}
+template <> __device__ __forceinline__ float staged_f32<__half>(unsigned short v) {
+  return __half2float(__ushort_as_half(v));
+}
+__device__ __forceinline__ float stage_value(float v) { return v; }
+__device__ __forceinline__ unsigned short stage_value(__nv_bfloat16 v) {
+  return __bfloat16_as_ushort(v);
+}
+__device__ __forceinline__ unsigned short stage_value(__half v) { return __half_as_ushort(v); }
 
 template <class TI, class TM, int CW, int CN>
 __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapParams P, int ntiles,
                                                                     int* err, uint32_t wlim) {
-  using V = typename Vec<CW>::T;
+  using SE = typename StageT<TI, CW>::E;  // a staged image value
+  using V = typename StageT<TI, CW>::V;
   constexpr int PC = 8 / (int)sizeof(TM);  // pixels per chunk
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[MB_Y][MB_NS];
@@ -238,7 +277,7 @@ __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapPara
   const uint32_t CHB = 16u * (uint32_t)ks2;  // bytes per chunk
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* ring = smem + (size_t)warp * MB_NS * CHB;
-  float* tiles = reinterpret_cast<float*>(smem + (size_t)MB_Y * MB_NS * CHB);  // [2][R][S][CW]
+  SE* tiles = reinterpret_cast<SE*>(smem + (size_t)MB_Y * MB_NS * CHB);  // [2][R][S][CW]
   const int ntx = (P.W + MT_X - 1) / MT_X, nty = (P.H + MB_Y - 1) / MB_Y;
   const int groups = (P.C + CW - 1) / CW;
   const size_t plane = (size_t)P.H * P.W;
@@ -259,7 +298,7 @@ __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapPara
 
   // the image tile of tile t (replicate padding by clamping), CW channels
   // interleaved: thread values first (registers), then the shared buffer
-  float pre[MB_PRE][CW];
+  SE pre[MB_PRE][CW];
   auto tile_load = [&](int t) {
     const int bx = t % ntx, r = t / ntx, by = r % nty, z = r / nty;
     const int n = z / groups, c0 = (z - n * groups) * CW, cp = min(CW, P.C - c0);
@@ -273,10 +312,10 @@ __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapPara
       const size_t src = (size_t)yy * P.W + xx;
 #pragma unroll
       for (int c = 0; c < CW; ++c)
-        pre[k][c] = (i < RS && c < cp) ? to_f32<TI>(img[c * plane + src]) : 0.f;
+        pre[k][c] = (i < RS && c < cp) ? stage_value(img[c * plane + src]) : SE(0);
     }
   };
-  auto tile_store = [&](float* dst) {
+  auto tile_store = [&](SE* dst) {
 #pragma unroll
     for (int k = 0; k < MB_PRE; ++k) {
       const int i = tid + k * MB_NT;
@@ -360,8 +399,9 @@ __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapPara
               const float kl = to_f32<TM>(K0[q * E + e]), kr = to_f32<TM>(K0[q * E + ks2 + e]);
 #pragma unroll
               for (int c = 0; c < CN; ++c) {
-                aL[q][c] = fmaf(comp(v, c), kl, aL[q][c]);
-                aR[q][c] = fmaf(comp(v, c), kr, aR[q][c]);
+                const float iv = staged_f32<TI>(comp(v, c));
+                aL[q][c] = fmaf(iv, kl, aL[q][c]);
+                aR[q][c] = fmaf(iv, kr, aR[q][c]);
               }
             }
           }
@@ -440,7 +480,7 @@ __global__ void __launch_bounds__(MB_NT, 1) render_map_bulk_kernel(const MapPara
 
 template <class TI, class TM, int CW, int CN>
 sd_status launch_map_bulk(MapParams& P, int* err, cudaStream_t s) {
-  const size_t smem = mb_smem_bytes(P.ks, CW);
+  const size_t smem = mb_smem_bytes(P.ks, CW, (int)sizeof(typename StageT<TI, CW>::E));
   auto k = render_map_bulk_kernel<TI, TM, CW, CN>;
   SD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0, occ = 0;
@@ -475,10 +515,14 @@ sd_status launch_map(MapParams& P, int* err, cudaStream_t s) {
   constexpr int PC = 8 / (int)sizeof(TM);
   if (err && P.ks * P.ks <= 32 * MB_NJ && P.W % PC == 0 &&
       (reinterpret_cast<uintptr_t>(P.map) & 15) == 0) {
-    if (P.C == 3 && mb_smem_bytes(P.ks, 4) <= cap) return launch_map_bulk<TI, TM, 4, 3>(P, err, s);
-    if (P.C > 3 && mb_smem_bytes(P.ks, 4) <= cap) return launch_map_bulk<TI, TM, 4, 4>(P, err, s);
-    if (P.C == 2 && mb_smem_bytes(P.ks, 2) <= cap) return launch_map_bulk<TI, TM, 2, 2>(P, err, s);
-    if (mb_smem_bytes(P.ks, 1) <= cap) return launch_map_bulk<TI, TM, 1, 1>(P, err, s);
+    const int esz = sizeof(TI) == 2 ? 2 : 4;
+    if (P.C == 3 && mb_smem_bytes(P.ks, 4, esz) <= cap)
+      return launch_map_bulk<TI, TM, 4, 3>(P, err, s);
+    if (P.C > 3 && mb_smem_bytes(P.ks, 4, esz) <= cap)
+      return launch_map_bulk<TI, TM, 4, 4>(P, err, s);
+    if (P.C == 2 && mb_smem_bytes(P.ks, 2, esz) <= cap)
+      return launch_map_bulk<TI, TM, 2, 2>(P, err, s);
+    if (mb_smem_bytes(P.ks, 1, esz) <= cap) return launch_map_bulk<TI, TM, 1, 1>(P, err, s);
   }
   // widest channel interleave that fits: 4 (RGB in one pass), 2, 1
   if (P.C > 2 && map_smem_bytes(P.ks, 4) <= cap) return launch_map_cw<TI, TM, 4>(P, s);
