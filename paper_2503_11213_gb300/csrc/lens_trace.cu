@@ -1556,8 +1556,10 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[NPAR_SURF], int lane
 // (reduce-scatter) and added by one lane per parameter to the warp's row of
 // a shared accumulator; the rows are added in warp order at the end (fixed
 // order: deterministic).
+// Three blocks per SM (80 registers, a few spilled): more warps to hide the
+// sweep's dependent chains and the ray rounds' block barriers than two.
 template <int NT>
-__global__ void __launch_bounds__(NT) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
+__global__ void __launch_bounds__(NT, 3) trace_adj_kernel(TraceParams P, const float* __restrict__ G,
                                                        float* __restrict__ greq,
                                                        long long* __restrict__ swept) {
   constexpr int NW = NT / 32;
