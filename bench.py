@@ -43,13 +43,13 @@ FP32_LANES_PER_SM = 128
 # kernel, None until a capture of this build exists.  Must be re-measured
 # whenever the kernel changes.
 TRAFFIC_BYTES = {
-    # the bank and the landing mask written (63.8 MB reached DRAM within the
+    # the bank and the landing mask written (63.3 MB reached DRAM within the
     # launch), 0.7 MB read
-    "trace_bin_kernel": 64.5e6,
+    "trace_bin_kernel": 64.0e6,
     # every request's gradient patch read once (also the zero patches it then
-    # skips) and the landing mask of the requests it traces again: 113.8 MB
+    # skips) and the landing mask of the requests it traces again: 115.5 MB
     # read + 2.0 MB written; independent of the image size
-    "trace_adj_kernel": 115.8e6,
+    "trace_adj_kernel": 117.5e6,
     # the image-gradient call as the phase times it: selection table 4.2 MB,
     # bank re-layout 103.9 + 94.6 MB, the two strip launches 81.3 + 91.1 MB
     "render_bwd_img_kernel": 375.1e6,
