@@ -732,6 +732,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : (NT <= 320 ? 2 : 1)) rende
   constexpr int NPX = TXB * RT_Y, NSEG = NPX / SEG;
   // one thread per segment builds the segment list below
   static_assert(NT >= NSEG, "the bank-gradient block needs a thread per segment");
+  // the tile lists and segment lists use full-warp ballots
+  static_assert(NT % 32 == 0, "the bank-gradient block must be whole warps");
   float* halo = reinterpret_cast<float*>(smem);          // HH x S
   float2* G = reinterpret_cast<float2*>(halo + (size_t)HH * S);  // NPX (L, R)
   int* segs = reinterpret_cast<int*>(G + NPX);            // NSEG
